@@ -1,0 +1,206 @@
+/*
+ * osbpd.h -- C ABI of the GB300 (sm_103a) library for the per-time-step hot path of linearized
+ * ordinary state-based peridynamics (OSB-PD), after T. Ni, M. Zaccariotto, Q. Zhu, U. Galvanetto,
+ * "Matrix-based implementation and GPU acceleration of linearized ordinary state-based peridynamic
+ * models in MATLAB", arXiv 2309.11273.
+ *
+ * One time step of the library evaluates, over every bond of every particle:
+ *   - the bond-status update of the critical-stretch criterion (Eqs 1.17, 1.30);
+ *   - the dilatation theta_i (Eq 1.6, discretized as the bond sum of Eq 2.3);
+ *   - the linearized bond force of Eq 2.2 summed over the family (Eq 2.1);
+ *   - the explicit update of Eq 2.11 with the diagonal mass rho V_i (Eq 2.12) and the boundary
+ *     conditions of the solver loop (Appendix B).
+ * The weighted volume m_i (Eq 1.9) and the damage denominator of Eq 1.31 are computed once when the
+ * family is built.
+ *
+ * Conventions shared by every entry point:
+ *   - Units are SI.  The influence function is w = 1 (Section 2.3).
+ *   - Particle arrays are in the caller's particle order; internally the library reorders particles
+ *     along a Morton curve and never exposes that order.
+ *   - Vector fields are passed as "SoA" host arrays of dim * n doubles: first the n x-components, then
+ *     the n y-components, then (3D only) the n z-components.
+ *   - Every pointer argument is a HOST pointer unless its name ends in _dev.  Host arrays are owned
+ *     by the caller, are read (or written) only during the call, and are never retained.
+ *   - The library owns all device memory of a context (allocated with cudaMalloc on the context's
+ *     device at creation / neighbour build, released by pd_destroy).
+ *   - Every call returns a pd_status; on failure pd_last_error() describes it.  No C++ exception
+ *     crosses the ABI.  A context must be used by one host thread at a time.
+ *   - Asynchrony: calls that return data to host memory synchronize the context's stream before
+ *     returning; pd_step only enqueues work (call pd_sync to wait).
+ */
+#ifndef OSBPD_H
+#define OSBPD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pd_ctx pd_ctx;
+
+typedef enum {
+  PD_OK = 0,
+  PD_ERR_ARG = -1,      /* invalid argument (null pointer, bad size, non-finite value, ...) */
+  PD_ERR_STATE = -2,    /* call out of order (e.g. pd_step before pd_build_neighbors) */
+  PD_ERR_OOM = -3,      /* a device or host allocation failed */
+  PD_ERR_CUDA = -4,     /* a CUDA runtime call failed */
+  PD_ERR_NUMERIC = -5,  /* the state became non-finite or exceeded the divergence guard */
+  PD_ERR_TIMEOUT = -6   /* reserved for bounded device waits */
+} pd_status;
+
+/* Eq 1.8 / 1.15 / 1.16 rows. */
+typedef enum { PD_3D = 0, PD_PLANE_STRESS = 1, PD_PLANE_STRAIN = 2 } pd_model;
+
+/* PD_FP64: every operation in double precision (the paper computes in double precision, Section 4).
+ * PD_MIXED: bond arithmetic (extension, stretch, dilatation and force sums) in FP32 with FP32
+ *   accumulation; displacement and velocity integration in FP64; any bond whose FP32 stretch lies
+ *   within a rigorous rounding bound of s0 is re-decided in FP64 from the FP64 displacement, so its
+ *   status equals the FP64 decision on the run's own state. */
+typedef enum { PD_FP64 = 0, PD_MIXED = 1 } pd_precision;
+
+typedef struct {
+  int32_t model;       /* pd_model */
+  int32_t precision;   /* pd_precision */
+  double E;            /* Young's modulus [Pa] */
+  double nu;           /* Poisson's ratio */
+  double rho;          /* mass density [kg/m^3] */
+  double horizon;      /* delta [m]; family = closed ball |xi| <= delta (Section 2.1) */
+  double s0;           /* critical stretch s_c (Eq 1.30); <= 0 disables bond breaking */
+  double dt;           /* time step [s] (Eq 2.11) */
+  double band_safety;  /* PD_MIXED only: safety factor on the FP32 rounding bound; <= 0 -> 4 */
+  int32_t device;      /* CUDA device ordinal */
+  int32_t reserved;    /* must be 0 */
+  void* stream;        /* cudaStream_t to run on, or NULL for a library-owned stream */
+} pd_params;
+
+/* A pre-crack / notch: bonds whose segment crosses it are never created (Section 4.2 / 4.4).
+ * 2D: the segment p0-p1 (p2 ignored).  3D: the parallelogram p0 + a (p1-p0) + b (p2-p0), a,b in
+ * [0,1].  A bond i-j is cut iff x_i and x_j lie strictly on opposite sides of the crack's line /
+ * plane and the crossing point lies on the closed segment / parallelogram.  body: in a batched
+ * context the body it applies to (-1: all bodies); ignored otherwise. */
+typedef struct {
+  double p0[3], p1[3], p2[3];
+  int32_t body;
+  int32_t reserved;
+} pd_crack;
+
+typedef struct {
+  int64_t steps;          /* time steps taken since creation */
+  int64_t bonds;          /* directed bonds in the built family */
+  int64_t broken_bonds;   /* directed bonds broken so far */
+  int64_t band_rechecks;  /* PD_MIXED: bonds re-decided in FP64 (cumulative) */
+  int64_t validate_mismatches; /* PD_MIXED with PD_OPT_VALIDATE: FP32+band vs pure FP64 decisions */
+  double max_abs_u;       /* max |u| component at the last refresh */
+} pd_stats;
+
+/* Options for pd_set_option / pd_get_option. */
+typedef enum {
+  PD_OPT_GRAPH_CHUNK = 1,  /* steps captured per CUDA graph launch (0: no graphs). Default 100. */
+  PD_OPT_PROFILE = 2,      /* 1: time every kernel launch with CUDA events (forces eager launches) */
+  PD_OPT_VALIDATE = 3,     /* PD_MIXED: 1 = also decide every bond in FP64 and count mismatches */
+  PD_OPT_BLOCK = 4,        /* threads per block of the step kernels (multiple of 32, <= 1024) */
+  PD_OPT_SPLIT = 5,        /* warps cooperating on one 32-particle slice: 1, 2 or 4 */
+  PD_OPT_DIVERGENCE_LIMIT_MM = 6 /* divergence guard: max |u| in micrometres checked by
+                                    pd_check_state (0: off) */
+} pd_option;
+
+/* Kernel identifiers for pd_get_profile. */
+typedef enum { PD_K_PASS1 = 0, PD_K_PASS2 = 1, PD_K_COUNT = 2 } pd_kernel;
+
+/* Critical stretch s_c from the critical energy release rate Gc [J/m^2] and the horizon (w = 1).
+ *   3D: Eq 1.26 with beta = 125 delta / 1848 and beta' = 5 delta / 24.  Eq 1.27 prints
+ *       beta' = 5 delta / (24 pi); integrating Eq 1.25 over the unit-weight sphere gives 5 delta / 24,
+ *       which is the value used here.
+ *   2D: Eq 1.28 with beta, beta' of Eq 1.29, as printed.
+ * Returns a negative value for invalid arguments. */
+double pd_critical_stretch(int32_t model, double E, double nu, double Gc, double delta);
+
+/* Creates a context for one body of n >= 1 particles (n <= 2^31 - 1).
+ * x, y, z: reference coordinates (z must be NULL for 2D models and non-NULL for PD_3D).
+ * vol: particle volumes V_i (NULL: every particle gets horizon^dim / 27, i.e. (delta/3)^dim -- pass
+ *      explicit volumes for any other spacing).  In 2D, V_i is the area times the thickness; the
+ *      thickness cancels from u, v and damage.
+ * Copies coordinates to the device; allocation failure -> PD_ERR_OOM. */
+pd_status pd_create_particles(pd_ctx** out, const pd_params* prm, int64_t n, const double* x,
+                              const double* y, const double* z, const double* vol);
+
+/* Creates one context holding nbodies independent bodies that step together in the same kernels
+ * (no bond ever joins two bodies).  Body b owns particles [body_offsets[b], body_offsets[b+1]) of
+ * the concatenated arrays; per_body[b] gives its material, horizon, s0 and dt.  All bodies must
+ * share model, precision, device and stream.  vol must be non-NULL. */
+pd_status pd_create_batch(pd_ctx** out, int32_t nbodies, const pd_params* per_body,
+                          const int64_t* body_offsets, const double* x, const double* y,
+                          const double* z, const double* vol);
+
+/* Builds the family of every particle on the device: closed horizon |xi| <= delta, minus the bonds
+ * cut by the cracks; then m_i (Eq 1.9) and D_i = sum_j V_j (Eq 1.31 denominator) in FP64 over the
+ * built family; every built bond starts intact.  Resets the state to u = v = 0.  May be called
+ * again (rebuilds from scratch). */
+pd_status pd_build_neighbors(pd_ctx* c, const pd_crack* cracks, int32_t ncracks);
+
+/* Boundary conditions and loads (Appendix B applies the constraints at the top of every iteration).
+ * flag[n]: 0 free, 1 fixed (u = v = 0), 2 prescribed rigid rotation: u = rate * t * a x (p - c),
+ *          v = rate * a x (p - c), with c = axis_point, a = axis_dir (unit), t = step * dt.
+ *          NULL: every particle free.
+ * b: body-force density [N/m^3] as dim * n SoA, or NULL (zero).  axis_point / axis_dir may be NULL
+ * when no particle is prescribed.  The constraints are applied to the current state at once. */
+pd_status pd_set_bc(pd_ctx* c, const uint8_t* flag, const double* b, const double* axis_point,
+                    const double* axis_dir, double rate);
+
+/* Sets the displacement u (dim * n SoA, required) and velocity v (dim * n SoA, NULL: zero) and
+ * applies the boundary conditions at the current time.  The next step does not apply the failure
+ * criterion before its force evaluation (the paper applies it after each update, Appendix B). */
+pd_status pd_set_state(pd_ctx* c, const double* u, const double* v);
+
+/* Advances nsteps >= 0 explicit time steps.  Per step: bond-status update on u^n (the failure block
+ * that follows the previous update in Appendix B), dilatation, force, velocity / displacement
+ * update with boundary conditions at t_{n+1}.  Runs as CUDA-graph chunks of PD_OPT_GRAPH_CHUNK
+ * steps when graphs are enabled.  Enqueue only: returns before the GPU finishes. */
+pd_status pd_step(pd_ctx* c, int64_t nsteps);
+
+/* Waits for all work of the context. */
+pd_status pd_sync(pd_ctx* c);
+
+/* Applies the pending failure check to the current state (if a step ran since the last check) and
+ * writes phi_i of Eq 1.31 in caller order (n doubles).  A particle without bonds gets 0. */
+pd_status pd_get_damage(pd_ctx* c, double* phi);
+
+/* Applies the pending failure check, then copies the state in caller order: u and v as dim * n SoA
+ * (FP64 master copies in PD_MIXED), theta (n) = the dilatation evaluated by the last step.  Any of
+ * the three may be NULL. */
+pd_status pd_get_state(pd_ctx* c, double* u, double* v, double* theta);
+
+/* Number of directed bonds of the built family. */
+pd_status pd_num_bonds(pd_ctx* c, int64_t* nbonds);
+
+/* The built family in caller order as CSR (row_ptr: n + 1 int64, col: nbonds int32, neighbours in
+ * ascending caller index) and, if intact != NULL, the bond status (1 intact, 0 broken) after the
+ * pending failure check.  Inspection / testing aid; not on the hot path. */
+pd_status pd_get_neighbors(pd_ctx* c, int64_t* row_ptr, int32_t* col, uint8_t* intact);
+
+/* Counters (see pd_stats); synchronizes. */
+pd_status pd_get_stats(pd_ctx* c, pd_stats* s);
+
+pd_status pd_set_option(pd_ctx* c, int32_t option, int64_t value);
+pd_status pd_get_option(pd_ctx* c, int32_t option, int64_t* value);
+
+/* With PD_OPT_PROFILE on: total device milliseconds and launch count of kernel `kernel` (pd_kernel)
+ * since profiling was switched on or reset.  reset != 0 clears the counters after reading. */
+pd_status pd_get_profile(pd_ctx* c, int32_t kernel, double* total_ms, int64_t* launches,
+                         int32_t reset);
+
+/* Number of particles, dimension and storage of the context (for sizing host buffers). */
+pd_status pd_get_info(pd_ctx* c, int64_t* n, int32_t* dim, int64_t* device_bytes);
+
+/* Thread-local description of the last failure on this host thread ("" if none). */
+const char* pd_last_error(void);
+
+/* Releases every resource of the context (NULL is ignored). */
+void pd_destroy(pd_ctx* c);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OSBPD_H */
