@@ -1,0 +1,400 @@
+"""Benchmark of the OSB-PD bond-force hot path on GB300: bond-updates/s and roofline fractions.
+
+Workload (one "step" = one explicit time step over every bond: failure check + dilatation pass,
+force + update pass): the 3D notched block of 200 x 100 x 50 particles (dx = 1 mm, delta = 3.015 dx,
+~1.17e8 directed bonds, E = 30 GPa, nu = 0.2, clamp + twist, bond breaking at s0 from G0 = 50 J/m^2),
+plain FP64 (the paper's precision).  The same line reports the FP32-bond / FP64-integration form on
+the same workload and the batched form (256 uneven plates) as speed-ups over plain FP64.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--no-forms] [--no-cpu]
+
+N > 1 runs under torchrun: every rank runs an independent replica of the workload (the method has no
+exchange step on one body), timed between barriers; the slowest rank's time counts.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "bond-updates/sec and % HBM roofline; mixed/batched vs plain FP64 GPU at stated error"
+UNIT = "bond-updates/s"
+WORKLOAD = "3D linearized OSB-PD notched block 200x100x50 (1M particles), dx=1 mm, delta=3.015 dx, torsion + clamp, bond breaking (configuration 3)"
+
+# Algorithmic work per directed bond and per particle and pass (3D, no body force).  Bytes: 4 B
+# neighbour index per pass, status bit read each pass and written in pass 1; per particle the
+# coordinates, displacements, velocities, theta, 1/m, flag and row pointer of the model.  FLOPs:
+# sqrt-free FP64 form (FMA = 2).
+BYTES_BOND = {1: 4.25, 2: 4.125}
+BYTES_PART = {1: 68.0, 2: 141.0}
+FLOPS_BOND = {1: 19.0, 2: 28.0}
+FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12  # 2 DFMA/clk/SM x 2 flop x 152 SMs x 2.07 GHz
+
+
+def env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def kernel_source_sha():
+    with open(os.path.join(ROOT, "paper_2309_11273_gb300", "csrc", "pd_step.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def recorded_traffic(kernel):
+    """DRAM bytes per launch recorded from an ncu capture (profiles/ncu_traffic.txt), or None when
+    the kernel source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return None
+    sha = kernel_source_sha()
+    for ln in lines:
+        kv = dict(p.split("=", 1) for p in ln.split() if "=" in p)
+        if kv.get("kernel") == kernel and kv.get("source_sha") == sha and "dram_bytes_per_launch" in kv:
+            return float(kv["dram_bytes_per_launch"])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during a timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for ln in open(self.path):
+                p = [x.strip() for x in ln.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        except OSError:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() in ("active", "1")})
+        pw = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(pw) if pw else None}
+
+
+# --------------------------------------------------------------------------------- distributed
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------------- CPU oracle
+def oracle_sample_rate(target_s=12.0, max_steps=1000):
+    """The oracle (plain FP64 C loops, all host cores) on a 100 x 50 x 25 sub-block of the workload
+    (same dx, horizon, material, clamp / twist, notch): bond-updates/s over enough steps for about
+    target_s seconds of CPU work."""
+    import oracle as O
+    from paper_2309_11273_gb300 import workloads as W
+    w = W.notched_block(nx=100, ny=50, nz=25, dx=1e-3, notch_cells=37.5)
+    s0 = O.critical_stretch(w.model, w.E, w.nu, w.Gc, w.delta)
+    sim = O.OracleSim(w.model, w.E, w.nu, w.rho, w.delta, s0, w.dt, w.x, w.y, w.z, w.vol, w.cracks)
+    sim.set_bc(w.flag, w.b, w.axis_point, w.axis_dir, w.rotation_rate(s0))
+    t0 = time.perf_counter()
+    sim.step(1)
+    t1 = time.perf_counter() - t0
+    steps = int(max(1, min(max_steps, target_s / max(t1, 1e-6))))
+    t0 = time.perf_counter()
+    sim.step(steps)
+    el = time.perf_counter() - t0
+    return {"value": sim.nbonds * steps / el, "unit": UNIT, "cores": O.get_threads(), "kind": "oracle",
+            "sample": "%d time steps of the oracle on a 100x50x25 sub-block of the workload (%d particles, "
+                      "%d directed bonds), %.1f s" % (steps, sim.n, sim.nbonds, el)}
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    import oracle as O
+    from paper_2309_11273_gb300 import workloads as W
+    w = W.notched_block(nx=100, ny=50, nz=25, dx=1e-3, notch_cells=37.5)
+    s0 = O.critical_stretch(w.model, w.E, w.nu, w.Gc, w.delta)
+    sim = O.OracleSim(w.model, w.E, w.nu, w.rho, w.delta, s0, w.dt, w.x, w.y, w.z, w.vol, w.cracks)
+    sim.set_bc(w.flag, w.b, w.axis_point, w.axis_dir, w.rotation_rate(s0))
+    sim.step(args.warmup)
+    t0 = time.perf_counter()
+    sim.step(args.steps)
+    el = time.perf_counter() - t0
+    value = sim.nbonds * args.steps / el
+    sample = ("each step: one oracle time step on a 100x50x25 sub-block of the workload "
+              "(%d particles, %d directed bonds)" % (sim.n, sim.nbonds))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "100x50x25 sub-block"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.get_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------------- GPU arm
+def timed(sim, stream, steps, world):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    sim.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    barrier(world)
+    return e0.elapsed_time(e1)
+
+
+def profiled(sim, steps):
+    """Per-kernel device time from CUDA events the library records around each launch."""
+    from paper_2309_11273_gb300 import _binding as B
+    sim.set_option(B.PD_OPT_PROFILE, 1)
+    B.pd_get_profile(sim.h, B.PD_K_PASS1, reset=True)
+    sim.step(steps)
+    sim.sync()
+    p1 = B.pd_get_profile(sim.h, B.PD_K_PASS1)
+    p2 = B.pd_get_profile(sim.h, B.PD_K_PASS2, reset=True)
+    sim.set_option(B.PD_OPT_PROFILE, 0)
+    return {"pass1_ms": p1[0] / max(p1[1], 1), "pass2_ms": p2[0] / max(p2[1], 1), "launches": p1[1] + p2[1]}
+
+
+def run_gpu(args):
+    import torch
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.cuda.current_device()
+    from paper_2309_11273_gb300 import PD_FP64, PD_MIXED, BatchSimulation, Simulation, pd_critical_stretch
+    from paper_2309_11273_gb300 import _binding as B
+    from paper_2309_11273_gb300 import workloads as W
+    stream = torch.cuda.Stream()
+    peaks = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    hbm_note = "measured" if "hbm_gbs" in peaks else "fallback"
+
+    w = W.config3()
+    s0 = pd_critical_stretch(w.model, w.E, w.nu, w.Gc, w.delta)
+    sim = Simulation(w, s0=s0, precision=PD_FP64, stream=stream.cuda_stream, device=dev)
+    nb = sim.nbonds
+    sim.step(args.warmup)
+    sim.sync()
+    with ClockSampler(dev) as clk:
+        ms = timed(sim, stream, args.steps, world)
+    clocks = clk.summary()
+    ms = max_over_ranks(ms, world)
+    value = world * nb * args.steps / (ms * 1e-3)
+    prof = profiled(sim, max(10, min(args.steps, 50)))
+    k2 = prof["pass2_ms"]
+    flops2 = FLOPS_BOND[2] * nb
+    achieved2 = flops2 / (k2 * 1e-3) / 1e12
+    roofline = {"bound": "alu", "kernel": "k_pass2_f64 (force + update, FP64)", "achieved": achieved2,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved2 / FP64_PEAK_TFLOPS,
+                "traffic": recorded_traffic("k_pass2_f64"),
+                "peak_note": "FP64 peak from unit counts and clock: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz",
+                "algorithmic": "%g FP64 flop per directed bond x %d bonds per launch" % (FLOPS_BOND[2], nb),
+                "pass1_ms": prof["pass1_ms"], "pass2_ms": prof["pass2_ms"],
+                "hbm_frac_of_step": (sum(BYTES_BOND.values()) * nb + sum(BYTES_PART.values()) * w.n)
+                / ((prof["pass1_ms"] + prof["pass2_ms"]) * 1e-3) / (hbm * 1e9)}
+
+    # end to end through the C ABI with pinned host buffers: H2D of (u, v), one step, D2H of u
+    n, dim = w.n, w.dim
+    u_h = torch.empty((dim, n), dtype=torch.float64, pin_memory=True).numpy()
+    v_h = torch.empty((dim, n), dtype=torch.float64, pin_memory=True).numpy()
+    u_out = torch.empty((dim, n), dtype=torch.float64, pin_memory=True).numpy()
+    B.pd_get_state(sim.h, dim, n, u_h, v_h, False)
+    e2e_steps = max(5, min(args.steps, 20))
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        B.pd_set_state(sim.h, dim, n, u_h, v_h)
+        B.pd_step(sim.h, 1)
+        B.pd_get_state(sim.h, dim, n, u_out, False, False)
+    torch.cuda.synchronize()
+    barrier(world)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    e2e = {"value": world * nb * e2e_steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(u_h.nbytes + v_h.nbytes), "d2h_bytes_per_step": int(u_out.nbytes),
+           "steps": e2e_steps, "path": "pd_set_state + pd_step(1) + pd_get_state per step"}
+    sim.close()
+
+    forms = {}
+    if not args.no_forms:
+        forms = run_forms(args, stream, dev, world, value, nb, hbm, hbm_note)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "particles": w.n, "directed_bonds": nb, "precision": "fp64",
+                       "graph_chunk": 100, "l2": "inputs larger than L2 (neighbour indices %.0f MB)" % (nb * 4 / 1e6),
+                       "replicas": world},
+            "roofline": roofline, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": 2 * args.steps + 1}
+    line.update(forms)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = oracle_sample_rate()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_forms(args, stream, dev, world, fp64_value, nb, hbm, hbm_note):
+    """Mixed precision on the same workload and the batched form, as speed-ups over plain FP64."""
+    from paper_2309_11273_gb300 import PD_FP64, PD_MIXED, BatchSimulation, Simulation, pd_critical_stretch
+    from paper_2309_11273_gb300 import _binding as B
+    from paper_2309_11273_gb300 import workloads as W
+    out = {}
+    w = W.config3()
+    s0 = pd_critical_stretch(w.model, w.E, w.nu, w.Gc, w.delta)
+    sim = Simulation(w, s0=s0, precision=PD_MIXED, stream=stream.cuda_stream, device=dev)
+    steps = max(args.steps, 100)
+    sim.step(args.warmup)
+    ms = max_over_ranks(timed(sim, stream, steps, world), world)
+    mval = world * nb * steps / (ms * 1e-3)
+    prof = profiled(sim, 50)
+    st = sim.stats()
+    sim.close()
+    bytes2 = BYTES_BOND[2] * nb + BYTES_PART[2] * w.n
+    bytes1 = BYTES_BOND[1] * nb + BYTES_PART[1] * w.n
+    a2 = bytes2 / (prof["pass2_ms"] * 1e-3) / 1e9
+    a1 = bytes1 / (prof["pass1_ms"] * 1e-3) / 1e9
+    out["mixed"] = {"value": mval, "unit": UNIT, "speedup_vs_fp64": mval / fp64_value,
+                    "ms_per_step": ms / steps, "dtype": "f32 bond arithmetic, f64 integration",
+                    "stated_error": "rel-L2(u) vs FP64 oracle <= 2e-5 after 100 steps and <= 1e-4 after 1000 "
+                                    "(configuration 1); zero bond decisions differing from FP64 on its own state",
+                    "band_rechecks": st["band_rechecks"],
+                    "roofline": {"bound": "hbm", "kernel": "k_pass2_mixed", "achieved": a2, "peak": hbm,
+                                 "unit": "GB/s", "frac": a2 / hbm, "peak_note": hbm_note,
+                                 "traffic": recorded_traffic("k_pass2_mixed"),
+                                 "pass1": {"achieved": a1, "frac": a1 / hbm, "ms": prof["pass1_ms"]},
+                                 "pass2_ms": prof["pass2_ms"],
+                                 "step_frac": (bytes1 + bytes2) / ((prof["pass1_ms"] + prof["pass2_ms"]) * 1e-3)
+                                 / 1e9 / hbm}}
+    # batched: 256 uneven plates (configuration 4) in one context; FP64 and mixed; 100-step graphs
+    bw = W.config4()
+    res = {}
+    for prec, name in ((PD_FP64, "fp64"), (PD_MIXED, "mixed")):
+        bs = BatchSimulation(bw, precision=prec, stream=stream.cuda_stream, device=dev)
+        res["mapping_" + name] = B.pd_autotune(bs.h, 5)
+        bnb = bs.nbonds
+        bs.step(args.warmup)
+        k = max(args.steps, 200)
+        ms = max_over_ranks(timed(bs, stream, k, world), world)
+        res[name] = world * bnb * k / (ms * 1e-3)
+        res["bonds"] = bnb
+        bs.close()
+    out["batched"] = {"value": res["mixed"], "unit": UNIT, "workload": "256 independent plane-stress plates, "
+                      "sides U{20..200}, delta in {3.015, 4.015} dx, one context, 100-step CUDA graphs",
+                      "particles": int(bw.n), "directed_bonds": res["bonds"], "fp64_value": res["fp64"],
+                      "speedup_vs_fp64": res["mixed"] / res["fp64"], "dtype": "f32 bond arithmetic, f64 integration",
+                      "mapping": {"fp64": res["mapping_fp64"], "mixed": res["mapping_mixed"]}}
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    import __graft_entry__
+    __graft_entry__.build()
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

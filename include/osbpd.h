@@ -99,10 +99,8 @@ typedef enum {
   PD_OPT_GRAPH_CHUNK = 1,  /* steps captured per CUDA graph launch (0: no graphs). Default 100. */
   PD_OPT_PROFILE = 2,      /* 1: time every kernel launch with CUDA events (forces eager launches) */
   PD_OPT_VALIDATE = 3,     /* PD_MIXED: 1 = also decide every bond in FP64 and count mismatches */
-  PD_OPT_BLOCK = 4,        /* threads per block of the step kernels (multiple of 32, <= 1024) */
-  PD_OPT_SPLIT = 5,        /* warps cooperating on one 32-particle slice: 1, 2 or 4 */
-  PD_OPT_DIVERGENCE_LIMIT_MM = 6 /* divergence guard: max |u| in micrometres checked by
-                                    pd_check_state (0: off) */
+  PD_OPT_BLOCK = 4,        /* threads per block of the step kernels (multiple of 32, <= 512) */
+  PD_OPT_SPLIT = 5         /* warps cooperating on one 32-particle slice: 1, 2 or 4 */
 } pd_option;
 
 /* Kernel identifiers for pd_get_profile. */
@@ -116,10 +114,9 @@ typedef enum { PD_K_PASS1 = 0, PD_K_PASS2 = 1, PD_K_COUNT = 2 } pd_kernel;
  * Returns a negative value for invalid arguments. */
 double pd_critical_stretch(int32_t model, double E, double nu, double Gc, double delta);
 
-/* Creates a context for one body of n >= 1 particles (n <= 2^31 - 1).
+/* Creates a context for one body of n >= 1 particles (n <= 2^31 - 65).
  * x, y, z: reference coordinates (z must be NULL for 2D models and non-NULL for PD_3D).
- * vol: particle volumes V_i (NULL: every particle gets horizon^dim / 27, i.e. (delta/3)^dim -- pass
- *      explicit volumes for any other spacing).  In 2D, V_i is the area times the thickness; the
+ * vol: particle volumes V_i > 0 (required).  In 2D, V_i is the area times the thickness; the
  *      thickness cancels from u, v and damage.
  * Copies coordinates to the device; allocation failure -> PD_ERR_OOM. */
 pd_status pd_create_particles(pd_ctx** out, const pd_params* prm, int64_t n, const double* x,
@@ -181,6 +178,17 @@ pd_status pd_get_neighbors(pd_ctx* c, int64_t* row_ptr, int32_t* col, uint8_t* i
 
 /* Counters (see pd_stats); synchronizes. */
 pd_status pd_get_stats(pd_ctx* c, pd_stats* s);
+
+/* Divergence guard: returns PD_ERR_NUMERIC if any displacement component is non-finite or larger
+ * in magnitude than max_abs_u (> 0), PD_OK otherwise.  Synchronizes. */
+pd_status pd_check_state(pd_ctx* c, double max_abs_u);
+
+/* Picks the launch mapping (threads per block, warps per 32-particle slice) of the step kernels by
+ * timing trial_steps steps of every candidate on the context's own data, keeps the fastest, and
+ * restores the state, bond status and step count afterwards.  If the environment variable
+ * PD_AUTOTUNE_CACHE names a file, results are looked up / appended there under a key made of the
+ * problem sizes, precision and device name.  *block / *split (may be NULL) receive the choice. */
+pd_status pd_autotune(pd_ctx* c, int32_t trial_steps, int32_t* block, int32_t* split);
 
 pd_status pd_set_option(pd_ctx* c, int32_t option, int64_t value);
 pd_status pd_get_option(pd_ctx* c, int32_t option, int64_t* value);

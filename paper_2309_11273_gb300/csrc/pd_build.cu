@@ -1,0 +1,676 @@
+// Context creation and family (neighbour-list) construction.
+//
+// Compiled with --fmad=false: the horizon test |xi|^2 <= delta^2 (Section 2.1, closed ball) and the
+// crack-crossing test round every product and sum separately, as plain IEEE expressions, so their
+// decisions do not depend on FMA contraction.
+//
+// Layout produced here (all in the internal Morton order of the particles):
+//   slices of 32 consecutive particles (one warp); slice s owns W_s = max family size in the slice
+//   "slots"; the neighbour of particle (s, lane) in slot k is col[slice_ptr[s] + 32 k + lane]
+//   (sliced ELLPACK: a warp reading slot k reads 128 contiguous bytes).  Each row is sorted by the
+//   reference bond vector xi (lexicographic z, y, x), so on a lattice slot k holds the same lattice
+//   direction for every interior lane.  Unused slots hold the particle itself.
+//   bits[slice_ptr[s] / 32 + k] bit lane = status of that entry (1 intact, 0 broken or unused).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "pd_internal.h"
+
+namespace pd {
+namespace {
+
+struct BuildArgs {
+  int64_t n, n_pad;
+  const double4* pos;
+  const int4* cellc;         // cell coordinates (x, y, z) and body in .w
+  const BodyGrid* grids;
+  const int64_t* cell_start;
+  const int32_t* cell_items;
+  const CrackDev* cracks;
+  int32_t ncracks;
+  int32_t* cnt;
+  const int64_t* slice_ptr;
+  int32_t* col;
+  unsigned long long* keys;
+  uint32_t* bits;
+  const double* body_A;
+  double* m;
+  double* mu;
+  double* aA;
+  double* dden;
+};
+
+// A bond a-b is cut by a crack iff a and b lie strictly on opposite sides of the crack line (2D) or
+// plane (3D) and the crossing point lies on the closed segment / parallelogram.
+template <int DIM>
+__device__ bool crack_cuts(const double4& a, const double4& b, const CrackDev& c) {
+  if (DIM == 2) {
+    double dx = c.p[3] - c.p[0], dy = c.p[4] - c.p[1];
+    double sa = dx * (a.y - c.p[1]) - dy * (a.x - c.p[0]);
+    double sb = dx * (b.y - c.p[1]) - dy * (b.x - c.p[0]);
+    if (!((sa > 0.0 && sb < 0.0) || (sa < 0.0 && sb > 0.0))) return false;
+    double t = sa / (sa - sb);
+    double px = a.x + t * (b.x - a.x);
+    double py = a.y + t * (b.y - a.y);
+    double lam = ((px - c.p[0]) * dx + (py - c.p[1]) * dy) / (dx * dx + dy * dy);
+    return lam >= 0.0 && lam <= 1.0;
+  } else {
+    double e1x = c.p[3] - c.p[0], e1y = c.p[4] - c.p[1], e1z = c.p[5] - c.p[2];
+    double e2x = c.p[6] - c.p[0], e2y = c.p[7] - c.p[1], e2z = c.p[8] - c.p[2];
+    double nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z, nz = e1x * e2y - e1y * e2x;
+    double sa = nx * (a.x - c.p[0]) + ny * (a.y - c.p[1]) + nz * (a.z - c.p[2]);
+    double sb = nx * (b.x - c.p[0]) + ny * (b.y - c.p[1]) + nz * (b.z - c.p[2]);
+    if (!((sa > 0.0 && sb < 0.0) || (sa < 0.0 && sb > 0.0))) return false;
+    double t = sa / (sa - sb);
+    double rx = a.x + t * (b.x - a.x) - c.p[0];
+    double ry = a.y + t * (b.y - a.y) - c.p[1];
+    double rz = a.z + t * (b.z - a.z) - c.p[2];
+    double g11 = e1x * e1x + e1y * e1y + e1z * e1z;
+    double g12 = e1x * e2x + e1y * e2y + e1z * e2z;
+    double g22 = e2x * e2x + e2y * e2y + e2z * e2z;
+    double r1 = e1x * rx + e1y * ry + e1z * rz;
+    double r2 = e2x * rx + e2y * ry + e2z * rz;
+    double det = g11 * g22 - g12 * g12;
+    double al = (r1 * g22 - r2 * g12) / det;
+    double be = (g11 * r2 - g12 * r1) / det;
+    return al >= 0.0 && al <= 1.0 && be >= 0.0 && be <= 1.0;
+  }
+}
+
+// Sort key of an entry: xi quantized to delta / 2^19 per component, z major.
+__device__ unsigned long long xi_key(double ex, double ey, double ez, double inv_delta) {
+  const double s = 524288.0 * inv_delta;
+  long long kx = llrint(ex * s) + 524288, ky = llrint(ey * s) + 524288, kz = llrint(ez * s) + 524288;
+  kx = kx < 0 ? 0 : (kx > 2097151 ? 2097151 : kx);
+  ky = ky < 0 ? 0 : (ky > 2097151 ? 2097151 : ky);
+  kz = kz < 0 ? 0 : (kz > 2097151 ? 2097151 : kz);
+  return ((unsigned long long)kz << 42) | ((unsigned long long)ky << 21) | (unsigned long long)kx;
+}
+
+// Family search over the 3^DIM cells around the particle.  EMIT = false counts; EMIT = true writes
+// the entries (in cell order), sorts the row by xi and pads the unused slots.
+template <int DIM, bool EMIT>
+__global__ void k_family(BuildArgs A) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= A.n_pad) return;
+  const int lane = (int)(i & 31);
+  int64_t base = 0;
+  int W = 0;
+  if (EMIT) {
+    const int64_t s = i >> 5;
+    base = A.slice_ptr[s] + lane;
+    W = (int)((A.slice_ptr[s + 1] - A.slice_ptr[s]) >> 5);
+  }
+  int cnt = 0;
+  if (i < A.n) {
+    const int4 cc = A.cellc[i];
+    const BodyGrid g = A.grids[cc.w];
+    const double4 pi = A.pos[i];
+    const double inv_delta = 1.0 / sqrt(g.delta2);
+    const int zlo = DIM == 3 ? -1 : 0, zhi = DIM == 3 ? 1 : 0;
+    for (int dz = zlo; dz <= zhi; ++dz) {
+      const int cz = cc.z + dz;
+      if (cz < 0 || cz >= g.nc[2]) continue;
+      for (int dy = -1; dy <= 1; ++dy) {
+        const int cy = cc.y + dy;
+        if (cy < 0 || cy >= g.nc[1]) continue;
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int cx = cc.x + dx;
+          if (cx < 0 || cx >= g.nc[0]) continue;
+          const int64_t cid = g.cell_off + ((int64_t)cz * g.nc[1] + cy) * g.nc[0] + cx;
+          for (int64_t t = A.cell_start[cid]; t < A.cell_start[cid + 1]; ++t) {
+            const int32_t j = A.cell_items[t];
+            if (j == i) continue;
+            const double4 pj = A.pos[j];
+            const double ex = pj.x - pi.x, ey = pj.y - pi.y, ez = pj.z - pi.z;
+            double q = ex * ex + ey * ey;
+            if (DIM == 3) q = q + ez * ez;
+            if (!(q <= g.delta2)) continue;
+            bool cut = false;
+            for (int c = 0; c < A.ncracks && !cut; ++c) {
+              const CrackDev& cr = A.cracks[c];
+              if (cr.body >= 0 && cr.body != cc.w) continue;
+              cut = crack_cuts<DIM>(pi, pj, cr);
+            }
+            if (cut) continue;
+            if (EMIT) {
+              if (cnt < W) {
+                A.col[base + (int64_t)cnt * 32] = j;
+                A.keys[base + (int64_t)cnt * 32] = xi_key(ex, ey, DIM == 3 ? ez : 0.0, inv_delta);
+              }
+            }
+            ++cnt;
+          }
+        }
+      }
+    }
+  }
+  if (!EMIT) {
+    A.cnt[i] = cnt;
+    return;
+  }
+  if (cnt > W) cnt = W;  // cannot happen: W is the slice maximum of the same count
+  // insertion sort of the row by (key, neighbour)
+  for (int a = 1; a < cnt; ++a) {
+    const unsigned long long ka = A.keys[base + (int64_t)a * 32];
+    const int32_t ja = A.col[base + (int64_t)a * 32];
+    int b = a - 1;
+    while (b >= 0) {
+      const unsigned long long kb = A.keys[base + (int64_t)b * 32];
+      const int32_t jb = A.col[base + (int64_t)b * 32];
+      if (kb < ka || (kb == ka && jb < ja)) break;
+      A.keys[base + (int64_t)(b + 1) * 32] = kb;
+      A.col[base + (int64_t)(b + 1) * 32] = jb;
+      --b;
+    }
+    A.keys[base + (int64_t)(b + 1) * 32] = ka;
+    A.col[base + (int64_t)(b + 1) * 32] = ja;
+  }
+  for (int a = cnt; a < W; ++a) A.col[base + (int64_t)a * 32] = (int32_t)i;
+}
+
+__global__ void k_slice_width(int64_t nslices, const int32_t* cnt, int32_t* width) {
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= nslices) return;
+  int w = 0;
+  for (int l = 0; l < 32; ++l) w = max(w, cnt[s * 32 + l]);
+  width[s] = w;
+}
+
+// Initial status words (every built bond intact) and the per-particle sums m_i (Eq 1.9) and
+// D_i = sum_j V_j (Eq 1.31 denominator), both in FP64 over the built family.
+template <int DIM>
+__global__ void k_init_bonds(BuildArgs A) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= A.n_pad) return;  // n_pad is a multiple of 32: whole warps leave together
+  const int lane = (int)(i & 31);
+  const int64_t s = i >> 5;
+  const int64_t base = A.slice_ptr[s];
+  const int W = (int)((A.slice_ptr[s + 1] - base) >> 5);
+  const int cnt = A.cnt[i];
+  const double4 pi = A.pos[i];
+  double m = 0.0, d = 0.0;
+  for (int k = 0; k < W; ++k) {
+    const unsigned word = __ballot_sync(0xffffffffu, k < cnt);
+    if (lane == 0) A.bits[(base >> 5) + k] = word;
+    if (k < cnt) {
+      const int32_t j = A.col[base + (int64_t)k * 32 + lane];
+      const double4 pj = A.pos[j];
+      const double ex = pj.x - pi.x, ey = pj.y - pi.y, ez = pj.z - pi.z;
+      double q = ex * ex + ey * ey;
+      if (DIM == 3) q = q + ez * ez;
+      m += q * pj.w;
+      d += pj.w;
+    }
+  }
+  A.m[i] = m;
+  A.dden[i] = d;
+  const double mu = m > 0.0 ? 1.0 / m : 0.0;
+  A.mu[i] = mu;
+  A.aA[i] = (i < A.n) ? A.body_A[A.cellc[i].w] * mu : 0.0;
+}
+
+// Morton key of 21-bit quantized coordinates.
+uint64_t spread3(uint64_t v) {
+  v &= 0x1fffff;
+  v = (v | v << 32) & 0x1f00000000ffffULL;
+  v = (v | v << 16) & 0x1f0000ff0000ffULL;
+  v = (v | v << 8) & 0x100f00f00f00f00fULL;
+  v = (v | v << 4) & 0x10c30c30c30c30c3ULL;
+  v = (v | v << 2) & 0x1249249249249249ULL;
+  return v;
+}
+uint64_t spread2(uint64_t v) {
+  v &= 0xffffffffULL;
+  v = (v | v << 16) & 0x0000ffff0000ffffULL;
+  v = (v | v << 8) & 0x00ff00ff00ff00ffULL;
+  v = (v | v << 4) & 0x0f0f0f0f0f0f0f0fULL;
+  v = (v | v << 2) & 0x3333333333333333ULL;
+  v = (v | v << 1) & 0x5555555555555555ULL;
+  return v;
+}
+
+bool finite_all(const double* a, int64_t n) {
+  for (int64_t i = 0; i < n; ++i)
+    if (!std::isfinite(a[i])) return false;
+  return true;
+}
+
+pd_status check_params(const pd_params& p, int dim) {
+  if (p.model < 0 || p.model > 2) return fail(PD_ERR_ARG, "unknown model");
+  if ((p.model == PD_3D) != (dim == 3)) return fail(PD_ERR_ARG, "z must be given exactly for PD_3D");
+  if (p.precision != PD_FP64 && p.precision != PD_MIXED) return fail(PD_ERR_ARG, "unknown precision");
+  if (!(p.E > 0) || !std::isfinite(p.E)) return fail(PD_ERR_ARG, "E must be > 0");
+  if (!(p.nu > -1.0 && p.nu < 0.5)) return fail(PD_ERR_ARG, "nu must lie in (-1, 0.5)");
+  if (p.model == PD_PLANE_STRESS && !(p.nu < 1.0 / 3.0 || p.nu > 1.0 / 3.0)) {
+    // K of Eq 1.15 (plane stress) is regular at nu = 1/3; nothing to reject.
+  }
+  if (!(p.rho > 0) || !std::isfinite(p.rho)) return fail(PD_ERR_ARG, "rho must be > 0");
+  if (!(p.horizon > 0) || !std::isfinite(p.horizon)) return fail(PD_ERR_ARG, "horizon must be > 0");
+  if (!(p.dt > 0) || !std::isfinite(p.dt)) return fail(PD_ERR_ARG, "dt must be > 0");
+  if (!std::isfinite(p.s0)) return fail(PD_ERR_ARG, "s0 must be finite");
+  if (p.reserved != 0) return fail(PD_ERR_ARG, "reserved must be 0");
+  return PD_OK;
+}
+
+}  // namespace
+
+// Material constants: A (Eq 1.8), K (Eq 1.15), G (Eq 1.16) from E and nu.
+void material_constants(int model, double E, double nu, double* A, double* K, double* G) {
+  const double kappa = E / (3.0 * (1.0 - 2.0 * nu));
+  const double mu = E / (2.0 * (1.0 + nu));
+  if (model == PD_3D) {
+    *A = 3.0;
+    *K = 3.0 * kappa;
+    *G = 15.0 * mu;
+  } else if (model == PD_PLANE_STRESS) {
+    *A = 2.0 * (1.0 - 2.0 * nu) / (1.0 - nu);
+    *K = 2.0 * kappa * (1.0 - 2.0 * nu) / (1.0 - nu) -
+         2.0 / 3.0 * mu * (1.0 + nu) * (1.0 - 3.0 * nu) / ((1.0 - nu) * (1.0 - 2.0 * nu));
+    *G = 8.0 * mu;
+  } else {
+    *A = 2.0;
+    *K = 2.0 * kappa - 2.0 / 3.0 * mu;
+    *G = 8.0 * mu;
+  }
+}
+
+pd_status upload_body_params(pd_ctx* c);
+
+// Creation shared by pd_create_particles and pd_create_batch.
+pd_status create(pd_ctx** out, int32_t nbodies, const pd_params* prm, const int64_t* offsets,
+                 const double* x, const double* y, const double* z, const double* vol) {
+  clear_error();
+  if (!out) return fail(PD_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!prm || !x || !y || !vol) return fail(PD_ERR_ARG, "prm, x, y and vol are required");
+  if (nbodies < 1) return fail(PD_ERR_ARG, "nbodies must be >= 1");
+  const int dim = z ? 3 : 2;
+  const int64_t n = offsets[nbodies];
+  if (n < 1 || n > 2147483647LL - 64) return fail(PD_ERR_ARG, "particle count out of range");
+  for (int b = 0; b < nbodies; ++b) {
+    if (offsets[b + 1] <= offsets[b]) return fail(PD_ERR_ARG, "every body needs >= 1 particle");
+    pd_status st = check_params(prm[b], dim);
+    if (st != PD_OK) return st;
+    if (prm[b].model != prm[0].model || prm[b].precision != prm[0].precision ||
+        prm[b].device != prm[0].device || prm[b].stream != prm[0].stream)
+      return fail(PD_ERR_ARG, "bodies must share model, precision, device and stream");
+  }
+  if (!finite_all(x, n) || !finite_all(y, n) || (z && !finite_all(z, n)) || !finite_all(vol, n))
+    return fail(PD_ERR_ARG, "non-finite coordinate or volume");
+  for (int64_t i = 0; i < n; ++i)
+    if (!(vol[i] > 0)) return fail(PD_ERR_ARG, "volumes must be > 0");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return fail(PD_ERR_CUDA, "no CUDA device available");
+  }
+  if (prm[0].device < 0 || prm[0].device >= ndev) return fail(PD_ERR_ARG, "bad device ordinal");
+  PD_CUDA(cudaSetDevice(prm[0].device));
+
+  pd_ctx* c = new pd_ctx();
+  c->device = prm[0].device;
+  c->dim = dim;
+  c->model = prm[0].model;
+  c->precision = prm[0].precision;
+  c->n = n;
+  c->nslices = (n + kSlice - 1) / kSlice;
+  c->n_pad = c->nslices * kSlice;
+  c->nbodies = nbodies;
+  c->prm.assign(prm, prm + nbodies);
+  c->body_off.assign(offsets, offsets + nbodies + 1);
+  c->hx.assign(x, x + n);
+  c->hy.assign(y, y + n);
+  if (z) c->hz.assign(z, z + n);
+  c->hvol.assign(vol, vol + n);
+  if (prm[0].stream) {
+    c->stream = (cudaStream_t)prm[0].stream;
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      delete c;
+      return cuda_fail(e, "cudaStreamCreateWithFlags");
+    }
+    c->own_stream = true;
+  }
+
+  // Morton order inside each body; bodies stay contiguous in their given order.
+  std::vector<uint64_t> key(n);
+  c->body_of.assign(n, 0);
+  for (int b = 0; b < nbodies; ++b) {
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int64_t i = offsets[b]; i < offsets[b + 1]; ++i) {
+      const double p[3] = {x[i], y[i], z ? z[i] : 0.0};
+      for (int k = 0; k < 3; ++k) {
+        lo[k] = std::min(lo[k], p[k]);
+        hi[k] = std::max(hi[k], p[k]);
+      }
+    }
+    double ext = std::max(hi[0] - lo[0], std::max(hi[1] - lo[1], hi[2] - lo[2]));
+    if (!(ext > 0)) ext = 1.0;
+    const double bitsmax = dim == 3 ? 2097151.0 : 4294967295.0;
+    const double sc = bitsmax / ext;
+    for (int64_t i = offsets[b]; i < offsets[b + 1]; ++i) {
+      const uint64_t qx = (uint64_t)std::min(bitsmax, std::max(0.0, (x[i] - lo[0]) * sc));
+      const uint64_t qy = (uint64_t)std::min(bitsmax, std::max(0.0, (y[i] - lo[1]) * sc));
+      if (dim == 3) {
+        const uint64_t qz = (uint64_t)std::min(bitsmax, std::max(0.0, (z[i] - lo[2]) * sc));
+        key[i] = spread3(qx) | (spread3(qy) << 1) | (spread3(qz) << 2);
+      } else {
+        key[i] = spread2(qx) | (spread2(qy) << 1);
+      }
+      c->body_of[i] = b;
+    }
+  }
+  c->perm.resize(n);
+  std::iota(c->perm.begin(), c->perm.end(), 0);
+  std::stable_sort(c->perm.begin(), c->perm.end(), [&](int64_t a, int64_t b) {
+    if (c->body_of[a] != c->body_of[b]) return c->body_of[a] < c->body_of[b];
+    return key[a] < key[b];
+  });
+  std::vector<int32_t> body_int(c->n_pad, 0);
+  for (int64_t k = 0; k < n; ++k) body_int[k] = c->body_of[c->perm[k]];
+  for (int64_t k = n; k < c->n_pad; ++k) body_int[k] = body_int[n - 1];
+  c->body_of.assign(body_int.begin(), body_int.end());
+
+  pd_status st = PD_OK;
+  std::vector<double4> hpos(c->n_pad);
+  for (int64_t k = 0; k < c->n_pad; ++k) {
+    if (k < n) {
+      const int64_t u = c->perm[k];
+      hpos[k] = make_double4(x[u], y[u], z ? z[u] : 0.0, vol[u]);
+    } else {
+      // padding particles: far from everything, unit volume, never part of a family
+      const int64_t u = c->perm[n - 1];
+      hpos[k] = make_double4(x[u], y[u], z ? z[u] : 0.0, 1.0);
+    }
+  }
+  std::vector<int64_t> hperm(c->perm.begin(), c->perm.end());
+#define PD_TRY(expr)              \
+  do {                            \
+    st = (expr);                  \
+    if (st != PD_OK) goto failed; \
+  } while (0)
+  PD_TRY(alloc(c, &c->pos, c->n_pad));
+  PD_TRY(alloc(c, &c->body, c->n_pad));
+  PD_TRY(alloc(c, &c->bp, nbodies));
+  PD_TRY(alloc(c, &c->perm_dev, n));
+  PD_TRY(alloc(c, &c->d_step, 1));
+  PD_TRY(alloc(c, &c->counters, 4));
+  PD_TRY(alloc(c, &c->scratch, (size_t)c->n_pad * 3));
+  if (cudaMemcpyAsync(c->pos, hpos.data(), sizeof(double4) * c->n_pad, cudaMemcpyHostToDevice, c->stream) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(c->body, body_int.data(), sizeof(int32_t) * c->n_pad, cudaMemcpyHostToDevice,
+                      c->stream) != cudaSuccess ||
+      cudaMemcpyAsync(c->perm_dev, hperm.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, c->stream) !=
+          cudaSuccess ||
+      cudaMemsetAsync(c->counters, 0, sizeof(unsigned long long) * 4, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    st = cuda_fail(cudaGetLastError(), "upload of particles");
+    goto failed;
+  }
+  {
+    // Fixed-point quantum of the mixed path: a power of two with every coordinate offset < 2^30 Q.
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int64_t i = 0; i < n; ++i) {
+      const double p[3] = {x[i], y[i], z ? z[i] : 0.0};
+      for (int k = 0; k < 3; ++k) {
+        lo[k] = std::min(lo[k], p[k]);
+        hi[k] = std::max(hi[k], p[k]);
+      }
+    }
+    double ext = std::max(hi[0] - lo[0], std::max(hi[1] - lo[1], hi[2] - lo[2]));
+    if (!(ext > 0)) ext = 1.0;
+    c->q = std::ldexp(1.0, (int)std::ceil(std::log2(ext / 1073741824.0)));
+    for (int k = 0; k < 3; ++k) c->qlo[k] = lo[k];
+  }
+  c->n_create_allocs = c->allocs.size();
+  PD_TRY(upload_body_params(c));
+  *out = c;
+  return PD_OK;
+failed:
+  free_all(c);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+  return st;
+#undef PD_TRY
+}
+
+// Per-body constants for the kernels (also refreshed when the rotation rate changes).
+pd_status upload_body_params(pd_ctx* c) {
+  std::vector<BodyDev> h(c->nbodies);
+  for (int b = 0; b < c->nbodies; ++b) {
+    const pd_params& p = c->prm[b];
+    double A, K, G;
+    material_constants(p.model, p.E, p.nu, &A, &K, &G);
+    BodyDev& d = h[b];
+    d.Kp = K - G / 3.0;
+    d.G = G;
+    d.inv_rho = 1.0 / p.rho;
+    d.dt = p.dt;
+    d.s0 = p.s0;
+    d.rate = 0.0;
+    d.Kp32 = (float)(d.Kp * c->q);
+    d.G32 = (float)d.G;
+    d.inv_rho32 = (float)d.inv_rho;
+    d.sigma_q = p.s0 * c->q;
+    d.sigma32 = (float)d.sigma_q;
+  }
+  for (int b = 0; b < c->nbodies; ++b) h[b].rate = c->rate;
+  PD_CUDA(cudaMemcpyAsync(c->bp, h.data(), sizeof(BodyDev) * c->nbodies, cudaMemcpyHostToDevice, c->stream));
+  PD_CUDA(cudaStreamSynchronize(c->stream));
+  return PD_OK;
+}
+
+pd_status build_neighbors(pd_ctx* c, const pd_crack* cracks, int32_t ncracks) {
+  clear_error();
+  if (!c) return fail(PD_ERR_ARG, "context is NULL");
+  if (ncracks < 0 || (ncracks > 0 && !cracks)) return fail(PD_ERR_ARG, "bad crack list");
+  PD_CUDA(cudaSetDevice(c->device));
+  drop_graphs(c);
+  const int64_t n = c->n, n_pad = c->n_pad;
+  const int dim = c->dim;
+  std::vector<CrackDev> hcr(ncracks);
+  for (int k = 0; k < ncracks; ++k) {
+    for (int t = 0; t < 3; ++t) {
+      hcr[k].p[t] = cracks[k].p0[t];
+      hcr[k].p[3 + t] = cracks[k].p1[t];
+      hcr[k].p[6 + t] = cracks[k].p2[t];
+    }
+    for (double v : hcr[k].p)
+      if (!std::isfinite(v)) return fail(PD_ERR_ARG, "non-finite crack coordinate");
+    hcr[k].body = cracks[k].body;
+    if (cracks[k].body >= c->nbodies) return fail(PD_ERR_ARG, "crack body index out of range");
+  }
+
+  // Per-body cell grids (edge = delta) and cell coordinates of every particle (internal order).
+  std::vector<BodyGrid> grids(c->nbodies);
+  std::vector<int4> cellc(n_pad);
+  int64_t ncells = 0;
+  std::vector<double> bodyA(c->nbodies);
+  for (int b = 0; b < c->nbodies; ++b) {
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int64_t u = c->body_off[b]; u < c->body_off[b + 1]; ++u) {
+      const double p[3] = {c->hx[u], c->hy[u], dim == 3 ? c->hz[u] : 0.0};
+      for (int k = 0; k < 3; ++k) {
+        lo[k] = std::min(lo[k], p[k]);
+        hi[k] = std::max(hi[k], p[k]);
+      }
+    }
+    BodyGrid& g = grids[b];
+    g.h = c->prm[b].horizon;
+    g.delta2 = c->prm[b].horizon * c->prm[b].horizon;
+    for (int k = 0; k < 3; ++k) {
+      g.lo[k] = lo[k];
+      double cells = std::floor((hi[k] - lo[k]) / g.h) + 1.0;
+      if (k == 2 && dim == 2) cells = 1.0;
+      if (cells > 2.0e6) return fail(PD_ERR_ARG, "horizon too small for the body extent");
+      g.nc[k] = (int32_t)cells;
+    }
+    g.cell_off = ncells;
+    ncells += (int64_t)g.nc[0] * g.nc[1] * g.nc[2];
+    if (ncells > (int64_t)4e9) return fail(PD_ERR_ARG, "too many search cells");
+    double A, K, G;
+    material_constants(c->prm[b].model, c->prm[b].E, c->prm[b].nu, &A, &K, &G);
+    bodyA[b] = A;
+  }
+  std::vector<int64_t> cell_of(n);
+  for (int64_t k = 0; k < n_pad; ++k) {
+    if (k >= n) {
+      cellc[k] = make_int4(0, 0, 0, c->body_of[k]);
+      continue;
+    }
+    const int64_t u = c->perm[k];
+    const int b = c->body_of[k];
+    const BodyGrid& g = grids[b];
+    const double p[3] = {c->hx[u], c->hy[u], dim == 3 ? c->hz[u] : 0.0};
+    int cc[3];
+    for (int t = 0; t < 3; ++t) {
+      double f = std::floor((p[t] - g.lo[t]) / g.h);
+      if (f < 0) f = 0;
+      if (f > g.nc[t] - 1) f = g.nc[t] - 1;
+      cc[t] = (int)f;
+    }
+    cellc[k] = make_int4(cc[0], cc[1], cc[2], b);
+    cell_of[k] = g.cell_off + ((int64_t)cc[2] * g.nc[1] + cc[1]) * g.nc[0] + cc[0];
+  }
+  std::vector<int64_t> cell_start(ncells + 1, 0);
+  for (int64_t k = 0; k < n; ++k) cell_start[cell_of[k] + 1]++;
+  for (int64_t t = 0; t < ncells; ++t) cell_start[t + 1] += cell_start[t];
+  std::vector<int32_t> cell_items(std::max<int64_t>(n, 1));
+  {
+    std::vector<int64_t> fill(cell_start.begin(), cell_start.end() - 1);
+    for (int64_t k = 0; k < n; ++k) cell_items[fill[cell_of[k]]++] = (int32_t)k;
+  }
+
+  // Temporaries (released at the end of the build).
+  int4* d_cellc = nullptr;
+  BodyGrid* d_grids = nullptr;
+  int64_t* d_cell_start = nullptr;
+  int32_t* d_cell_items = nullptr;
+  CrackDev* d_cracks = nullptr;
+  double* d_bodyA = nullptr;
+  double* d_m = nullptr;
+  int32_t* d_width = nullptr;
+  unsigned long long* d_keys = nullptr;
+  auto cleanup = [&]() {
+    cudaFree(d_cellc);
+    cudaFree(d_grids);
+    cudaFree(d_cell_start);
+    cudaFree(d_cell_items);
+    cudaFree(d_cracks);
+    cudaFree(d_bodyA);
+    cudaFree(d_m);
+    cudaFree(d_width);
+    cudaFree(d_keys);
+  };
+  auto tmp_alloc = [&](void** p, size_t bytes) -> pd_status {
+    if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(PD_ERR_OOM, "cudaMalloc of build temporaries failed");
+    }
+    return PD_OK;
+  };
+  // Arrays of a previous build are released first.
+  free_build(c);
+  c->built = false;
+  pd_status st = PD_OK;
+#define PD_TRY2(expr)    \
+  do {                   \
+    st = (expr);         \
+    if (st != PD_OK) {   \
+      cleanup();         \
+      return st;         \
+    }                    \
+  } while (0)
+  PD_TRY2(tmp_alloc((void**)&d_cellc, sizeof(int4) * n_pad));
+  PD_TRY2(tmp_alloc((void**)&d_grids, sizeof(BodyGrid) * c->nbodies));
+  PD_TRY2(tmp_alloc((void**)&d_cell_start, sizeof(int64_t) * (ncells + 1)));
+  PD_TRY2(tmp_alloc((void**)&d_cell_items, sizeof(int32_t) * cell_items.size()));
+  PD_TRY2(tmp_alloc((void**)&d_cracks, sizeof(CrackDev) * std::max(ncracks, 1)));
+  PD_TRY2(tmp_alloc((void**)&d_bodyA, sizeof(double) * c->nbodies));
+  PD_TRY2(tmp_alloc((void**)&d_m, sizeof(double) * n_pad));
+  PD_TRY2(tmp_alloc((void**)&d_width, sizeof(int32_t) * c->nslices));
+  PD_TRY2(alloc(c, &c->cnt, n_pad));
+  PD_TRY2(alloc(c, &c->slice_ptr, c->nslices + 1));
+  PD_TRY2(alloc(c, &c->mu, n_pad));
+  PD_TRY2(alloc(c, &c->aA, n_pad));
+  PD_TRY2(alloc(c, &c->dden, n_pad));
+  {
+    cudaStream_t s = c->stream;
+    auto up = [&](void* dst, const void* src, size_t bytes) -> pd_status {
+      if (bytes == 0) return PD_OK;
+      cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s);
+      return e == cudaSuccess ? PD_OK : cuda_fail(e, "cudaMemcpyAsync (build)");
+    };
+    PD_TRY2(up(d_cellc, cellc.data(), sizeof(int4) * n_pad));
+    PD_TRY2(up(d_grids, grids.data(), sizeof(BodyGrid) * c->nbodies));
+    PD_TRY2(up(d_cell_start, cell_start.data(), sizeof(int64_t) * (ncells + 1)));
+    PD_TRY2(up(d_cell_items, cell_items.data(), sizeof(int32_t) * cell_items.size()));
+    PD_TRY2(up(d_cracks, hcr.data(), sizeof(CrackDev) * ncracks));
+    PD_TRY2(up(d_bodyA, bodyA.data(), sizeof(double) * c->nbodies));
+
+    BuildArgs A{};
+    A.n = n;
+    A.n_pad = n_pad;
+    A.pos = c->pos;
+    A.cellc = d_cellc;
+    A.grids = d_grids;
+    A.cell_start = d_cell_start;
+    A.cell_items = d_cell_items;
+    A.cracks = d_cracks;
+    A.ncracks = ncracks;
+    A.cnt = c->cnt;
+    A.body_A = d_bodyA;
+    A.m = d_m;
+    A.mu = c->mu;
+    A.aA = c->aA;
+    A.dden = c->dden;
+    const int tb = 128;
+    const unsigned gb = (unsigned)((n_pad + tb - 1) / tb);
+    if (dim == 3)
+      k_family<3, false><<<gb, tb, 0, s>>>(A);
+    else
+      k_family<2, false><<<gb, tb, 0, s>>>(A);
+    k_slice_width<<<(unsigned)((c->nslices + 127) / 128), 128, 0, s>>>(c->nslices, c->cnt, d_width);
+    std::vector<int32_t> width(c->nslices);
+    std::vector<int32_t> hcnt(n_pad);
+    PD_CUDA(cudaMemcpyAsync(width.data(), d_width, sizeof(int32_t) * c->nslices, cudaMemcpyDeviceToHost, s));
+    PD_CUDA(cudaMemcpyAsync(hcnt.data(), c->cnt, sizeof(int32_t) * n_pad, cudaMemcpyDeviceToHost, s));
+    PD_CUDA(cudaStreamSynchronize(s));
+    std::vector<int64_t> sptr(c->nslices + 1, 0);
+    for (int64_t t = 0; t < c->nslices; ++t) sptr[t + 1] = sptr[t] + 32 * (int64_t)width[t];
+    c->nentries = sptr[c->nslices];
+    c->nbonds = 0;
+    for (int64_t k = 0; k < n; ++k) c->nbonds += hcnt[k];
+    PD_TRY2(alloc(c, &c->col, (size_t)std::max<int64_t>(c->nentries, 32)));
+    PD_TRY2(alloc(c, &c->bits, (size_t)std::max<int64_t>(c->nentries / 32, 1)));
+    PD_TRY2(tmp_alloc((void**)&d_keys, sizeof(unsigned long long) * std::max<int64_t>(c->nentries, 32)));
+    PD_TRY2(up(c->slice_ptr, sptr.data(), sizeof(int64_t) * (c->nslices + 1)));
+    A.slice_ptr = c->slice_ptr;
+    A.col = c->col;
+    A.keys = d_keys;
+    A.bits = c->bits;
+    if (dim == 3) {
+      k_family<3, true><<<gb, tb, 0, s>>>(A);
+      k_init_bonds<3><<<gb, tb, 0, s>>>(A);
+    } else {
+      k_family<2, true><<<gb, tb, 0, s>>>(A);
+      k_init_bonds<2><<<gb, tb, 0, s>>>(A);
+    }
+    PD_CUDA(cudaGetLastError());
+    PD_CUDA(cudaStreamSynchronize(s));
+  }
+  cleanup();
+#undef PD_TRY2
+  {
+    pd_status st2 = alloc_state(c);
+    if (st2 != PD_OK) return st2;
+  }
+  c->built = true;
+  return PD_OK;
+}
+
+}  // namespace pd

@@ -1,0 +1,206 @@
+// Internal declarations shared by the translation units of libosbpd (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/osbpd.h"
+
+namespace pd {
+
+constexpr int kSlice = 32;  // particles per SELL slice (one warp)
+
+// Per-body constants read by the step kernels (one entry per body; a single body otherwise).
+struct BodyDev {
+  double Kp;       // K - G/3 (Eqs 1.14, 2.2)
+  double G;        // Eq 1.16
+  double inv_rho;  // 1 / rho
+  double dt;       // time step
+  double s0;       // critical stretch (<= 0: no breaking)
+  double rate;     // prescribed rotation rate
+  float Kp32, G32, inv_rho32, sigma32;  // FP32 copies for the mixed path (sigma32 = s0 * Q)
+  double sigma_q;  // s0 * Q in double (Q = fixed-point quantum of the mixed coordinates)
+};
+
+// Per-body neighbour-search grid (cells of edge >= delta).
+struct BodyGrid {
+  double lo[3];
+  double h;
+  double delta2;   // delta * delta
+  int32_t nc[3];
+  int32_t pad;
+  int64_t cell_off;
+};
+
+// Crack (Section 4.2 / 4.4 pre-cracks and notches) as used by the build kernels.
+struct CrackDev {
+  double p[9];
+  int32_t body;
+  int32_t pad;
+};
+
+// Arguments shared by the step kernels.
+struct StepArgs {
+  int64_t n_pad;
+  const int64_t* slice_ptr;
+  const int32_t* col;
+  uint32_t* bits;
+  const double4* pos;      // x, y, z (0 in 2D), V
+  const int32_t* body;     // nullptr: single body
+  const BodyDev* bp;
+  const double* aA;        // A / m_i
+  const double* mu;        // 1 / m_i
+  double* theta;           // theta_i (Eq 1.6)
+  double2* thm;            // (theta_i / m_i, 1 / m_i) gathered by pass 2
+  double4* vel;            // v (x, y, z, 0)
+  const uint8_t* flag;     // nullptr: all free
+  const double4* bacc;     // body force density b (x, y, z, 0) or nullptr
+  const double4* gvec;     // a x (p - c) per particle (prescribed rotation) or nullptr
+  int64_t* d_step;         // device step counter (index of the step being executed)
+  // mixed path
+  const int4* pos32;       // fixed-point coordinates (x, y, z) and V as float bits in .w
+  float2* thm32;           // (theta_i / m_i, 1 / m_i) in FP32
+  float* mu32;             // 1 / m_i in FP32
+  float* aA32;             // A / m_i * Q in FP32 (Q folded in)
+  float* theta32;          // theta_i in FP32
+  unsigned long long* counters;  // [0] band rechecks, [1] validate mismatches
+  float band_c;            // safety factor of the band
+  int validate;            // mixed: also decide every bond in FP64 and count mismatches
+  int check;               // apply the failure criterion at the head of pass 1
+};
+
+struct KernelTimes {
+  std::vector<cudaEvent_t> ev;  // pairs (start, stop) per launch
+  std::vector<int> which;       // kernel id per pair
+  double ms[PD_K_COUNT] = {0, 0};
+  int64_t launches[PD_K_COUNT] = {0, 0};
+};
+
+}  // namespace pd
+
+struct pd_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int dim = 3;
+  int model = 0;
+  int precision = 0;
+  int64_t n = 0, n_pad = 0, nslices = 0;
+  int32_t nbodies = 1;
+  std::vector<pd_params> prm;
+  std::vector<int64_t> body_off;  // caller-order offsets of the bodies (nbodies + 1)
+  std::vector<double> hx, hy, hz, hvol;   // caller order, host copies
+  std::vector<int64_t> perm;              // internal k -> caller index (k < n)
+  std::vector<int32_t> body_of;           // internal k -> body
+  // device storage
+  double4* pos = nullptr;
+  int32_t* body = nullptr;
+  pd::BodyDev* bp = nullptr;
+  int64_t* slice_ptr = nullptr;
+  int32_t* col = nullptr;
+  uint32_t* bits = nullptr;
+  int32_t* cnt = nullptr;
+  int64_t nentries = 0, nbonds = 0;
+  double* mu = nullptr;
+  double* aA = nullptr;
+  double* dden = nullptr;
+  double* theta = nullptr;
+  double2* thm = nullptr;
+  double4* disp[2] = {nullptr, nullptr};
+  double4* vel = nullptr;
+  uint8_t* flag = nullptr;
+  double4* bacc = nullptr;
+  double4* gvec = nullptr;
+  int64_t* d_step = nullptr;
+  int64_t* perm_dev = nullptr;   // internal -> caller (n)
+  double* scratch = nullptr;     // n_pad * 3 doubles for transfers
+  // mixed path
+  int4* pos32 = nullptr;
+  float4* u32[2] = {nullptr, nullptr};
+  float2* thm32 = nullptr;
+  float* mu32 = nullptr;
+  float* aA32 = nullptr;
+  float* theta32 = nullptr;
+  unsigned long long* counters = nullptr;
+  double q = 0.0;               // fixed-point quantum of the mixed coordinates [m]
+  double qlo[3] = {0, 0, 0};     // origin of the fixed-point coordinates
+  // state
+  int cur = 0;
+  int64_t steps = 0;
+  bool built = false;
+  bool check_pending = false;   // a step ran since the last failure check
+  bool skip_next_check = true;  // first step after set_state / build: no check at its head
+  bool has_flag = false, has_b = false, has_prescribed = false;
+  double rate = 0.0;                      // prescribed rotation rate
+  double bc_point[3] = {0, 0, 0}, bc_dir[3] = {0, 0, 0};
+  // options
+  int graph_chunk = 100;
+  int profile = 0;
+  int validate = 0;
+  int block = 256;
+  int split = 1;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  pd::KernelTimes times;
+  int64_t device_bytes = 0;
+  std::vector<void*> allocs;
+  std::vector<size_t> alloc_bytes;
+  size_t n_create_allocs = 0;  // allocations made at creation; later ones belong to the build
+};
+
+namespace pd {
+// error reporting (thread-local message)
+pd_status fail(pd_status st, const std::string& msg);
+pd_status cuda_fail(cudaError_t e, const char* what);
+void clear_error();
+// device memory owned by the context
+template <class T>
+pd_status alloc(pd_ctx* c, T** p, size_t count);
+void free_all(pd_ctx* c);
+void free_build(pd_ctx* c);
+void material_constants(int model, double E, double nu, double* A, double* K, double* G);
+pd_status upload_body_params(pd_ctx* c);
+pd_status create(pd_ctx** out, int32_t nbodies, const pd_params* prm, const int64_t* offsets,
+                 const double* x, const double* y, const double* z, const double* vol);
+pd_status build_neighbors(pd_ctx* c, const pd_crack* cracks, int32_t ncracks);
+pd_status alloc_state(pd_ctx* c);
+void drop_graphs(pd_ctx* c);
+// launches (pd_step.cu)
+pd_status launch_step(pd_ctx* c, bool check);
+pd_status launch_refresh_check(pd_ctx* c);
+pd_status launch_damage(pd_ctx* c, double* phi_caller);
+pd_status launch_set_step(pd_ctx* c, int64_t value);
+pd_status upload_field(pd_ctx* c, const double* host_soa, double4* dst, int comps);
+pd_status download_field(pd_ctx* c, const double4* src, double* host_soa, int comps);
+pd_status download_scalar(pd_ctx* c, const double* src, double* host);
+pd_status apply_bc_now(pd_ctx* c);
+pd_status sync_shadow(pd_ctx* c);
+pd_status max_abs_u(pd_ctx* c, double* out, int* nonfinite);
+pd_status run_steps(pd_ctx* c, int64_t nsteps);
+pd_status read_profile(pd_ctx* c);
+}  // namespace pd
+
+#define PD_CUDA(call)                                        \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return pd::cuda_fail(e_, #call);  \
+  } while (0)
+
+template <class T>
+pd_status pd::alloc(pd_ctx* c, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return pd::fail(PD_ERR_OOM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed");
+  }
+  c->allocs.push_back(q);
+  c->alloc_bytes.push_back(count * sizeof(T));
+  c->device_bytes += (int64_t)(count * sizeof(T));
+  *p = static_cast<T*>(q);
+  return PD_OK;
+}

@@ -1,0 +1,779 @@
+// Per-time-step kernels of linearized OSB-PD and their launch sequence.
+//
+// One time step = two kernels over the sliced neighbour layout built in pd_build.cu:
+//   pass 1: failure criterion on u^n (Eqs 1.17, 1.30: the paper's failure block after the previous
+//           update), then the dilatation theta_i = (A/m_i) sum_j V_j rho_ij xi.(u_j - u_i)
+//           (Eq 1.6 with x e = xi.(u_j - u_i) for the linearized extension of Eqs 2.4, 2.7);
+//   pass 2: the bond forces of Eq 2.2 summed over the family,
+//           F_i / V_i = sum_j rho_ij V_j [ (K - G/3)(theta_i/m_i + theta_j/m_j)
+//                                         + G (1/m_i + 1/m_j) xi.(u_j - u_i) / |xi|^2 ] xi,
+//           followed by the explicit update of Eq 2.11 and the boundary conditions (Appendix B).
+// Both passes gather: every directed bond is visited from its own particle, so no atomics are
+// needed and every sum runs in a fixed order.  A warp owns one 32-particle slice (one particle
+// per lane); with SPLIT > 1 several warps share a slice, each taking every SPLIT-th slot, and
+// their partial sums are combined in shared memory in a fixed order.
+//
+// The break test is evaluated without square roots: s = e/|xi| >= s0  <=>  xi.du >= s0 |xi|^2.
+#include <algorithm>
+#include <cmath>
+
+#include "pd_internal.h"
+
+namespace pd {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+struct SliceIdx {
+  int64_t i;
+  int64_t base;
+  int W;
+  int lane;
+  int sub;
+  bool active;
+};
+
+template <int SPLIT>
+__device__ __forceinline__ SliceIdx slice_index(int64_t n_pad, const int64_t* __restrict__ slice_ptr) {
+  SliceIdx r;
+  const int64_t gwarp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  r.lane = threadIdx.x & 31;
+  r.sub = (int)(gwarp % SPLIT);
+  const int64_t s = gwarp / SPLIT;
+  r.i = s * 32 + r.lane;
+  r.active = r.i < n_pad;  // n_pad is a multiple of 32: uniform over the warp
+  r.base = 0;
+  r.W = 0;
+  if (r.active) {
+    r.base = slice_ptr[s];
+    r.W = (int)((slice_ptr[s + 1] - r.base) >> 5);
+  }
+  return r;
+}
+
+// Partial sums of the SPLIT warps sharing a slice, combined by the first warp (fixed order).
+template <int SPLIT, int NC, class T>
+__device__ __forceinline__ void split_reduce(T (&v)[NC]) {
+  if (SPLIT == 1) return;
+  extern __shared__ unsigned char smem_raw[];
+  T* red = reinterpret_cast<T*>(smem_raw);
+#pragma unroll
+  for (int c = 0; c < NC; ++c) red[c * blockDim.x + threadIdx.x] = v[c];
+  __syncthreads();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (w % SPLIT == 0) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      T s = red[c * blockDim.x + w * 32 + lane];
+#pragma unroll
+      for (int q = 1; q < SPLIT; ++q) s += red[c * blockDim.x + (w + q) * 32 + lane];
+      v[c] = s;
+    }
+  }
+}
+
+// xi = x_j - x_i, du = u_j - u_i, d = xi . du, q = xi . xi in FP64.  Shared by the FP64 path and by
+// the FP64 re-decision of the mixed path, so both decide a bond with identical arithmetic.
+template <int DIM>
+__device__ __forceinline__ void bond_f64(const double4& pi, const double4& pj, const double4& ui,
+                                         const double4& uj, double& ex, double& ey, double& ez,
+                                         double& d, double& q) {
+  ex = pj.x - pi.x;
+  ey = pj.y - pi.y;
+  const double dx = uj.x - ui.x, dy = uj.y - ui.y;
+  d = ex * dx + ey * dy;
+  q = ex * ex + ey * ey;
+  if (DIM == 3) {
+    ez = pj.z - pi.z;
+    const double dz = uj.z - ui.z;
+    d = fma(ez, dz, d);
+    q = fma(ez, ez, q);
+  } else {
+    ez = 0.0;
+  }
+}
+
+template <int DIM>
+__device__ __forceinline__ bool fp64_breaks(const StepArgs& a, int64_t i, int32_t j,
+                                            const double4* __restrict__ disp, double s0) {
+  double ex, ey, ez, d, q;
+  bond_f64<DIM>(a.pos[i], a.pos[j], disp[i], disp[j], ex, ey, ez, d, q);
+  return d >= s0 * q;
+}
+
+// Explicit update (Eq 2.11) with the diagonal mass rho V_i (Eqs 2.1, 2.12) and the boundary
+// conditions at t_{n+1}; f = F_i / V_i.
+__device__ __forceinline__ void update(const StepArgs& a, int64_t i, int b, const double f[3],
+                                       const double4* __restrict__ disp, double4* __restrict__ disp_out,
+                                       double4& u) {
+  const BodyDev& bp = a.bp[b];
+  const uint8_t fl = a.flag ? a.flag[i] : (uint8_t)0;
+  u = disp[i];
+  double4 v = a.vel[i];
+  if (fl == 0) {
+    const double4 bb = a.bacc ? a.bacc[i] : make_double4(0.0, 0.0, 0.0, 0.0);
+    v.x = v.x + bp.dt * ((f[0] + bb.x) * bp.inv_rho);
+    v.y = v.y + bp.dt * ((f[1] + bb.y) * bp.inv_rho);
+    v.z = v.z + bp.dt * ((f[2] + bb.z) * bp.inv_rho);
+    u.x = u.x + bp.dt * v.x;
+    u.y = u.y + bp.dt * v.y;
+    u.z = u.z + bp.dt * v.z;
+  } else if (fl == 1) {
+    u = make_double4(0.0, 0.0, 0.0, 0.0);
+    v = u;
+  } else {
+    const double t1 = (double)(*a.d_step + 1) * bp.dt;
+    const double4 g = a.gvec[i];
+    const double rt = bp.rate * t1;
+    u = make_double4(rt * g.x, rt * g.y, rt * g.z, 0.0);
+    v = make_double4(bp.rate * g.x, bp.rate * g.y, bp.rate * g.z, 0.0);
+  }
+  disp_out[i] = u;
+  a.vel[i] = v;
+}
+
+// Slot batches: each thread handles U slots per iteration; the neighbour indices and status words
+// of the next batch are loaded while the current batch's gathers are in flight, so that several
+// dependent index -> gather chains overlap.
+template <int U, int SPLIT>
+__device__ __forceinline__ void load_slots(const SliceIdx& t, const int32_t* __restrict__ cl,
+                                           const uint32_t* __restrict__ bw, int k0, int32_t (&j)[U],
+                                           uint32_t (&wd)[U]) {
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int k = k0 + u * SPLIT;
+    const bool ok = k < t.W;
+    j[u] = ok ? cl[(int64_t)k << 5] : (int32_t)t.i;  // past the row: the particle itself, status 0
+    wd[u] = ok ? bw[k] : 0u;
+  }
+}
+
+// ------------------------------------------------------------------------------------ FP64 path
+constexpr int kU64 = 2;
+constexpr int kU32 = 4;
+
+template <int DIM, int SPLIT>
+__global__ void __launch_bounds__(512) k_pass1_f64(StepArgs a, const double4* __restrict__ disp,
+                                                    int write_theta) {
+  const SliceIdx t = slice_index<SPLIT>(a.n_pad, a.slice_ptr);
+  if (write_theta && blockIdx.x == 0 && threadIdx.x == 0) *a.d_step += 1;
+  double acc[1] = {0.0};
+  int b = 0;
+  if (t.active) {
+    b = a.body ? a.body[t.i] : 0;
+    const double s0 = a.bp[b].s0;
+    const bool can_break = s0 > 0.0;
+    const double4 pi = a.pos[t.i], ui = disp[t.i];
+    uint32_t* __restrict__ bw = a.bits + (t.base >> 5);
+    const int32_t* __restrict__ cl = a.col + t.base + t.lane;
+    constexpr int U = kU64;
+    int32_t jn[U];
+    uint32_t wn[U];
+    load_slots<U, SPLIT>(t, cl, bw, t.sub, jn, wn);
+    for (int k0 = t.sub; k0 < t.W; k0 += U * SPLIT) {
+      int32_t j[U];
+      uint32_t wd[U];
+      double4 pj[U], uj[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        j[u] = jn[u];
+        wd[u] = wn[u];
+        pj[u] = a.pos[j[u]];
+        uj[u] = disp[j[u]];
+      }
+      load_slots<U, SPLIT>(t, cl, bw, k0 + U * SPLIT, jn, wn);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        double ex, ey, ez, d, q;
+        bond_f64<DIM>(pi, pj[u], ui, uj[u], ex, ey, ez, d, q);
+        bool intact = (wd[u] >> t.lane) & 1u;
+        if (a.check) {
+          const bool brk = intact && can_break && d >= s0 * q;
+          const unsigned m = __ballot_sync(kFull, brk);
+          if (m) {
+            intact = intact && !brk;
+            if (t.lane == 0) bw[k0 + u * SPLIT] = wd[u] & ~m;
+          }
+        }
+        acc[0] += intact ? pj[u].w * d : 0.0;
+      }
+    }
+  }
+  split_reduce<SPLIT, 1>(acc);
+  if (t.active && t.sub == 0 && write_theta) {
+    const double th = a.aA[t.i] * acc[0];
+    const double mu = a.mu[t.i];
+    a.theta[t.i] = th;
+    // gathered by pass 2: (K - G/3) theta_i / m_i and G / m_i
+    a.thm[t.i] = make_double2(a.bp[b].Kp * (th * mu), a.bp[b].G * mu);
+  }
+}
+
+template <int DIM, int SPLIT>
+__global__ void __launch_bounds__(512) k_pass2_f64(StepArgs a, const double4* __restrict__ disp,
+                                                    double4* __restrict__ disp_out) {
+  const SliceIdx t = slice_index<SPLIT>(a.n_pad, a.slice_ptr);
+  double f[3] = {0.0, 0.0, 0.0};
+  int b = 0;
+  if (t.active) {
+    b = a.body ? a.body[t.i] : 0;
+    const double4 pi = a.pos[t.i], ui = disp[t.i];
+    const double2 ti = a.thm[t.i];
+    const uint32_t* __restrict__ bw = a.bits + (t.base >> 5);
+    const int32_t* __restrict__ cl = a.col + t.base + t.lane;
+    constexpr int U = kU64;
+    int32_t jn[U];
+    uint32_t wn[U];
+    load_slots<U, SPLIT>(t, cl, bw, t.sub, jn, wn);
+    for (int k0 = t.sub; k0 < t.W; k0 += U * SPLIT) {
+      uint32_t wd[U];
+      double4 pj[U], uj[U];
+      double2 tj[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        wd[u] = wn[u];
+        pj[u] = a.pos[jn[u]];
+        uj[u] = disp[jn[u]];
+        tj[u] = a.thm[jn[u]];
+      }
+      load_slots<U, SPLIT>(t, cl, bw, k0 + U * SPLIT, jn, wn);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        double ex, ey, ez, d, q;
+        bond_f64<DIM>(pi, pj[u], ui, uj[u], ex, ey, ez, d, q);
+        // Eq 2.2: [(K - G/3)(theta_i/m_i + theta_j/m_j) + G (1/m_i + 1/m_j) xi.du / |xi|^2] V_j xi
+        double c = fma(ti.y + tj[u].y, d / q, ti.x + tj[u].x);
+        c = ((wd[u] >> t.lane) & 1u) ? c * pj[u].w : 0.0;
+        f[0] = fma(c, ex, f[0]);
+        f[1] = fma(c, ey, f[1]);
+        if (DIM == 3) f[2] = fma(c, ez, f[2]);
+      }
+    }
+  }
+  split_reduce<SPLIT, 3>(f);
+  if (t.active && t.sub == 0) {
+    double4 u;
+    update(a, t.i, b, f, disp, disp_out, u);
+  }
+}
+
+// ----------------------------------------------------------------------------------- mixed path
+// FP32 bond arithmetic on fixed-point coordinates (xi exact as an integer multiple of the quantum Q,
+// then rounded once to FP32) and an FP32 shadow copy of u.  The band half-width B bounds
+// |g32 - g| for g = xi.du - s0 |xi|^2 (in Q units) from the FP32 representation of u, the rounding
+// of xi, du, the dot products and the final FMA; outside the band the FP32 sign equals the FP64
+// decision, inside it the bond is re-decided in FP64 from the FP64 master state.
+template <int DIM, int SPLIT>
+__global__ void __launch_bounds__(512) k_pass1_mixed(StepArgs a, const float4* __restrict__ u32,
+                                                      const double4* __restrict__ disp, int write_theta) {
+  const SliceIdx t = slice_index<SPLIT>(a.n_pad, a.slice_ptr);
+  if (write_theta && blockIdx.x == 0 && threadIdx.x == 0) *a.d_step += 1;
+  float acc[1] = {0.0f};
+  int b = 0;
+  if (t.active) {
+    b = a.body ? a.body[t.i] : 0;
+    const double s0 = a.bp[b].s0;
+    const float sig = a.bp[b].sigma32;
+    const bool can_break = s0 > 0.0;
+    const int4 Pi = a.pos32[t.i];
+    const float4 Ui = u32[t.i];
+    const float ui1 = fabsf(Ui.x) + fabsf(Ui.y) + (DIM == 3 ? fabsf(Ui.z) : 0.0f);
+    uint32_t* __restrict__ bw = a.bits + (t.base >> 5);
+    const int32_t* __restrict__ cl = a.col + t.base + t.lane;
+    constexpr int U = kU32;
+    int32_t jn[U];
+    uint32_t wn[U];
+    load_slots<U, SPLIT>(t, cl, bw, t.sub, jn, wn);
+    for (int k0 = t.sub; k0 < t.W; k0 += U * SPLIT) {
+      int32_t j[U];
+      uint32_t wd[U];
+      int4 Pj[U];
+      float4 Uj[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        j[u] = jn[u];
+        wd[u] = wn[u];
+        Pj[u] = a.pos32[j[u]];
+        Uj[u] = u32[j[u]];
+      }
+      load_slots<U, SPLIT>(t, cl, bw, k0 + U * SPLIT, jn, wn);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const float ex = (float)(Pj[u].x - Pi.x), ey = (float)(Pj[u].y - Pi.y);
+        const float ez = DIM == 3 ? (float)(Pj[u].z - Pi.z) : 0.0f;
+        const float dx = Uj[u].x - Ui.x, dy = Uj[u].y - Ui.y, dz = DIM == 3 ? Uj[u].z - Ui.z : 0.0f;
+        float d = ex * dx + ey * dy;
+        if (DIM == 3) d = fmaf(ez, dz, d);
+        bool intact = (wd[u] >> t.lane) & 1u;
+        if (a.check) {
+          bool brk = false;
+          if (intact && can_break) {
+            float q = ex * ex + ey * ey;
+            if (DIM == 3) q = fmaf(ez, ez, q);
+            const float g = fmaf(-sig, q, d);
+            const float xi1 = fabsf(ex) + fabsf(ey) + fabsf(ez);
+            const float du1 = fabsf(dx) + fabsf(dy) + fabsf(dz);
+            const float B = a.band_c * (1.01f * du1 + sig * (2.01f * xi1 + 3.02f) +
+                                        5.9604645e-8f * (xi1 * (2.0f * ui1 + 6.0f * du1) + 6.0f * sig * q +
+                                                         fabsf(g)));
+            if (fabsf(g) > B) {
+              brk = g >= 0.0f;
+            } else {
+              brk = fp64_breaks<DIM>(a, t.i, j[u], disp, s0);
+              atomicAdd(&a.counters[0], 1ull);
+            }
+            if (a.validate && brk != fp64_breaks<DIM>(a, t.i, j[u], disp, s0)) atomicAdd(&a.counters[1], 1ull);
+          }
+          const unsigned m = __ballot_sync(kFull, brk);
+          if (m) {
+            intact = intact && !brk;
+            if (t.lane == 0) bw[k0 + u * SPLIT] = wd[u] & ~m;
+          }
+        }
+        acc[0] += intact ? __int_as_float(Pj[u].w) * d : 0.0f;
+      }
+    }
+  }
+  split_reduce<SPLIT, 1>(acc);
+  if (t.active && t.sub == 0 && write_theta) {
+    const float th = a.aA32[t.i] * acc[0];
+    const float mu = a.mu32[t.i];
+    a.theta32[t.i] = th;
+    // gathered by pass 2: (K - G/3) Q theta_i / m_i and G / m_i (Q folded into the first)
+    a.thm32[t.i] = make_float2(a.bp[b].Kp32 * (th * mu), a.bp[b].G32 * mu);
+  }
+}
+
+template <int DIM, int SPLIT>
+__global__ void __launch_bounds__(512) k_pass2_mixed(StepArgs a, const float4* __restrict__ u32,
+                                                      float4* __restrict__ u32_out,
+                                                      const double4* __restrict__ disp,
+                                                      double4* __restrict__ disp_out) {
+  const SliceIdx t = slice_index<SPLIT>(a.n_pad, a.slice_ptr);
+  float f[3] = {0.0f, 0.0f, 0.0f};
+  int b = 0;
+  if (t.active) {
+    b = a.body ? a.body[t.i] : 0;
+    const int4 Pi = a.pos32[t.i];
+    const float4 Ui = u32[t.i];
+    const float2 ti = a.thm32[t.i];
+    const uint32_t* __restrict__ bw = a.bits + (t.base >> 5);
+    const int32_t* __restrict__ cl = a.col + t.base + t.lane;
+    constexpr int U = kU32;
+    int32_t jn[U];
+    uint32_t wn[U];
+    load_slots<U, SPLIT>(t, cl, bw, t.sub, jn, wn);
+    for (int k0 = t.sub; k0 < t.W; k0 += U * SPLIT) {
+      uint32_t wd[U];
+      int4 Pj[U];
+      float4 Uj[U];
+      float2 tj[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        wd[u] = wn[u];
+        Pj[u] = a.pos32[jn[u]];
+        Uj[u] = u32[jn[u]];
+        tj[u] = a.thm32[jn[u]];
+      }
+      load_slots<U, SPLIT>(t, cl, bw, k0 + U * SPLIT, jn, wn);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const float ex = (float)(Pj[u].x - Pi.x), ey = (float)(Pj[u].y - Pi.y);
+        const float ez = DIM == 3 ? (float)(Pj[u].z - Pi.z) : 0.0f;
+        float d = ex * (Uj[u].x - Ui.x) + ey * (Uj[u].y - Ui.y);
+        float q = ex * ex + ey * ey;
+        if (DIM == 3) {
+          d = fmaf(ez, Uj[u].z - Ui.z, d);
+          q = fmaf(ez, ez, q);
+        }
+        float c = fmaf(ti.y + tj[u].y, d * __frcp_rn(q), ti.x + tj[u].x);
+        c = ((wd[u] >> t.lane) & 1u) ? c * __int_as_float(Pj[u].w) : 0.0f;
+        f[0] = fmaf(c, ex, f[0]);
+        f[1] = fmaf(c, ey, f[1]);
+        if (DIM == 3) f[2] = fmaf(c, ez, f[2]);
+      }
+    }
+  }
+  split_reduce<SPLIT, 3>(f);
+  if (t.active && t.sub == 0) {
+    const double fd[3] = {(double)f[0], (double)f[1], (double)f[2]};
+    double4 u;
+    update(a, t.i, b, fd, disp, disp_out, u);
+    u32_out[t.i] = make_float4((float)u.x, (float)u.y, (float)u.z, 0.0f);
+  }
+}
+
+// ----------------------------------------------------------------------------- auxiliary kernels
+__global__ void k_set_step(int64_t* d_step, int64_t v) { *d_step = v; }
+
+// phi_i of Eq 1.31 (w = 1), written in caller order.
+__global__ void k_damage(StepArgs a, int64_t n, const double* __restrict__ dden,
+                         const int64_t* __restrict__ perm, double* __restrict__ out) {
+  const SliceIdx t = slice_index<1>(a.n_pad, a.slice_ptr);
+  if (!t.active) return;
+  double num = 0.0;
+  for (int k = 0; k < t.W; ++k) {
+    const uint32_t word = a.bits[(t.base >> 5) + k];
+    if ((word >> t.lane) & 1u) num += a.pos[a.col[t.base + t.lane + ((int64_t)k << 5)]].w;
+  }
+  if (t.i < n) out[perm[t.i]] = dden[t.i] > 0.0 ? 1.0 - num / dden[t.i] : 0.0;
+}
+
+__global__ void k_gather_soa(int64_t n, int64_t n_pad, int comps, const double* __restrict__ src,
+                             const int64_t* __restrict__ perm, double4* __restrict__ dst) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= n_pad) return;
+  if (k >= n) {
+    dst[k] = make_double4(0.0, 0.0, 0.0, 0.0);
+    return;
+  }
+  const int64_t u = perm[k];
+  dst[k] = make_double4(src[u], src[n + u], comps == 3 ? src[2 * n + u] : 0.0, 0.0);
+}
+
+__global__ void k_scatter_soa(int64_t n, int comps, const double4* __restrict__ src,
+                              const int64_t* __restrict__ perm, double* __restrict__ dst) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const int64_t u = perm[k];
+  const double4 v = src[k];
+  dst[u] = v.x;
+  dst[n + u] = v.y;
+  if (comps == 3) dst[2 * n + u] = v.z;
+}
+
+__global__ void k_scatter_scalar(int64_t n, const double* __restrict__ src, const float* __restrict__ src32,
+                                 const int64_t* __restrict__ perm, double* __restrict__ dst) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  dst[perm[k]] = src ? src[k] : (double)src32[k];
+}
+
+// Boundary values at the current time for the constrained particles (fixed / prescribed).
+__global__ void k_apply_bc(StepArgs a, double4* __restrict__ disp, int64_t step) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= a.n_pad || !a.flag) return;
+  const uint8_t fl = a.flag[i];
+  if (fl == 0) return;
+  if (fl == 1) {
+    disp[i] = make_double4(0.0, 0.0, 0.0, 0.0);
+    a.vel[i] = disp[i];
+    return;
+  }
+  const BodyDev& bp = a.bp[a.body ? a.body[i] : 0];
+  const double tn = (double)step * bp.dt;
+  const double4 g = a.gvec[i];
+  const double rt = bp.rate * tn;
+  disp[i] = make_double4(rt * g.x, rt * g.y, rt * g.z, 0.0);
+  a.vel[i] = make_double4(bp.rate * g.x, bp.rate * g.y, bp.rate * g.z, 0.0);
+}
+
+__global__ void k_shadow(int64_t n_pad, const double4* __restrict__ disp, float4* __restrict__ u32) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n_pad) return;
+  const double4 u = disp[i];
+  u32[i] = make_float4((float)u.x, (float)u.y, (float)u.z, 0.0f);
+}
+
+// max |u_k| over all particles and components (order-independent: max of non-negative doubles as
+// integers), plus a count of non-finite components.
+__global__ void k_max_abs(int64_t n, const double4* __restrict__ disp, unsigned long long* out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double m = 0.0;
+  unsigned bad = 0;
+  if (i < n) {
+    const double4 u = disp[i];
+    const double c[3] = {u.x, u.y, u.z};
+    for (int k = 0; k < 3; ++k) {
+      if (!isfinite(c[k])) bad = 1;
+      else m = fmax(m, fabs(c[k]));
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    m = fmax(m, __shfl_down_sync(kFull, m, o));
+    bad |= __shfl_down_sync(kFull, bad, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&out[0], (unsigned long long)__double_as_longlong(m));
+    if (bad) atomicAdd(&out[1], 1ull);
+  }
+}
+
+// ------------------------------------------------------------------------------ host dispatch
+StepArgs make_args(pd_ctx* c) {
+  StepArgs a{};
+  a.n_pad = c->n_pad;
+  a.slice_ptr = c->slice_ptr;
+  a.col = c->col;
+  a.bits = c->bits;
+  a.pos = c->pos;
+  a.body = c->nbodies > 1 ? c->body : nullptr;
+  a.bp = c->bp;
+  a.aA = c->aA;
+  a.mu = c->mu;
+  a.theta = c->theta;
+  a.thm = c->thm;
+  a.vel = c->vel;
+  a.flag = c->has_flag ? c->flag : nullptr;
+  a.bacc = c->has_b ? c->bacc : nullptr;
+  a.gvec = c->gvec;
+  a.d_step = c->d_step;
+  a.pos32 = c->pos32;
+  a.thm32 = c->thm32;
+  a.mu32 = c->mu32;
+  a.aA32 = c->aA32;
+  a.theta32 = c->theta32;
+  a.counters = c->counters;
+  double bc = 4.0;
+  if (c->prm[0].band_safety > 0) bc = c->prm[0].band_safety;
+  a.band_c = (float)bc;
+  a.validate = c->validate;
+  a.check = 1;
+  return a;
+}
+
+template <int DIM, int SPLIT>
+void launch_pass1(pd_ctx* c, const StepArgs& a, int write_theta, unsigned grid, int block, size_t sm) {
+  if (c->precision == PD_FP64)
+    k_pass1_f64<DIM, SPLIT><<<grid, block, sm, c->stream>>>(a, c->disp[c->cur], write_theta);
+  else
+    k_pass1_mixed<DIM, SPLIT><<<grid, block, sm, c->stream>>>(a, c->u32[c->cur], c->disp[c->cur], write_theta);
+}
+
+template <int DIM, int SPLIT>
+void launch_pass2(pd_ctx* c, const StepArgs& a, unsigned grid, int block, size_t sm) {
+  if (c->precision == PD_FP64)
+    k_pass2_f64<DIM, SPLIT><<<grid, block, sm, c->stream>>>(a, c->disp[c->cur], c->disp[c->cur ^ 1]);
+  else
+    k_pass2_mixed<DIM, SPLIT>
+        <<<grid, block, sm, c->stream>>>(a, c->u32[c->cur], c->u32[c->cur ^ 1], c->disp[c->cur], c->disp[c->cur ^ 1]);
+}
+
+template <int DIM>
+void dispatch_pass(pd_ctx* c, const StepArgs& a, int pass, int write_theta) {
+  const int block = c->block;
+  const int split = c->split;
+  const int64_t threads = c->nslices * 32 * (int64_t)split;
+  const unsigned grid = (unsigned)((threads + block - 1) / block);
+  const size_t sm = split > 1 ? (size_t)block * 3 * sizeof(double) : 0;
+  if (pass == 1) {
+    if (split == 1) launch_pass1<DIM, 1>(c, a, write_theta, grid, block, sm);
+    else if (split == 2) launch_pass1<DIM, 2>(c, a, write_theta, grid, block, sm);
+    else launch_pass1<DIM, 4>(c, a, write_theta, grid, block, sm);
+  } else {
+    if (split == 1) launch_pass2<DIM, 1>(c, a, grid, block, sm);
+    else if (split == 2) launch_pass2<DIM, 2>(c, a, grid, block, sm);
+    else launch_pass2<DIM, 4>(c, a, grid, block, sm);
+  }
+}
+
+void dispatch(pd_ctx* c, const StepArgs& a, int pass, int write_theta) {
+  if (c->dim == 3) dispatch_pass<3>(c, a, pass, write_theta);
+  else dispatch_pass<2>(c, a, pass, write_theta);
+}
+
+cudaEvent_t take_event(pd_ctx* c) {
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+}  // namespace
+
+pd_status launch_set_step(pd_ctx* c, int64_t value) {
+  k_set_step<<<1, 1, 0, c->stream>>>(c->d_step, value);
+  PD_CUDA(cudaGetLastError());
+  return PD_OK;
+}
+
+// One full time step (pass 1 + pass 2); flips the double buffers.
+pd_status launch_step(pd_ctx* c, bool check) {
+  StepArgs a = make_args(c);
+  a.check = check ? 1 : 0;
+  const bool prof = c->profile != 0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+  if (prof) {
+    e0 = take_event(c);
+    e1 = take_event(c);
+    e2 = take_event(c);
+    cudaEventRecord(e0, c->stream);
+  }
+  dispatch(c, a, 1, 1);
+  if (prof) cudaEventRecord(e1, c->stream);
+  dispatch(c, a, 2, 1);
+  if (prof) {
+    cudaEventRecord(e2, c->stream);
+    c->times.ev.push_back(e0);
+    c->times.ev.push_back(e1);
+    c->times.which.push_back(PD_K_PASS1);
+    c->times.ev.push_back(e1);
+    c->times.ev.push_back(e2);
+    c->times.which.push_back(PD_K_PASS2);
+  }
+  c->cur ^= 1;
+  PD_CUDA(cudaGetLastError());
+  return PD_OK;
+}
+
+pd_status read_profile(pd_ctx* c) {
+  if (c->times.which.empty()) return PD_OK;
+  PD_CUDA(cudaStreamSynchronize(c->stream));
+  for (size_t k = 0; k < c->times.which.size(); ++k) {
+    float ms = 0.0f;
+    PD_CUDA(cudaEventElapsedTime(&ms, c->times.ev[2 * k], c->times.ev[2 * k + 1]));
+    c->times.ms[c->times.which[k]] += ms;
+    c->times.launches[c->times.which[k]] += 1;
+  }
+  // events are shared between consecutive pairs: destroy each distinct handle once
+  std::vector<cudaEvent_t> uniq(c->times.ev.begin(), c->times.ev.end());
+  std::sort(uniq.begin(), uniq.end());
+  uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
+  for (cudaEvent_t e : uniq) cudaEventDestroy(e);
+  c->times.ev.clear();
+  c->times.which.clear();
+  return PD_OK;
+}
+
+// The failure criterion on the current state, without advancing (used before reading damage,
+// status or state, so that they equal the paper's end-of-iteration failure block).
+pd_status launch_refresh_check(pd_ctx* c) {
+  if (!c->check_pending) return PD_OK;
+  StepArgs a = make_args(c);
+  a.check = 1;
+  dispatch(c, a, 1, 0);
+  PD_CUDA(cudaGetLastError());
+  c->check_pending = false;
+  c->skip_next_check = true;  // the next step must not apply the same check again
+  return PD_OK;
+}
+
+pd_status launch_damage(pd_ctx* c, double* phi_caller_dev) {
+  StepArgs a = make_args(c);
+  const int tb = 256;
+  k_damage<<<(unsigned)((c->n_pad + tb - 1) / tb), tb, 0, c->stream>>>(a, c->n, c->dden, c->perm_dev,
+                                                                      phi_caller_dev);
+  PD_CUDA(cudaGetLastError());
+  return PD_OK;
+}
+
+pd_status upload_field(pd_ctx* c, const double* host_soa, double4* dst, int comps) {
+  const int64_t n = c->n;
+  PD_CUDA(cudaMemcpyAsync(c->scratch, host_soa, sizeof(double) * comps * n, cudaMemcpyHostToDevice, c->stream));
+  const int tb = 256;
+  k_gather_soa<<<(unsigned)((c->n_pad + tb - 1) / tb), tb, 0, c->stream>>>(n, c->n_pad, comps, c->scratch,
+                                                                          c->perm_dev, dst);
+  PD_CUDA(cudaGetLastError());
+  return PD_OK;
+}
+
+pd_status download_field(pd_ctx* c, const double4* src, double* host_soa, int comps) {
+  const int64_t n = c->n;
+  const int tb = 256;
+  k_scatter_soa<<<(unsigned)((n + tb - 1) / tb), tb, 0, c->stream>>>(n, comps, src, c->perm_dev, c->scratch);
+  PD_CUDA(cudaGetLastError());
+  PD_CUDA(cudaMemcpyAsync(host_soa, c->scratch, sizeof(double) * comps * n, cudaMemcpyDeviceToHost, c->stream));
+  return PD_OK;
+}
+
+pd_status download_scalar(pd_ctx* c, const double* src, double* host) {
+  const int64_t n = c->n;
+  const int tb = 256;
+  const bool mixed = c->precision == PD_MIXED && src == c->theta;
+  k_scatter_scalar<<<(unsigned)((n + tb - 1) / tb), tb, 0, c->stream>>>(
+      n, mixed ? nullptr : src, mixed ? c->theta32 : nullptr, c->perm_dev, c->scratch);
+  PD_CUDA(cudaGetLastError());
+  PD_CUDA(cudaMemcpyAsync(host, c->scratch, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+  return PD_OK;
+}
+
+pd_status apply_bc_now(pd_ctx* c) {
+  if (!c->has_flag) return PD_OK;
+  StepArgs a = make_args(c);
+  const int tb = 256;
+  k_apply_bc<<<(unsigned)((c->n_pad + tb - 1) / tb), tb, 0, c->stream>>>(a, c->disp[c->cur], c->steps);
+  PD_CUDA(cudaGetLastError());
+  return PD_OK;
+}
+
+pd_status sync_shadow(pd_ctx* c) {
+  if (c->precision != PD_MIXED) return PD_OK;
+  const int tb = 256;
+  k_shadow<<<(unsigned)((c->n_pad + tb - 1) / tb), tb, 0, c->stream>>>(c->n_pad, c->disp[c->cur], c->u32[c->cur]);
+  PD_CUDA(cudaGetLastError());
+  return PD_OK;
+}
+
+pd_status max_abs_u(pd_ctx* c, double* out, int* nonfinite) {
+  unsigned long long* acc = c->counters + 2;
+  PD_CUDA(cudaMemsetAsync(acc, 0, 2 * sizeof(unsigned long long), c->stream));
+  const int tb = 256;
+  k_max_abs<<<(unsigned)((c->n + tb - 1) / tb), tb, 0, c->stream>>>(c->n, c->disp[c->cur], acc);
+  PD_CUDA(cudaGetLastError());
+  unsigned long long h[2];
+  PD_CUDA(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  PD_CUDA(cudaStreamSynchronize(c->stream));
+  double m;
+  memcpy(&m, &h[0], sizeof(double));
+  *out = m;
+  *nonfinite = (int)h[1];
+  return PD_OK;
+}
+
+// nsteps time steps: the first step after a state change skips the failure check at its head (the
+// paper checks after each update, never before the first force evaluation); then CUDA-graph
+// chunks of graph_chunk steps, then single steps.
+pd_status run_steps(pd_ctx* c, int64_t nsteps) {
+  if (nsteps <= 0) return PD_OK;
+  pd_status st = launch_set_step(c, c->steps - 1);
+  if (st != PD_OK) return st;
+  int64_t left = nsteps;
+  if (c->skip_next_check) {
+    st = launch_step(c, false);
+    if (st != PD_OK) return st;
+    c->skip_next_check = false;
+    --left;
+    c->steps += 1;
+  }
+  const int chunk = c->graph_chunk;
+  while (left > 0) {
+    if (chunk > 0 && !c->profile && left >= chunk) {
+      cudaGraphExec_t& ge = c->graph[c->cur];
+      const int cur0 = c->cur;
+      if (!ge) {
+        cudaGraph_t g = nullptr;
+        PD_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        for (int s = 0; s < chunk; ++s) {
+          st = launch_step(c, true);
+          if (st != PD_OK) {
+            cudaStreamEndCapture(c->stream, &g);
+            if (g) cudaGraphDestroy(g);
+            c->cur = cur0;
+            return st;
+          }
+        }
+        PD_CUDA(cudaStreamEndCapture(c->stream, &g));
+        cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+          ge = nullptr;
+          c->cur = cur0;
+          return cuda_fail(e, "cudaGraphInstantiate");
+        }
+        c->cur = cur0;
+      }
+      PD_CUDA(cudaGraphLaunch(ge, c->stream));
+      if (chunk & 1) c->cur ^= 1;
+      left -= chunk;
+      c->steps += chunk;
+    } else {
+      st = launch_step(c, true);
+      if (st != PD_OK) return st;
+      --left;
+      c->steps += 1;
+    }
+  }
+  c->check_pending = true;
+  return PD_OK;
+}
+
+}  // namespace pd

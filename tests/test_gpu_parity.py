@@ -1,0 +1,315 @@
+"""CUDA path vs the CPU oracle, element by element, on seeded synthetic workloads (GPU only).
+
+Tolerances: FP64 path rel-L2 of u and v <= 1e-12 at every checkpoint; theta within 1e-12 of the
+magnitude of the terms of its sum (see theta_error); bond status (and so damage) exactly equal while
+the oracle's minimum relative stretch margin stays above 1e-9.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2309_11273_gb300 import PD_FP64, PD_MIXED, BatchSimulation, Simulation
+from paper_2309_11273_gb300 import _binding as B
+from paper_2309_11273_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def s0_of(w):
+    return O.critical_stretch(w.model, w.E, w.nu, w.Gc, w.delta) if w.Gc else 0.0
+
+
+def theta_error(th, ref):
+    """L2 error of theta relative to the L2 size of the terms it sums.  theta_i is a cancelling sum
+    (Eq 1.6), so two correct evaluations agree to eps * S_i with S_i = (A/m_i) sum_j V_j |xi.du|, not to
+    eps |theta_i|; S is evaluated at the current displacement (same size as the one theta came from)."""
+    P = np.stack([ref.x, ref.y] + ([ref.z] if ref.dim == 3 else []))
+    rows = np.repeat(np.arange(ref.n), np.diff(ref.row_ptr))
+    xi = P[:, ref.col] - P[:, rows]
+    du = ref.u[:, ref.col] - ref.u[:, rows]
+    t = np.abs((xi * du).sum(0)) * ref.vol[ref.col]
+    S = ref.A * np.bincount(rows, weights=t, minlength=ref.n) / np.where(ref.m > 0, ref.m, np.inf)
+    return float(np.linalg.norm(th - ref.theta) / max(np.linalg.norm(S), 1e-300))
+
+
+def oracle_for(w, s0, rate=None):
+    ref = O.OracleSim(w.model, w.E, w.nu, w.rho, w.delta, s0, w.dt, w.x, w.y, w.z, w.vol, w.cracks)
+    ref.set_bc(w.flag, w.b, w.axis_point, w.axis_dir, w.rotation_rate(s0) if rate is None else rate)
+    ref.set_state(w.initial_u(), w.initial_v())
+    return ref
+
+
+def run_pair(w, nsteps, every, precision=PD_FP64, rate=None, **kw):
+    """Advance GPU and oracle side by side; returns per-checkpoint comparisons."""
+    s0 = s0_of(w)
+    sim = Simulation(w, s0=s0, precision=precision, rate=rate, **kw)
+    ref = oracle_for(w, s0, rate)
+    exact_status = True
+    out = []
+    done = 0
+    while done < nsteps:
+        k = min(every, nsteps - done)
+        margins, broken = ref.step(k)
+        sim.step(k)
+        done += k
+        if margins.size and margins.min() <= 1e-9:
+            exact_status = False
+        u, v, th = sim.state()
+        rp, col, intact = sim.neighbors()
+        out.append(dict(step=done, ru=rel(u, ref.u), rv=rel(v, ref.v), rt=theta_error(th, ref),
+                        status_equal=np.array_equal(intact, ref.status), exact=exact_status,
+                        broken=int((ref.status == 0).sum()), u=u, ref_u=ref.u.copy()))
+    stats = sim.stats()
+    phi = sim.damage()
+    sim.close()
+    return out, stats, phi, ref
+
+
+def assert_fp64(out, ref_phi=None, phi=None):
+    for c in out:
+        assert c["ru"] <= TOL and c["rv"] <= TOL and c["rt"] <= TOL, {k: c[k] for k in ("step", "ru", "rv", "rt")}
+        if c["exact"]:
+            assert c["status_equal"], "bond status differs at step %d" % c["step"]
+    if phi is not None and out[-1]["exact"]:
+        assert np.array_equal(phi, ref_phi)
+
+
+# ------------------------------------------------------------------------------------- family
+FAMILY_CASES = {
+    "cracked_plate": lambda: W.cracked_plate(nx=60, ny=24, dx=2.5e-4, crack_cells=30.125),
+    "notched_block": lambda: W.notched_block(nx=24, ny=12, nz=10, dx=1e-3, notch_cells=9.5),
+    "ratio_4": lambda: W.plate_vibration(nx=30, ny=17, ratio=4.015),
+}
+
+
+@pytest.mark.parametrize("case", sorted(FAMILY_CASES))
+def test_family_matches_oracle(case):
+    w = FAMILY_CASES[case]()
+    sim = Simulation(w, s0=0.0)
+    rp, col, intact = sim.neighbors()
+    sim.close()
+    orp, ocol = O.family(w.x, w.y, w.z, w.delta, w.cracks)
+    assert np.array_equal(rp, orp) and np.array_equal(col, ocol)
+    assert intact.all()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_family_random_cloud_nonuniform_volumes(dim):
+    rng = np.random.default_rng(10 + dim)
+    n = 1500 if dim == 2 else 3000
+    pts = rng.uniform(0.0, 1e-2, size=(dim, n))
+    vol = rng.uniform(0.5, 1.5, n) * (2.5e-4) ** dim
+    w = W.Workload("cloud", W.MODEL_3D if dim == 3 else W.MODEL_PLANE_STRAIN, E=1e9, nu=0.25, rho=1000.0,
+                   dx=2.5e-4, delta=8e-4, dt=1e-9, nsteps=50, x=pts[0], y=pts[1],
+                   z=pts[2] if dim == 3 else None, vol=vol,
+                   u0=1e-7 * rng.normal(size=(dim, n)))
+    s0 = 0.0
+    sim = Simulation(w, s0=s0)
+    rp, col, _ = sim.neighbors()
+    orp, ocol = O.family(w.x, w.y, w.z, w.delta)
+    assert np.array_equal(rp, orp) and np.array_equal(col, ocol)
+    ref = oracle_for(w, s0)
+    ref.step(50)
+    sim.step(50)
+    u, v, th = sim.state()
+    sim.close()
+    assert rel(u, ref.u) <= TOL and rel(v, ref.v) <= TOL and rel(th, ref.theta) <= TOL
+
+
+# ------------------------------------------------------------------------------ FP64 dynamics
+def test_config1_fp64_parity():
+    """Configuration 1 in full: 40 x 40 plane stress plate, 1000 steps, checkpoints every 100."""
+    w = W.config1()
+    out, stats, phi, ref = run_pair(w, w.nsteps, 100)
+    assert_fp64(out)
+    assert stats["broken_bonds"] == 0 and stats["steps"] == w.nsteps
+
+
+def test_cracked_plate_breaking_parity():
+    """A small pre-cracked plate under a traction large enough to break bonds."""
+    w = W.cracked_plate(nx=60, ny=24, dx=2.5e-4, crack_cells=30.125, sigma=1.5e8, nsteps=400)
+    out, stats, phi, ref = run_pair(w, w.nsteps, 50)
+    assert out[-1]["broken"] > 0
+    assert_fp64(out, ref.damage(), phi)
+
+
+def test_notched_block_twist_parity():
+    """3D notched block, clamped + twisted ends, random initial displacement, breaking on."""
+    w = W.notched_block(nx=24, ny=12, nz=10, dx=1e-3, notch_cells=9.5, nsteps=300, seed=3, amp=2e-6)
+    out, stats, phi, ref = run_pair(w, w.nsteps, 50, rate=5e3)
+    assert out[-1]["broken"] > 0
+    assert_fp64(out, ref.damage(), phi)
+    # prescribed particles follow the rigid rotation exactly
+    pres = w.flag == W.PRESCRIBED
+    assert np.array_equal(out[-1]["u"][:, pres], out[-1]["ref_u"][:, pres])
+
+
+def test_config2_fp64_parity_first_1000_steps():
+    """Configuration 2 at full size (64,000 particles), first 1000 of its 5000 steps."""
+    w = W.config2()
+    out, stats, phi, ref = run_pair(w, 1000, 250)
+    assert_fp64(out, ref.damage(), phi)
+
+
+def test_config3_quarter_scale_parity():
+    """Configuration 3 geometry at quarter size (100 x 50 x 25), random u0, 40 steps."""
+    w = W.notched_block(nx=100, ny=50, nz=25, dx=2e-3, nsteps=40, dt=3.790e-7 * 2, seed=5, amp=3e-6)
+    out, stats, phi, ref = run_pair(w, w.nsteps, 20, rate=2e3)
+    assert_fp64(out, ref.damage(), phi)
+
+
+def test_config3_full_size_first_steps():
+    """Configuration 3 at full size (1M particles, ~1.17e8 bonds): 2 steps from a random state,
+    every particle compared (the oracle runs multi-threaded)."""
+    w = W.notched_block(seed=7, amp=1e-6)
+    s0 = s0_of(w)
+    sim = Simulation(w, s0=s0)
+    ref = oracle_for(w, s0)
+    assert ref.nbonds == sim.nbonds
+    ref.step(2)
+    sim.step(2)
+    u, v, th = sim.state()
+    sim.close()
+    assert rel(u, ref.u) <= TOL and rel(v, ref.v) <= TOL and rel(th, ref.theta) <= TOL
+
+
+# --------------------------------------------------------------------- launch-shape invariance
+def test_graph_chunks_match_eager_launches():
+    w = W.config1()
+    res = []
+    for chunk in (0, 100, 7):
+        sim = Simulation(w, s0=0.0, graph_chunk=chunk)
+        sim.step(250)
+        res.append(sim.state()[0])
+        sim.close()
+    assert np.array_equal(res[0], res[1]) and np.array_equal(res[0], res[2])
+
+
+@pytest.mark.parametrize("block,split", [(128, 1), (512, 1), (256, 2), (128, 4), (512, 4)])
+def test_mapping_variants_agree(block, split):
+    w = W.notched_block(nx=30, ny=14, nz=12, dx=1e-3, notch_cells=11.5, nsteps=60, seed=1, amp=2e-6)
+    base = Simulation(w, s0=s0_of(w), rate=5e3)
+    base.step(60)
+    ub = base.state()[0]
+    base.close()
+    sim = Simulation(w, s0=s0_of(w), rate=5e3)
+    sim.set_option(B.PD_OPT_SPLIT, 1)
+    sim.set_option(B.PD_OPT_BLOCK, block)
+    sim.set_option(B.PD_OPT_SPLIT, split)
+    sim.set_state(w.initial_u())
+    sim.step(60)
+    u = sim.state()[0]
+    sim.close()
+    assert rel(u, ub) <= 1e-13
+
+
+# --------------------------------------------------------------------------------- edge cases
+def test_single_particle_and_ragged_sizes():
+    for nx, ny in ((1, 1), (33, 1), (7, 5)):
+        w = W.plate_vibration(nx=nx, ny=ny, nsteps=20, amp=1e-6)
+        out, stats, phi, ref = run_pair(w, 20, 10)
+        assert_fp64(out)
+        if nx * ny == 1:
+            assert stats["bonds"] == 0 and np.all(phi == 0.0)
+
+
+def test_crack_removing_every_bond():
+    """A crack between every pair of columns leaves particles without bonds: no force, phi = 0."""
+    w = W.plate_vibration(nx=4, ny=6, ratio=1.2, nsteps=10)
+    w.cracks = [(x0, -1.0, 0, x0, 1.0, 0, 0, 0, 0) for x0 in (1e-3, 2e-3, 3e-3)]
+    w.cracks += [(-1.0, y0, 0, 1.0, y0, 0, 0, 0, 0) for y0 in (1e-3, 2e-3, 3e-3, 4e-3, 5e-3)]
+    out, stats, phi, ref = run_pair(w, 10, 10)
+    assert stats["bonds"] == 0 and np.all(phi == 0.0)
+    assert np.array_equal(out[-1]["u"], w.initial_u())
+
+
+def test_state_errors_and_divergence_guard():
+    w = W.plate_vibration(nx=8, ny=8)
+    prm = B.make_params(w.model, w.E, w.nu, w.rho, w.delta, 0.0, w.dt)
+    h = B.pd_create_particles(prm, w.x, w.y, None, w.vol)
+    with pytest.raises(B.PDError) as e:
+        B.pd_step(h, 1)
+    assert e.value.status == B.PD_ERR_STATE
+    B.pd_build_neighbors(h)
+    B.pd_set_state(h, 2, w.n, w.initial_u())
+    assert B.pd_check_state(h, 1.0) == B.PD_OK
+    assert B.pd_check_state(h, 1e-9) == B.PD_ERR_NUMERIC
+    with pytest.raises(B.PDError):
+        B.pd_set_state(h, 2, w.n, np.full((2, w.n), np.nan))
+    B.pd_destroy(h)
+
+
+def test_unstable_time_step_trips_the_guard():
+    """dt = 1.2 x the stable bound diverges: the guard reports PD_ERR_NUMERIC (no GPU fault)."""
+    w = W.plate_vibration(dt=1.2 * 3.3693e-7)
+    sim = Simulation(w, s0=0.0)
+    sim.step(600)
+    assert B.pd_check_state(sim.h, 1e-3) == B.PD_ERR_NUMERIC
+    sim.close()
+
+
+# ------------------------------------------------------------------------------------ batched
+def _small_batch(n=5, seed=4):
+    return W.plate_batch(nplates=n, seed=seed, side_lo=10, side_hi=40, nsteps=200)
+
+
+def test_batch_equals_separate_runs_bitwise():
+    bw = _small_batch()
+    s0s = [s0_of(b) for b in bw.bodies]
+    bs = BatchSimulation(bw, s0s)
+    bs.step(200)
+    ub = bs.state()[0]
+    bs.close()
+    for k, b in enumerate(bw.bodies):
+        sim = Simulation(b, s0=s0s[k])
+        sim.step(200)
+        u = sim.state()[0]
+        sim.close()
+        assert np.array_equal(u, ub[:, bw.offsets[k]:bw.offsets[k + 1]]), k
+
+
+def test_batch_vs_oracle():
+    bw = _small_batch(n=3, seed=9)
+    s0s = [s0_of(b) for b in bw.bodies]
+    bs = BatchSimulation(bw, s0s)
+    bs.step(150)
+    ub = bs.state()[0]
+    rp, col, intact = bs.neighbors()
+    bs.close()
+    for k, b in enumerate(bw.bodies):
+        ref = oracle_for(b, s0s[k])
+        margins, _ = ref.step(150)
+        sl = slice(bw.offsets[k], bw.offsets[k + 1])
+        assert rel(ub[:, sl], ref.u) <= TOL
+        if margins.min() > 1e-9:
+            lo, hi = rp[bw.offsets[k]], rp[bw.offsets[k + 1]]
+            assert np.array_equal(intact[lo:hi], ref.status)
+
+
+# -------------------------------------------------------------------------------------- mixed
+def test_mixed_config1_error_bound():
+    """FP32 bond arithmetic with FP64 integration: rel-L2(u) vs the FP64 oracle after 100 and 1000
+    steps of configuration 1 (stated bound 2e-5 / 1e-4)."""
+    w = W.config1()
+    out, stats, phi, ref = run_pair(w, 1000, 100, precision=PD_MIXED)
+    assert out[0]["ru"] <= 2e-5, out[0]["ru"]
+    assert max(c["ru"] for c in out) <= 1e-4, [c["ru"] for c in out]
+
+
+def test_mixed_decisions_equal_fp64_on_own_state():
+    """Zero spurious breaks: with validation on, every bond decision of the FP32 + band path equals
+    the pure FP64 decision on the mixed run's own state."""
+    w = W.cracked_plate(nx=60, ny=24, dx=2.5e-4, crack_cells=30.125, sigma=1.5e8, nsteps=400)
+    sim = Simulation(w, s0=s0_of(w), precision=PD_MIXED)
+    sim.set_option(B.PD_OPT_VALIDATE, 1)
+    sim.step(400)
+    st = sim.stats()
+    sim.close()
+    assert st["broken_bonds"] > 0
+    assert st["validate_mismatches"] == 0
