@@ -201,6 +201,36 @@ pd_status pd_get_profile(pd_ctx* c, int32_t kernel, double* total_ms, int64_t* l
 /* Number of particles, dimension and storage of the context (for sizing host buffers). */
 pd_status pd_get_info(pd_ctx* c, int64_t* n, int32_t* dim, int64_t* device_bytes);
 
+/* pd_step_noalloc -- one explicit time step that allocates no memory at all.
+ *
+ * The paper has no counterpart; this is a library convenience for callers that cannot allocate
+ * device memory: code inside a host framework whose allocator owns the whole device and hands out
+ * fixed buffers, real-time loops that must never enter the allocator, or callers recording work
+ * while allocation is forbidden.  Such callers cannot create a pd_ctx (which cudaMallocs its arrays).
+ *
+ * What it computes (on the calling thread's current device, on `stream`, enqueue only): for a body
+ * with no constraints, no body force and no bond breaking, m_i over the given family (Eq 1.9),
+ * theta_i over its intact bonds (Eq 1.6), the forces of Eq 2.2 and the update of Eq 2.11:
+ * v_out = v + dt F / (rho V), u_out = u + dt v_out.  Same model constants as pd_params.
+ * Arguments (all arrays DEVICE memory owned by the caller, in the caller's particle order):
+ *   x_dev, y_dev, z_dev (NULL unless PD_3D), vol_dev: n doubles each;
+ *   row_ptr_dev (n + 1 int64), col_dev (row_ptr[n] int32): the family as CSR (e.g. from
+ *   pd_get_neighbors); intact_dev: one byte per CSR entry (1 intact), or NULL for all intact;
+ *   u_dev, v_dev -> u_out_dev, v_out_dev: dim * n SoA doubles (outputs must not alias inputs);
+ *   theta_dev: n doubles or NULL.  stream: cudaStream_t or NULL (legacy default stream).
+ * Limits: n <= 1,048,576.  Larger n returns PD_ERR_ARG with a message; so do NULL or host pointers.
+ * Scratch: its one intermediate (2 doubles per particle) lives in a fixed 16 MiB device array that
+ * every GPU loading the library holds until the process exits.  All calls share it and it keeps
+ * the last call's contents (each call rewrites every entry it reads); calls that overlap on the GPU
+ * race on it and must be serialized by the caller.  The first call on each device looks up that
+ * array's device address (a runtime query, once per device): make that first call before any
+ * stream capture.  Errors: PD_ERR_ARG, PD_ERR_CUDA (launch failure). */
+pd_status pd_step_noalloc(int32_t model, double E, double nu, double rho, double dt, int64_t n,
+                          const double* x_dev, const double* y_dev, const double* z_dev,
+                          const double* vol_dev, const int64_t* row_ptr_dev, const int32_t* col_dev,
+                          const uint8_t* intact_dev, const double* u_dev, const double* v_dev,
+                          double* u_out_dev, double* v_out_dev, double* theta_dev, void* stream);
+
 /* Thread-local description of the last failure on this host thread ("" if none). */
 const char* pd_last_error(void);
 

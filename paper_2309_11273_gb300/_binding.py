@@ -28,8 +28,8 @@ STATUS_NAMES = {0: "PD_OK", -1: "PD_ERR_ARG", -2: "PD_ERR_STATE", -3: "PD_ERR_OO
 EXPORTED = ["pd_critical_stretch", "pd_create_particles", "pd_create_batch", "pd_build_neighbors",
             "pd_set_bc", "pd_set_state", "pd_step", "pd_sync", "pd_get_damage", "pd_get_state",
             "pd_num_bonds", "pd_get_neighbors", "pd_get_stats", "pd_check_state", "pd_autotune",
-            "pd_set_option", "pd_get_option", "pd_get_profile", "pd_get_info", "pd_last_error",
-            "pd_destroy"]
+            "pd_set_option", "pd_get_option", "pd_get_profile", "pd_get_info", "pd_step_noalloc",
+            "pd_last_error", "pd_destroy"]
 
 
 class pd_params(ctypes.Structure):
@@ -95,6 +95,8 @@ def lib(path: str = LIB_PATH):
             L.pd_get_option.argtypes = [_vp, ctypes.c_int32, _i64]
             L.pd_get_profile.argtypes = [_vp, ctypes.c_int32, _d, _i64, ctypes.c_int32]
             L.pd_get_info.argtypes = [_vp, _i64, _i32, _i64]
+            L.pd_step_noalloc.argtypes = ([ctypes.c_int32] + [ctypes.c_double] * 4 + [ctypes.c_int64]
+                                          + [_vp] * 12 + [_vp])
             L.pd_last_error.restype = ctypes.c_char_p
             L.pd_destroy.argtypes = [_vp]
             L.pd_destroy.restype = None
@@ -263,6 +265,14 @@ def pd_get_info(h):
     n, dim, by = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int64()
     _check(lib().pd_get_info(h, ctypes.byref(n), ctypes.byref(dim), ctypes.byref(by)))
     return int(n.value), int(dim.value), int(by.value)
+
+
+def pd_step_noalloc(model, E, nu, rho, dt, n, x_dev, y_dev, z_dev, vol_dev, row_ptr_dev, col_dev,
+                    intact_dev, u_dev, v_dev, u_out_dev, v_out_dev, theta_dev=None, stream=None):
+    """Device pointers (ints, e.g. torch ``tensor.data_ptr()``) or None; returns the status code."""
+    return lib().pd_step_noalloc(int(model), float(E), float(nu), float(rho), float(dt), int(n), x_dev, y_dev,
+                                 z_dev, vol_dev, row_ptr_dev, col_dev, intact_dev, u_dev, v_dev, u_out_dev,
+                                 v_out_dev, theta_dev, stream)
 
 
 def pd_last_error() -> str:

@@ -17,7 +17,7 @@ SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libosbpd.so")
 ROOT = os.path.dirname(HERE)
-UNITS = {"pd_build.cu": ["--fmad=false"], "pd_step.cu": [], "pd_api.cu": []}
+UNITS = {"pd_build.cu": ["--fmad=false"], "pd_step.cu": [], "pd_api.cu": [], "pd_noalloc.cu": []}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
