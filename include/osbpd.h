@@ -59,6 +59,13 @@ typedef enum { PD_3D = 0, PD_PLANE_STRESS = 1, PD_PLANE_STRAIN = 2 } pd_model;
  *   status equals the FP64 decision on the run's own state. */
 typedef enum { PD_FP64 = 0, PD_MIXED = 1 } pd_precision;
 
+/* Internal particle order (results do not depend on it beyond rounding).
+ * PD_ORDER_BRICKS: bricks of 32 x 4 x 4 (3D) or 32 x 8 (2D) points of the typical spacing
+ *   (mean V)^(1/dim), x fastest inside a brick, bricks along a Morton curve: a warp's 32 particles
+ *   form one row, so its neighbour gathers are contiguous on lattices.
+ * PD_ORDER_MORTON: a Morton curve of the coordinates. */
+typedef enum { PD_ORDER_BRICKS = 0, PD_ORDER_MORTON = 1 } pd_ordering;
+
 typedef struct {
   int32_t model;       /* pd_model */
   int32_t precision;   /* pd_precision */
@@ -70,7 +77,7 @@ typedef struct {
   double dt;           /* time step [s] (Eq 2.11) */
   double band_safety;  /* PD_MIXED only: safety factor on the FP32 rounding bound; <= 0 -> 4 */
   int32_t device;      /* CUDA device ordinal */
-  int32_t reserved;    /* must be 0 */
+  int32_t ordering;    /* internal particle order: PD_ORDER_BRICKS (0, default) or PD_ORDER_MORTON */
   void* stream;        /* cudaStream_t to run on, or NULL for a library-owned stream */
 } pd_params;
 
@@ -100,7 +107,11 @@ typedef enum {
   PD_OPT_PROFILE = 2,      /* 1: time every kernel launch with CUDA events (forces eager launches) */
   PD_OPT_VALIDATE = 3,     /* PD_MIXED: 1 = also decide every bond in FP64 and count mismatches */
   PD_OPT_BLOCK = 4,        /* threads per block of the step kernels (multiple of 32, <= 512) */
-  PD_OPT_SPLIT = 5         /* warps cooperating on one 32-particle slice: 1, 2 or 4 */
+  PD_OPT_SPLIT = 5,        /* warps cooperating on one 32-particle slice: 1, 2 or 4 */
+  PD_OPT_BOND_CACHE = 6    /* PD_FP64: 1 (default) = keep a per-bond table of the reference
+                              geometry (xi, 1/|xi|^2, s0 |xi|^2; 40 bytes per bond slot) so each
+                              step evaluates only displacement-dependent FP64 terms; 0 = recompute
+                              the geometry from the coordinates every step */
 } pd_option;
 
 /* Kernel identifiers for pd_get_profile. */

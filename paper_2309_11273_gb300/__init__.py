@@ -21,18 +21,20 @@ class Simulation:
     """One body: create -> build family -> boundary conditions -> initial state, then step."""
 
     def __init__(self, w, s0=None, precision=PD_FP64, rate=None, device=0, stream=None,
-                 band_safety=0.0, graph_chunk=None):
+                 band_safety=0.0, graph_chunk=None, ordering=B.PD_ORDER_BRICKS, bond_cache=None):
         self.w = w
         self.n, self.dim = w.n, w.dim
         if s0 is None:
             s0 = pd_critical_stretch(w.model, w.E, w.nu, w.Gc, w.delta) if w.Gc else 0.0
         self.s0 = float(s0)
         prm = B.make_params(w.model, w.E, w.nu, w.rho, w.delta, self.s0, w.dt, precision, band_safety,
-                            device, stream)
+                            device, stream, ordering)
         self.h = B.pd_create_particles(prm, w.x, w.y, w.z, w.vol)
         try:
             if graph_chunk is not None:
                 B.pd_set_option(self.h, B.PD_OPT_GRAPH_CHUNK, graph_chunk)
+            if bond_cache is not None:
+                B.pd_set_option(self.h, B.PD_OPT_BOND_CACHE, int(bond_cache))
             B.pd_build_neighbors(self.h, w.cracks)
             self.rate = w.rotation_rate(self.s0) if rate is None else float(rate)
             if w.flag is not None or w.b is not None:
@@ -87,19 +89,21 @@ class BatchSimulation(Simulation):
     """Many independent bodies (``workloads.BatchWorkload``) in one context and the same kernels."""
 
     def __init__(self, bw, s0s=None, precision=PD_FP64, device=0, stream=None, band_safety=0.0,
-                 graph_chunk=None):
+                 graph_chunk=None, ordering=B.PD_ORDER_BRICKS, bond_cache=None):
         self.w = bw
         self.n, self.dim = bw.n, 2 if bw.bodies[0].z is None else 3
         if s0s is None:
             s0s = [pd_critical_stretch(b.model, b.E, b.nu, b.Gc, b.delta) if b.Gc else 0.0 for b in bw.bodies]
         self.s0s = [float(s) for s in s0s]
-        prms = [B.make_params(b.model, b.E, b.nu, b.rho, b.delta, s, b.dt, precision, band_safety, device, stream)
-                for b, s in zip(bw.bodies, self.s0s)]
+        prms = [B.make_params(b.model, b.E, b.nu, b.rho, b.delta, s, b.dt, precision, band_safety, device, stream,
+                              ordering) for b, s in zip(bw.bodies, self.s0s)]
         z = bw.concat("z") if self.dim == 3 else None
         self.h = B.pd_create_batch(prms, bw.offsets, bw.concat("x"), bw.concat("y"), z, bw.concat("vol"))
         try:
             if graph_chunk is not None:
                 B.pd_set_option(self.h, B.PD_OPT_GRAPH_CHUNK, graph_chunk)
+            if bond_cache is not None:
+                B.pd_set_option(self.h, B.PD_OPT_BOND_CACHE, int(bond_cache))
             B.pd_build_neighbors(self.h, [])
             bs = [b.b if b.b is not None else np.zeros((self.dim, b.n)) for b in bw.bodies]
             if any(b.b is not None for b in bw.bodies):

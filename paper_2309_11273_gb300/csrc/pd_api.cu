@@ -52,6 +52,8 @@ void free_build(pd_ctx* c) {
   c->vel = c->bacc = c->gvec = nullptr;
   c->flag = nullptr;
   c->pos32 = nullptr;
+  c->bc = nullptr;
+  c->bt = nullptr;
   c->u32[0] = c->u32[1] = nullptr;
   c->thm32 = nullptr;
   c->mu32 = c->aA32 = c->theta32 = nullptr;
@@ -126,6 +128,7 @@ pd_status alloc_state(pd_ctx* c) {
   const int tb = 256;
   const unsigned gb = (unsigned)((np + tb - 1) / tb);
   k_init_thm<<<gb, tb, 0, s>>>(np, c->mu, c->thm);
+  if ((st = init_disp_w(c)) != PD_OK) return st;
   if (c->precision == PD_MIXED) {
     if ((st = alloc(c, &c->pos32, np)) != PD_OK) return st;
     if ((st = alloc(c, &c->u32[0], np)) != PD_OK) return st;
@@ -452,6 +455,9 @@ pd_status pd_set_option(pd_ctx* c, int32_t option, int64_t value) {
       if ((c->block / 32) % value) return fail(PD_ERR_ARG, "block warps must be a multiple of split");
       c->split = (int)value;
       break;
+    case PD_OPT_BOND_CACHE:
+      c->bond_cache = value != 0;
+      break;
     default:
       return fail(PD_ERR_ARG, "unknown option");
   }
@@ -469,6 +475,7 @@ pd_status pd_get_option(pd_ctx* c, int32_t option, int64_t* value) {
     case PD_OPT_VALIDATE: *value = c->validate; break;
     case PD_OPT_BLOCK: *value = c->block; break;
     case PD_OPT_SPLIT: *value = c->split; break;
+    case PD_OPT_BOND_CACHE: *value = c->bond_cache; break;
     default: return fail(PD_ERR_ARG, "unknown option");
   }
   return PD_OK;

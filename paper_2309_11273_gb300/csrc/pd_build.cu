@@ -251,7 +251,7 @@ pd_status check_params(const pd_params& p, int dim) {
   if (!(p.horizon > 0) || !std::isfinite(p.horizon)) return fail(PD_ERR_ARG, "horizon must be > 0");
   if (!(p.dt > 0) || !std::isfinite(p.dt)) return fail(PD_ERR_ARG, "dt must be > 0");
   if (!std::isfinite(p.s0)) return fail(PD_ERR_ARG, "s0 must be finite");
-  if (p.reserved != 0) return fail(PD_ERR_ARG, "reserved must be 0");
+  if (p.ordering != PD_ORDER_BRICKS && p.ordering != PD_ORDER_MORTON) return fail(PD_ERR_ARG, "unknown ordering");
   return PD_OK;
 }
 
@@ -336,32 +336,53 @@ pd_status create(pd_ctx** out, int32_t nbodies, const pd_params* prm, const int6
     c->own_stream = true;
   }
 
-  // Morton order inside each body; bodies stay contiguous in their given order.
+  // Internal order inside each body (bodies stay contiguous in their given order):
+  //   PD_ORDER_MORTON: Morton curve of the coordinates;
+  //   PD_ORDER_BRICKS: bricks of 32 x 4 x 4 (3D) / 32 x 8 (2D) points of the body's typical spacing
+  //     h = (mean V)^(1/dim), row-major (x fastest) inside a brick, bricks along a Morton curve.  A
+  //     32-particle slice is then one x-row, and the 32 neighbours a warp gathers for one slot (the
+  //     same bond direction on a lattice) form a shifted contiguous row.
   std::vector<uint64_t> key(n);
   c->body_of.assign(n, 0);
+  const int ordering = prm[0].ordering;
   for (int b = 0; b < nbodies; ++b) {
     double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    double vsum = 0.0;
     for (int64_t i = offsets[b]; i < offsets[b + 1]; ++i) {
       const double p[3] = {x[i], y[i], z ? z[i] : 0.0};
       for (int k = 0; k < 3; ++k) {
         lo[k] = std::min(lo[k], p[k]);
         hi[k] = std::max(hi[k], p[k]);
       }
+      vsum += vol[i];
     }
     double ext = std::max(hi[0] - lo[0], std::max(hi[1] - lo[1], hi[2] - lo[2]));
     if (!(ext > 0)) ext = 1.0;
-    const double bitsmax = dim == 3 ? 2097151.0 : 4294967295.0;
-    const double sc = bitsmax / ext;
+    const int64_t nb = offsets[b + 1] - offsets[b];
+    double h = std::pow(vsum / (double)nb, 1.0 / dim);
+    if (!(h > 0) || ext / h > 1e6) h = ext / 1e6;
     for (int64_t i = offsets[b]; i < offsets[b + 1]; ++i) {
-      const uint64_t qx = (uint64_t)std::min(bitsmax, std::max(0.0, (x[i] - lo[0]) * sc));
-      const uint64_t qy = (uint64_t)std::min(bitsmax, std::max(0.0, (y[i] - lo[1]) * sc));
-      if (dim == 3) {
-        const uint64_t qz = (uint64_t)std::min(bitsmax, std::max(0.0, (z[i] - lo[2]) * sc));
-        key[i] = spread3(qx) | (spread3(qy) << 1) | (spread3(qz) << 2);
-      } else {
-        key[i] = spread2(qx) | (spread2(qy) << 1);
-      }
       c->body_of[i] = b;
+      const double p[3] = {x[i], y[i], z ? z[i] : 0.0};
+      if (ordering == PD_ORDER_MORTON) {
+        const double bitsmax = dim == 3 ? 2097151.0 : 4294967295.0;
+        const double sc = bitsmax / ext;
+        uint64_t q[3];
+        for (int k = 0; k < 3; ++k) q[k] = (uint64_t)std::min(bitsmax, std::max(0.0, (p[k] - lo[k]) * sc));
+        key[i] = dim == 3 ? (spread3(q[0]) | (spread3(q[1]) << 1) | (spread3(q[2]) << 2))
+                          : (spread2(q[0]) | (spread2(q[1]) << 1));
+      } else {
+        int64_t g[3];
+        for (int k = 0; k < 3; ++k) g[k] = std::max<int64_t>(0, std::llrint((p[k] - lo[k]) / h));
+        if (dim == 3) {
+          const uint64_t loc = (uint64_t)(((g[2] & 3) * 4 + (g[1] & 3)) * 32 + (g[0] & 31));
+          key[i] = ((spread3((uint64_t)(g[0] >> 5)) | (spread3((uint64_t)(g[1] >> 2)) << 1) |
+                     (spread3((uint64_t)(g[2] >> 2)) << 2)) << 9) | loc;
+        } else {
+          const uint64_t loc = (uint64_t)((g[1] & 7) * 32 + (g[0] & 31));
+          key[i] = ((spread2((uint64_t)(g[0] >> 5)) | (spread2((uint64_t)(g[1] >> 3)) << 1)) << 8) | loc;
+        }
+      }
     }
   }
   c->perm.resize(n);

@@ -70,6 +70,8 @@ struct StepArgs {
   float band_c;            // safety factor of the band
   int validate;            // mixed: also decide every bond in FP64 and count mismatches
   int check;               // apply the failure criterion at the head of pass 1
+  const double4* bc;       // cached FP64 path: per slot (xi, 1/|xi|^2), or nullptr
+  const double* bt;        // cached FP64 path: per slot s0 |xi|^2
 };
 
 struct KernelTimes {
@@ -125,6 +127,9 @@ struct pd_ctx {
   float* aA32 = nullptr;
   float* theta32 = nullptr;
   unsigned long long* counters = nullptr;
+  double4* bc = nullptr;          // FP64 per-slot geometry table (xi, 1/|xi|^2)
+  double* bt = nullptr;           // FP64 per-slot s0 |xi|^2
+  int bond_cache = 1;             // use the table in the FP64 path
   double q = 0.0;               // fixed-point quantum of the mixed coordinates [m]
   double qlo[3] = {0, 0, 0};     // origin of the fixed-point coordinates
   // state
@@ -172,6 +177,8 @@ pd_status launch_step(pd_ctx* c, bool check);
 pd_status launch_refresh_check(pd_ctx* c);
 pd_status launch_damage(pd_ctx* c, double* phi_caller);
 pd_status launch_set_step(pd_ctx* c, int64_t value);
+pd_status init_disp_w(pd_ctx* c);
+pd_status ensure_bond_cache(pd_ctx* c);
 pd_status upload_field(pd_ctx* c, const double* host_soa, double4* dst, int comps);
 pd_status download_field(pd_ctx* c, const double4* src, double* host_soa, int comps);
 pd_status download_scalar(pd_ctx* c, const double* src, double* host);

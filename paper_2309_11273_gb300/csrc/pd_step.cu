@@ -93,9 +93,10 @@ __device__ __forceinline__ void bond_f64(const double4& pi, const double4& pj, c
   }
 }
 
+// Out of line: the mixed path calls it only for the few bonds inside its rounding band.
 template <int DIM>
-__device__ __forceinline__ bool fp64_breaks(const StepArgs& a, int64_t i, int32_t j,
-                                            const double4* __restrict__ disp, double s0) {
+__device__ __noinline__ bool fp64_breaks(const StepArgs& a, int64_t i, int32_t j,
+                                         const double4* __restrict__ disp, double s0) {
   double ex, ey, ez, d, q;
   bond_f64<DIM>(a.pos[i], a.pos[j], disp[i], disp[j], ex, ey, ez, d, q);
   return d >= s0 * q;
@@ -119,16 +120,16 @@ __device__ __forceinline__ void update(const StepArgs& a, int64_t i, int b, cons
     u.y = u.y + bp.dt * v.y;
     u.z = u.z + bp.dt * v.z;
   } else if (fl == 1) {
-    u = make_double4(0.0, 0.0, 0.0, 0.0);
-    v = u;
+    u = make_double4(0.0, 0.0, 0.0, u.w);
+    v = make_double4(0.0, 0.0, 0.0, 0.0);
   } else {
     const double t1 = (double)(*a.d_step + 1) * bp.dt;
     const double4 g = a.gvec[i];
     const double rt = bp.rate * t1;
-    u = make_double4(rt * g.x, rt * g.y, rt * g.z, 0.0);
+    u = make_double4(rt * g.x, rt * g.y, rt * g.z, u.w);
     v = make_double4(bp.rate * g.x, bp.rate * g.y, bp.rate * g.z, 0.0);
   }
-  disp_out[i] = u;
+  disp_out[i] = u;  // .w carries V_i unchanged
   a.vel[i] = v;
 }
 
@@ -152,7 +153,10 @@ __device__ __forceinline__ void load_slots(const SliceIdx& t, const int32_t* __r
 constexpr int kU64 = 2;
 constexpr int kU32 = 4;
 
-template <int DIM, int SPLIT>
+// With CACHE the reference geometry of every slot is read from the per-slot table built once
+// (xi, 1/|xi|^2 and s0 |xi|^2 in FP64), so the FP64 pipe -- GB300's scarcest unit, 1/64 of the FP32
+// rate -- only evaluates the displacement-dependent terms; V_j rides in the .w lane of u_j.
+template <int DIM, int SPLIT, bool CACHE>
 __global__ void __launch_bounds__(512) k_pass1_f64(StepArgs a, const double4* __restrict__ disp,
                                                     int write_theta) {
   const SliceIdx t = slice_index<SPLIT>(a.n_pad, a.slice_ptr);
@@ -166,36 +170,47 @@ __global__ void __launch_bounds__(512) k_pass1_f64(StepArgs a, const double4* __
     const double4 pi = a.pos[t.i], ui = disp[t.i];
     uint32_t* __restrict__ bw = a.bits + (t.base >> 5);
     const int32_t* __restrict__ cl = a.col + t.base + t.lane;
+    const double4* __restrict__ ce = a.bc + t.base + t.lane;
+    const double* __restrict__ ct = a.bt + t.base + t.lane;
     constexpr int U = kU64;
     int32_t jn[U];
     uint32_t wn[U];
     load_slots<U, SPLIT>(t, cl, bw, t.sub, jn, wn);
     for (int k0 = t.sub; k0 < t.W; k0 += U * SPLIT) {
-      int32_t j[U];
       uint32_t wd[U];
-      double4 pj[U], uj[U];
+      double4 gj[U], uj[U];
+      double tq[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        j[u] = jn[u];
+        const int k = min(k0 + u * SPLIT, t.W - 1);
         wd[u] = wn[u];
-        pj[u] = a.pos[j[u]];
-        uj[u] = disp[j[u]];
+        gj[u] = CACHE ? ce[(int64_t)k << 5] : a.pos[jn[u]];
+        if (CACHE) tq[u] = ct[(int64_t)k << 5];
+        uj[u] = disp[jn[u]];
       }
       load_slots<U, SPLIT>(t, cl, bw, k0 + U * SPLIT, jn, wn);
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         double ex, ey, ez, d, q;
-        bond_f64<DIM>(pi, pj[u], ui, uj[u], ex, ey, ez, d, q);
+        if (CACHE) {
+          ex = gj[u].x;
+          ey = gj[u].y;
+          ez = gj[u].z;
+          d = ex * (uj[u].x - ui.x) + ey * (uj[u].y - ui.y);
+          if (DIM == 3) d = fma(ez, uj[u].z - ui.z, d);
+        } else {
+          bond_f64<DIM>(pi, gj[u], ui, uj[u], ex, ey, ez, d, q);
+        }
         bool intact = (wd[u] >> t.lane) & 1u;
         if (a.check) {
-          const bool brk = intact && can_break && d >= s0 * q;
+          const bool brk = intact && can_break && d >= (CACHE ? tq[u] : s0 * q);
           const unsigned m = __ballot_sync(kFull, brk);
           if (m) {
             intact = intact && !brk;
             if (t.lane == 0) bw[k0 + u * SPLIT] = wd[u] & ~m;
           }
         }
-        acc[0] += intact ? pj[u].w * d : 0.0;
+        acc[0] += intact ? uj[u].w * d : 0.0;
       }
     }
   }
@@ -209,7 +224,7 @@ __global__ void __launch_bounds__(512) k_pass1_f64(StepArgs a, const double4* __
   }
 }
 
-template <int DIM, int SPLIT>
+template <int DIM, int SPLIT, bool CACHE>
 __global__ void __launch_bounds__(512) k_pass2_f64(StepArgs a, const double4* __restrict__ disp,
                                                     double4* __restrict__ disp_out) {
   const SliceIdx t = slice_index<SPLIT>(a.n_pad, a.slice_ptr);
@@ -221,29 +236,40 @@ __global__ void __launch_bounds__(512) k_pass2_f64(StepArgs a, const double4* __
     const double2 ti = a.thm[t.i];
     const uint32_t* __restrict__ bw = a.bits + (t.base >> 5);
     const int32_t* __restrict__ cl = a.col + t.base + t.lane;
+    const double4* __restrict__ ce = a.bc + t.base + t.lane;
     constexpr int U = kU64;
     int32_t jn[U];
     uint32_t wn[U];
     load_slots<U, SPLIT>(t, cl, bw, t.sub, jn, wn);
     for (int k0 = t.sub; k0 < t.W; k0 += U * SPLIT) {
       uint32_t wd[U];
-      double4 pj[U], uj[U];
+      double4 gj[U], uj[U];
       double2 tj[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
+        const int k = min(k0 + u * SPLIT, t.W - 1);
         wd[u] = wn[u];
-        pj[u] = a.pos[jn[u]];
+        gj[u] = CACHE ? ce[(int64_t)k << 5] : a.pos[jn[u]];
         uj[u] = disp[jn[u]];
         tj[u] = a.thm[jn[u]];
       }
       load_slots<U, SPLIT>(t, cl, bw, k0 + U * SPLIT, jn, wn);
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        double ex, ey, ez, d, q;
-        bond_f64<DIM>(pi, pj[u], ui, uj[u], ex, ey, ez, d, q);
+        double ex, ey, ez, d, q, r;
+        if (CACHE) {
+          ex = gj[u].x;
+          ey = gj[u].y;
+          ez = gj[u].z;
+          r = gj[u].w;
+          d = ex * (uj[u].x - ui.x) + ey * (uj[u].y - ui.y);
+          if (DIM == 3) d = fma(ez, uj[u].z - ui.z, d);
+        } else {
+          bond_f64<DIM>(pi, gj[u], ui, uj[u], ex, ey, ez, d, q);
+        }
         // Eq 2.2: [(K - G/3)(theta_i/m_i + theta_j/m_j) + G (1/m_i + 1/m_j) xi.du / |xi|^2] V_j xi
-        double c = fma(ti.y + tj[u].y, d / q, ti.x + tj[u].x);
-        c = ((wd[u] >> t.lane) & 1u) ? c * pj[u].w : 0.0;
+        double c = fma(ti.y + tj[u].y, CACHE ? d * r : d / q, ti.x + tj[u].x);
+        c = ((wd[u] >> t.lane) & 1u) ? c * uj[u].w : 0.0;
         f[0] = fma(c, ex, f[0]);
         f[1] = fma(c, ey, f[1]);
         if (DIM == 3) f[2] = fma(c, ez, f[2]);
@@ -254,6 +280,26 @@ __global__ void __launch_bounds__(512) k_pass2_f64(StepArgs a, const double4* __
   if (t.active && t.sub == 0) {
     double4 u;
     update(a, t.i, b, f, disp, disp_out, u);
+  }
+}
+
+// Per-slot reference geometry for the cached FP64 path: (xi, 1/|xi|^2) and s0 |xi|^2, with xi and
+// |xi|^2 evaluated exactly as bond_f64 does (so both variants decide a bond identically).
+template <int DIM>
+__global__ void k_bond_cache(StepArgs a, double4* __restrict__ bc, double* __restrict__ bt) {
+  const SliceIdx t = slice_index<1>(a.n_pad, a.slice_ptr);
+  if (!t.active) return;
+  const int b = a.body ? a.body[t.i] : 0;
+  const double s0 = a.bp[b].s0;
+  const double4 pi = a.pos[t.i];
+  const double4 zero = make_double4(0.0, 0.0, 0.0, 0.0);
+  for (int k = 0; k < t.W; ++k) {
+    const int64_t e = t.base + t.lane + ((int64_t)k << 5);
+    const int32_t j = a.col[e];
+    double ex, ey, ez, d, q;
+    bond_f64<DIM>(pi, a.pos[j], zero, zero, ex, ey, ez, d, q);
+    bc[e] = make_double4(ex, ey, ez, q > 0.0 ? 1.0 / q : 0.0);
+    bt[e] = s0 * q;
   }
 }
 
@@ -419,16 +465,28 @@ __global__ void k_damage(StepArgs a, int64_t n, const double* __restrict__ dden,
   if (t.i < n) out[perm[t.i]] = dden[t.i] > 0.0 ? 1.0 - num / dden[t.i] : 0.0;
 }
 
+// Caller-order SoA -> internal double4; .w taken from wsrc[k].w (the particle volume) when given.
 __global__ void k_gather_soa(int64_t n, int64_t n_pad, int comps, const double* __restrict__ src,
-                             const int64_t* __restrict__ perm, double4* __restrict__ dst) {
+                             const int64_t* __restrict__ perm, const double4* __restrict__ wsrc,
+                             double4* __restrict__ dst) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= n_pad) return;
+  const double w = wsrc ? wsrc[k].w : 0.0;
   if (k >= n) {
-    dst[k] = make_double4(0.0, 0.0, 0.0, 0.0);
+    dst[k] = make_double4(0.0, 0.0, 0.0, w);
     return;
   }
   const int64_t u = perm[k];
-  dst[k] = make_double4(src[u], src[n + u], comps == 3 ? src[2 * n + u] : 0.0, 0.0);
+  dst[k] = make_double4(src[u], src[n + u], comps == 3 ? src[2 * n + u] : 0.0, w);
+}
+
+// disp[.].w = V (set once after allocation; every writer of disp keeps it).
+__global__ void k_set_w(int64_t n_pad, const double4* __restrict__ pos, double4* __restrict__ d0,
+                        double4* __restrict__ d1) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= n_pad) return;
+  d0[k].w = pos[k].w;
+  d1[k].w = pos[k].w;
 }
 
 __global__ void k_scatter_soa(int64_t n, int comps, const double4* __restrict__ src,
@@ -455,16 +513,17 @@ __global__ void k_apply_bc(StepArgs a, double4* __restrict__ disp, int64_t step)
   if (i >= a.n_pad || !a.flag) return;
   const uint8_t fl = a.flag[i];
   if (fl == 0) return;
+  const double w = disp[i].w;
   if (fl == 1) {
-    disp[i] = make_double4(0.0, 0.0, 0.0, 0.0);
-    a.vel[i] = disp[i];
+    disp[i] = make_double4(0.0, 0.0, 0.0, w);
+    a.vel[i] = make_double4(0.0, 0.0, 0.0, 0.0);
     return;
   }
   const BodyDev& bp = a.bp[a.body ? a.body[i] : 0];
   const double tn = (double)step * bp.dt;
   const double4 g = a.gvec[i];
   const double rt = bp.rate * tn;
-  disp[i] = make_double4(rt * g.x, rt * g.y, rt * g.z, 0.0);
+  disp[i] = make_double4(rt * g.x, rt * g.y, rt * g.z, w);
   a.vel[i] = make_double4(bp.rate * g.x, bp.rate * g.y, bp.rate * g.z, 0.0);
 }
 
@@ -529,21 +588,27 @@ StepArgs make_args(pd_ctx* c) {
   a.band_c = (float)bc;
   a.validate = c->validate;
   a.check = 1;
+  a.bc = c->bond_cache ? c->bc : nullptr;
+  a.bt = c->bond_cache ? c->bt : nullptr;
   return a;
 }
 
 template <int DIM, int SPLIT>
 void launch_pass1(pd_ctx* c, const StepArgs& a, int write_theta, unsigned grid, int block, size_t sm) {
-  if (c->precision == PD_FP64)
-    k_pass1_f64<DIM, SPLIT><<<grid, block, sm, c->stream>>>(a, c->disp[c->cur], write_theta);
+  if (c->precision == PD_FP64 && a.bc)
+    k_pass1_f64<DIM, SPLIT, true><<<grid, block, sm, c->stream>>>(a, c->disp[c->cur], write_theta);
+  else if (c->precision == PD_FP64)
+    k_pass1_f64<DIM, SPLIT, false><<<grid, block, sm, c->stream>>>(a, c->disp[c->cur], write_theta);
   else
     k_pass1_mixed<DIM, SPLIT><<<grid, block, sm, c->stream>>>(a, c->u32[c->cur], c->disp[c->cur], write_theta);
 }
 
 template <int DIM, int SPLIT>
 void launch_pass2(pd_ctx* c, const StepArgs& a, unsigned grid, int block, size_t sm) {
-  if (c->precision == PD_FP64)
-    k_pass2_f64<DIM, SPLIT><<<grid, block, sm, c->stream>>>(a, c->disp[c->cur], c->disp[c->cur ^ 1]);
+  if (c->precision == PD_FP64 && a.bc)
+    k_pass2_f64<DIM, SPLIT, true><<<grid, block, sm, c->stream>>>(a, c->disp[c->cur], c->disp[c->cur ^ 1]);
+  else if (c->precision == PD_FP64)
+    k_pass2_f64<DIM, SPLIT, false><<<grid, block, sm, c->stream>>>(a, c->disp[c->cur], c->disp[c->cur ^ 1]);
   else
     k_pass2_mixed<DIM, SPLIT>
         <<<grid, block, sm, c->stream>>>(a, c->u32[c->cur], c->u32[c->cur ^ 1], c->disp[c->cur], c->disp[c->cur ^ 1]);
@@ -579,6 +644,31 @@ cudaEvent_t take_event(pd_ctx* c) {
 }
 
 }  // namespace
+
+pd_status init_disp_w(pd_ctx* c) {
+  const int tb = 256;
+  k_set_w<<<(unsigned)((c->n_pad + tb - 1) / tb), tb, 0, c->stream>>>(c->n_pad, c->pos, c->disp[0], c->disp[1]);
+  PD_CUDA(cudaGetLastError());
+  return PD_OK;
+}
+
+// Allocates and fills the per-slot geometry table of the cached FP64 path (once per build).
+pd_status ensure_bond_cache(pd_ctx* c) {
+  if (!c->bond_cache || c->precision != PD_FP64 || c->bc) return PD_OK;
+  pd_status st;
+  const size_t ne = (size_t)std::max<int64_t>(c->nentries, 32);
+  if ((st = alloc(c, &c->bc, ne)) != PD_OK) return st;
+  if ((st = alloc(c, &c->bt, ne)) != PD_OK) return st;
+  StepArgs a = make_args(c);
+  const int tb = 256;
+  const unsigned grid = (unsigned)((c->n_pad + tb - 1) / tb);
+  if (c->dim == 3)
+    k_bond_cache<3><<<grid, tb, 0, c->stream>>>(a, c->bc, c->bt);
+  else
+    k_bond_cache<2><<<grid, tb, 0, c->stream>>>(a, c->bc, c->bt);
+  PD_CUDA(cudaGetLastError());
+  return PD_OK;
+}
 
 pd_status launch_set_step(pd_ctx* c, int64_t value) {
   k_set_step<<<1, 1, 0, c->stream>>>(c->d_step, value);
@@ -660,8 +750,9 @@ pd_status upload_field(pd_ctx* c, const double* host_soa, double4* dst, int comp
   const int64_t n = c->n;
   PD_CUDA(cudaMemcpyAsync(c->scratch, host_soa, sizeof(double) * comps * n, cudaMemcpyHostToDevice, c->stream));
   const int tb = 256;
+  const bool is_disp = dst == c->disp[0] || dst == c->disp[1];
   k_gather_soa<<<(unsigned)((c->n_pad + tb - 1) / tb), tb, 0, c->stream>>>(n, c->n_pad, comps, c->scratch,
-                                                                          c->perm_dev, dst);
+                                                                          c->perm_dev, is_disp ? c->pos : nullptr, dst);
   PD_CUDA(cudaGetLastError());
   return PD_OK;
 }
@@ -724,7 +815,9 @@ pd_status max_abs_u(pd_ctx* c, double* out, int* nonfinite) {
 // chunks of graph_chunk steps, then single steps.
 pd_status run_steps(pd_ctx* c, int64_t nsteps) {
   if (nsteps <= 0) return PD_OK;
-  pd_status st = launch_set_step(c, c->steps - 1);
+  pd_status st = ensure_bond_cache(c);
+  if (st != PD_OK) return st;
+  st = launch_set_step(c, c->steps - 1);
   if (st != PD_OK) return st;
   int64_t left = nsteps;
   if (c->skip_next_check) {

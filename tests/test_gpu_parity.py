@@ -209,6 +209,23 @@ def test_mapping_variants_agree(block, split):
     assert rel(u, ub) <= 1e-13
 
 
+@pytest.mark.parametrize("precision", [PD_FP64, PD_MIXED])
+def test_orderings_and_bond_cache_agree(precision):
+    """Internal particle order (bricks / Morton) and the FP64 geometry table change only rounding."""
+    w = W.notched_block(nx=30, ny=14, nz=12, dx=1e-3, notch_cells=11.5, nsteps=60, seed=1, amp=2e-6)
+    res = {}
+    for order in (B.PD_ORDER_BRICKS, B.PD_ORDER_MORTON):
+        for cache in ((1, 0) if precision == PD_FP64 else (1,)):
+            sim = Simulation(w, s0=s0_of(w), rate=5e3, precision=precision, ordering=order, bond_cache=cache)
+            sim.step(60)
+            res[(order, cache)] = sim.state()[0]
+            sim.close()
+    ref = res[(B.PD_ORDER_BRICKS, 1)]
+    tol = 1e-13 if precision == PD_FP64 else 1e-5
+    for k, u in res.items():
+        assert rel(u, ref) <= tol, (k, rel(u, ref))
+
+
 # --------------------------------------------------------------------------------- edge cases
 def test_single_particle_and_ragged_sizes():
     for nx, ny in ((1, 1), (33, 1), (7, 5)):
