@@ -108,10 +108,14 @@ typedef enum {
   PD_OPT_VALIDATE = 3,     /* PD_MIXED: 1 = also decide every bond in FP64 and count mismatches */
   PD_OPT_BLOCK = 4,        /* threads per block of the step kernels (multiple of 32, <= 512) */
   PD_OPT_SPLIT = 5,        /* warps cooperating on one 32-particle slice: 1, 2 or 4 */
-  PD_OPT_BOND_CACHE = 6    /* PD_FP64: 1 (default) = keep a per-bond table of the reference
+  PD_OPT_BOND_CACHE = 6,   /* PD_FP64: 1 (default) = keep a per-bond table of the reference
                               geometry (xi, 1/|xi|^2, s0 |xi|^2; 40 bytes per bond slot) so each
                               step evaluates only displacement-dependent FP64 terms; 0 = recompute
                               the geometry from the coordinates every step */
+  PD_OPT_STAGE = 7         /* PD_MIXED with split 1: 1 (default) = stream each warp's neighbour
+                              indices and status words into shared memory with bulk asynchronous
+                              copies (bounded waits; an expired wait makes the next pd_sync /
+                              pd_get_* return PD_ERR_TIMEOUT); 0 = direct loads */
 } pd_option;
 
 /* Kernel identifiers for pd_get_profile. */

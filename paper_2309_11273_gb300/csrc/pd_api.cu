@@ -52,8 +52,9 @@ void free_build(pd_ctx* c) {
   c->vel = c->bacc = c->gvec = nullptr;
   c->flag = nullptr;
   c->pos32 = nullptr;
-  c->bc = nullptr;
-  c->bt = nullptr;
+  c->bA = nullptr;
+  c->bB = nullptr;
+  c->bd = nullptr;
   c->u32[0] = c->u32[1] = nullptr;
   c->thm32 = nullptr;
   c->mu32 = c->aA32 = c->theta32 = nullptr;
@@ -316,7 +317,7 @@ pd_status pd_sync(pd_ctx* c) {
   pd_status st = check_ctx(c, false);
   if (st != PD_OK) return st;
   PD_CUDA(cudaStreamSynchronize(c->stream));
-  return PD_OK;
+  return c->built ? check_device_error(c) : PD_OK;
 }
 
 pd_status pd_get_damage(pd_ctx* c, double* phi) {
@@ -324,6 +325,7 @@ pd_status pd_get_damage(pd_ctx* c, double* phi) {
   if (st != PD_OK) return st;
   if (!phi) return fail(PD_ERR_ARG, "phi is NULL");
   if ((st = launch_refresh_check(c)) != PD_OK) return st;
+  if ((st = check_device_error(c)) != PD_OK) return st;
   if ((st = launch_damage(c, c->scratch)) != PD_OK) return st;
   PD_CUDA(cudaMemcpyAsync(phi, c->scratch, sizeof(double) * c->n, cudaMemcpyDeviceToHost, c->stream));
   PD_CUDA(cudaStreamSynchronize(c->stream));
@@ -334,6 +336,7 @@ pd_status pd_get_state(pd_ctx* c, double* u, double* v, double* theta) {
   pd_status st = check_ctx(c, true);
   if (st != PD_OK) return st;
   if ((st = launch_refresh_check(c)) != PD_OK) return st;
+  if ((st = check_device_error(c)) != PD_OK) return st;
   if (u) {
     if ((st = download_field(c, c->disp[c->cur], u, c->dim)) != PD_OK) return st;
     PD_CUDA(cudaStreamSynchronize(c->stream));
@@ -458,6 +461,9 @@ pd_status pd_set_option(pd_ctx* c, int32_t option, int64_t value) {
     case PD_OPT_BOND_CACHE:
       c->bond_cache = value != 0;
       break;
+    case PD_OPT_STAGE:
+      c->stage = value != 0;
+      break;
     default:
       return fail(PD_ERR_ARG, "unknown option");
   }
@@ -476,6 +482,7 @@ pd_status pd_get_option(pd_ctx* c, int32_t option, int64_t* value) {
     case PD_OPT_BLOCK: *value = c->block; break;
     case PD_OPT_SPLIT: *value = c->split; break;
     case PD_OPT_BOND_CACHE: *value = c->bond_cache; break;
+    case PD_OPT_STAGE: *value = c->stage; break;
     default: return fail(PD_ERR_ARG, "unknown option");
   }
   return PD_OK;
@@ -577,7 +584,7 @@ pd_status pd_autotune(pd_ctx* c, int32_t trial_steps, int32_t* block_out, int32_
     c->profile = 0;
     c->graph_chunk = 0;
     double best_ms = 1e300;
-    const int blocks[] = {128, 256, 512};
+    const int blocks[] = {64, 128, 256, 512};
     const int splits[] = {1, 2, 4};
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);

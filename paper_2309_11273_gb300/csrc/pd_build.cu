@@ -419,7 +419,7 @@ pd_status create(pd_ctx** out, int32_t nbodies, const pd_params* prm, const int6
   PD_TRY(alloc(c, &c->bp, nbodies));
   PD_TRY(alloc(c, &c->perm_dev, n));
   PD_TRY(alloc(c, &c->d_step, 1));
-  PD_TRY(alloc(c, &c->counters, 4));
+  PD_TRY(alloc(c, &c->counters, 8));
   PD_TRY(alloc(c, &c->scratch, (size_t)c->n_pad * 3));
   if (cudaMemcpyAsync(c->pos, hpos.data(), sizeof(double4) * c->n_pad, cudaMemcpyHostToDevice, c->stream) !=
           cudaSuccess ||
@@ -427,7 +427,7 @@ pd_status create(pd_ctx** out, int32_t nbodies, const pd_params* prm, const int6
                       c->stream) != cudaSuccess ||
       cudaMemcpyAsync(c->perm_dev, hperm.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, c->stream) !=
           cudaSuccess ||
-      cudaMemsetAsync(c->counters, 0, sizeof(unsigned long long) * 4, c->stream) != cudaSuccess ||
+      cudaMemsetAsync(c->counters, 0, sizeof(unsigned long long) * 8, c->stream) != cudaSuccess ||
       cudaStreamSynchronize(c->stream) != cudaSuccess) {
     st = cuda_fail(cudaGetLastError(), "upload of particles");
     goto failed;
@@ -662,7 +662,9 @@ pd_status build_neighbors(pd_ctx* c, const pd_crack* cracks, int32_t ncracks) {
     PD_CUDA(cudaMemcpyAsync(hcnt.data(), c->cnt, sizeof(int32_t) * n_pad, cudaMemcpyDeviceToHost, s));
     PD_CUDA(cudaStreamSynchronize(s));
     std::vector<int64_t> sptr(c->nslices + 1, 0);
-    for (int64_t t = 0; t < c->nslices; ++t) sptr[t + 1] = sptr[t] + 32 * (int64_t)width[t];
+    // slot counts rounded up to a multiple of 4: every slice's status words then start on a
+    // 16-byte boundary, as the bulk copies of the staged kernels require
+    for (int64_t t = 0; t < c->nslices; ++t) sptr[t + 1] = sptr[t] + 32 * (((int64_t)width[t] + 3) & ~3LL);
     c->nentries = sptr[c->nslices];
     c->nbonds = 0;
     for (int64_t k = 0; k < n; ++k) c->nbonds += hcnt[k];

@@ -66,12 +66,13 @@ struct StepArgs {
   float* mu32;             // 1 / m_i in FP32
   float* aA32;             // A / m_i * Q in FP32 (Q folded in)
   float* theta32;          // theta_i in FP32
-  unsigned long long* counters;  // [0] band rechecks, [1] validate mismatches
+  unsigned long long* counters;  // [0] band rechecks, [1] validate mismatches, [2..3] max |u|, [4] wait expired
   float band_c;            // safety factor of the band
   int validate;            // mixed: also decide every bond in FP64 and count mismatches
   int check;               // apply the failure criterion at the head of pass 1
-  const double4* bc;       // cached FP64 path: per slot (xi, 1/|xi|^2), or nullptr
-  const double* bt;        // cached FP64 path: per slot s0 |xi|^2
+  const double4* bA;       // tabled FP64 path: per slot (xi, s0 |xi|^2), or nullptr
+  const double4* bB;       // tabled FP64 path: per slot (V_j xi, 1 / |xi|^2)
+  double* bd;              // tabled FP64 path: per slot xi.(u_j - u_i), written by pass 1
 };
 
 struct KernelTimes {
@@ -127,9 +128,11 @@ struct pd_ctx {
   float* aA32 = nullptr;
   float* theta32 = nullptr;
   unsigned long long* counters = nullptr;
-  double4* bc = nullptr;          // FP64 per-slot geometry table (xi, 1/|xi|^2)
-  double* bt = nullptr;           // FP64 per-slot s0 |xi|^2
+  double4* bA = nullptr;          // FP64 per-slot table (xi, s0 |xi|^2)
+  double4* bB = nullptr;          // FP64 per-slot table (V_j xi, 1/|xi|^2)
+  double* bd = nullptr;           // FP64 per-slot xi.du of the current step
   int bond_cache = 1;             // use the table in the FP64 path
+  int stage = 1;                  // mixed path: TMA-staged index streams (split 1)
   double q = 0.0;               // fixed-point quantum of the mixed coordinates [m]
   double qlo[3] = {0, 0, 0};     // origin of the fixed-point coordinates
   // state
@@ -185,6 +188,7 @@ pd_status download_scalar(pd_ctx* c, const double* src, double* host);
 pd_status apply_bc_now(pd_ctx* c);
 pd_status sync_shadow(pd_ctx* c);
 pd_status max_abs_u(pd_ctx* c, double* out, int* nonfinite);
+pd_status check_device_error(pd_ctx* c);
 pd_status run_steps(pd_ctx* c, int64_t nsteps);
 pd_status read_profile(pd_ctx* c);
 }  // namespace pd

@@ -153,10 +153,8 @@ __device__ __forceinline__ void load_slots(const SliceIdx& t, const int32_t* __r
 constexpr int kU64 = 2;
 constexpr int kU32 = 4;
 
-// With CACHE the reference geometry of every slot is read from the per-slot table built once
-// (xi, 1/|xi|^2 and s0 |xi|^2 in FP64), so the FP64 pipe -- GB300's scarcest unit, 1/64 of the FP32
-// rate -- only evaluates the displacement-dependent terms; V_j rides in the .w lane of u_j.
-template <int DIM, int SPLIT, bool CACHE>
+// Plain FP64 kernels: the reference geometry of each bond is recomputed from the coordinates.
+template <int DIM, int SPLIT>
 __global__ void __launch_bounds__(512) k_pass1_f64(StepArgs a, const double4* __restrict__ disp,
                                                     int write_theta) {
   const SliceIdx t = slice_index<SPLIT>(a.n_pad, a.slice_ptr);
@@ -170,47 +168,34 @@ __global__ void __launch_bounds__(512) k_pass1_f64(StepArgs a, const double4* __
     const double4 pi = a.pos[t.i], ui = disp[t.i];
     uint32_t* __restrict__ bw = a.bits + (t.base >> 5);
     const int32_t* __restrict__ cl = a.col + t.base + t.lane;
-    const double4* __restrict__ ce = a.bc + t.base + t.lane;
-    const double* __restrict__ ct = a.bt + t.base + t.lane;
     constexpr int U = kU64;
     int32_t jn[U];
     uint32_t wn[U];
     load_slots<U, SPLIT>(t, cl, bw, t.sub, jn, wn);
     for (int k0 = t.sub; k0 < t.W; k0 += U * SPLIT) {
       uint32_t wd[U];
-      double4 gj[U], uj[U];
-      double tq[U];
+      double4 pj[U], uj[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const int k = min(k0 + u * SPLIT, t.W - 1);
         wd[u] = wn[u];
-        gj[u] = CACHE ? ce[(int64_t)k << 5] : a.pos[jn[u]];
-        if (CACHE) tq[u] = ct[(int64_t)k << 5];
+        pj[u] = a.pos[jn[u]];
         uj[u] = disp[jn[u]];
       }
       load_slots<U, SPLIT>(t, cl, bw, k0 + U * SPLIT, jn, wn);
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         double ex, ey, ez, d, q;
-        if (CACHE) {
-          ex = gj[u].x;
-          ey = gj[u].y;
-          ez = gj[u].z;
-          d = ex * (uj[u].x - ui.x) + ey * (uj[u].y - ui.y);
-          if (DIM == 3) d = fma(ez, uj[u].z - ui.z, d);
-        } else {
-          bond_f64<DIM>(pi, gj[u], ui, uj[u], ex, ey, ez, d, q);
-        }
+        bond_f64<DIM>(pi, pj[u], ui, uj[u], ex, ey, ez, d, q);
         bool intact = (wd[u] >> t.lane) & 1u;
         if (a.check) {
-          const bool brk = intact && can_break && d >= (CACHE ? tq[u] : s0 * q);
+          const bool brk = intact && can_break && d >= s0 * q;
           const unsigned m = __ballot_sync(kFull, brk);
           if (m) {
             intact = intact && !brk;
             if (t.lane == 0) bw[k0 + u * SPLIT] = wd[u] & ~m;
           }
         }
-        acc[0] += intact ? uj[u].w * d : 0.0;
+        acc[0] = fma(intact ? pj[u].w : 0.0, d, acc[0]);
       }
     }
   }
@@ -224,7 +209,7 @@ __global__ void __launch_bounds__(512) k_pass1_f64(StepArgs a, const double4* __
   }
 }
 
-template <int DIM, int SPLIT, bool CACHE>
+template <int DIM, int SPLIT>
 __global__ void __launch_bounds__(512) k_pass2_f64(StepArgs a, const double4* __restrict__ disp,
                                                     double4* __restrict__ disp_out) {
   const SliceIdx t = slice_index<SPLIT>(a.n_pad, a.slice_ptr);
@@ -236,40 +221,29 @@ __global__ void __launch_bounds__(512) k_pass2_f64(StepArgs a, const double4* __
     const double2 ti = a.thm[t.i];
     const uint32_t* __restrict__ bw = a.bits + (t.base >> 5);
     const int32_t* __restrict__ cl = a.col + t.base + t.lane;
-    const double4* __restrict__ ce = a.bc + t.base + t.lane;
     constexpr int U = kU64;
     int32_t jn[U];
     uint32_t wn[U];
     load_slots<U, SPLIT>(t, cl, bw, t.sub, jn, wn);
     for (int k0 = t.sub; k0 < t.W; k0 += U * SPLIT) {
       uint32_t wd[U];
-      double4 gj[U], uj[U];
+      double4 pj[U], uj[U];
       double2 tj[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const int k = min(k0 + u * SPLIT, t.W - 1);
         wd[u] = wn[u];
-        gj[u] = CACHE ? ce[(int64_t)k << 5] : a.pos[jn[u]];
+        pj[u] = a.pos[jn[u]];
         uj[u] = disp[jn[u]];
         tj[u] = a.thm[jn[u]];
       }
       load_slots<U, SPLIT>(t, cl, bw, k0 + U * SPLIT, jn, wn);
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        double ex, ey, ez, d, q, r;
-        if (CACHE) {
-          ex = gj[u].x;
-          ey = gj[u].y;
-          ez = gj[u].z;
-          r = gj[u].w;
-          d = ex * (uj[u].x - ui.x) + ey * (uj[u].y - ui.y);
-          if (DIM == 3) d = fma(ez, uj[u].z - ui.z, d);
-        } else {
-          bond_f64<DIM>(pi, gj[u], ui, uj[u], ex, ey, ez, d, q);
-        }
+        double ex, ey, ez, d, q;
+        bond_f64<DIM>(pi, pj[u], ui, uj[u], ex, ey, ez, d, q);
         // Eq 2.2: [(K - G/3)(theta_i/m_i + theta_j/m_j) + G (1/m_i + 1/m_j) xi.du / |xi|^2] V_j xi
-        double c = fma(ti.y + tj[u].y, CACHE ? d * r : d / q, ti.x + tj[u].x);
-        c = ((wd[u] >> t.lane) & 1u) ? c * uj[u].w : 0.0;
+        double c = fma(ti.y + tj[u].y, d / q, ti.x + tj[u].x);
+        c = ((wd[u] >> t.lane) & 1u) ? c * pj[u].w : 0.0;
         f[0] = fma(c, ex, f[0]);
         f[1] = fma(c, ey, f[1]);
         if (DIM == 3) f[2] = fma(c, ez, f[2]);
@@ -283,10 +257,124 @@ __global__ void __launch_bounds__(512) k_pass2_f64(StepArgs a, const double4* __
   }
 }
 
-// Per-slot reference geometry for the cached FP64 path: (xi, 1/|xi|^2) and s0 |xi|^2, with xi and
-// |xi|^2 evaluated exactly as bond_f64 does (so both variants decide a bond identically).
+// Tabled FP64 kernels.  GB300 issues FP64 at 1/64 of the FP32 rate, so everything that does not
+// depend on the displacement is computed once per family into per-slot tables:
+//   bA = (xi, s0 |xi|^2)            read by pass 1 (the break test xi.du >= s0 |xi|^2, Eq 1.30);
+//   bB = (V_j xi, 1 / |xi|^2)       read by pass 2;
+// and pass 1 stores each slot's xi.du (the per-bond extension times |xi|, the paper's E array of
+// Appendix B) in bd for pass 2, which then needs neither u_j nor a divide: per bond it issues
+// 7 FP64 instructions instead of 14, and pass 1 8 instead of 15.
+template <int DIM, int SPLIT>
+__global__ void __launch_bounds__(512) k_pass1_f64t(StepArgs a, const double4* __restrict__ disp,
+                                                     int write_theta) {
+  const SliceIdx t = slice_index<SPLIT>(a.n_pad, a.slice_ptr);
+  if (write_theta && blockIdx.x == 0 && threadIdx.x == 0) *a.d_step += 1;
+  double acc[1] = {0.0};
+  int b = 0;
+  if (t.active) {
+    b = a.body ? a.body[t.i] : 0;
+    const bool can_break = a.bp[b].s0 > 0.0;
+    const double4 ui = disp[t.i];
+    uint32_t* __restrict__ bw = a.bits + (t.base >> 5);
+    const int32_t* __restrict__ cl = a.col + t.base + t.lane;
+    const double4* __restrict__ ta = a.bA + t.base + t.lane;
+    double* __restrict__ td = a.bd + t.base + t.lane;
+    constexpr int U = kU64;
+    int32_t jn[U];
+    uint32_t wn[U];
+    load_slots<U, SPLIT>(t, cl, bw, t.sub, jn, wn);
+    for (int k0 = t.sub; k0 < t.W; k0 += U * SPLIT) {
+      uint32_t wd[U];
+      double4 g[U], uj[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int k = min(k0 + u * SPLIT, t.W - 1);
+        wd[u] = wn[u];
+        g[u] = ta[(int64_t)k << 5];
+        uj[u] = disp[jn[u]];
+      }
+      load_slots<U, SPLIT>(t, cl, bw, k0 + U * SPLIT, jn, wn);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        double d = g[u].x * (uj[u].x - ui.x) + g[u].y * (uj[u].y - ui.y);
+        if (DIM == 3) d = fma(g[u].z, uj[u].z - ui.z, d);
+        const int k = k0 + u * SPLIT;
+        if (k < t.W) td[(int64_t)k << 5] = d;
+        bool intact = (wd[u] >> t.lane) & 1u;
+        if (a.check) {
+          const bool brk = intact && can_break && d >= g[u].w;
+          const unsigned m = __ballot_sync(kFull, brk);
+          if (m) {
+            intact = intact && !brk;
+            if (t.lane == 0) bw[k] = wd[u] & ~m;
+          }
+        }
+        acc[0] = fma(intact ? uj[u].w : 0.0, d, acc[0]);
+      }
+    }
+  }
+  split_reduce<SPLIT, 1>(acc);
+  if (t.active && t.sub == 0 && write_theta) {
+    const double th = a.aA[t.i] * acc[0];
+    const double mu = a.mu[t.i];
+    a.theta[t.i] = th;
+    a.thm[t.i] = make_double2(a.bp[b].Kp * (th * mu), a.bp[b].G * mu);
+  }
+}
+
+template <int DIM, int SPLIT>
+__global__ void __launch_bounds__(512) k_pass2_f64t(StepArgs a, const double4* __restrict__ disp,
+                                                     double4* __restrict__ disp_out) {
+  const SliceIdx t = slice_index<SPLIT>(a.n_pad, a.slice_ptr);
+  double f[3] = {0.0, 0.0, 0.0};
+  int b = 0;
+  if (t.active) {
+    b = a.body ? a.body[t.i] : 0;
+    const double2 ti = a.thm[t.i];
+    const uint32_t* __restrict__ bw = a.bits + (t.base >> 5);
+    const int32_t* __restrict__ cl = a.col + t.base + t.lane;
+    const double4* __restrict__ tb = a.bB + t.base + t.lane;
+    const double* __restrict__ td = a.bd + t.base + t.lane;
+    constexpr int U = 4;
+    int32_t jn[U];
+    uint32_t wn[U];
+    load_slots<U, SPLIT>(t, cl, bw, t.sub, jn, wn);
+    for (int k0 = t.sub; k0 < t.W; k0 += U * SPLIT) {
+      uint32_t wd[U];
+      double4 g[U];
+      double d[U];
+      double2 tj[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int k = min(k0 + u * SPLIT, t.W - 1);
+        wd[u] = wn[u];
+        g[u] = tb[(int64_t)k << 5];
+        d[u] = td[(int64_t)k << 5];
+        tj[u] = a.thm[jn[u]];
+      }
+      load_slots<U, SPLIT>(t, cl, bw, k0 + U * SPLIT, jn, wn);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        // Eq 2.2 with V_j folded into the tabled xi: [(K - G/3) theta~ + G e~ / |xi|] (V_j xi)
+        double c = fma(ti.y + tj[u].y, d[u] * g[u].w, ti.x + tj[u].x);
+        c = ((wd[u] >> t.lane) & 1u) ? c : 0.0;
+        f[0] = fma(c, g[u].x, f[0]);
+        f[1] = fma(c, g[u].y, f[1]);
+        if (DIM == 3) f[2] = fma(c, g[u].z, f[2]);
+      }
+    }
+  }
+  split_reduce<SPLIT, 3>(f);
+  if (t.active && t.sub == 0) {
+    double4 u;
+    update(a, t.i, b, f, disp, disp_out, u);
+  }
+}
+
+// Per-slot tables of the tabled FP64 path, with xi and |xi|^2 evaluated exactly as bond_f64 does
+// (so both FP64 variants decide a bond identically).
 template <int DIM>
-__global__ void k_bond_cache(StepArgs a, double4* __restrict__ bc, double* __restrict__ bt) {
+__global__ void k_bond_tables(StepArgs a, double4* __restrict__ bA, double4* __restrict__ bB) {
   const SliceIdx t = slice_index<1>(a.n_pad, a.slice_ptr);
   if (!t.active) return;
   const int b = a.body ? a.body[t.i] : 0;
@@ -296,10 +384,11 @@ __global__ void k_bond_cache(StepArgs a, double4* __restrict__ bc, double* __res
   for (int k = 0; k < t.W; ++k) {
     const int64_t e = t.base + t.lane + ((int64_t)k << 5);
     const int32_t j = a.col[e];
+    const double4 pj = a.pos[j];
     double ex, ey, ez, d, q;
-    bond_f64<DIM>(pi, a.pos[j], zero, zero, ex, ey, ez, d, q);
-    bc[e] = make_double4(ex, ey, ez, q > 0.0 ? 1.0 / q : 0.0);
-    bt[e] = s0 * q;
+    bond_f64<DIM>(pi, pj, zero, zero, ex, ey, ez, d, q);
+    bA[e] = make_double4(ex, ey, ez, s0 * q);
+    bB[e] = make_double4(pj.w * ex, pj.w * ey, pj.w * ez, q > 0.0 ? 1.0 / q : 0.0);
   }
 }
 
@@ -449,6 +538,258 @@ __global__ void __launch_bounds__(512) k_pass2_mixed(StepArgs a, const float4* _
   }
 }
 
+// ------------------------------------------------------------ mixed path, TMA-staged index stream
+// The neighbour indices and status words of a warp's slice are one contiguous stream.  Lane 0 keeps
+// kStageBuf chunks of kStageCh slots in flight with 1D bulk copies (cp.async.bulk, completion on an
+// mbarrier) into the warp's shared-memory ring, so the DRAM stream runs far ahead of the gathers,
+// which read their indices from shared memory.  Every wait is bounded: on expiry the kernel records
+// an error word, drains (again bounded) the copies it issued and skips its outputs.
+constexpr int kStageCh = 16;   // slots per chunk: 2 KB of indices + 64 B of status words
+constexpr int kStageBuf = 3;   // chunks in flight per warp
+constexpr int kStageWarpBytes = kStageBuf * (kStageCh * 128 + kStageCh * 4) + 64;
+constexpr unsigned kWaitLimit = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_to_smem(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  for (unsigned it = 0; it < kWaitLimit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+struct Stage {
+  uint64_t* bar;    // kStageBuf barriers
+  int32_t* col;     // kStageBuf x kStageCh x 32 indices
+  uint32_t* words;  // kStageBuf x kStageCh status words
+  const int32_t* gcol;
+  const uint32_t* gwords;
+  int W, nchunks, issued;
+};
+
+__device__ __forceinline__ Stage stage_init(unsigned char* smem, const SliceIdx& t, const StepArgs& a) {
+  Stage st;
+  unsigned char* base = smem + (threadIdx.x >> 5) * kStageWarpBytes;
+  st.bar = reinterpret_cast<uint64_t*>(base);
+  st.col = reinterpret_cast<int32_t*>(base + 64);
+  st.words = reinterpret_cast<uint32_t*>(base + 64 + kStageBuf * kStageCh * 128);
+  st.gcol = a.col + t.base;
+  st.gwords = a.bits + (t.base >> 5);
+  st.W = t.W;
+  st.nchunks = (t.W + kStageCh - 1) / kStageCh;
+  st.issued = 0;
+  if ((threadIdx.x & 31) == 0)
+    for (int b = 0; b < kStageBuf; ++b) mbar_init(&st.bar[b], 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  __syncwarp();
+  return st;
+}
+
+// Lane 0: start the copy of chunk c into buffer c % kStageBuf.
+__device__ __forceinline__ void stage_issue(Stage& st, int c) {
+  const int b = c % kStageBuf;
+  const int k0 = c * kStageCh;
+  const int n = min(kStageCh, st.W - k0);  // a multiple of 4 (slot counts are)
+  const unsigned cb = (unsigned)n * 128u, wb = (unsigned)n * 4u;
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  mbar_expect_tx(&st.bar[b], cb + wb);
+  bulk_to_smem(st.col + b * kStageCh * 32, st.gcol + (int64_t)k0 * 32, cb, &st.bar[b]);
+  bulk_to_smem(st.words + b * kStageCh, st.gwords + k0, wb, &st.bar[b]);
+}
+
+// After a failed wait: wait (bounded) for every chunk still in flight, so that no copy lands in
+// shared memory after the block has moved on.
+__device__ __forceinline__ void stage_drain(Stage& st, int from) {
+  for (int c = from; c < st.issued; ++c) mbar_wait(&st.bar[c % kStageBuf], (unsigned)((c / kStageBuf) & 1));
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(512) k_pass1_mixed_staged(StepArgs a, const float4* __restrict__ u32,
+                                                             const double4* __restrict__ disp, int write_theta) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const SliceIdx t = slice_index<1>(a.n_pad, a.slice_ptr);
+  if (write_theta && blockIdx.x == 0 && threadIdx.x == 0) *a.d_step += 1;
+  if (!t.active) return;  // whole warps: the staging below is per warp
+  Stage st = stage_init(smem, t, a);
+  const int lane = t.lane;
+  const int b = a.body ? a.body[t.i] : 0;
+  const double s0 = a.bp[b].s0;
+  const float sig = a.bp[b].sigma32;
+  const bool can_break = s0 > 0.0;
+  const int4 Pi = a.pos32[t.i];
+  const float4 Ui = u32[t.i];
+  const float ui1 = fabsf(Ui.x) + fabsf(Ui.y) + (DIM == 3 ? fabsf(Ui.z) : 0.0f);
+  uint32_t* __restrict__ bw = a.bits + (t.base >> 5);
+  if (lane == 0)
+    for (; st.issued < min(kStageBuf, st.nchunks); ++st.issued) stage_issue(st, st.issued);
+  float acc = 0.0f;
+  bool ok = true;
+  for (int c = 0; c < st.nchunks; ++c) {
+    const int buf = c % kStageBuf;
+    if (!mbar_wait(&st.bar[buf], (unsigned)((c / kStageBuf) & 1))) {
+      ok = false;
+      if (lane == 0) atomicExch(&a.counters[4], 1ull);
+      stage_drain(st, c + 1);
+      break;
+    }
+    const int32_t* cs = st.col + buf * kStageCh * 32 + lane;
+    const uint32_t* ws = st.words + buf * kStageCh;
+    const int k0 = c * kStageCh;
+    const int n = min(kStageCh, st.W - k0);
+    constexpr int U = kU32;
+    for (int kk = 0; kk < n; kk += U) {
+      int4 Pj[U];
+      float4 Uj[U];
+      int32_t j[U];
+      uint32_t wd[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {  // n is a multiple of 4 = U
+        j[u] = cs[(kk + u) * 32];
+        wd[u] = ws[kk + u];
+        Pj[u] = a.pos32[j[u]];
+        Uj[u] = u32[j[u]];
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const float ex = (float)(Pj[u].x - Pi.x), ey = (float)(Pj[u].y - Pi.y);
+        const float ez = DIM == 3 ? (float)(Pj[u].z - Pi.z) : 0.0f;
+        const float dx = Uj[u].x - Ui.x, dy = Uj[u].y - Ui.y, dz = DIM == 3 ? Uj[u].z - Ui.z : 0.0f;
+        float d = ex * dx + ey * dy;
+        if (DIM == 3) d = fmaf(ez, dz, d);
+        bool intact = (wd[u] >> lane) & 1u;
+        if (a.check) {
+          bool brk = false;
+          if (intact && can_break) {
+            float q = ex * ex + ey * ey;
+            if (DIM == 3) q = fmaf(ez, ez, q);
+            const float g = fmaf(-sig, q, d);
+            const float xi1 = fabsf(ex) + fabsf(ey) + fabsf(ez);
+            const float du1 = fabsf(dx) + fabsf(dy) + fabsf(dz);
+            const float B = a.band_c * (1.01f * du1 + sig * (2.01f * xi1 + 3.02f) +
+                                        5.9604645e-8f * (xi1 * (2.0f * ui1 + 6.0f * du1) + 6.0f * sig * q +
+                                                         fabsf(g)));
+            if (fabsf(g) > B) {
+              brk = g >= 0.0f;
+            } else {
+              brk = fp64_breaks<DIM>(a, t.i, j[u], disp, s0);
+              atomicAdd(&a.counters[0], 1ull);
+            }
+            if (a.validate && brk != fp64_breaks<DIM>(a, t.i, j[u], disp, s0)) atomicAdd(&a.counters[1], 1ull);
+          }
+          const unsigned m = __ballot_sync(kFull, brk);
+          if (m) {
+            intact = intact && !brk;
+            if (lane == 0) bw[k0 + kk + u] = wd[u] & ~m;
+          }
+        }
+        acc += intact ? __int_as_float(Pj[u].w) * d : 0.0f;
+      }
+    }
+    __syncwarp();  // every lane is done with this buffer before it is refilled
+    if (lane == 0 && st.issued < st.nchunks) stage_issue(st, st.issued++);
+  }
+  if (ok && write_theta) {
+    const float th = a.aA32[t.i] * acc;
+    const float mu = a.mu32[t.i];
+    a.theta32[t.i] = th;
+    a.thm32[t.i] = make_float2(a.bp[b].Kp32 * (th * mu), a.bp[b].G32 * mu);
+  }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(512) k_pass2_mixed_staged(StepArgs a, const float4* __restrict__ u32,
+                                                             float4* __restrict__ u32_out,
+                                                             const double4* __restrict__ disp,
+                                                             double4* __restrict__ disp_out) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const SliceIdx t = slice_index<1>(a.n_pad, a.slice_ptr);
+  if (!t.active) return;
+  Stage st = stage_init(smem, t, a);
+  const int lane = t.lane;
+  const int b = a.body ? a.body[t.i] : 0;
+  const int4 Pi = a.pos32[t.i];
+  const float4 Ui = u32[t.i];
+  const float2 ti = a.thm32[t.i];
+  if (lane == 0)
+    for (; st.issued < min(kStageBuf, st.nchunks); ++st.issued) stage_issue(st, st.issued);
+  float f[3] = {0.0f, 0.0f, 0.0f};
+  bool ok = true;
+  for (int c = 0; c < st.nchunks; ++c) {
+    const int buf = c % kStageBuf;
+    if (!mbar_wait(&st.bar[buf], (unsigned)((c / kStageBuf) & 1))) {
+      ok = false;
+      if (lane == 0) atomicExch(&a.counters[4], 1ull);
+      stage_drain(st, c + 1);
+      break;
+    }
+    const int32_t* cs = st.col + buf * kStageCh * 32 + lane;
+    const uint32_t* ws = st.words + buf * kStageCh;
+    const int n = min(kStageCh, st.W - c * kStageCh);
+    constexpr int U = kU32;
+    for (int kk = 0; kk < n; kk += U) {
+      int4 Pj[U];
+      float4 Uj[U];
+      float2 tj[U];
+      uint32_t wd[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int32_t j = cs[(kk + u) * 32];
+        wd[u] = ws[kk + u];
+        Pj[u] = a.pos32[j];
+        Uj[u] = u32[j];
+        tj[u] = a.thm32[j];
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const float ex = (float)(Pj[u].x - Pi.x), ey = (float)(Pj[u].y - Pi.y);
+        const float ez = DIM == 3 ? (float)(Pj[u].z - Pi.z) : 0.0f;
+        float d = ex * (Uj[u].x - Ui.x) + ey * (Uj[u].y - Ui.y);
+        float q = ex * ex + ey * ey;
+        if (DIM == 3) {
+          d = fmaf(ez, Uj[u].z - Ui.z, d);
+          q = fmaf(ez, ez, q);
+        }
+        float cf = fmaf(ti.y + tj[u].y, d * __frcp_rn(q), ti.x + tj[u].x);
+        cf = ((wd[u] >> lane) & 1u) ? cf * __int_as_float(Pj[u].w) : 0.0f;
+        f[0] = fmaf(cf, ex, f[0]);
+        f[1] = fmaf(cf, ey, f[1]);
+        if (DIM == 3) f[2] = fmaf(cf, ez, f[2]);
+      }
+    }
+    __syncwarp();
+    if (lane == 0 && st.issued < st.nchunks) stage_issue(st, st.issued++);
+  }
+  if (ok) {
+    const double fd[3] = {(double)f[0], (double)f[1], (double)f[2]};
+    double4 u;
+    update(a, t.i, b, fd, disp, disp_out, u);
+    u32_out[t.i] = make_float4((float)u.x, (float)u.y, (float)u.z, 0.0f);
+  }
+}
+
 // ----------------------------------------------------------------------------- auxiliary kernels
 __global__ void k_set_step(int64_t* d_step, int64_t v) { *d_step = v; }
 
@@ -588,27 +929,28 @@ StepArgs make_args(pd_ctx* c) {
   a.band_c = (float)bc;
   a.validate = c->validate;
   a.check = 1;
-  a.bc = c->bond_cache ? c->bc : nullptr;
-  a.bt = c->bond_cache ? c->bt : nullptr;
+  a.bA = c->bond_cache ? c->bA : nullptr;
+  a.bB = c->bond_cache ? c->bB : nullptr;
+  a.bd = c->bond_cache ? c->bd : nullptr;
   return a;
 }
 
 template <int DIM, int SPLIT>
 void launch_pass1(pd_ctx* c, const StepArgs& a, int write_theta, unsigned grid, int block, size_t sm) {
-  if (c->precision == PD_FP64 && a.bc)
-    k_pass1_f64<DIM, SPLIT, true><<<grid, block, sm, c->stream>>>(a, c->disp[c->cur], write_theta);
+  if (c->precision == PD_FP64 && a.bA)
+    k_pass1_f64t<DIM, SPLIT><<<grid, block, sm, c->stream>>>(a, c->disp[c->cur], write_theta);
   else if (c->precision == PD_FP64)
-    k_pass1_f64<DIM, SPLIT, false><<<grid, block, sm, c->stream>>>(a, c->disp[c->cur], write_theta);
+    k_pass1_f64<DIM, SPLIT><<<grid, block, sm, c->stream>>>(a, c->disp[c->cur], write_theta);
   else
     k_pass1_mixed<DIM, SPLIT><<<grid, block, sm, c->stream>>>(a, c->u32[c->cur], c->disp[c->cur], write_theta);
 }
 
 template <int DIM, int SPLIT>
 void launch_pass2(pd_ctx* c, const StepArgs& a, unsigned grid, int block, size_t sm) {
-  if (c->precision == PD_FP64 && a.bc)
-    k_pass2_f64<DIM, SPLIT, true><<<grid, block, sm, c->stream>>>(a, c->disp[c->cur], c->disp[c->cur ^ 1]);
+  if (c->precision == PD_FP64 && a.bA)
+    k_pass2_f64t<DIM, SPLIT><<<grid, block, sm, c->stream>>>(a, c->disp[c->cur], c->disp[c->cur ^ 1]);
   else if (c->precision == PD_FP64)
-    k_pass2_f64<DIM, SPLIT, false><<<grid, block, sm, c->stream>>>(a, c->disp[c->cur], c->disp[c->cur ^ 1]);
+    k_pass2_f64<DIM, SPLIT><<<grid, block, sm, c->stream>>>(a, c->disp[c->cur], c->disp[c->cur ^ 1]);
   else
     k_pass2_mixed<DIM, SPLIT>
         <<<grid, block, sm, c->stream>>>(a, c->u32[c->cur], c->u32[c->cur ^ 1], c->disp[c->cur], c->disp[c->cur ^ 1]);
@@ -620,6 +962,25 @@ void dispatch_pass(pd_ctx* c, const StepArgs& a, int pass, int write_theta) {
   const int split = c->split;
   const int64_t threads = c->nslices * 32 * (int64_t)split;
   const unsigned grid = (unsigned)((threads + block - 1) / block);
+  if (c->precision == PD_MIXED && split == 1 && c->stage) {
+    const size_t smb = (size_t)(block / 32) * kStageWarpBytes;
+    static bool attr_set[4] = {false, false, false, false};
+    const int slot = (DIM == 3 ? 2 : 0) + (pass == 1 ? 0 : 1);
+    if (!attr_set[slot]) {
+      const int maxb = 16 * kStageWarpBytes;
+      if (pass == 1)
+        cudaFuncSetAttribute(k_pass1_mixed_staged<DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb);
+      else
+        cudaFuncSetAttribute(k_pass2_mixed_staged<DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb);
+      attr_set[slot] = true;
+    }
+    if (pass == 1)
+      k_pass1_mixed_staged<DIM><<<grid, block, smb, c->stream>>>(a, c->u32[c->cur], c->disp[c->cur], write_theta);
+    else
+      k_pass2_mixed_staged<DIM><<<grid, block, smb, c->stream>>>(a, c->u32[c->cur], c->u32[c->cur ^ 1],
+                                                                 c->disp[c->cur], c->disp[c->cur ^ 1]);
+    return;
+  }
   const size_t sm = split > 1 ? (size_t)block * 3 * sizeof(double) : 0;
   if (pass == 1) {
     if (split == 1) launch_pass1<DIM, 1>(c, a, write_theta, grid, block, sm);
@@ -652,20 +1013,21 @@ pd_status init_disp_w(pd_ctx* c) {
   return PD_OK;
 }
 
-// Allocates and fills the per-slot geometry table of the cached FP64 path (once per build).
+// Allocates and fills the per-slot tables of the tabled FP64 path (once per build).
 pd_status ensure_bond_cache(pd_ctx* c) {
-  if (!c->bond_cache || c->precision != PD_FP64 || c->bc) return PD_OK;
+  if (!c->bond_cache || c->precision != PD_FP64 || c->bA) return PD_OK;
   pd_status st;
   const size_t ne = (size_t)std::max<int64_t>(c->nentries, 32);
-  if ((st = alloc(c, &c->bc, ne)) != PD_OK) return st;
-  if ((st = alloc(c, &c->bt, ne)) != PD_OK) return st;
+  if ((st = alloc(c, &c->bA, ne)) != PD_OK) return st;
+  if ((st = alloc(c, &c->bB, ne)) != PD_OK) return st;
+  if ((st = alloc(c, &c->bd, ne)) != PD_OK) return st;
   StepArgs a = make_args(c);
   const int tb = 256;
   const unsigned grid = (unsigned)((c->n_pad + tb - 1) / tb);
   if (c->dim == 3)
-    k_bond_cache<3><<<grid, tb, 0, c->stream>>>(a, c->bc, c->bt);
+    k_bond_tables<3><<<grid, tb, 0, c->stream>>>(a, c->bA, c->bB);
   else
-    k_bond_cache<2><<<grid, tb, 0, c->stream>>>(a, c->bc, c->bt);
+    k_bond_tables<2><<<grid, tb, 0, c->stream>>>(a, c->bA, c->bB);
   PD_CUDA(cudaGetLastError());
   return PD_OK;
 }
@@ -791,6 +1153,19 @@ pd_status sync_shadow(pd_ctx* c) {
   const int tb = 256;
   k_shadow<<<(unsigned)((c->n_pad + tb - 1) / tb), tb, 0, c->stream>>>(c->n_pad, c->disp[c->cur], c->u32[c->cur]);
   PD_CUDA(cudaGetLastError());
+  return PD_OK;
+}
+
+// Error word of the staged kernels (a bounded wait expired); cleared after it is reported.
+pd_status check_device_error(pd_ctx* c) {
+  unsigned long long flag = 0;
+  PD_CUDA(cudaMemcpyAsync(&flag, c->counters + 4, sizeof(flag), cudaMemcpyDeviceToHost, c->stream));
+  PD_CUDA(cudaStreamSynchronize(c->stream));
+  if (flag) {
+    PD_CUDA(cudaMemsetAsync(c->counters + 4, 0, sizeof(flag), c->stream));
+    return fail(PD_ERR_TIMEOUT, "a staged neighbour-index copy did not complete within the wait limit; "
+                                "the step's results were not written");
+  }
   return PD_OK;
 }
 
