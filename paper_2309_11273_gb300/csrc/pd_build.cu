@@ -434,6 +434,8 @@ pd_status create(pd_ctx** out, int32_t nbodies, const pd_params* prm, const int6
   }
   {
     // Fixed-point quantum of the mixed path: a power of two with every coordinate offset < 2^30 Q.
+    // (A quantum that makes lattice bond vectors exact was measured to give larger FP32 errors: the
+    // rounding becomes systematic across the symmetric family.)
     double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
     for (int64_t i = 0; i < n; ++i) {
       const double p[3] = {x[i], y[i], z ? z[i] : 0.0};
@@ -472,12 +474,17 @@ pd_status upload_body_params(pd_ctx* c) {
     d.inv_rho = 1.0 / p.rho;
     d.dt = p.dt;
     d.s0 = p.s0;
+    d.breaks = p.s0 > 0.0 ? 1 : 0;
     d.rate = 0.0;
     d.Kp32 = (float)(d.Kp * c->q);
     d.G32 = (float)d.G;
     d.inv_rho32 = (float)d.inv_rho;
     d.sigma_q = p.s0 * c->q;
     d.sigma32 = (float)d.sigma_q;
+    // |xi| <= delta; each fixed-point component of xi is within one quantum of the exact value
+    const double lq = p.horizon / c->q + 2.0;
+    d.xi1max = (float)(std::sqrt((double)c->dim) * lq * 1.0001);
+    d.qmax = (float)(lq * lq * 1.0001);
   }
   for (int b = 0; b < c->nbodies; ++b) h[b].rate = c->rate;
   PD_CUDA(cudaMemcpyAsync(c->bp, h.data(), sizeof(BodyDev) * c->nbodies, cudaMemcpyHostToDevice, c->stream));

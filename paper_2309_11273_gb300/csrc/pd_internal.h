@@ -7,7 +7,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/osbpd.h"
+#include "osbpd.h"
 
 namespace pd {
 
@@ -23,6 +23,9 @@ struct BodyDev {
   double rate;     // prescribed rotation rate
   float Kp32, G32, inv_rho32, sigma32;  // FP32 copies for the mixed path (sigma32 = s0 * Q)
   double sigma_q;  // s0 * Q in double (Q = fixed-point quantum of the mixed coordinates)
+  int32_t breaks;  // 1 if s0 > 0 (bond breaking on), else 0
+  float xi1max;    // upper bound of |xi|_1 in quanta: sqrt(dim) (delta / Q + 2)
+  float qmax;      // upper bound of |xi|^2 in quanta^2: (delta / Q + 2)^2
 };
 
 // Per-body neighbour-search grid (cells of edge >= delta).

@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(512) k_pass1_f64(StepArgs a, const double4* __
   if (t.active) {
     b = a.body ? a.body[t.i] : 0;
     const double s0 = a.bp[b].s0;
-    const bool can_break = s0 > 0.0;
+    const bool can_break = a.bp[b].breaks != 0;
     const double4 pi = a.pos[t.i], ui = disp[t.i];
     uint32_t* __restrict__ bw = a.bits + (t.base >> 5);
     const int32_t* __restrict__ cl = a.col + t.base + t.lane;
@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(512) k_pass1_f64t(StepArgs a, const double4* _
   int b = 0;
   if (t.active) {
     b = a.body ? a.body[t.i] : 0;
-    const bool can_break = a.bp[b].s0 > 0.0;
+    const bool can_break = a.bp[b].breaks != 0;
     const double4 ui = disp[t.i];
     uint32_t* __restrict__ bw = a.bits + (t.base >> 5);
     const int32_t* __restrict__ cl = a.col + t.base + t.lane;
@@ -409,10 +409,17 @@ __global__ void __launch_bounds__(512) k_pass1_mixed(StepArgs a, const float4* _
     b = a.body ? a.body[t.i] : 0;
     const double s0 = a.bp[b].s0;
     const float sig = a.bp[b].sigma32;
-    const bool can_break = s0 > 0.0;
+    const bool can_break = a.bp[b].breaks != 0;
     const int4 Pi = a.pos32[t.i];
     const float4 Ui = u32[t.i];
     const float ui1 = fabsf(Ui.x) + fabsf(Ui.y) + (DIM == 3 ? fabsf(Ui.z) : 0.0f);
+    // Band half-width B (see the comment above k_pass1_mixed) with |xi|_1 and |xi|^2 replaced by
+    // their per-body maxima: B <= du1 k1 + k2 + k3 |g|, two FMAs per bond.
+    const float xim = a.bp[b].xi1max, qm = a.bp[b].qmax;
+    const float band_k1 = a.band_c * fmaf(6.0f * 5.9604645e-8f, xim, 1.01f);
+    const float band_k2 = a.band_c * fmaf(sig, fmaf(2.01f, xim, 3.02f),
+                                          5.9604645e-8f * fmaf(2.0f * xim, ui1, 6.0f * sig * qm));
+    const float band_k3 = a.band_c * 5.9604645e-8f;
     uint32_t* __restrict__ bw = a.bits + (t.base >> 5);
     const int32_t* __restrict__ cl = a.col + t.base + t.lane;
     constexpr int U = kU32;
@@ -432,6 +439,11 @@ __global__ void __launch_bounds__(512) k_pass1_mixed(StepArgs a, const float4* _
         Uj[u] = u32[j[u]];
       }
       load_slots<U, SPLIT>(t, cl, bw, k0 + U * SPLIT, jn, wn);
+      // FP32 decisions of the batch; bonds inside the rounding band are flagged (code 2) and re-decided
+      // in FP64 below, in a warp-uniform block outside the unrolled arithmetic.
+      float dv[U], vj[U];
+      int code[U];
+      bool intact[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const float ex = (float)(Pj[u].x - Pi.x), ey = (float)(Pj[u].y - Pi.y);
@@ -439,34 +451,46 @@ __global__ void __launch_bounds__(512) k_pass1_mixed(StepArgs a, const float4* _
         const float dx = Uj[u].x - Ui.x, dy = Uj[u].y - Ui.y, dz = DIM == 3 ? Uj[u].z - Ui.z : 0.0f;
         float d = ex * dx + ey * dy;
         if (DIM == 3) d = fmaf(ez, dz, d);
-        bool intact = (wd[u] >> t.lane) & 1u;
-        if (a.check) {
-          bool brk = false;
-          if (intact && can_break) {
-            float q = ex * ex + ey * ey;
-            if (DIM == 3) q = fmaf(ez, ez, q);
-            const float g = fmaf(-sig, q, d);
-            const float xi1 = fabsf(ex) + fabsf(ey) + fabsf(ez);
-            const float du1 = fabsf(dx) + fabsf(dy) + fabsf(dz);
-            const float B = a.band_c * (1.01f * du1 + sig * (2.01f * xi1 + 3.02f) +
-                                        5.9604645e-8f * (xi1 * (2.0f * ui1 + 6.0f * du1) + 6.0f * sig * q +
-                                                         fabsf(g)));
-            if (fabsf(g) > B) {
-              brk = g >= 0.0f;
-            } else {
-              brk = fp64_breaks<DIM>(a, t.i, j[u], disp, s0);
+        dv[u] = d;
+        vj[u] = __int_as_float(Pj[u].w);
+        intact[u] = (wd[u] >> t.lane) & 1u;
+        code[u] = 0;
+        if (a.check && can_break && intact[u]) {
+          float q = ex * ex + ey * ey;
+          if (DIM == 3) q = fmaf(ez, ez, q);
+          const float g = fmaf(-sig, q, d);
+          const float du1 = fabsf(dx) + fabsf(dy) + fabsf(dz);
+          const float B = fmaf(du1, band_k1, fmaf(band_k3, fabsf(g), band_k2));
+          code[u] = fabsf(g) > B ? (g >= 0.0f ? 1 : 0) : 2;
+        }
+      }
+      if (a.check) {
+        bool band = false;
+#pragma unroll
+        for (int u = 0; u < U; ++u) band = band || code[u] == 2;
+        if (__any_sync(kFull, band)) {
+          for (int u = 0; u < U; ++u)
+            if (code[u] == 2) {
+              code[u] = fp64_breaks<DIM>(a, t.i, j[u], disp, s0) ? 1 : 0;
               atomicAdd(&a.counters[0], 1ull);
             }
-            if (a.validate && brk != fp64_breaks<DIM>(a, t.i, j[u], disp, s0)) atomicAdd(&a.counters[1], 1ull);
-          }
-          const unsigned m = __ballot_sync(kFull, brk);
+        }
+        if (a.validate) {
+          for (int u = 0; u < U; ++u)
+            if (can_break && intact[u] && (code[u] == 1) != fp64_breaks<DIM>(a, t.i, j[u], disp, s0))
+              atomicAdd(&a.counters[1], 1ull);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const unsigned m = __ballot_sync(kFull, code[u] == 1);
           if (m) {
-            intact = intact && !brk;
+            intact[u] = intact[u] && code[u] != 1;
             if (t.lane == 0) bw[k0 + u * SPLIT] = wd[u] & ~m;
           }
         }
-        acc[0] += intact ? __int_as_float(Pj[u].w) * d : 0.0f;
       }
+#pragma unroll
+      for (int u = 0; u < U; ++u) acc[0] += intact[u] ? vj[u] * dv[u] : 0.0f;
     }
   }
   split_reduce<SPLIT, 1>(acc);
@@ -638,10 +662,17 @@ __global__ void __launch_bounds__(512) k_pass1_mixed_staged(StepArgs a, const fl
   const int b = a.body ? a.body[t.i] : 0;
   const double s0 = a.bp[b].s0;
   const float sig = a.bp[b].sigma32;
-  const bool can_break = s0 > 0.0;
+  const bool can_break = a.bp[b].breaks != 0;
   const int4 Pi = a.pos32[t.i];
   const float4 Ui = u32[t.i];
   const float ui1 = fabsf(Ui.x) + fabsf(Ui.y) + (DIM == 3 ? fabsf(Ui.z) : 0.0f);
+  // Band half-width B (see the comment above k_pass1_mixed) with |xi|_1 and |xi|^2 replaced by
+  // their per-body maxima: B <= du1 k1 + k2 + k3 |g|, two FMAs per bond.
+  const float xim = a.bp[b].xi1max, qm = a.bp[b].qmax;
+  const float band_k1 = a.band_c * fmaf(6.0f * 5.9604645e-8f, xim, 1.01f);
+  const float band_k2 = a.band_c * fmaf(sig, fmaf(2.01f, xim, 3.02f),
+                                        5.9604645e-8f * fmaf(2.0f * xim, ui1, 6.0f * sig * qm));
+  const float band_k3 = a.band_c * 5.9604645e-8f;
   uint32_t* __restrict__ bw = a.bits + (t.base >> 5);
   if (lane == 0)
     for (; st.issued < min(kStageBuf, st.nchunks); ++st.issued) stage_issue(st, st.issued);
@@ -672,6 +703,11 @@ __global__ void __launch_bounds__(512) k_pass1_mixed_staged(StepArgs a, const fl
         Pj[u] = a.pos32[j[u]];
         Uj[u] = u32[j[u]];
       }
+      // FP32 decisions of the batch; bonds inside the rounding band are flagged (code 2) and re-decided
+      // in FP64 below, in a warp-uniform block outside the unrolled arithmetic.
+      float dv[U], vj[U];
+      int code[U];
+      bool intact[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const float ex = (float)(Pj[u].x - Pi.x), ey = (float)(Pj[u].y - Pi.y);
@@ -679,34 +715,46 @@ __global__ void __launch_bounds__(512) k_pass1_mixed_staged(StepArgs a, const fl
         const float dx = Uj[u].x - Ui.x, dy = Uj[u].y - Ui.y, dz = DIM == 3 ? Uj[u].z - Ui.z : 0.0f;
         float d = ex * dx + ey * dy;
         if (DIM == 3) d = fmaf(ez, dz, d);
-        bool intact = (wd[u] >> lane) & 1u;
-        if (a.check) {
-          bool brk = false;
-          if (intact && can_break) {
-            float q = ex * ex + ey * ey;
-            if (DIM == 3) q = fmaf(ez, ez, q);
-            const float g = fmaf(-sig, q, d);
-            const float xi1 = fabsf(ex) + fabsf(ey) + fabsf(ez);
-            const float du1 = fabsf(dx) + fabsf(dy) + fabsf(dz);
-            const float B = a.band_c * (1.01f * du1 + sig * (2.01f * xi1 + 3.02f) +
-                                        5.9604645e-8f * (xi1 * (2.0f * ui1 + 6.0f * du1) + 6.0f * sig * q +
-                                                         fabsf(g)));
-            if (fabsf(g) > B) {
-              brk = g >= 0.0f;
-            } else {
-              brk = fp64_breaks<DIM>(a, t.i, j[u], disp, s0);
+        dv[u] = d;
+        vj[u] = __int_as_float(Pj[u].w);
+        intact[u] = (wd[u] >> lane) & 1u;
+        code[u] = 0;
+        if (a.check && can_break && intact[u]) {
+          float q = ex * ex + ey * ey;
+          if (DIM == 3) q = fmaf(ez, ez, q);
+          const float g = fmaf(-sig, q, d);
+          const float du1 = fabsf(dx) + fabsf(dy) + fabsf(dz);
+          const float B = fmaf(du1, band_k1, fmaf(band_k3, fabsf(g), band_k2));
+          code[u] = fabsf(g) > B ? (g >= 0.0f ? 1 : 0) : 2;
+        }
+      }
+      if (a.check) {
+        bool band = false;
+#pragma unroll
+        for (int u = 0; u < U; ++u) band = band || code[u] == 2;
+        if (__any_sync(kFull, band)) {
+          for (int u = 0; u < U; ++u)
+            if (code[u] == 2) {
+              code[u] = fp64_breaks<DIM>(a, t.i, j[u], disp, s0) ? 1 : 0;
               atomicAdd(&a.counters[0], 1ull);
             }
-            if (a.validate && brk != fp64_breaks<DIM>(a, t.i, j[u], disp, s0)) atomicAdd(&a.counters[1], 1ull);
-          }
-          const unsigned m = __ballot_sync(kFull, brk);
+        }
+        if (a.validate) {
+          for (int u = 0; u < U; ++u)
+            if (can_break && intact[u] && (code[u] == 1) != fp64_breaks<DIM>(a, t.i, j[u], disp, s0))
+              atomicAdd(&a.counters[1], 1ull);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const unsigned m = __ballot_sync(kFull, code[u] == 1);
           if (m) {
-            intact = intact && !brk;
+            intact[u] = intact[u] && code[u] != 1;
             if (lane == 0) bw[k0 + kk + u] = wd[u] & ~m;
           }
         }
-        acc += intact ? __int_as_float(Pj[u].w) * d : 0.0f;
       }
+#pragma unroll
+      for (int u = 0; u < U; ++u) acc += intact[u] ? vj[u] * dv[u] : 0.0f;
     }
     __syncwarp();  // every lane is done with this buffer before it is refilled
     if (lane == 0 && st.issued < st.nchunks) stage_issue(st, st.issued++);

@@ -150,6 +150,15 @@ def test_notched_block_twist_parity():
     assert np.array_equal(out[-1]["u"][:, pres], out[-1]["ref_u"][:, pres])
 
 
+def test_plane_strain_breaking_parity():
+    """Plane strain (Eq 1.8 / 1.15 / 1.28 plane-strain rows), steel-like material, breaking on."""
+    w = W.cracked_plate(nx=50, ny=20, dx=2.5e-4, crack_cells=25.125, sigma=4e8, nsteps=300, dt=4.5e-8)
+    w.model, w.E, w.nu, w.rho, w.Gc = W.MODEL_PLANE_STRAIN, 190e9, 0.25, 7800.0, 50.0
+    out, stats, phi, ref = run_pair(w, w.nsteps, 50)
+    assert out[-1]["broken"] > 0
+    assert_fp64(out, ref.damage(), phi)
+
+
 def test_config2_fp64_parity_first_1000_steps():
     """Configuration 2 at full size (64,000 particles), first 1000 of its 5000 steps."""
     w = W.config2()

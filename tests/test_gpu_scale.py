@@ -1,0 +1,34 @@
+"""Configuration 5 at full size (400 x 200 x 100 = 8M particles, ~9.6e8 directed bonds) on the GPU,
+every particle compared with the oracle after two steps from a random state (GPU only; the oracle
+runs on all host cores and holds the ~5 GB family in host memory)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2309_11273_gb300 import PD_FP64, PD_MIXED, Simulation
+from paper_2309_11273_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def test_config5_full_size_two_steps():
+    w = W.notched_block(nx=400, ny=200, nz=100, dx=5e-4, nsteps=1000, dt=1.895e-7, seed=11, amp=5e-7)
+    s0 = O.critical_stretch(w.model, w.E, w.nu, w.Gc, w.delta)
+    ref = O.OracleSim(w.model, w.E, w.nu, w.rho, w.delta, s0, w.dt, w.x, w.y, w.z, w.vol, w.cracks)
+    ref.set_bc(w.flag, w.b, w.axis_point, w.axis_dir, w.rotation_rate(s0))
+    ref.set_state(w.initial_u(), w.initial_v())
+    assert ref.nbonds > 9.4e8
+    ref.step(2)
+    for precision, tol in ((PD_FP64, 1e-12), (PD_MIXED, 1e-4)):
+        sim = Simulation(w, s0=s0, precision=precision)
+        assert sim.nbonds == ref.nbonds
+        sim.step(2)
+        u, v, th = sim.state()
+        sim.close()
+        assert rel(u, ref.u) <= tol and rel(v, ref.v) <= tol, (precision, rel(u, ref.u), rel(v, ref.v))
+        if precision == PD_FP64:
+            assert rel(th, ref.theta) <= 1e-11
