@@ -244,9 +244,6 @@ pd_status check_params(const pd_params& p, int dim) {
   if (p.precision != PD_FP64 && p.precision != PD_MIXED) return fail(PD_ERR_ARG, "unknown precision");
   if (!(p.E > 0) || !std::isfinite(p.E)) return fail(PD_ERR_ARG, "E must be > 0");
   if (!(p.nu > -1.0 && p.nu < 0.5)) return fail(PD_ERR_ARG, "nu must lie in (-1, 0.5)");
-  if (p.model == PD_PLANE_STRESS && !(p.nu < 1.0 / 3.0 || p.nu > 1.0 / 3.0)) {
-    // K of Eq 1.15 (plane stress) is regular at nu = 1/3; nothing to reject.
-  }
   if (!(p.rho > 0) || !std::isfinite(p.rho)) return fail(PD_ERR_ARG, "rho must be > 0");
   if (!(p.horizon > 0) || !std::isfinite(p.horizon)) return fail(PD_ERR_ARG, "horizon must be > 0");
   if (!(p.dt > 0) || !std::isfinite(p.dt)) return fail(PD_ERR_ARG, "dt must be > 0");

@@ -185,6 +185,7 @@ pd_status launch_damage(pd_ctx* c, double* phi_caller);
 pd_status launch_set_step(pd_ctx* c, int64_t value);
 pd_status init_disp_w(pd_ctx* c);
 pd_status ensure_bond_cache(pd_ctx* c);
+pd_status prepare_staged_kernels(pd_ctx* c);  // shared-memory opt-in of the staged kernels
 pd_status upload_field(pd_ctx* c, const double* host_soa, double4* dst, int comps);
 pd_status download_field(pd_ctx* c, const double4* src, double* host_soa, int comps);
 pd_status download_scalar(pd_ctx* c, const double* src, double* host);

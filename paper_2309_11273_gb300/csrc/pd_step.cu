@@ -1005,6 +1005,25 @@ void launch_pass2(pd_ctx* c, const StepArgs& a, unsigned grid, int block, size_t
 }
 
 template <int DIM>
+void optin_staged() {
+  cudaFuncSetAttribute(k_pass1_mixed_staged<DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 16 * kStageWarpBytes);
+  cudaFuncSetAttribute(k_pass2_mixed_staged<DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 16 * kStageWarpBytes);
+}
+
+}  // namespace
+
+// Shared-memory opt-in of the staged kernels (up to 512 threads per block) on the current device;
+// called when a mixed context is built, outside any stream capture.
+pd_status prepare_staged_kernels(pd_ctx* c) {
+  if (c->dim == 3) optin_staged<3>();
+  else optin_staged<2>();
+  PD_CUDA(cudaGetLastError());
+  return PD_OK;
+}
+
+namespace {
+
+template <int DIM>
 void dispatch_pass(pd_ctx* c, const StepArgs& a, int pass, int write_theta) {
   const int block = c->block;
   const int split = c->split;
@@ -1012,16 +1031,6 @@ void dispatch_pass(pd_ctx* c, const StepArgs& a, int pass, int write_theta) {
   const unsigned grid = (unsigned)((threads + block - 1) / block);
   if (c->precision == PD_MIXED && split == 1 && c->stage) {
     const size_t smb = (size_t)(block / 32) * kStageWarpBytes;
-    static bool attr_set[4] = {false, false, false, false};
-    const int slot = (DIM == 3 ? 2 : 0) + (pass == 1 ? 0 : 1);
-    if (!attr_set[slot]) {
-      const int maxb = 16 * kStageWarpBytes;
-      if (pass == 1)
-        cudaFuncSetAttribute(k_pass1_mixed_staged<DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb);
-      else
-        cudaFuncSetAttribute(k_pass2_mixed_staged<DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb);
-      attr_set[slot] = true;
-    }
     if (pass == 1)
       k_pass1_mixed_staged<DIM><<<grid, block, smb, c->stream>>>(a, c->u32[c->cur], c->disp[c->cur], write_theta);
     else
