@@ -15,6 +15,7 @@ sequences the calls.  Equation references are to the paper:
 * Eq 1.9                -> :func:`weighted_volume`
 * Eq 1.6 / 2.3          -> :func:`dilatation`
 * Eq 2.2                -> :func:`force`
+* Eqs 1.10, 1.13, 1.14  -> the same functions with ``kin=NONLINEAR`` (geometrically exact bonds)
 * Eqs 1.17, 1.30        -> :func:`failure`
 * Eq 1.31               -> :func:`damage`
 * Eq 2.11 + Appendix B  -> :class:`OracleSim`
@@ -39,6 +40,7 @@ _lib = None
 
 MODEL_3D, MODEL_PLANE_STRESS, MODEL_PLANE_STRAIN = 0, 1, 2
 FREE, FIXED, PRESCRIBED = 0, 1, 2
+LINEARIZED, NONLINEAR = 0, 1  # bond kinematics: Eqs 2.4/2.7 (the paper's method) or Eqs 1.10/1.13
 
 _d = ctypes.POINTER(ctypes.c_double)
 _i64 = ctypes.POINTER(ctypes.c_int64)
@@ -78,15 +80,15 @@ def lib():
             L.orc_weighted_volume.argtypes = [ctypes.c_int64, ctypes.c_int, _d, _d, _d, _d, _i64, _i32,
                                               _d]
             L.orc_damage_denominator.argtypes = [ctypes.c_int64, _d, _i64, _i32, _d]
-            L.orc_dilatation.argtypes = [ctypes.c_int64, ctypes.c_int, _d, _d, _d, _d, _i64, _i32, _u8,
+            L.orc_dilatation.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int, _d, _d, _d, _d, _i64, _i32, _u8,
                                          _d, ctypes.c_double, _d, _d, _d, _d]
-            L.orc_force.argtypes = [ctypes.c_int64, ctypes.c_int, _d, _d, _d, _d, _i64, _i32, _u8, _d,
+            L.orc_force.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int, _d, _d, _d, _d, _i64, _i32, _u8, _d,
                                     _d, ctypes.c_double, ctypes.c_double, _d, _d, _d, _d, _d, _d]
-            L.orc_failure.argtypes = [ctypes.c_int64, ctypes.c_int, _d, _d, _d, _i64, _i32, _u8,
+            L.orc_failure.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int, _d, _d, _d, _i64, _i32, _u8,
                                       ctypes.c_double, _d, _d, _d, _d]
             L.orc_failure.restype = ctypes.c_int64
             L.orc_damage.argtypes = [ctypes.c_int64, _d, _i64, _i32, _u8, _d]
-            L.orc_run.argtypes = ([ctypes.c_int64, ctypes.c_int, _d, _d, _d, _d, _i64, _i32, _u8, _d]
+            L.orc_run.argtypes = ([ctypes.c_int, ctypes.c_int64, ctypes.c_int, _d, _d, _d, _d, _i64, _i32, _u8, _d]
                                   + [ctypes.c_double] * 6
                                   + [_u8, _d, _d, _d, _d, _d, ctypes.c_double, ctypes.c_int64,
                                      ctypes.c_int64]
@@ -175,7 +177,7 @@ def damage_denominator(vol, row_ptr, col):
     return D
 
 
-def dilatation(x, y, z, vol, row_ptr, col, status, m, A, u):
+def dilatation(x, y, z, vol, row_ptr, col, status, m, A, u, kin=LINEARIZED):
     """theta_i (Eq 1.6 / 2.3) for displacement ``u`` of shape (dim, n)."""
     x, y, z, vol, m = _f64(x), _f64(y), _f64(z), _f64(vol), _f64(m)
     u = np.ascontiguousarray(u, dtype=np.float64)
@@ -183,29 +185,29 @@ def dilatation(x, y, z, vol, row_ptr, col, status, m, A, u):
     th = np.zeros(n)
     zz = z if z is not None else x
     uz = u[2] if dim == 3 else u[0]
-    lib().orc_dilatation(n, dim, _p(x, _d), _p(y, _d), _p(zz, _d), _p(vol, _d), _p(row_ptr, _i64),
+    lib().orc_dilatation(int(kin), n, dim, _p(x, _d), _p(y, _d), _p(zz, _d), _p(vol, _d), _p(row_ptr, _i64),
                          _p(col, _i32), _p(status, _u8), _p(m, _d), float(A),
                          _p(np.ascontiguousarray(u[0]), _d), _p(np.ascontiguousarray(u[1]), _d),
                          _p(np.ascontiguousarray(uz), _d), _p(th, _d))
     return th
 
 
-def force(x, y, z, vol, row_ptr, col, status, m, theta, K, G, u):
-    """Internal force F_i = sum_j F_i^{xi_ij} (Eq 2.2), shape (dim, n)."""
+def force(x, y, z, vol, row_ptr, col, status, m, theta, K, G, u, kin=LINEARIZED):
+    """Internal force F_i = sum_j F_i^{xi_ij} (Eq 2.2; Eqs 1.11-1.14 with kin=NONLINEAR), shape (dim, n)."""
     x, y, z, vol, m, theta = _f64(x), _f64(y), _f64(z), _f64(vol), _f64(m), _f64(theta)
     u = np.ascontiguousarray(u, dtype=np.float64)
     n, dim = x.size, u.shape[0]
     f = np.zeros((3, n))
     zz = z if z is not None else x
     uz = u[2] if dim == 3 else u[0]
-    lib().orc_force(n, dim, _p(x, _d), _p(y, _d), _p(zz, _d), _p(vol, _d), _p(row_ptr, _i64),
+    lib().orc_force(int(kin), n, dim, _p(x, _d), _p(y, _d), _p(zz, _d), _p(vol, _d), _p(row_ptr, _i64),
                     _p(col, _i32), _p(status, _u8), _p(m, _d), _p(theta, _d), float(K), float(G),
                     _p(np.ascontiguousarray(u[0]), _d), _p(np.ascontiguousarray(u[1]), _d),
                     _p(np.ascontiguousarray(uz), _d), _p(f[0], _d), _p(f[1], _d), _p(f[2], _d))
     return f[:dim].copy()
 
 
-def failure(x, y, z, row_ptr, col, status, s0, u):
+def failure(x, y, z, row_ptr, col, status, s0, u, kin=LINEARIZED):
     """Apply Eq 1.30 in place on ``status``; returns (newly broken, min relative margin)."""
     x, y, z = _f64(x), _f64(y), _f64(z)
     u = np.ascontiguousarray(u, dtype=np.float64)
@@ -213,7 +215,7 @@ def failure(x, y, z, row_ptr, col, status, s0, u):
     mm = ctypes.c_double()
     zz = z if z is not None else x
     uz = u[2] if dim == 3 else u[0]
-    nb = lib().orc_failure(n, dim, _p(x, _d), _p(y, _d), _p(zz, _d), _p(row_ptr, _i64), _p(col, _i32),
+    nb = lib().orc_failure(int(kin), n, dim, _p(x, _d), _p(y, _d), _p(zz, _d), _p(row_ptr, _i64), _p(col, _i32),
                            _p(status, _u8), float(s0), _p(np.ascontiguousarray(u[0]), _d),
                            _p(np.ascontiguousarray(u[1]), _d), _p(np.ascontiguousarray(uz), _d),
                            ctypes.byref(mm))
@@ -237,8 +239,9 @@ class OracleSim:
     """
 
     def __init__(self, model, E, nu, rho, delta, s0, dt, x, y, z=None, vol=None, cracks=(),
-                 family_method="binned"):
+                 family_method="binned", kin=LINEARIZED):
         self.model = int(model)
+        self.kin = int(kin)
         self.dim = 3 if z is not None else 2
         self.x, self.y = _f64(x), _f64(y)
         self.z = _f64(z) if z is not None else None
@@ -295,7 +298,7 @@ class OracleSim:
         bx = b[0].copy() if b is not None else None
         by = b[1].copy() if b is not None else None
         bz = b[2].copy() if (b is not None and self.dim == 3) else None
-        lib().orc_run(self.n, self.dim, _p(self.x, _d), _p(self.y, _d), _p(zz, _d), _p(self.vol, _d),
+        lib().orc_run(self.kin, self.n, self.dim, _p(self.x, _d), _p(self.y, _d), _p(zz, _d), _p(self.vol, _d),
                       _p(self.row_ptr, _i64), _p(self.col, _i32), _p(self.status, _u8), _p(self.m, _d),
                       self.A, self.K, self.G, self.rho, self.dt, self.s0, _p(self.flag, _u8),
                       _p(bx, _d), _p(by, _d), _p(bz, _d), _p(self.axis_point, _d),
@@ -312,9 +315,9 @@ class OracleSim:
         """theta and F for displacement u (default: current state) with the current bond status."""
         u = self.u if u is None else np.asarray(u, dtype=np.float64).reshape(self.dim, self.n)
         th = dilatation(self.x, self.y, self.z, self.vol, self.row_ptr, self.col, self.status, self.m,
-                        self.A, u)
+                        self.A, u, self.kin)
         f = force(self.x, self.y, self.z, self.vol, self.row_ptr, self.col, self.status, self.m, th,
-                  self.K, self.G, u)
+                  self.K, self.G, u, self.kin)
         return th, f
 
     def damage(self):

@@ -15,6 +15,8 @@
  *   x_ij   = |xi_ij|                       reference bond length           (Eq 1.5)
  *   M_ij   = xi_ij / x_ij                  linearized unit state           (Eq 1.13, small-deformation form)
  *   e_ij   = M_ij . (u_j - u_i)            linearized extension            (Eqs 1.10, 2.4, 2.7)
+ *   (with kin = ORC_NONLINEAR: Y_ij = xi_ij + u_j - u_i, e_ij = |Y_ij| - x_ij, M_ij = Y_ij / |Y_ij|,
+ *    Eqs 1.10 and 1.13 without the small-deformation approximation)
  *   w      = 1                             influence function              (Section 2.3, text after Eq 1.26)
  *   rho_ij = 1 intact, 0 broken            bond status                     (Eq 1.30)
  *
@@ -32,6 +34,7 @@
 
 enum { ORC_3D = 0, ORC_PLANE_STRESS = 1, ORC_PLANE_STRAIN = 2 };
 enum { ORC_FREE = 0, ORC_FIXED = 1, ORC_PRESCRIBED = 2 };
+enum { ORC_LINEARIZED = 0, ORC_NONLINEAR = 1 };  /* bond kinematics, see bond_kinematics() */
 
 void orc_set_threads(int n) {
 #ifdef _OPENMP
@@ -306,12 +309,35 @@ static double bond_vector(int dim, const double* x, const double* y, const doubl
   return sqrt(q);
 }
 
-/* Linearized extension e_ij = M_ij . (u_j - u_i), M_ij = xi_ij / x_ij (Eqs 1.10, 1.13, 2.4, 2.7). */
-static double bond_extension(int dim, const double xi[3], double xlen, const double* ux,
-                             const double* uy, const double* uz, int64_t i, int64_t j) {
-  double e = (xi[0] / xlen) * (ux[j] - ux[i]) + (xi[1] / xlen) * (uy[j] - uy[i]);
-  if (dim == 3) e += (xi[2] / xlen) * (uz[j] - uz[i]);
-  return e;
+/* Extension scalar e_ij and unit direction M_ij of a bond with reference vector xi (length xlen).
+ *   kin = ORC_LINEARIZED (the paper's method, Eqs 2.4, 2.7): M = xi / |xi| (the small-deformation
+ *     approximation stated under Eq 1.13) and e = M . (u_j - u_i).
+ *   kin = ORC_NONLINEAR (Eqs 1.10 and 1.13 as written): Y = xi + eta with eta = u_j - u_i,
+ *     e = |Y| - |xi| and M = Y / |Y|.  The difference of the two lengths is evaluated as
+ *     (|Y|^2 - |xi|^2) / (|Y| + |xi|) with |Y|^2 - |xi|^2 = 2 xi.eta + eta.eta, the same number
+ *     without the cancellation of two nearly equal lengths. */
+static double bond_kinematics(int kin, int dim, const double xi[3], double xlen, const double* ux,
+                              const double* uy, const double* uz, int64_t i, int64_t j, double M[3]) {
+  double eta[3] = {ux[j] - ux[i], uy[j] - uy[i], dim == 3 ? uz[j] - uz[i] : 0.0};
+  if (kin == ORC_LINEARIZED) {
+    double e = 0.0;
+    for (int k = 0; k < dim; ++k) {
+      M[k] = xi[k] / xlen;
+      e += M[k] * eta[k];
+    }
+    if (dim == 2) M[2] = 0.0;
+    return e;
+  }
+  double Y[3], yy = 0.0, p = 0.0;
+  for (int k = 0; k < dim; ++k) {
+    Y[k] = xi[k] + eta[k];
+    yy += Y[k] * Y[k];
+    p += 2.0 * xi[k] * eta[k] + eta[k] * eta[k];
+  }
+  double ylen = sqrt(yy);
+  for (int k = 0; k < dim; ++k) M[k] = Y[k] / ylen;
+  if (dim == 2) M[2] = 0.0;
+  return p / (ylen + xlen);
 }
 
 /* Weighted volume m_i = sum_j w x_ij^2 V_j over the built family (Eq 1.9, discretized, w = 1). */
@@ -342,7 +368,7 @@ void orc_damage_denominator(int64_t n, const double* vol, const int64_t* row_ptr
 
 /* Dilatation theta_i = (A / m_i) sum_j w x_ij e_ij V_j rho_ij (Eq 1.6 discretized; the sum over all
  * bonds of the per-bond contributions of Eq 2.3).  A particle with m_i = 0 has no bonds: theta_i = 0. */
-void orc_dilatation(int64_t n, int dim, const double* x, const double* y, const double* z,
+void orc_dilatation(int kin, int64_t n, int dim, const double* x, const double* y, const double* z,
                     const double* vol, const int64_t* row_ptr, const int32_t* col,
                     const uint8_t* status, const double* m, double A, const double* ux,
                     const double* uy, const double* uz, double* theta) {
@@ -353,8 +379,9 @@ void orc_dilatation(int64_t n, int dim, const double* x, const double* y, const 
       if (!status[b]) continue;
       int64_t j = col[b];
       double xi[3];
+      double M[3];
       double xl = bond_vector(dim, x, y, z, i, j, xi);
-      double e = bond_extension(dim, xi, xl, ux, uy, uz, i, j);
+      double e = bond_kinematics(kin, dim, xi, xl, ux, uy, uz, i, j, M);
       s += xl * e * vol[j];
     }
     theta[i] = (m[i] > 0.0) ? A * s / m[i] : 0.0;
@@ -365,7 +392,7 @@ void orc_dilatation(int64_t n, int dim, const double* x, const double* y, const 
  *   F_i^{xi_ij} = [ (K - G/3) theta~_ij x_ij + G e~_ij ] w M_ij V_i V_j rho_ij,
  *   theta~_ij = theta_i / m_i + theta_j / m_j,   e~_ij = e_ij / m_i + e_ij / m_j.
  * F points from i towards j for a stretched bond (Appendix B adds it to the external force). */
-void orc_force(int64_t n, int dim, const double* x, const double* y, const double* z,
+void orc_force(int kin, int64_t n, int dim, const double* x, const double* y, const double* z,
                const double* vol, const int64_t* row_ptr, const int32_t* col,
                const uint8_t* status, const double* m, const double* theta, double K, double G,
                const double* ux, const double* uy, const double* uz, double* fx, double* fy,
@@ -377,12 +404,13 @@ void orc_force(int64_t n, int dim, const double* x, const double* y, const doubl
       if (!status[b]) continue;
       int64_t j = col[b];
       double xi[3];
+      double M[3];
       double xl = bond_vector(dim, x, y, z, i, j, xi);
-      double e = bond_extension(dim, xi, xl, ux, uy, uz, i, j);
+      double e = bond_kinematics(kin, dim, xi, xl, ux, uy, uz, i, j, M);
       double th = theta[i] / m[i] + theta[j] / m[j];
       double et = e / m[i] + e / m[j];
       double mag = ((K - G / 3.0) * th * xl + G * et) * vol[i] * vol[j];
-      for (int k = 0; k < dim; ++k) f[k] += mag * (xi[k] / xl);
+      for (int k = 0; k < dim; ++k) f[k] += mag * M[k];
     }
     fx[i] = f[0];
     fy[i] = f[1];
@@ -393,7 +421,7 @@ void orc_force(int64_t n, int dim, const double* x, const double* y, const doubl
 /* Failure criterion (Eqs 1.17, 1.30): stretch s_ij = e_ij / x_ij; an intact bond breaks for good when
  * s_ij >= s0.  Returns the number of bonds broken by this call; *min_margin receives
  * min |s_ij - s0| / s0 over the bonds that are still intact afterwards (1e300 if there are none). */
-int64_t orc_failure(int64_t n, int dim, const double* x, const double* y, const double* z,
+int64_t orc_failure(int kin, int64_t n, int dim, const double* x, const double* y, const double* z,
                     const int64_t* row_ptr, const int32_t* col, uint8_t* status, double s0,
                     const double* ux, const double* uy, const double* uz, double* min_margin) {
   int64_t broken = 0;
@@ -404,8 +432,9 @@ int64_t orc_failure(int64_t n, int dim, const double* x, const double* y, const 
       if (!status[b]) continue;
       int64_t j = col[b];
       double xi[3];
+      double M[3];
       double xl = bond_vector(dim, x, y, z, i, j, xi);
-      double s = bond_extension(dim, xi, xl, ux, uy, uz, i, j) / xl;
+      double s = bond_kinematics(kin, dim, xi, xl, ux, uy, uz, i, j, M) / xl;
       if (s >= s0) {
         status[b] = 0;
         ++broken;
@@ -484,7 +513,7 @@ static void apply_bc(int64_t n, int dim, const double* x, const double* y, const
  * broken[k] (may be NULL) the number of bonds broken in it.  theta holds the last iteration's
  * dilatation on return; fx/fy/fz its internal force.  b* may be NULL (no body force).
  * ---------------------------------------------------------------------------------------------- */
-void orc_run(int64_t n, int dim, const double* x, const double* y, const double* z,
+void orc_run(int kin, int64_t n, int dim, const double* x, const double* y, const double* z,
              const double* vol, const int64_t* row_ptr, const int32_t* col, uint8_t* status,
              const double* m, double A, double K, double G, double rho, double dt, double s0,
              const uint8_t* flag, const double* bx, const double* by, const double* bz,
@@ -500,8 +529,8 @@ void orc_run(int64_t n, int dim, const double* x, const double* y, const double*
     int64_t step = step0 + s;
     double tn = (double)step * dt, tn1 = (double)(step + 1) * dt;
     apply_bc(n, dim, x, y, z, flag, c, a, rate, tn, ux, uy, uz, vx, vy, vz);
-    orc_dilatation(n, dim, x, y, z, vol, row_ptr, col, status, m, A, ux, uy, uz, theta);
-    orc_force(n, dim, x, y, z, vol, row_ptr, col, status, m, theta, K, G, ux, uy, uz, fx, fy, fz);
+    orc_dilatation(kin, n, dim, x, y, z, vol, row_ptr, col, status, m, A, ux, uy, uz, theta);
+    orc_force(kin, n, dim, x, y, z, vol, row_ptr, col, status, m, theta, K, G, ux, uy, uz, fx, fy, fz);
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
       if (flag && flag[i] != ORC_FREE) continue;
@@ -518,7 +547,7 @@ void orc_run(int64_t n, int dim, const double* x, const double* y, const double*
     apply_bc(n, dim, x, y, z, flag, c, a, rate, tn1, ux, uy, uz, vx, vy, vz);
     double mm = 1e300;
     int64_t nb = 0;
-    if (s0 > 0.0) nb = orc_failure(n, dim, x, y, z, row_ptr, col, status, s0, ux, uy, uz, &mm);
+    if (s0 > 0.0) nb = orc_failure(kin, n, dim, x, y, z, row_ptr, col, status, s0, ux, uy, uz, &mm);
     if (margins) margins[s] = mm;
     if (broken) broken[s] = nb;
   }
