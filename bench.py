@@ -15,6 +15,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import os
 import statistics
@@ -60,9 +61,17 @@ def measured_peaks():
         return {}
 
 
-def kernel_source_sha():
-    with open(os.path.join(ROOT, "paper_2309_11273_gb300", "csrc", "pd_step.cu"), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+def kernel_source_sha(kernel):
+    """First 16 hex digits of the sha256 of a step kernel's definition in pd_step.cu (from its
+    __global__ line to the closing brace at column 0), so that edits elsewhere in the file do not
+    invalidate a recorded capture."""
+    with open(os.path.join(ROOT, "paper_2309_11273_gb300", "csrc", "pd_step.cu")) as f:
+        src = f.read()
+    m = re.search(r"__global__[^\n]*\b%s\(" % re.escape(kernel), src)
+    if not m:
+        return None
+    end = src.find("\n}\n", m.start())
+    return hashlib.sha256(src[m.start():end].encode()).hexdigest()[:16]
 
 
 def recorded_traffic(kernel):
@@ -73,7 +82,7 @@ def recorded_traffic(kernel):
         lines = open(path).read().splitlines()
     except OSError:
         return None
-    sha = kernel_source_sha()
+    sha = kernel_source_sha(kernel)
     for ln in lines:
         kv = dict(p.split("=", 1) for p in ln.split() if "=" in p)
         if kv.get("kernel") == kernel and kv.get("source_sha") == sha and "dram_bytes_per_launch" in kv:
