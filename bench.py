@@ -43,6 +43,13 @@ BYTES_BOND = {1: 4.25, 2: 4.125}
 BYTES_PART = {1: 68.0, 2: 141.0}
 FLOPS_BOND = {1: 19.0, 2: 28.0}
 FLOPS_BOND_TABLED = {1: 10.0, 2: 11.0}
+# Geometrically nonlinear bonds (Eqs 1.10, 1.13), FP64, square root and divide counted as one flop
+# each: pass 1 forms xi, eta, Y, |Y|^2 - |xi|^2, |xi|^2, |Y|^2, two roots, e and the theta term and
+# the break test; pass 2 the same geometry, the Eq 1.14 coefficient and the force along Y / |Y|.
+FLOPS_BOND_NL = {1: 36.0, 2: 44.0}
+# ... and its per-step part when (xi, |xi|) come from the per-slot table and pass 1 leaves (e, 1/|Y|)
+# for pass 2 (rsqrt counted as one flop).
+FLOPS_BOND_NL_TABLED = {1: 29.0, 2: 19.0}
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12  # 2 DFMA/clk/SM x 2 flop x 152 SMs x 2.07 GHz
 
 
@@ -359,7 +366,7 @@ def mixed_roofline(prof, a1, a2, bytes1, bytes2, hbm, hbm_note, staged):
 
 def run_forms(args, stream, dev, world, fp64_value, nb, hbm, hbm_note):
     """Mixed precision on the same workload and the batched form, as speed-ups over plain FP64."""
-    from paper_2309_11273_gb300 import PD_FP64, PD_MIXED, BatchSimulation, Simulation, pd_critical_stretch
+    from paper_2309_11273_gb300 import PD_FP64, PD_MIXED, PD_NONLINEAR, BatchSimulation, Simulation, pd_critical_stretch
     from paper_2309_11273_gb300 import _binding as B
     from paper_2309_11273_gb300 import workloads as W
     out = {}
@@ -385,6 +392,29 @@ def run_forms(args, stream, dev, world, fp64_value, nb, hbm, hbm_note):
                                     "(configuration 1); zero bond decisions differing from FP64 on its own state",
                     "band_rechecks": st["band_rechecks"], "mapping": {"block": mmap[0], "split": mmap[1]},
                     "roofline": mixed_roofline(prof, a1, a2, bytes1, bytes2, hbm, hbm_note, staged)}
+    # geometrically nonlinear bonds (Eqs 1.10, 1.13, 1.14) in FP64 on the same workload
+    sim = Simulation(w, s0=s0, precision=PD_FP64, kinematics=PD_NONLINEAR, stream=stream.cuda_stream, device=dev)
+    nmap = B.pd_autotune(sim.h, 2)
+    sim.step(args.warmup)
+    k = 20
+    ms = max_over_ranks(timed(sim, stream, k, world), world)
+    nval = world * nb * k / (ms * 1e-3)
+    prof = profiled(sim, 5)
+    ntab = B.pd_get_option(sim.h, B.PD_OPT_BOND_CACHE) == 1
+    sim.close()
+    kp = 1 if prof["pass1_ms"] >= prof["pass2_ms"] else 2
+    nfl = (FLOPS_BOND_NL_TABLED if ntab else FLOPS_BOND_NL)[kp]
+    ach = nfl * nb / (prof["pass%d_ms" % kp] * 1e-3) / 1e12
+    nkern = "k_pass%d_nl%s" % (kp, "t" if ntab else "")
+    out["nonlinear"] = {"value": nval, "unit": UNIT, "ms_per_step": ms / k, "steps": k, "dtype": "f64",
+                        "kinematics": "e = |Y| - |xi|, force along Y/|Y| (Eqs 1.10, 1.13, 1.14)",
+                        "vs_linearized_fp64": nval / fp64_value, "mapping": {"block": nmap[0], "split": nmap[1]},
+                        "roofline": {"bound": "alu", "kernel": nkern, "achieved": ach,
+                                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                                     "traffic": recorded_traffic(nkern),
+                                     "algorithmic": "%g FP64 flop per directed bond (%s form; root, divide = 1) x %d"
+                                                    " bonds" % (nfl, "tabled" if ntab else "recompute", nb),
+                                     "pass1_ms": prof["pass1_ms"], "pass2_ms": prof["pass2_ms"]}}
     # batched: 256 uneven plates (configuration 4) in one context; FP64 and mixed; 100-step graphs
     bw = W.config4()
     res = {}
@@ -414,7 +444,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--profile-target", choices=["fp64", "mixed"], default=None,
+    ap.add_argument("--profile-target", choices=["fp64", "mixed", "nonlinear"], default=None,
                     help="only build the workload and run 4 eager steps (the command profiled by ncu)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -430,11 +460,12 @@ def main():
 
 def profile_target(form):
     """Workload of the benchmark in one precision, 4 eager time steps (ncu captures this command)."""
-    from paper_2309_11273_gb300 import PD_FP64, PD_MIXED, Simulation, pd_critical_stretch
+    from paper_2309_11273_gb300 import PD_FP64, PD_LINEARIZED, PD_MIXED, PD_NONLINEAR, Simulation, pd_critical_stretch
     from paper_2309_11273_gb300 import workloads as W
     w = W.config3()
     s0 = pd_critical_stretch(w.model, w.E, w.nu, w.Gc, w.delta)
-    sim = Simulation(w, s0=s0, precision=PD_FP64 if form == "fp64" else PD_MIXED, graph_chunk=0)
+    sim = Simulation(w, s0=s0, precision=PD_MIXED if form == "mixed" else PD_FP64, graph_chunk=0,
+                     kinematics=PD_NONLINEAR if form == "nonlinear" else PD_LINEARIZED)
     sim.step(4)
     sim.sync()
     print(json.dumps({"profile_target": form, "stats": sim.stats()}))

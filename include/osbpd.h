@@ -59,6 +59,15 @@ typedef enum { PD_3D = 0, PD_PLANE_STRESS = 1, PD_PLANE_STRAIN = 2 } pd_model;
  *   status equals the FP64 decision on the run's own state. */
 typedef enum { PD_FP64 = 0, PD_MIXED = 1 } pd_precision;
 
+/* Bond kinematics.
+ * PD_LINEARIZED: the paper's linearized model (Section 3, Eqs 2.2-2.4): extension e = M . (u_j - u_i)
+ *   along the reference direction M = xi / |xi|, the small-deformation approximation of Eq 1.13.
+ * PD_NONLINEAR: the state-based model of Section 2 without that approximation: Y = xi + u_j - u_i,
+ *   e = |Y| - |xi| (Eq 1.10) and the force along the deformed bond M = Y / |Y| (Eq 1.13), with the
+ *   force state of Eq 1.14 (as in the loop scheme of Appendix C).  Stretch for Eq 1.30: e / |xi|.
+ *   PD_FP64 only. */
+typedef enum { PD_LINEARIZED = 0, PD_NONLINEAR = 1 } pd_kinematics;
+
 /* Internal particle order (results do not depend on it beyond rounding).
  * PD_ORDER_BRICKS: bricks of 32 x 4 x 4 (3D) or 32 x 8 (2D) points of the typical spacing
  *   (mean V)^(1/dim), x fastest inside a brick, bricks along a Morton curve: a warp's 32 particles
@@ -79,6 +88,8 @@ typedef struct {
   int32_t device;      /* CUDA device ordinal */
   int32_t ordering;    /* internal particle order: PD_ORDER_BRICKS (0, default) or PD_ORDER_MORTON */
   void* stream;        /* cudaStream_t to run on, or NULL for a library-owned stream */
+  int32_t kinematics;  /* pd_kinematics; every body of a batch takes the same */
+  int32_t reserved;    /* 0 */
 } pd_params;
 
 /* A pre-crack / notch: bonds whose segment crosses it are never created (Section 4.2 / 4.4).

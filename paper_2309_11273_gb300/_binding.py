@@ -19,6 +19,7 @@ PD_OK, PD_ERR_ARG, PD_ERR_STATE, PD_ERR_OOM, PD_ERR_CUDA, PD_ERR_NUMERIC, PD_ERR
 PD_3D, PD_PLANE_STRESS, PD_PLANE_STRAIN = 0, 1, 2
 PD_FP64, PD_MIXED = 0, 1
 PD_ORDER_BRICKS, PD_ORDER_MORTON = 0, 1
+PD_LINEARIZED, PD_NONLINEAR = 0, 1
 PD_OPT_GRAPH_CHUNK, PD_OPT_PROFILE, PD_OPT_VALIDATE, PD_OPT_BLOCK, PD_OPT_SPLIT, PD_OPT_BOND_CACHE = 1, 2, 3, 4, 5, 6
 PD_OPT_STAGE = 7
 PD_K_PASS1, PD_K_PASS2 = 0, 1
@@ -38,7 +39,8 @@ class pd_params(ctypes.Structure):
     _fields_ = [("model", ctypes.c_int32), ("precision", ctypes.c_int32), ("E", ctypes.c_double),
                 ("nu", ctypes.c_double), ("rho", ctypes.c_double), ("horizon", ctypes.c_double),
                 ("s0", ctypes.c_double), ("dt", ctypes.c_double), ("band_safety", ctypes.c_double),
-                ("device", ctypes.c_int32), ("ordering", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+                ("device", ctypes.c_int32), ("ordering", ctypes.c_int32), ("stream", ctypes.c_void_p),
+                ("kinematics", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class pd_crack(ctypes.Structure):
@@ -133,9 +135,9 @@ def pd_critical_stretch(model, E, nu, Gc, delta) -> float:
 
 
 def make_params(model, E, nu, rho, horizon, s0, dt, precision=PD_FP64, band_safety=0.0, device=0,
-                stream=None, ordering=PD_ORDER_BRICKS) -> pd_params:
+                stream=None, ordering=PD_ORDER_BRICKS, kinematics=PD_LINEARIZED) -> pd_params:
     return pd_params(int(model), int(precision), float(E), float(nu), float(rho), float(horizon), float(s0),
-                     float(dt), float(band_safety), int(device), int(ordering), stream)
+                     float(dt), float(band_safety), int(device), int(ordering), stream, int(kinematics), 0)
 
 
 def pd_create_particles(prm: pd_params, x, y, z=None, vol=None):

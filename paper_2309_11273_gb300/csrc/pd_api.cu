@@ -55,6 +55,7 @@ void free_build(pd_ctx* c) {
   c->bA = nullptr;
   c->bB = nullptr;
   c->bd = nullptr;
+  c->bE = nullptr;
   c->u32[0] = c->u32[1] = nullptr;
   c->thm32 = nullptr;
   c->mu32 = c->aA32 = c->theta32 = nullptr;

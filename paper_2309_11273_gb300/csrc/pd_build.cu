@@ -249,6 +249,9 @@ pd_status check_params(const pd_params& p, int dim) {
   if (!(p.dt > 0) || !std::isfinite(p.dt)) return fail(PD_ERR_ARG, "dt must be > 0");
   if (!std::isfinite(p.s0)) return fail(PD_ERR_ARG, "s0 must be finite");
   if (p.ordering != PD_ORDER_BRICKS && p.ordering != PD_ORDER_MORTON) return fail(PD_ERR_ARG, "unknown ordering");
+  if (p.kinematics != PD_LINEARIZED && p.kinematics != PD_NONLINEAR) return fail(PD_ERR_ARG, "unknown kinematics");
+  if (p.kinematics == PD_NONLINEAR && p.precision != PD_FP64)
+    return fail(PD_ERR_ARG, "PD_NONLINEAR runs in PD_FP64 only");
   return PD_OK;
 }
 
@@ -292,8 +295,9 @@ pd_status create(pd_ctx** out, int32_t nbodies, const pd_params* prm, const int6
     pd_status st = check_params(prm[b], dim);
     if (st != PD_OK) return st;
     if (prm[b].model != prm[0].model || prm[b].precision != prm[0].precision ||
-        prm[b].device != prm[0].device || prm[b].stream != prm[0].stream)
-      return fail(PD_ERR_ARG, "bodies must share model, precision, device and stream");
+        prm[b].device != prm[0].device || prm[b].stream != prm[0].stream ||
+        prm[b].kinematics != prm[0].kinematics)
+      return fail(PD_ERR_ARG, "bodies must share model, precision, kinematics, device and stream");
   }
   if (!finite_all(x, n) || !finite_all(y, n) || (z && !finite_all(z, n)) || !finite_all(vol, n))
     return fail(PD_ERR_ARG, "non-finite coordinate or volume");
@@ -312,6 +316,7 @@ pd_status create(pd_ctx** out, int32_t nbodies, const pd_params* prm, const int6
   c->dim = dim;
   c->model = prm[0].model;
   c->precision = prm[0].precision;
+  c->kin = prm[0].kinematics;
   c->n = n;
   c->nslices = (n + kSlice - 1) / kSlice;
   c->n_pad = c->nslices * kSlice;
@@ -471,6 +476,7 @@ pd_status upload_body_params(pd_ctx* c) {
     d.inv_rho = 1.0 / p.rho;
     d.dt = p.dt;
     d.s0 = p.s0;
+    d.s0nl = p.s0 * (2.0 + p.s0);
     d.breaks = p.s0 > 0.0 ? 1 : 0;
     d.rate = 0.0;
     d.Kp32 = (float)(d.Kp * c->q);

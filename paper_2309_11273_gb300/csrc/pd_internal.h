@@ -20,6 +20,7 @@ struct BodyDev {
   double inv_rho;  // 1 / rho
   double dt;       // time step
   double s0;       // critical stretch (<= 0: no breaking)
+  double s0nl;     // s0 (2 + s0): nonlinear break test |Y|^2 - |xi|^2 >= s0nl |xi|^2
   double rate;     // prescribed rotation rate
   float Kp32, G32, inv_rho32, sigma32;  // FP32 copies for the mixed path (sigma32 = s0 * Q)
   double sigma_q;  // s0 * Q in double (Q = fixed-point quantum of the mixed coordinates)
@@ -76,6 +77,7 @@ struct StepArgs {
   const double4* bA;       // tabled FP64 path: per slot (xi, s0 |xi|^2), or nullptr
   const double4* bB;       // tabled FP64 path: per slot (V_j xi, 1 / |xi|^2)
   double* bd;              // tabled FP64 path: per slot xi.(u_j - u_i), written by pass 1
+  double2* bE;             // tabled nonlinear path: per slot (e, 1 / |Y|), written by pass 1 (bA = (xi, |xi|))
 };
 
 struct KernelTimes {
@@ -94,6 +96,7 @@ struct pd_ctx {
   int dim = 3;
   int model = 0;
   int precision = 0;
+  int kin = 0;                    // pd_kinematics
   int64_t n = 0, n_pad = 0, nslices = 0;
   int32_t nbodies = 1;
   std::vector<pd_params> prm;
@@ -134,6 +137,7 @@ struct pd_ctx {
   double4* bA = nullptr;          // FP64 per-slot table (xi, s0 |xi|^2)
   double4* bB = nullptr;          // FP64 per-slot table (V_j xi, 1/|xi|^2)
   double* bd = nullptr;           // FP64 per-slot xi.du of the current step
+  double2* bE = nullptr;          // nonlinear FP64: per-slot (e, 1/|Y|) of the current step
   int bond_cache = 1;             // use the table in the FP64 path
   int stage = 1;                  // mixed path: TMA-staged index streams (split 1)
   double q = 0.0;               // fixed-point quantum of the mixed coordinates [m]

@@ -257,6 +257,284 @@ __global__ void __launch_bounds__(512) k_pass2_f64(StepArgs a, const double4* __
   }
 }
 
+// Geometrically nonlinear FP64 kernels (PD_NONLINEAR): Y = xi + eta, e = |Y| - |xi| (Eq 1.10) and the
+// pair force along M = Y / |Y| (Eq 1.13) with the force state of Eq 1.14.  |Y|^2 - |xi|^2 is formed
+// as eta . (xi + Y) = 2 xi.eta + eta.eta, so e = (|Y|^2 - |xi|^2) / (|Y| + |xi|) carries no
+// cancellation, and the break test e / |xi| >= s0 (Eq 1.30) is taken without square roots as
+// |Y|^2 - |xi|^2 >= s0 (2 + s0) |xi|^2.
+template <int DIM>
+struct BondNL {
+  double yx, yy, yz;  // Y
+  double p;           // |Y|^2 - |xi|^2
+  double q;           // |xi|^2
+};
+
+template <int DIM>
+__device__ __forceinline__ BondNL<DIM> bond_nl(const double4& pi, const double4& pj, const double4& ui,
+                                              const double4& uj) {
+  BondNL<DIM> r;
+  const double ex = pj.x - pi.x, ey = pj.y - pi.y, ez = DIM == 3 ? pj.z - pi.z : 0.0;
+  const double hx = uj.x - ui.x, hy = uj.y - ui.y, hz = DIM == 3 ? uj.z - ui.z : 0.0;
+  r.yx = ex + hx;
+  r.yy = ey + hy;
+  r.yz = ez + hz;
+  r.p = hx * (ex + r.yx) + hy * (ey + r.yy);
+  r.q = ex * ex + ey * ey;
+  if (DIM == 3) {
+    r.p = fma(hz, ez + r.yz, r.p);
+    r.q = fma(ez, ez, r.q);
+  }
+  return r;
+}
+
+template <int DIM, int SPLIT>
+__global__ void __launch_bounds__(512) k_pass1_nl(StepArgs a, const double4* __restrict__ disp,
+                                                   int write_theta) {
+  const SliceIdx t = slice_index<SPLIT>(a.n_pad, a.slice_ptr);
+  if (write_theta && blockIdx.x == 0 && threadIdx.x == 0) *a.d_step += 1;
+  double acc[1] = {0.0};
+  int b = 0;
+  if (t.active) {
+    b = a.body ? a.body[t.i] : 0;
+    const double s0nl = a.bp[b].s0nl;
+    const bool can_break = a.bp[b].breaks != 0;
+    const double4 pi = a.pos[t.i], ui = disp[t.i];
+    uint32_t* __restrict__ bw = a.bits + (t.base >> 5);
+    const int32_t* __restrict__ cl = a.col + t.base + t.lane;
+    constexpr int U = kU64;
+    int32_t jn[U];
+    uint32_t wn[U];
+    load_slots<U, SPLIT>(t, cl, bw, t.sub, jn, wn);
+    for (int k0 = t.sub; k0 < t.W; k0 += U * SPLIT) {
+      uint32_t wd[U];
+      double4 pj[U], uj[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        wd[u] = wn[u];
+        pj[u] = a.pos[jn[u]];
+        uj[u] = disp[jn[u]];
+      }
+      load_slots<U, SPLIT>(t, cl, bw, k0 + U * SPLIT, jn, wn);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const BondNL<DIM> r = bond_nl<DIM>(pi, pj[u], ui, uj[u]);
+        bool intact = (wd[u] >> t.lane) & 1u;
+        if (a.check) {
+          const bool brk = intact && can_break && r.p >= s0nl * r.q;
+          const unsigned m = __ballot_sync(kFull, brk);
+          if (m) {
+            intact = intact && !brk;
+            if (t.lane == 0) bw[k0 + u * SPLIT] = wd[u] & ~m;
+          }
+        }
+        if (intact) {
+          double yl2 = r.yx * r.yx + r.yy * r.yy;
+          if (DIM == 3) yl2 = fma(r.yz, r.yz, yl2);
+          const double xl = sqrt(r.q);
+          const double e = r.p / (sqrt(yl2) + xl);
+          acc[0] = fma(pj[u].w * xl, e, acc[0]);  // Eq 1.6: w x e V_j
+        }
+      }
+    }
+  }
+  split_reduce<SPLIT, 1>(acc);
+  if (t.active && t.sub == 0 && write_theta) {
+    const double th = a.aA[t.i] * acc[0];
+    const double mu = a.mu[t.i];
+    a.theta[t.i] = th;
+    a.thm[t.i] = make_double2(a.bp[b].Kp * (th * mu), a.bp[b].G * mu);
+  }
+}
+
+template <int DIM, int SPLIT>
+__global__ void __launch_bounds__(512) k_pass2_nl(StepArgs a, const double4* __restrict__ disp,
+                                                   double4* __restrict__ disp_out) {
+  const SliceIdx t = slice_index<SPLIT>(a.n_pad, a.slice_ptr);
+  double f[3] = {0.0, 0.0, 0.0};
+  int b = 0;
+  if (t.active) {
+    b = a.body ? a.body[t.i] : 0;
+    const double4 pi = a.pos[t.i], ui = disp[t.i];
+    const double2 ti = a.thm[t.i];
+    const uint32_t* __restrict__ bw = a.bits + (t.base >> 5);
+    const int32_t* __restrict__ cl = a.col + t.base + t.lane;
+    constexpr int U = kU64;
+    int32_t jn[U];
+    uint32_t wn[U];
+    load_slots<U, SPLIT>(t, cl, bw, t.sub, jn, wn);
+    for (int k0 = t.sub; k0 < t.W; k0 += U * SPLIT) {
+      uint32_t wd[U];
+      double4 pj[U], uj[U];
+      double2 tj[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        wd[u] = wn[u];
+        pj[u] = a.pos[jn[u]];
+        uj[u] = disp[jn[u]];
+        tj[u] = a.thm[jn[u]];
+      }
+      load_slots<U, SPLIT>(t, cl, bw, k0 + U * SPLIT, jn, wn);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (!((wd[u] >> t.lane) & 1u)) continue;
+        const BondNL<DIM> r = bond_nl<DIM>(pi, pj[u], ui, uj[u]);
+        double yl2 = r.yx * r.yx + r.yy * r.yy;
+        if (DIM == 3) yl2 = fma(r.yz, r.yz, yl2);
+        const double yl = sqrt(yl2), xl = sqrt(r.q);
+        const double e = r.p / (yl + xl);
+        // Eq 1.14 for both ends: [(K - G/3)(theta_i/m_i + theta_j/m_j) |xi| + G (1/m_i + 1/m_j) e] V_j,
+        // along M = Y / |Y| (Eq 1.13)
+        const double c = fma(ti.x + tj[u].x, xl, (ti.y + tj[u].y) * e) * pj[u].w / yl;
+        f[0] = fma(c, r.yx, f[0]);
+        f[1] = fma(c, r.yy, f[1]);
+        if (DIM == 3) f[2] = fma(c, r.yz, f[2]);
+      }
+    }
+  }
+  split_reduce<SPLIT, 3>(f);
+  if (t.active && t.sub == 0) {
+    double4 u;
+    update(a, t.i, b, f, disp, disp_out, u);
+  }
+}
+
+// Tabled nonlinear FP64 kernels (PD_OPT_BOND_CACHE on): per slot the reference vector and length
+// (xi, |xi|) are read from a table built once per family, and pass 1 leaves (e, 1/|Y|) of every slot
+// in a second table, so pass 2 forms only Y = xi + eta and the force along Y / |Y| (no root, no divide).
+template <int DIM, int SPLIT>
+__global__ void __launch_bounds__(512) k_pass1_nlt(StepArgs a, const double4* __restrict__ disp,
+                                                    int write_theta) {
+  const SliceIdx t = slice_index<SPLIT>(a.n_pad, a.slice_ptr);
+  if (write_theta && blockIdx.x == 0 && threadIdx.x == 0) *a.d_step += 1;
+  double acc[1] = {0.0};
+  int b = 0;
+  if (t.active) {
+    b = a.body ? a.body[t.i] : 0;
+    const double s0nl = a.bp[b].s0nl;
+    const bool can_break = a.bp[b].breaks != 0;
+    const double4 ui = disp[t.i];
+    uint32_t* __restrict__ bw = a.bits + (t.base >> 5);
+    const int32_t* __restrict__ cl = a.col + t.base + t.lane;
+    const double4* __restrict__ ta = a.bA + t.base + t.lane;
+    double2* __restrict__ te = a.bE + t.base + t.lane;
+    constexpr int U = kU64;
+    int32_t jn[U];
+    uint32_t wn[U];
+    load_slots<U, SPLIT>(t, cl, bw, t.sub, jn, wn);
+    for (int k0 = t.sub; k0 < t.W; k0 += U * SPLIT) {
+      uint32_t wd[U];
+      double4 g[U], uj[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int k = min(k0 + u * SPLIT, t.W - 1);
+        wd[u] = wn[u];
+        g[u] = ta[(int64_t)k << 5];
+        uj[u] = disp[jn[u]];
+      }
+      load_slots<U, SPLIT>(t, cl, bw, k0 + U * SPLIT, jn, wn);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const double hx = uj[u].x - ui.x, hy = uj[u].y - ui.y, hz = DIM == 3 ? uj[u].z - ui.z : 0.0;
+        const double yx = g[u].x + hx, yy = g[u].y + hy, yz = g[u].z + hz;
+        double p = hx * (g[u].x + yx) + hy * (g[u].y + yy);
+        if (DIM == 3) p = fma(hz, g[u].z + yz, p);
+        const int k = k0 + u * SPLIT;
+        bool intact = (wd[u] >> t.lane) & 1u;
+        if (a.check) {
+          const bool brk = intact && can_break && p >= s0nl * (g[u].w * g[u].w);
+          const unsigned m = __ballot_sync(kFull, brk);
+          if (m) {
+            intact = intact && !brk;
+            if (t.lane == 0) bw[k] = wd[u] & ~m;
+          }
+        }
+        if (intact) {
+          double yl2 = yx * yx + yy * yy;
+          if (DIM == 3) yl2 = fma(yz, yz, yl2);
+          const double ry = rsqrt(yl2);
+          const double e = p / fma(yl2, ry, g[u].w);
+          te[(int64_t)k << 5] = make_double2(e, ry);
+          acc[0] = fma(uj[u].w * g[u].w, e, acc[0]);  // Eq 1.6: w x e V_j
+        }
+      }
+    }
+  }
+  split_reduce<SPLIT, 1>(acc);
+  if (t.active && t.sub == 0 && write_theta) {
+    const double th = a.aA[t.i] * acc[0];
+    const double mu = a.mu[t.i];
+    a.theta[t.i] = th;
+    a.thm[t.i] = make_double2(a.bp[b].Kp * (th * mu), a.bp[b].G * mu);
+  }
+}
+
+template <int DIM, int SPLIT>
+__global__ void __launch_bounds__(512) k_pass2_nlt(StepArgs a, const double4* __restrict__ disp,
+                                                    double4* __restrict__ disp_out) {
+  const SliceIdx t = slice_index<SPLIT>(a.n_pad, a.slice_ptr);
+  double f[3] = {0.0, 0.0, 0.0};
+  int b = 0;
+  if (t.active) {
+    b = a.body ? a.body[t.i] : 0;
+    const double4 ui = disp[t.i];
+    const double2 ti = a.thm[t.i];
+    const uint32_t* __restrict__ bw = a.bits + (t.base >> 5);
+    const int32_t* __restrict__ cl = a.col + t.base + t.lane;
+    const double4* __restrict__ ta = a.bA + t.base + t.lane;
+    const double2* __restrict__ te = a.bE + t.base + t.lane;
+    constexpr int U = kU64;
+    int32_t jn[U];
+    uint32_t wn[U];
+    load_slots<U, SPLIT>(t, cl, bw, t.sub, jn, wn);
+    for (int k0 = t.sub; k0 < t.W; k0 += U * SPLIT) {
+      uint32_t wd[U];
+      double4 g[U], uj[U];
+      double2 tj[U], ev[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int k = min(k0 + u * SPLIT, t.W - 1);
+        wd[u] = wn[u];
+        const bool on = (wd[u] >> t.lane) & 1u;
+        g[u] = ta[(int64_t)k << 5];
+        ev[u] = on ? te[(int64_t)k << 5] : make_double2(0.0, 0.0);
+        uj[u] = disp[jn[u]];
+        tj[u] = a.thm[jn[u]];
+      }
+      load_slots<U, SPLIT>(t, cl, bw, k0 + U * SPLIT, jn, wn);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const double yx = g[u].x + (uj[u].x - ui.x), yy = g[u].y + (uj[u].y - ui.y);
+        const double yz = DIM == 3 ? g[u].z + (uj[u].z - ui.z) : 0.0;
+        // Eq 1.14 for both ends along M = Y / |Y| (Eq 1.13); 0 for broken and unused slots (ev = 0)
+        const double c = fma(ti.x + tj[u].x, g[u].w, (ti.y + tj[u].y) * ev[u].x) * (uj[u].w * ev[u].y);
+        f[0] = fma(c, yx, f[0]);
+        f[1] = fma(c, yy, f[1]);
+        if (DIM == 3) f[2] = fma(c, yz, f[2]);
+      }
+    }
+  }
+  split_reduce<SPLIT, 3>(f);
+  if (t.active && t.sub == 0) {
+    double4 u;
+    update(a, t.i, b, f, disp, disp_out, u);
+  }
+}
+
+template <int DIM>
+__global__ void k_bond_tables_nl(StepArgs a, double4* __restrict__ bA) {
+  const SliceIdx t = slice_index<1>(a.n_pad, a.slice_ptr);
+  if (!t.active) return;
+  const double4 pi = a.pos[t.i];
+  const double4 zero = make_double4(0.0, 0.0, 0.0, 0.0);
+  for (int k = 0; k < t.W; ++k) {
+    const int64_t e = t.base + t.lane + ((int64_t)k << 5);
+    const double4 pj = a.pos[a.col[e]];
+    double ex, ey, ez, d, q;
+    bond_f64<DIM>(pi, pj, zero, zero, ex, ey, ez, d, q);
+    bA[e] = make_double4(ex, ey, ez, sqrt(q));
+  }
+}
+
 // Tabled FP64 kernels.  GB300 issues FP64 at 1/64 of the FP32 rate, so everything that does not
 // depend on the displacement is computed once per family into per-slot tables:
 //   bA = (xi, s0 |xi|^2)            read by pass 1 (the break test xi.du >= s0 |xi|^2, Eq 1.30);
@@ -980,12 +1258,17 @@ StepArgs make_args(pd_ctx* c) {
   a.bA = c->bond_cache ? c->bA : nullptr;
   a.bB = c->bond_cache ? c->bB : nullptr;
   a.bd = c->bond_cache ? c->bd : nullptr;
+  a.bE = c->bond_cache ? c->bE : nullptr;
   return a;
 }
 
 template <int DIM, int SPLIT>
 void launch_pass1(pd_ctx* c, const StepArgs& a, int write_theta, unsigned grid, int block, size_t sm) {
-  if (c->precision == PD_FP64 && a.bA)
+  if (c->kin == PD_NONLINEAR && a.bA)
+    k_pass1_nlt<DIM, SPLIT><<<grid, block, sm, c->stream>>>(a, c->disp[c->cur], write_theta);
+  else if (c->kin == PD_NONLINEAR)
+    k_pass1_nl<DIM, SPLIT><<<grid, block, sm, c->stream>>>(a, c->disp[c->cur], write_theta);
+  else if (c->precision == PD_FP64 && a.bA)
     k_pass1_f64t<DIM, SPLIT><<<grid, block, sm, c->stream>>>(a, c->disp[c->cur], write_theta);
   else if (c->precision == PD_FP64)
     k_pass1_f64<DIM, SPLIT><<<grid, block, sm, c->stream>>>(a, c->disp[c->cur], write_theta);
@@ -995,7 +1278,11 @@ void launch_pass1(pd_ctx* c, const StepArgs& a, int write_theta, unsigned grid, 
 
 template <int DIM, int SPLIT>
 void launch_pass2(pd_ctx* c, const StepArgs& a, unsigned grid, int block, size_t sm) {
-  if (c->precision == PD_FP64 && a.bA)
+  if (c->kin == PD_NONLINEAR && a.bA)
+    k_pass2_nlt<DIM, SPLIT><<<grid, block, sm, c->stream>>>(a, c->disp[c->cur], c->disp[c->cur ^ 1]);
+  else if (c->kin == PD_NONLINEAR)
+    k_pass2_nl<DIM, SPLIT><<<grid, block, sm, c->stream>>>(a, c->disp[c->cur], c->disp[c->cur ^ 1]);
+  else if (c->precision == PD_FP64 && a.bA)
     k_pass2_f64t<DIM, SPLIT><<<grid, block, sm, c->stream>>>(a, c->disp[c->cur], c->disp[c->cur ^ 1]);
   else if (c->precision == PD_FP64)
     k_pass2_f64<DIM, SPLIT><<<grid, block, sm, c->stream>>>(a, c->disp[c->cur], c->disp[c->cur ^ 1]);
@@ -1075,6 +1362,19 @@ pd_status ensure_bond_cache(pd_ctx* c) {
   if (!c->bond_cache || c->precision != PD_FP64 || c->bA) return PD_OK;
   pd_status st;
   const size_t ne = (size_t)std::max<int64_t>(c->nentries, 32);
+  if (c->kin == PD_NONLINEAR) {
+    if ((st = alloc(c, &c->bA, ne)) != PD_OK) return st;
+    if ((st = alloc(c, &c->bE, ne)) != PD_OK) return st;
+    StepArgs a = make_args(c);
+    const int tb = 256;
+    const unsigned grid = (unsigned)((c->n_pad + tb - 1) / tb);
+    if (c->dim == 3)
+      k_bond_tables_nl<3><<<grid, tb, 0, c->stream>>>(a, c->bA);
+    else
+      k_bond_tables_nl<2><<<grid, tb, 0, c->stream>>>(a, c->bA);
+    PD_CUDA(cudaGetLastError());
+    return PD_OK;
+  }
   if ((st = alloc(c, &c->bA, ne)) != PD_OK) return st;
   if ((st = alloc(c, &c->bB, ne)) != PD_OK) return st;
   if ((st = alloc(c, &c->bd, ne)) != PD_OK) return st;

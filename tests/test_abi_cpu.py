@@ -61,7 +61,9 @@ def _prm(**kw):
 
 @pytest.mark.parametrize("kw,msg", [(dict(E=-1.0), "E"), (dict(nu=0.5), "nu"), (dict(rho=0.0), "rho"),
                                     (dict(horizon=0.0), "horizon"), (dict(dt=float("nan")), "dt"),
-                                    (dict(model=5), "model"), (dict(precision=3), "precision")])
+                                    (dict(model=5), "model"), (dict(precision=3), "precision"),
+                                    (dict(kinematics=2), "kinematics"),
+                                    (dict(kinematics=B.PD_NONLINEAR, precision=B.PD_MIXED), "PD_FP64 only")])
 def test_create_rejects_bad_parameters(lib, kw, msg):
     with pytest.raises(B.PDError) as e:
         B.pd_create_particles(_prm(**kw), np.zeros(4), np.arange(4.0), None, np.ones(4))
@@ -84,3 +86,10 @@ def test_null_context_is_an_argument_error(lib):
     assert lib.pd_step(None, 1) == B.PD_ERR_ARG
     assert lib.pd_sync(None) == B.PD_ERR_ARG
     lib.pd_destroy(None)  # no-op
+
+
+def test_batch_bodies_must_share_kinematics(lib):
+    prms = [_prm(), _prm(kinematics=B.PD_NONLINEAR)]
+    with pytest.raises(B.PDError) as e:
+        B.pd_create_batch(prms, [0, 2, 4], np.arange(4.0), np.zeros(4), None, np.ones(4))
+    assert e.value.status == B.PD_ERR_ARG and "kinematics" in str(e.value)
