@@ -123,10 +123,14 @@ typedef enum {
                               geometry (xi, 1/|xi|^2, s0 |xi|^2; 40 bytes per bond slot) so each
                               step evaluates only displacement-dependent FP64 terms; 0 = recompute
                               the geometry from the coordinates every step */
-  PD_OPT_STAGE = 7         /* PD_MIXED with split 1: 1 (default) = stream each warp's neighbour
+  PD_OPT_STAGE = 7,        /* PD_MIXED with split 1: 1 (default) = stream each warp's neighbour
                               indices and status words into shared memory with bulk asynchronous
                               copies (bounded waits; an expired wait makes the next pd_sync /
                               pd_get_* return PD_ERR_TIMEOUT); 0 = direct loads */
+  PD_OPT_EXPIRE_WAITS = 8  /* testing the failure path: 1 = the staged kernels (PD_MIXED, split 1)
+                              do not issue each warp's first index copy, so its bounded wait (1 s
+                              of the GPU's global timer) expires; the warps skip their outputs
+                              and the next pd_sync / pd_get_* returns PD_ERR_TIMEOUT.  Default 0. */
 } pd_option;
 
 /* Kernel identifiers for pd_get_profile. */

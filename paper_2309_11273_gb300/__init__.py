@@ -74,6 +74,9 @@ class Simulation:
     def set_option(self, opt, value):
         B.pd_set_option(self.h, opt, value)
 
+    def get_option(self, opt) -> int:
+        return B.pd_get_option(self.h, opt)
+
     def close(self):
         if self.h:
             B.pd_destroy(self.h)

@@ -466,6 +466,9 @@ pd_status pd_set_option(pd_ctx* c, int32_t option, int64_t value) {
     case PD_OPT_STAGE:
       c->stage = value != 0;
       break;
+    case PD_OPT_EXPIRE_WAITS:
+      c->expire_waits = value != 0;
+      break;
     default:
       return fail(PD_ERR_ARG, "unknown option");
   }
@@ -485,6 +488,7 @@ pd_status pd_get_option(pd_ctx* c, int32_t option, int64_t* value) {
     case PD_OPT_SPLIT: *value = c->split; break;
     case PD_OPT_BOND_CACHE: *value = c->bond_cache; break;
     case PD_OPT_STAGE: *value = c->stage; break;
+    case PD_OPT_EXPIRE_WAITS: *value = c->expire_waits; break;
     default: return fail(PD_ERR_ARG, "unknown option");
   }
   return PD_OK;

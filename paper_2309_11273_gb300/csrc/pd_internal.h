@@ -78,6 +78,7 @@ struct StepArgs {
   const double4* bB;       // tabled FP64 path: per slot (V_j xi, 1 / |xi|^2)
   double* bd;              // tabled FP64 path: per slot xi.(u_j - u_i), written by pass 1
   double2* bE;             // tabled nonlinear path: per slot (e, 1 / |Y|), written by pass 1 (bA = (xi, |xi|))
+  int expire;              // testing (PD_OPT_EXPIRE_WAITS): staged kernels skip their first copy
 };
 
 struct KernelTimes {
@@ -140,6 +141,7 @@ struct pd_ctx {
   double2* bE = nullptr;          // nonlinear FP64: per-slot (e, 1/|Y|) of the current step
   int bond_cache = 1;             // use the table in the FP64 path
   int stage = 1;                  // mixed path: TMA-staged index streams (split 1)
+  int expire_waits = 0;           // testing: make the staged kernels' first wait expire
   double q = 0.0;               // fixed-point quantum of the mixed coordinates [m]
   double qlo[3] = {0, 0, 0};     // origin of the fixed-point coordinates
   // state

@@ -280,6 +280,31 @@ def test_unstable_time_step_trips_the_guard():
     sim.close()
 
 
+def test_expired_wait_reports_timeout_and_context_recovers():
+    """Failure path of the bounded waits: with PD_OPT_EXPIRE_WAITS the staged kernels never issue
+    each warp's first index copy, so that wait runs out (1 s of the GPU timer), the warps skip their
+    outputs and the next pd_sync returns PD_ERR_TIMEOUT; the context stays usable and a clean rerun
+    equals a fresh run bitwise."""
+    w = W.plate_vibration(nx=16, ny=8, nsteps=20)
+    sim = Simulation(w, s0=0.0, precision=PD_MIXED, graph_chunk=0)
+    assert sim.get_option(B.PD_OPT_STAGE) == 1 and sim.get_option(B.PD_OPT_SPLIT) == 1
+    sim.set_option(B.PD_OPT_EXPIRE_WAITS, 1)
+    sim.step(1)
+    with pytest.raises(B.PDError) as e:
+        sim.sync()
+    assert e.value.status == B.PD_ERR_TIMEOUT
+    sim.set_option(B.PD_OPT_EXPIRE_WAITS, 0)
+    sim.sync()  # the error word was cleared when it was reported
+    sim.set_state(w.initial_u())
+    sim.step(20)
+    u = sim.state()[0]
+    sim.close()
+    ref = Simulation(w, s0=0.0, precision=PD_MIXED, graph_chunk=0)
+    ref.step(20)
+    assert np.array_equal(u, ref.state()[0])
+    ref.close()
+
+
 # ------------------------------------------------------------------------------------ batched
 def _small_batch(n=5, seed=4):
     return W.plate_batch(nplates=n, seed=seed, side_lo=10, side_hi=40, nsteps=200)
