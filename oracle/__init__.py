@@ -19,6 +19,8 @@ sequences the calls.  Equation references are to the paper:
 * Eqs 1.17, 1.30        -> :func:`failure`
 * Eq 1.31               -> :func:`damage`
 * Eq 2.11 + Appendix B  -> :class:`OracleSim`
+* adaptive dynamic relaxation (Section 4.4's quasi-static solver) -> :func:`adr_lambda`,
+  :meth:`OracleSim.adr_step`
 
 Parity unpinned: none (every function is pinned by the ``-m "not gpu"`` tests).
 """
@@ -93,6 +95,13 @@ def lib():
                                   + [_u8, _d, _d, _d, _d, _d, ctypes.c_double, ctypes.c_int64,
                                      ctypes.c_int64]
                                   + [_d] * 10 + [_d, _i64])
+            L.orc_adr_lambda.argtypes = [ctypes.c_int64, ctypes.c_int, _d, _d, _d, _d, _i64, _i32, _d, _d,
+                                         _d, _d, _d]
+            L.orc_adr_run.argtypes = ([ctypes.c_int, ctypes.c_int64, ctypes.c_int, _d, _d, _d, _d, _i64, _i32,
+                                       _u8, _d, _d, _d, _d, _d, ctypes.c_double, _u8, _d, _d, _d, _d, _d,
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_int64, ctypes.c_int64,
+                                       ctypes.c_int]
+                                      + [_d] * 13 + [_d, _d, _i64])
             _lib = L
     return _lib
 
@@ -222,6 +231,20 @@ def failure(x, y, z, row_ptr, col, status, s0, u, kin=LINEARIZED):
     return int(nb), mm.value
 
 
+def adr_lambda(x, y, z, vol, row_ptr, col, m, A, K, G):
+    """Fictitious ADR density lambda_i = R_i / 4 (R_i: Gerschgorin bound of the force-density
+    stiffness row sums); A, K, G per particle."""
+    x, y, z, vol, m = _f64(x), _f64(y), _f64(z), _f64(vol), _f64(m)
+    n = x.size
+    A, K, G = (np.broadcast_to(np.asarray(t, dtype=np.float64), (n,)).copy() for t in (A, K, G))
+    lam = np.zeros(n)
+    dim = 3 if z is not None else 2
+    zz = z if z is not None else x
+    lib().orc_adr_lambda(n, dim, _p(x, _d), _p(y, _d), _p(zz, _d), _p(vol, _d), _p(row_ptr, _i64),
+                         _p(col, _i32), _p(m, _d), _p(A, _d), _p(K, _d), _p(G, _d), _p(lam, _d))
+    return lam
+
+
 def damage(vol, row_ptr, col, status):
     """phi_i (Eq 1.31)."""
     vol = _f64(vol)
@@ -279,6 +302,7 @@ class OracleSim:
         self.rate = float(rate)
 
     def set_state(self, u, v=None):
+        self._adr_fresh = True
         self.u = np.array(u, dtype=np.float64).reshape(self.dim, self.n).copy()
         self.v = (np.zeros_like(self.u) if v is None
                   else np.array(v, dtype=np.float64).reshape(self.dim, self.n).copy())
@@ -322,3 +346,44 @@ class OracleSim:
 
     def damage(self):
         return damage(self.vol, self.row_ptr, self.col, self.status)
+
+    def adr_step(self, nsteps: int):
+        """Adaptive dynamic relaxation iterations (``orc_adr_run``) from the current state.  The first
+        call after ``set_state`` starts from rest (v = 0); returns (damping c per iteration, min
+        margin per iteration, broken count per iteration).  ``self.v`` holds v^{n-1/2}."""
+        nsteps = int(nsteps)
+        if getattr(self, "lam", None) is None:
+            self.lam = adr_lambda(self.x, self.y, self.z, self.vol, self.row_ptr, self.col, self.m,
+                                  self.A, self.K, self.G)
+        first = 1 if getattr(self, "_adr_fresh", True) else 0
+        if first:
+            self.v = np.zeros_like(self.u)
+            self.g = np.zeros((3, self.n))
+        damping = np.zeros(max(nsteps, 1))
+        margins = np.zeros(max(nsteps, 1))
+        broken = np.zeros(max(nsteps, 1), dtype=np.int64)
+        u = [np.ascontiguousarray(self.u[k]) if k < self.dim else np.zeros(self.n) for k in range(3)]
+        v = [np.ascontiguousarray(self.v[k]) if k < self.dim else np.zeros(self.n) for k in range(3)]
+        g = [np.ascontiguousarray(self.g[k]) for k in range(3)]
+        f = [np.zeros(self.n) for _ in range(3)]
+        zz = self.z if self.z is not None else self.x
+        b = self.b
+        bx = b[0].copy() if b is not None else None
+        by = b[1].copy() if b is not None else None
+        bz = b[2].copy() if (b is not None and self.dim == 3) else None
+        A, K, G = (np.full(self.n, t) for t in (self.A, self.K, self.G))
+        lib().orc_adr_run(self.kin, self.n, self.dim, _p(self.x, _d), _p(self.y, _d), _p(zz, _d),
+                          _p(self.vol, _d), _p(self.row_ptr, _i64), _p(self.col, _i32), _p(self.status, _u8),
+                          _p(self.m, _d), _p(A, _d), _p(K, _d), _p(G, _d), _p(self.lam, _d), self.s0,
+                          _p(self.flag, _u8), _p(bx, _d), _p(by, _d), _p(bz, _d), _p(self.axis_point, _d),
+                          _p(self.axis_dir, _d), self.rate, self.dt, self.steps_done, nsteps, first,
+                          _p(u[0], _d), _p(u[1], _d), _p(u[2], _d), _p(v[0], _d), _p(v[1], _d), _p(v[2], _d),
+                          _p(g[0], _d), _p(g[1], _d), _p(g[2], _d), _p(self.theta, _d), _p(f[0], _d),
+                          _p(f[1], _d), _p(f[2], _d), _p(damping, _d), _p(margins, _d), _p(broken, _i64))
+        self.u = np.stack(u[:self.dim])
+        self.v = np.stack(v[:self.dim])
+        self.g = np.stack(g)
+        self.f = np.stack(f[:self.dim])
+        self._adr_fresh = False
+        self.steps_done += nsteps
+        return damping[:nsteps], margins[:nsteps], broken[:nsteps]

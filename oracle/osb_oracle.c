@@ -552,3 +552,152 @@ void orc_run(int kin, int64_t n, int dim, const double* x, const double* y, cons
     if (broken) broken[s] = nb;
   }
 }
+
+/* ------------------------------------------------------------------------------------------------
+ * Adaptive dynamic relaxation (the quasi-static solver of Section 4.4, which cites Underwood 1983 and
+ * Kilic & Madenci 2010 for it).  The static problem f(u) + b = 0 (f = F_i / V_i, the internal force
+ * density) is solved as the damped fictitious dynamics  L u'' + c L u' = f(u) + b  with a diagonal
+ * fictitious density L = diag(lambda_i), fictitious time step 1, and the damping c re-estimated every
+ * iteration from a Rayleigh quotient of the local (diagonal) stiffness.
+ * ---------------------------------------------------------------------------------------------- */
+
+/* Fictitious density lambda_i = (1/4) R_i (time step 1), where R_i bounds the absolute row sums of
+ * the stiffness of the force density, |d f_ia / d u_kb| summed over k, b, for every component a
+ * (Gerschgorin: then every eigenvalue of L^-1 K is at most 4 and the unit step is stable).  For the
+ * linearized force of Eq 2.2, with |M_ij|_1 = |xi_ij|_1 / |xi_ij| and
+ *   alpha_i = (A / m_i) sum_l |xi_il| V_l |M_il|_1        (bound of sum |d theta_i / d u|, halved),
+ *   R_i = 2 G sum_j (1/m_i + 1/m_j) V_j |M_ij|_1 + 2 |K - G/3| sum_j |xi_ij| V_j (alpha_i/m_i + alpha_j/m_j),
+ * the first term from the extension part and the second from the dilatation part; sums over the
+ * built family.  K, G, A per particle (a body's constants). */
+void orc_adr_lambda(int64_t n, int dim, const double* x, const double* y, const double* z,
+                    const double* vol, const int64_t* row_ptr, const int32_t* col, const double* m,
+                    const double* A, const double* K, const double* G, double* lambda) {
+  double* alpha = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    double s = 0.0;
+    for (int64_t b = row_ptr[i]; b < row_ptr[i + 1]; ++b) {
+      double xi[3];
+      double xl = bond_vector(dim, x, y, z, i, col[b], xi);
+      double m1 = (fabs(xi[0]) + fabs(xi[1]) + fabs(xi[2])) / xl;
+      s += xl * vol[col[b]] * m1;
+    }
+    alpha[i] = (m[i] > 0.0) ? A[i] * s / m[i] : 0.0;
+  }
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    double rg = 0.0, rt = 0.0;
+    for (int64_t b = row_ptr[i]; b < row_ptr[i + 1]; ++b) {
+      int64_t j = col[b];
+      double xi[3];
+      double xl = bond_vector(dim, x, y, z, i, j, xi);
+      double m1 = (fabs(xi[0]) + fabs(xi[1]) + fabs(xi[2])) / xl;
+      rg += (1.0 / m[i] + 1.0 / m[j]) * vol[j] * m1;
+      rt += xl * vol[j] * (alpha[i] / m[i] + alpha[j] / m[j]);
+    }
+    double R = 2.0 * G[i] * rg + 2.0 * fabs(K[i] - G[i] / 3.0) * rt;
+    lambda[i] = 0.25 * R;
+  }
+  free(alpha);
+}
+
+/* ADR iterations.  Iteration n (fictitious time step 1; boundary values at t_n = n dt as in orc_run):
+ *   1. boundary conditions at t_n;
+ *   2. g^n = f(u^n) + b (force density: internal force / V_i plus the body-force density);
+ *   3. damping: c^n = 2 sqrt( sum u.(k u) / sum u.u ) over the free particles' components, with the
+ *      local stiffness k_ia = -(g_ia^n - g_ia^{n-1}) / (lambda_i v_ia^{n-1/2}) (0 where v_ia = 0);
+ *      c^n = 0 when the quotient is not positive or sum u.u = 0;
+ *   4. free particles: v^{n+1/2} = ((2 - c^n) v^{n-1/2} + 2 g^n / lambda_i) / (2 + c^n), except on the
+ *      first iteration of a run (first != 0), which starts from rest: v^{1/2} = g^0 / (2 lambda_i);
+ *      u^{n+1} = u^n + v^{n+1/2};  constrained particles take their boundary value at t_{n+1};
+ *   5. failure check on u^{n+1} (Eq 1.30), when s0 > 0.
+ * v holds v^{n-1/2} on entry and g_prev (3 arrays) the previous g; both are updated.  damping[k]
+ * (may be NULL) receives c of iteration k. */
+void orc_adr_run(int kin, int64_t n, int dim, const double* x, const double* y, const double* z,
+                 const double* vol, const int64_t* row_ptr, const int32_t* col, uint8_t* status,
+                 const double* m, const double* A, const double* K, const double* G,
+                 const double* lambda, double s0, const uint8_t* flag, const double* bx,
+                 const double* by, const double* bz, const double* axis_point, const double* axis_dir,
+                 double rate, double dt, int64_t step0, int64_t nsteps, int first, double* ux,
+                 double* uy, double* uz, double* vx, double* vy, double* vz, double* gx, double* gy,
+                 double* gz, double* theta, double* fx, double* fy, double* fz, double* damping,
+                 double* margins, int64_t* broken) {
+  double c[3] = {0, 0, 0}, a[3] = {0, 0, 0};
+  if (axis_point)
+    for (int k = 0; k < 3; ++k) c[k] = axis_point[k];
+  if (axis_dir)
+    for (int k = 0; k < 3; ++k) a[k] = axis_dir[k];
+  double* u[3] = {ux, uy, uz};
+  double* v[3] = {vx, vy, vz};
+  double* gp[3] = {gx, gy, gz};
+  double* f[3] = {fx, fy, fz};
+  const double* bb[3] = {bx, by, bz};
+  for (int64_t s = 0; s < nsteps; ++s) {
+    int64_t step = step0 + s;
+    double tn = (double)step * dt, tn1 = (double)(step + 1) * dt;
+    apply_bc(n, dim, x, y, z, flag, c, a, rate, tn, ux, uy, uz, vx, vy, vz);
+    /* theta and internal forces with per-particle constants: one call per distinct (A, K, G) would
+     * do, but bodies are independent, so the per-particle form below is the same sum. */
+    for (int64_t i = 0; i < n; ++i) theta[i] = 0.0;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+      double sum = 0.0;
+      for (int64_t b = row_ptr[i]; b < row_ptr[i + 1]; ++b) {
+        if (!status[b]) continue;
+        int64_t j = col[b];
+        double xi[3], M[3];
+        double xl = bond_vector(dim, x, y, z, i, j, xi);
+        sum += xl * bond_kinematics(kin, dim, xi, xl, ux, uy, uz, i, j, M) * vol[j];
+      }
+      theta[i] = (m[i] > 0.0) ? A[i] * sum / m[i] : 0.0;
+    }
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+      double fi[3] = {0.0, 0.0, 0.0};
+      for (int64_t b = row_ptr[i]; b < row_ptr[i + 1]; ++b) {
+        if (!status[b]) continue;
+        int64_t j = col[b];
+        double xi[3], M[3];
+        double xl = bond_vector(dim, x, y, z, i, j, xi);
+        double e = bond_kinematics(kin, dim, xi, xl, ux, uy, uz, i, j, M);
+        double th = theta[i] / m[i] + theta[j] / m[j];
+        double et = e / m[i] + e / m[j];
+        double mag = ((K[i] - G[i] / 3.0) * th * xl + G[i] * et) * vol[j];  /* per unit V_i */
+        for (int k = 0; k < dim; ++k) fi[k] += mag * M[k];
+      }
+      for (int k = 0; k < dim; ++k) f[k][i] = fi[k] + (bb[k] ? bb[k][i] : 0.0);
+    }
+    double num = 0.0, den = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+      if (flag && flag[i] != ORC_FREE) continue;
+      for (int k = 0; k < dim; ++k) {
+        double kk = 0.0;
+        if (v[k][i] != 0.0) kk = -(f[k][i] - gp[k][i]) / (lambda[i] * v[k][i]);
+        num += u[k][i] * kk * u[k][i];
+        den += u[k][i] * u[k][i];
+      }
+    }
+    double cn = (den > 0.0 && num > 0.0) ? 2.0 * sqrt(num / den) : 0.0;
+    int start = first && s == 0;
+    if (damping) damping[s] = start ? 0.0 : cn;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+      if (flag && flag[i] != ORC_FREE) continue;
+      for (int k = 0; k < dim; ++k) {
+        if (start)
+          v[k][i] = f[k][i] / (2.0 * lambda[i]);
+        else
+          v[k][i] = ((2.0 - cn) * v[k][i] + 2.0 * f[k][i] / lambda[i]) / (2.0 + cn);
+        u[k][i] = u[k][i] + v[k][i];
+      }
+    }
+    for (int k = 0; k < dim; ++k)
+      for (int64_t i = 0; i < n; ++i) gp[k][i] = f[k][i];
+    apply_bc(n, dim, x, y, z, flag, c, a, rate, tn1, ux, uy, uz, vx, vy, vz);
+    double mm = 1e300;
+    int64_t nb = 0;
+    if (s0 > 0.0) nb = orc_failure(kin, n, dim, x, y, z, row_ptr, col, status, s0, ux, uy, uz, &mm);
+    if (margins) margins[s] = mm;
+    if (broken) broken[s] = nb;
+  }
+}
