@@ -415,6 +415,21 @@ def run_forms(args, stream, dev, world, fp64_value, nb, hbm, hbm_note):
                                      "algorithmic": "%g FP64 flop per directed bond (%s form; root, divide = 1) x %d"
                                                     " bonds" % (nfl, "tabled" if ntab else "recompute", nb),
                                      "pass1_ms": prof["pass1_ms"], "pass2_ms": prof["pass2_ms"]}}
+    # adaptive dynamic relaxation (the quasi-static solver) on the same block, FP64: per iteration
+    # the two passes plus a damping reduction and the relaxation update
+    sim = Simulation(w, s0=s0, precision=PD_FP64, stream=stream.cuda_stream, device=dev)
+    sim.set_option(B.PD_OPT_SOLVER, B.PD_SOLVER_ADR)
+    amap = B.pd_autotune(sim.h, 3)
+    sim.step(args.warmup)
+    k = max(args.steps, 100)
+    ms = max_over_ranks(timed(sim, stream, k, world), world)
+    aval = world * nb * k / (ms * 1e-3)
+    prof = profiled(sim, 20)
+    sim.close()
+    out["adr"] = {"value": aval, "unit": UNIT, "ms_per_iteration": ms / k, "iterations": k, "dtype": "f64",
+                  "solver": "adaptive dynamic relaxation, clamp + prescribed twist load-stepped per iteration",
+                  "vs_explicit_fp64": aval / fp64_value, "mapping": {"block": amap[0], "split": amap[1]},
+                  "pass1_ms": prof["pass1_ms"], "pass2_and_relaxation_ms": prof["pass2_ms"]}
     # batched: 256 uneven plates (configuration 4) in one context; FP64 and mixed; 100-step graphs
     bw = W.config4()
     res = {}

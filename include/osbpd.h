@@ -127,11 +127,28 @@ typedef enum {
                               indices and status words into shared memory with bulk asynchronous
                               copies (bounded waits; an expired wait makes the next pd_sync /
                               pd_get_* return PD_ERR_TIMEOUT); 0 = direct loads */
-  PD_OPT_EXPIRE_WAITS = 8  /* testing the failure path: 1 = the staged kernels (PD_MIXED, split 1)
+  PD_OPT_EXPIRE_WAITS = 8, /* testing the failure path: 1 = the staged kernels (PD_MIXED, split 1)
                               do not issue each warp's first index copy, so its bounded wait (1 s
                               of the GPU's global timer) expires; the warps skip their outputs
                               and the next pd_sync / pd_get_* returns PD_ERR_TIMEOUT.  Default 0. */
+  PD_OPT_SOLVER = 9        /* pd_solver: PD_SOLVER_EXPLICIT (0, default) or PD_SOLVER_ADR (1) */
 } pd_option;
+
+/* Solvers (PD_OPT_SOLVER).
+ * PD_SOLVER_EXPLICIT: the dynamics of Eq 2.11 with time step pd_params.dt.
+ * PD_SOLVER_ADR: adaptive dynamic relaxation for quasi-static solutions (the solver of the paper's
+ *   Section 4.4, which cites it from the literature): every pd_step iteration solves
+ *   L u'' + c L u' = f(u) + b with fictitious time step 1, a diagonal fictitious density
+ *   lambda_i = R_i / 4 (R_i an upper bound of the absolute row sums of the force-density stiffness,
+ *   so the unit step is stable) and the damping c = 2 sqrt(u.(k u) / u.u) over the free particles'
+ *   components, k_ia = -(g_ia^n - g_ia^{n-1}) / (lambda_i v_ia^{n-1/2}) (g = f + b).  The first
+ *   iteration after selecting the solver or pd_set_state starts from rest (v^{1/2} = g / (2 lambda)).
+ *   pd_params.dt then only advances the boundary-condition clock (t_n = n dt), so a prescribed
+ *   rotation grows by rate * dt per iteration (load stepping); a particle without bonds is held in
+ *   place.  Bond failure is checked after every iteration as in the explicit solver.  PD_FP64 and
+ *   single-body contexts only (PD_ERR_ARG otherwise).  With PD_OPT_PROFILE, the reduction and update
+ *   kernels of an iteration are counted with PD_K_PASS2. */
+typedef enum { PD_SOLVER_EXPLICIT = 0, PD_SOLVER_ADR = 1 } pd_solver;
 
 /* Kernel identifiers for pd_get_profile. */
 typedef enum { PD_K_PASS1 = 0, PD_K_PASS2 = 1, PD_K_COUNT = 2 } pd_kernel;

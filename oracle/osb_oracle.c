@@ -609,6 +609,7 @@ void orc_adr_lambda(int64_t n, int dim, const double* x, const double* y, const 
  *      c^n = 0 when the quotient is not positive or sum u.u = 0;
  *   4. free particles: v^{n+1/2} = ((2 - c^n) v^{n-1/2} + 2 g^n / lambda_i) / (2 + c^n), except on the
  *      first iteration of a run (first != 0), which starts from rest: v^{1/2} = g^0 / (2 lambda_i);
+ *      a particle without bonds (lambda_i = 0, no stiffness) is held in place (v = 0);
  *      u^{n+1} = u^n + v^{n+1/2};  constrained particles take their boundary value at t_{n+1};
  *   5. failure check on u^{n+1} (Eq 1.30), when s0 > 0.
  * v holds v^{n-1/2} on entry and g_prev (3 arrays) the previous g; both are updated.  damping[k]
@@ -669,7 +670,7 @@ void orc_adr_run(int kin, int64_t n, int dim, const double* x, const double* y, 
     }
     double num = 0.0, den = 0.0;
     for (int64_t i = 0; i < n; ++i) {
-      if (flag && flag[i] != ORC_FREE) continue;
+      if ((flag && flag[i] != ORC_FREE) || !(lambda[i] > 0.0)) continue;
       for (int k = 0; k < dim; ++k) {
         double kk = 0.0;
         if (v[k][i] != 0.0) kk = -(f[k][i] - gp[k][i]) / (lambda[i] * v[k][i]);
@@ -683,6 +684,10 @@ void orc_adr_run(int kin, int64_t n, int dim, const double* x, const double* y, 
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
       if (flag && flag[i] != ORC_FREE) continue;
+      if (!(lambda[i] > 0.0)) {  /* no bonds, no stiffness: held in place */
+        for (int k = 0; k < dim; ++k) v[k][i] = 0.0;
+        continue;
+      }
       for (int k = 0; k < dim; ++k) {
         if (start)
           v[k][i] = f[k][i] / (2.0 * lambda[i]);

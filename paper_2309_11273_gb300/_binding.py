@@ -23,6 +23,8 @@ PD_LINEARIZED, PD_NONLINEAR = 0, 1
 PD_OPT_GRAPH_CHUNK, PD_OPT_PROFILE, PD_OPT_VALIDATE, PD_OPT_BLOCK, PD_OPT_SPLIT, PD_OPT_BOND_CACHE = 1, 2, 3, 4, 5, 6
 PD_OPT_STAGE = 7
 PD_OPT_EXPIRE_WAITS = 8
+PD_OPT_SOLVER = 9
+PD_SOLVER_EXPLICIT, PD_SOLVER_ADR = 0, 1
 PD_K_PASS1, PD_K_PASS2 = 0, 1
 
 STATUS_NAMES = {0: "PD_OK", -1: "PD_ERR_ARG", -2: "PD_ERR_STATE", -3: "PD_ERR_OOM", -4: "PD_ERR_CUDA",

@@ -56,6 +56,11 @@ void free_build(pd_ctx* c) {
   c->bB = nullptr;
   c->bd = nullptr;
   c->bE = nullptr;
+  c->lam = nullptr;
+  c->gnew = c->gold = nullptr;
+  c->adr_part = c->adr_st = nullptr;
+  c->adr_first = nullptr;
+  c->adr_restart = true;
   c->u32[0] = c->u32[1] = nullptr;
   c->thm32 = nullptr;
   c->mu32 = c->aA32 = c->theta32 = nullptr;
@@ -304,6 +309,7 @@ pd_status pd_set_state(pd_ctx* c, const double* u, const double* v) {
   if (st != PD_OK) return st;
   c->check_pending = false;
   c->skip_next_check = true;
+  c->adr_restart = true;
   PD_CUDA(cudaStreamSynchronize(c->stream));
   return PD_OK;
 }
@@ -469,6 +475,14 @@ pd_status pd_set_option(pd_ctx* c, int32_t option, int64_t value) {
     case PD_OPT_EXPIRE_WAITS:
       c->expire_waits = value != 0;
       break;
+    case PD_OPT_SOLVER:
+      if (value != PD_SOLVER_EXPLICIT && value != PD_SOLVER_ADR) return fail(PD_ERR_ARG, "unknown solver");
+      if (value == PD_SOLVER_ADR && c->precision != PD_FP64) return fail(PD_ERR_ARG, "PD_SOLVER_ADR runs in PD_FP64 only");
+      if (value == PD_SOLVER_ADR && c->nbodies > 1)
+        return fail(PD_ERR_ARG, "PD_SOLVER_ADR needs a single-body context (its damping is one Rayleigh quotient)");
+      c->solver = (int)value;
+      c->adr_restart = true;
+      break;
     default:
       return fail(PD_ERR_ARG, "unknown option");
   }
@@ -489,6 +503,7 @@ pd_status pd_get_option(pd_ctx* c, int32_t option, int64_t* value) {
     case PD_OPT_BOND_CACHE: *value = c->bond_cache; break;
     case PD_OPT_STAGE: *value = c->stage; break;
     case PD_OPT_EXPIRE_WAITS: *value = c->expire_waits; break;
+    case PD_OPT_SOLVER: *value = c->solver; break;
     default: return fail(PD_ERR_ARG, "unknown option");
   }
   return PD_OK;
@@ -552,20 +567,24 @@ pd_status pd_autotune(pd_ctx* c, int32_t trial_steps, int32_t* block_out, int32_
   if (best_block < 0) {
     // snapshot of everything a step modifies
     const int64_t np = c->n_pad;
-    double4 *su = nullptr, *sv = nullptr;
+    double4 *su = nullptr, *sv = nullptr, *sg = nullptr;
     uint32_t* sb = nullptr;
     float4* s32 = nullptr;
     const size_t nw = (size_t)std::max<int64_t>(c->nentries / 32, 1);
     if (cudaMalloc(&su, sizeof(double4) * np) != cudaSuccess || cudaMalloc(&sv, sizeof(double4) * np) != cudaSuccess ||
         cudaMalloc(&sb, sizeof(uint32_t) * nw) != cudaSuccess ||
-        (c->precision == PD_MIXED && cudaMalloc(&s32, sizeof(float4) * np) != cudaSuccess)) {
+        (c->precision == PD_MIXED && cudaMalloc(&s32, sizeof(float4) * np) != cudaSuccess) ||
+        (c->gold && cudaMalloc(&sg, sizeof(double4) * np) != cudaSuccess)) {
       cudaGetLastError();
       cudaFree(su);
       cudaFree(sv);
       cudaFree(sb);
       cudaFree(s32);
+      cudaFree(sg);
       return fail(PD_ERR_OOM, "autotune snapshot allocation failed");
     }
+    double4* const gold0 = c->gold;  // ADR: previous force density (allocated at the first ADR step)
+    const bool adr_restart0 = c->adr_restart;
     const int cur0 = c->cur;
     const int64_t steps0 = c->steps;
     const bool skip0 = c->skip_next_check, pend0 = c->check_pending;
@@ -575,13 +594,18 @@ pd_status pd_autotune(pd_ctx* c, int32_t trial_steps, int32_t* block_out, int32_
     PD_CUDA(cudaMemcpyAsync(sv, c->vel, sizeof(double4) * np, cudaMemcpyDeviceToDevice, s));
     PD_CUDA(cudaMemcpyAsync(sb, c->bits, sizeof(uint32_t) * nw, cudaMemcpyDeviceToDevice, s));
     if (s32) PD_CUDA(cudaMemcpyAsync(s32, c->u32[cur0], sizeof(float4) * np, cudaMemcpyDeviceToDevice, s));
+    if (sg) PD_CUDA(cudaMemcpyAsync(sg, gold0, sizeof(double4) * np, cudaMemcpyDeviceToDevice, s));
     auto restore = [&]() -> pd_status {
       c->cur = cur0;
       PD_CUDA(cudaMemcpyAsync(c->disp[cur0], su, sizeof(double4) * np, cudaMemcpyDeviceToDevice, s));
       PD_CUDA(cudaMemcpyAsync(c->vel, sv, sizeof(double4) * np, cudaMemcpyDeviceToDevice, s));
       PD_CUDA(cudaMemcpyAsync(c->bits, sb, sizeof(uint32_t) * nw, cudaMemcpyDeviceToDevice, s));
       if (s32) PD_CUDA(cudaMemcpyAsync(c->u32[cur0], s32, sizeof(float4) * np, cudaMemcpyDeviceToDevice, s));
+      if (sg) PD_CUDA(cudaMemcpyAsync(gold0, sg, sizeof(double4) * np, cudaMemcpyDeviceToDevice, s));
       PD_CUDA(cudaStreamSynchronize(s));
+      // an ADR run in progress continues from the restored v and g_prev; one that had not started
+      // (or whose arrays were allocated by the trials) starts from rest
+      c->adr_restart = adr_restart0 || !gold0;
       c->steps = steps0;
       c->skip_next_check = skip0;
       c->check_pending = pend0;
@@ -623,6 +647,7 @@ pd_status pd_autotune(pd_ctx* c, int32_t trial_steps, int32_t* block_out, int32_
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     pd_status st2 = restore();
+    cudaFree(sg);
     cudaFree(su);
     cudaFree(sv);
     cudaFree(sb);

@@ -79,6 +79,8 @@ struct StepArgs {
   double* bd;              // tabled FP64 path: per slot xi.(u_j - u_i), written by pass 1
   double2* bE;             // tabled nonlinear path: per slot (e, 1 / |Y|), written by pass 1 (bA = (xi, |xi|))
   int expire;              // testing (PD_OPT_EXPIRE_WAITS): staged kernels skip their first copy
+  int adr;                 // PD_SOLVER_ADR: pass 2 stores g = f + b in gnew instead of updating
+  double4* gnew;           // ADR: force density g^n of this iteration
 };
 
 struct KernelTimes {
@@ -142,6 +144,14 @@ struct pd_ctx {
   int bond_cache = 1;             // use the table in the FP64 path
   int stage = 1;                  // mixed path: TMA-staged index streams (split 1)
   int expire_waits = 0;           // testing: make the staged kernels' first wait expire
+  int solver = 0;                 // pd_solver
+  bool adr_restart = true;        // next ADR iteration starts from rest
+  double* lam = nullptr;          // ADR fictitious density lambda_i
+  double4* gnew = nullptr;        // ADR g^n (force density incl. body force)
+  double4* gold = nullptr;        // ADR g^{n-1}
+  double2* adr_part = nullptr;    // ADR per-block partial sums (u.k.u, u.u)
+  double2* adr_st = nullptr;      // ADR (c^n, start flag) of the current iteration
+  int* adr_first = nullptr;       // ADR: 1 = the next iteration starts from rest
   double q = 0.0;               // fixed-point quantum of the mixed coordinates [m]
   double qlo[3] = {0, 0, 0};     // origin of the fixed-point coordinates
   // state
@@ -191,6 +201,7 @@ pd_status launch_damage(pd_ctx* c, double* phi_caller);
 pd_status launch_set_step(pd_ctx* c, int64_t value);
 pd_status init_disp_w(pd_ctx* c);
 pd_status ensure_bond_cache(pd_ctx* c);
+pd_status ensure_adr(pd_ctx* c);      // ADR arrays and lambda (once per build)
 pd_status prepare_staged_kernels(pd_ctx* c);  // shared-memory opt-in of the staged kernels
 pd_status upload_field(pd_ctx* c, const double* host_soa, double4* dst, int comps);
 pd_status download_field(pd_ctx* c, const double4* src, double* host_soa, int comps);

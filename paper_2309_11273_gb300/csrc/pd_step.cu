@@ -108,6 +108,12 @@ __device__ __forceinline__ void update(const StepArgs& a, int64_t i, int b, cons
                                        const double4* __restrict__ disp, double4* __restrict__ disp_out,
                                        double4& u) {
   const BodyDev& bp = a.bp[b];
+  if (a.adr) {  // adaptive dynamic relaxation: k_adr_update moves the particles after the reduction
+    const double4 bb = a.bacc ? a.bacc[i] : make_double4(0.0, 0.0, 0.0, 0.0);
+    a.gnew[i] = make_double4(f[0] + bb.x, f[1] + bb.y, f[2] + bb.z, 0.0);
+    u = disp[i];
+    return;
+  }
   const uint8_t fl = a.flag ? a.flag[i] : (uint8_t)0;
   u = disp[i];
   double4 v = a.vel[i];
@@ -1130,6 +1136,169 @@ __global__ void __launch_bounds__(512) k_pass2_mixed_staged(StepArgs a, const fl
   }
 }
 
+
+// ---------------------------------------------------------------- adaptive dynamic relaxation
+// The quasi-static solver of Section 4.4 (cited there from the literature): fictitious dynamics
+// L u'' + c L u' = g(u), g = f + b, unit fictitious step.  Pass 1 and pass 2 run as in the explicit
+// step (pass 2 stores g instead of moving the particles); three small kernels then form the damping
+// c from a Rayleigh quotient of the local stiffness (a deterministic two-level reduction) and move
+// the particles.
+
+// alpha_i = (A / m_i) sum_j |xi_ij| V_j |M_ij|_1 over the built family (unused slots have xi = 0).
+template <int DIM>
+__global__ void k_adr_alpha(StepArgs a, double* __restrict__ alpha) {
+  const SliceIdx t = slice_index<1>(a.n_pad, a.slice_ptr);
+  if (!t.active) return;
+  const double4 pi = a.pos[t.i];
+  const double4 zero = make_double4(0.0, 0.0, 0.0, 0.0);
+  double s = 0.0;
+  for (int k = 0; k < t.W; ++k) {
+    const double4 pj = a.pos[a.col[t.base + t.lane + ((int64_t)k << 5)]];
+    double ex, ey, ez, d, q;
+    bond_f64<DIM>(pi, pj, zero, zero, ex, ey, ez, d, q);
+    if (q > 0.0) {
+      const double xl = sqrt(q);
+      s += xl * pj.w * ((fabs(ex) + fabs(ey) + fabs(ez)) / xl);
+    }
+  }
+  alpha[t.i] = a.aA[t.i] * s;
+}
+
+// lambda_i = R_i / 4 with R_i = 2 G sum_j (1/m_i + 1/m_j) V_j |M_ij|_1
+//                              + 2 |K - G/3| sum_j |xi_ij| V_j (alpha_i / m_i + alpha_j / m_j),
+// an upper bound of the absolute row sums of the force-density stiffness (Gerschgorin).
+template <int DIM>
+__global__ void k_adr_lambda(StepArgs a, const double* __restrict__ alpha, double* __restrict__ lam) {
+  const SliceIdx t = slice_index<1>(a.n_pad, a.slice_ptr);
+  if (!t.active) return;
+  const int b = a.body ? a.body[t.i] : 0;
+  const double4 pi = a.pos[t.i];
+  const double4 zero = make_double4(0.0, 0.0, 0.0, 0.0);
+  const double mui = a.mu[t.i], ai = alpha[t.i];
+  double rg = 0.0, rt = 0.0;
+  for (int k = 0; k < t.W; ++k) {
+    const int32_t j = a.col[t.base + t.lane + ((int64_t)k << 5)];
+    const double4 pj = a.pos[j];
+    double ex, ey, ez, d, q;
+    bond_f64<DIM>(pi, pj, zero, zero, ex, ey, ez, d, q);
+    if (q > 0.0) {
+      const double xl = sqrt(q);
+      const double m1 = (fabs(ex) + fabs(ey) + fabs(ez)) / xl;
+      rg += (mui + a.mu[j]) * pj.w * m1;
+      rt += xl * pj.w * (ai * mui + alpha[j] * a.mu[j]);
+    }
+  }
+  const double R = 2.0 * a.bp[b].G * rg + 2.0 * fabs(a.bp[b].Kp) * rt;
+  lam[t.i] = 0.25 * R;
+}
+
+constexpr int kAdrBlock = 256;
+
+// Per block: sum over its free particles' components of u (k u) and u u, k = -(g - g_prev) / (lambda v).
+__global__ void __launch_bounds__(kAdrBlock) k_adr_sums(StepArgs a, const double4* __restrict__ disp,
+                                                         const double4* __restrict__ gold,
+                                                         const double* __restrict__ lam,
+                                                         double2* __restrict__ part) {
+  __shared__ double sn[kAdrBlock], sd[kAdrBlock];
+  const int64_t i = blockIdx.x * (int64_t)kAdrBlock + threadIdx.x;
+  double num = 0.0, den = 0.0;
+  if (i < a.n_pad && (!a.flag || a.flag[i] == 0) && lam[i] > 0.0) {
+    const double4 u = disp[i], v = a.vel[i], g = a.gnew[i], go = gold[i];
+    const double li = lam[i];
+    const double uu[3] = {u.x, u.y, u.z}, vv[3] = {v.x, v.y, v.z}, gg[3] = {g.x, g.y, g.z},
+                 gp[3] = {go.x, go.y, go.z};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const double kk = vv[k] != 0.0 ? -(gg[k] - gp[k]) / (li * vv[k]) : 0.0;
+      num += uu[k] * kk * uu[k];
+      den += uu[k] * uu[k];
+    }
+  }
+  sn[threadIdx.x] = num;
+  sd[threadIdx.x] = den;
+  __syncthreads();
+  for (int w = kAdrBlock / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      sn[threadIdx.x] += sn[threadIdx.x + w];
+      sd[threadIdx.x] += sd[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = make_double2(sn[0], sd[0]);
+}
+
+// One block: c = 2 sqrt(num / den) (0 unless both are positive), and the start flag of this iteration.
+__global__ void __launch_bounds__(1024) k_adr_coef(const double2* __restrict__ part, int nblk, int* first,
+                                                   double2* st) {
+  __shared__ double sn[1024], sd[1024];
+  double num = 0.0, den = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += 1024) {
+    num += part[b].x;
+    den += part[b].y;
+  }
+  sn[threadIdx.x] = num;
+  sd[threadIdx.x] = den;
+  __syncthreads();
+  for (int w = 512; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      sn[threadIdx.x] += sn[threadIdx.x + w];
+      sd[threadIdx.x] += sd[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double c = (sd[0] > 0.0 && sn[0] > 0.0) ? 2.0 * sqrt(sn[0] / sd[0]) : 0.0;
+    *st = make_double2(c, (double)*first);
+    *first = 0;
+  }
+}
+
+// v^{n+1/2} = ((2 - c) v^{n-1/2} + 2 g / lambda) / (2 + c) (from rest on a start: g / (2 lambda)),
+// u^{n+1} = u^n + v^{n+1/2}; constrained particles take their boundary value at t_{n+1}.
+__global__ void __launch_bounds__(kAdrBlock) k_adr_update(StepArgs a, const double4* __restrict__ disp,
+                                                           double4* __restrict__ disp_out,
+                                                           double4* __restrict__ gold,
+                                                           const double* __restrict__ lam,
+                                                           const double2* __restrict__ st) {
+  const int64_t i = blockIdx.x * (int64_t)kAdrBlock + threadIdx.x;
+  if (i >= a.n_pad) return;
+  const int b = a.body ? a.body[i] : 0;
+  const BodyDev& bp = a.bp[b];
+  const uint8_t fl = a.flag ? a.flag[i] : (uint8_t)0;
+  double4 u = disp[i], v = a.vel[i];
+  const double4 g = a.gnew[i];
+  if (fl == 0) {
+    const double li = lam[i];
+    if (li > 0.0) {
+      const double c = st->x;
+      if (st->y != 0.0) {
+        v = make_double4(g.x / (2.0 * li), g.y / (2.0 * li), g.z / (2.0 * li), 0.0);
+      } else {
+        v.x = ((2.0 - c) * v.x + 2.0 * g.x / li) / (2.0 + c);
+        v.y = ((2.0 - c) * v.y + 2.0 * g.y / li) / (2.0 + c);
+        v.z = ((2.0 - c) * v.z + 2.0 * g.z / li) / (2.0 + c);
+      }
+      u.x = u.x + v.x;
+      u.y = u.y + v.y;
+      u.z = u.z + v.z;
+    } else {
+      v = make_double4(0.0, 0.0, 0.0, 0.0);
+    }
+  } else if (fl == 1) {
+    u = make_double4(0.0, 0.0, 0.0, u.w);
+    v = make_double4(0.0, 0.0, 0.0, 0.0);
+  } else {
+    const double t1 = (double)(*a.d_step + 1) * bp.dt;
+    const double4 gv = a.gvec[i];
+    const double rt = bp.rate * t1;
+    u = make_double4(rt * gv.x, rt * gv.y, rt * gv.z, u.w);
+    v = make_double4(bp.rate * gv.x, bp.rate * gv.y, bp.rate * gv.z, 0.0);
+  }
+  disp_out[i] = u;
+  a.vel[i] = v;
+  gold[i] = g;
+}
+
 // ----------------------------------------------------------------------------- auxiliary kernels
 __global__ void k_set_step(int64_t* d_step, int64_t v) { *d_step = v; }
 
@@ -1274,6 +1443,8 @@ StepArgs make_args(pd_ctx* c) {
   a.bd = c->bond_cache ? c->bd : nullptr;
   a.bE = c->bond_cache ? c->bE : nullptr;
   a.expire = c->expire_waits;
+  a.adr = c->solver == PD_SOLVER_ADR ? 1 : 0;
+  a.gnew = c->gnew;
   return a;
 }
 
@@ -1404,6 +1575,50 @@ pd_status ensure_bond_cache(pd_ctx* c) {
   return PD_OK;
 }
 
+__global__ void k_set_flag(int* p, int v) { *p = v; }
+
+pd_status ensure_adr(pd_ctx* c) {
+  if (c->solver != PD_SOLVER_ADR) return PD_OK;
+  pd_status st;
+  if (!c->lam) {
+    const int64_t np = c->n_pad;
+    const size_t nblk = (size_t)((np + kAdrBlock - 1) / kAdrBlock);
+    if ((st = alloc(c, &c->lam, np)) != PD_OK) return st;
+    if ((st = alloc(c, &c->gnew, np)) != PD_OK) return st;
+    if ((st = alloc(c, &c->gold, np)) != PD_OK) return st;
+    if ((st = alloc(c, &c->adr_part, nblk)) != PD_OK) return st;
+    if ((st = alloc(c, &c->adr_st, 1)) != PD_OK) return st;
+    if ((st = alloc(c, &c->adr_first, 1)) != PD_OK) return st;
+    PD_CUDA(cudaMemsetAsync(c->gnew, 0, sizeof(double4) * np, c->stream));
+    PD_CUDA(cudaMemsetAsync(c->gold, 0, sizeof(double4) * np, c->stream));
+    double* alpha = nullptr;
+    if (cudaMalloc(&alpha, sizeof(double) * np) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(PD_ERR_OOM, "cudaMalloc of the ADR temporary failed");
+    }
+    StepArgs a = make_args(c);
+    const int tb = 256;
+    const unsigned grid = (unsigned)((np + tb - 1) / tb);
+    if (c->dim == 3) {
+      k_adr_alpha<3><<<grid, tb, 0, c->stream>>>(a, alpha);
+      k_adr_lambda<3><<<grid, tb, 0, c->stream>>>(a, alpha, c->lam);
+    } else {
+      k_adr_alpha<2><<<grid, tb, 0, c->stream>>>(a, alpha);
+      k_adr_lambda<2><<<grid, tb, 0, c->stream>>>(a, alpha, c->lam);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(alpha);
+    if (e != cudaSuccess) return cuda_fail(e, "ADR density");
+  }
+  if (c->adr_restart) {
+    k_set_flag<<<1, 1, 0, c->stream>>>(c->adr_first, 1);
+    PD_CUDA(cudaGetLastError());
+    c->adr_restart = false;
+  }
+  return PD_OK;
+}
+
 pd_status launch_set_step(pd_ctx* c, int64_t value) {
   k_set_step<<<1, 1, 0, c->stream>>>(c->d_step, value);
   PD_CUDA(cudaGetLastError());
@@ -1425,6 +1640,13 @@ pd_status launch_step(pd_ctx* c, bool check) {
   dispatch(c, a, 1, 1);
   if (prof) cudaEventRecord(e1, c->stream);
   dispatch(c, a, 2, 1);
+  if (a.adr) {
+    const unsigned nblk = (unsigned)((c->n_pad + kAdrBlock - 1) / kAdrBlock);
+    k_adr_sums<<<nblk, kAdrBlock, 0, c->stream>>>(a, c->disp[c->cur], c->gold, c->lam, c->adr_part);
+    k_adr_coef<<<1, 1024, 0, c->stream>>>(c->adr_part, (int)nblk, c->adr_first, c->adr_st);
+    k_adr_update<<<nblk, kAdrBlock, 0, c->stream>>>(a, c->disp[c->cur], c->disp[c->cur ^ 1], c->gold, c->lam,
+                                                    c->adr_st);
+  }
   if (prof) {
     cudaEventRecord(e2, c->stream);
     c->times.ev.push_back(e0);
@@ -1564,6 +1786,7 @@ pd_status run_steps(pd_ctx* c, int64_t nsteps) {
   if (nsteps <= 0) return PD_OK;
   pd_status st = ensure_bond_cache(c);
   if (st != PD_OK) return st;
+  if ((st = ensure_adr(c)) != PD_OK) return st;
   st = launch_set_step(c, c->steps - 1);
   if (st != PD_OK) return st;
   int64_t left = nsteps;
