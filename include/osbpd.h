@@ -161,6 +161,11 @@ typedef enum { PD_K_PASS1 = 0, PD_K_PASS2 = 1, PD_K_COUNT = 2 } pd_kernel;
  * Returns a negative value for invalid arguments. */
 double pd_critical_stretch(int32_t model, double E, double nu, double Gc, double delta);
 
+/* Material constants of the model: A (Eq 1.8), K (Eq 1.15) and G (Eq 1.16) with the bulk and shear
+ * moduli kappa = E / (3 (1 - 2 nu)), mu = E / (2 (1 + nu)).  Host helper (no context, no device).
+ * PD_ERR_ARG for an unknown model, E <= 0, nu outside (-1, 0.5) or a NULL output. */
+pd_status pd_material_constants(int32_t model, double E, double nu, double* A, double* K, double* G);
+
 /* Creates a context for one body of n >= 1 particles (n <= 2^31 - 65).
  * x, y, z: reference coordinates (z must be NULL for 2D models and non-NULL for PD_3D).
  * vol: particle volumes V_i > 0 (required).  In 2D, V_i is the area times the thickness; the

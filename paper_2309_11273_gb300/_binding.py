@@ -31,7 +31,7 @@ STATUS_NAMES = {0: "PD_OK", -1: "PD_ERR_ARG", -2: "PD_ERR_STATE", -3: "PD_ERR_OO
                 -5: "PD_ERR_NUMERIC", -6: "PD_ERR_TIMEOUT"}
 
 # Every function the header declares (checked against the shared object by the CPU tests).
-EXPORTED = ["pd_critical_stretch", "pd_create_particles", "pd_create_batch", "pd_build_neighbors",
+EXPORTED = ["pd_critical_stretch", "pd_material_constants", "pd_create_particles", "pd_create_batch", "pd_build_neighbors",
             "pd_set_bc", "pd_set_state", "pd_step", "pd_sync", "pd_get_damage", "pd_get_state",
             "pd_num_bonds", "pd_get_neighbors", "pd_get_stats", "pd_check_state", "pd_autotune",
             "pd_set_option", "pd_get_option", "pd_get_profile", "pd_get_info", "pd_step_noalloc",
@@ -82,6 +82,7 @@ def lib(path: str = LIB_PATH):
             L = ctypes.CDLL(path)
             L.pd_critical_stretch.argtypes = [ctypes.c_int32] + [ctypes.c_double] * 4
             L.pd_critical_stretch.restype = ctypes.c_double
+            L.pd_material_constants.argtypes = [ctypes.c_int32, ctypes.c_double, ctypes.c_double] + [_d] * 3
             L.pd_create_particles.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(pd_params), ctypes.c_int64,
                                               _d, _d, _d, _d]
             L.pd_create_batch.argtypes = [ctypes.POINTER(_vp), ctypes.c_int32, ctypes.POINTER(pd_params), _i64,
@@ -133,6 +134,14 @@ def _soa(a, dim, n):
 
 
 # ------------------------------------------------------------------ entry points (same names as C)
+def pd_material_constants(model, E, nu):
+    """(A, K, G) of Eqs 1.8, 1.15, 1.16."""
+    A, K, G = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().pd_material_constants(int(model), float(E), float(nu), ctypes.byref(A), ctypes.byref(K),
+                                       ctypes.byref(G)))
+    return A.value, K.value, G.value
+
+
 def pd_critical_stretch(model, E, nu, Gc, delta) -> float:
     return float(lib().pd_critical_stretch(int(model), float(E), float(nu), float(Gc), float(delta)))
 

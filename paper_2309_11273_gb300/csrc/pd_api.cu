@@ -179,6 +179,14 @@ extern "C" {
 
 const char* pd_last_error(void) { return g_err.c_str(); }
 
+pd_status pd_material_constants(int32_t model, double E, double nu, double* A, double* K, double* G) {
+  clear_error();
+  if (model < 0 || model > 2 || !(E > 0) || !(nu > -1.0 && nu < 0.5)) return fail(PD_ERR_ARG, "bad model, E or nu");
+  if (!A || !K || !G) return fail(PD_ERR_ARG, "A, K and G are required");
+  material_constants(model, E, nu, A, K, G);
+  return PD_OK;
+}
+
 double pd_critical_stretch(int32_t model, double E, double nu, double Gc, double delta) {
   if (model < 0 || model > 2 || !(E > 0) || !(nu > -1.0 && nu < 0.5) || !(Gc > 0) || !(delta > 0))
     return -1.0;

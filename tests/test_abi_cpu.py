@@ -93,3 +93,12 @@ def test_batch_bodies_must_share_kinematics(lib):
     with pytest.raises(B.PDError) as e:
         B.pd_create_batch(prms, [0, 2, 4], np.arange(4.0), np.zeros(4), None, np.ones(4))
     assert e.value.status == B.PD_ERR_ARG and "kinematics" in str(e.value)
+
+
+@pytest.mark.parametrize("model,E,nu", [(0, 30e9, 0.2), (1, 72e9, 0.22), (2, 72e9, 0.33)])
+def test_material_constants_match_oracle(lib, model, E, nu):
+    A, K, G = B.pd_material_constants(model, E, nu)
+    ref = O.constants(model, E, nu)
+    assert (A, K, G) == pytest.approx((ref["A"], ref["K"], ref["G"]), rel=1e-15)
+    with pytest.raises(B.PDError):
+        B.pd_material_constants(5, E, nu)
