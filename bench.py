@@ -446,7 +446,17 @@ def run_forms(args, stream, dev, world, fp64_value, nb, hbm, hbm_note):
     nfl = (FLOPS_BOND_NL_TABLED if ntab else FLOPS_BOND_NL)[kp]
     ach = nfl * nb / (prof["pass%d_ms" % kp] * 1e-3) / 1e12
     nkern = "k_pass%d_nl%s" % (kp, "t" if ntab else "")
+    # the same nonlinear bonds in the mixed form (FP32 bond arithmetic, FP64 state and re-decisions)
+    sim = Simulation(w, s0=s0, precision=PD_MIXED, kinematics=PD_NONLINEAR, stream=stream.cuda_stream, device=dev)
+    B.pd_autotune(sim.h, 3)
+    sim.step(args.warmup)
+    km = max(args.steps, 100)
+    msm = max_over_ranks(timed(sim, stream, km, world), world)
+    sim.close()
+    nmixed = {"value": world * nb * km / (msm * 1e-3), "ms_per_step": msm / km, "steps": km,
+              "dtype": "f32 bond arithmetic, f64 integration", "speedup_vs_fp64_nonlinear": (nb * km / (msm * 1e-3)) / nval}
     out["nonlinear"] = {"value": nval, "unit": UNIT, "ms_per_step": ms / k, "steps": k, "dtype": "f64",
+                        "mixed": nmixed,
                         "kinematics": "e = |Y| - |xi|, force along Y/|Y| (Eqs 1.10, 1.13, 1.14)",
                         "vs_linearized_fp64": nval / fp64_value, "mapping": {"block": nmap[0], "split": nmap[1]},
                         "roofline": {"bound": "alu", "kernel": nkern, "achieved": ach,

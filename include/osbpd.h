@@ -65,7 +65,9 @@ typedef enum { PD_FP64 = 0, PD_MIXED = 1 } pd_precision;
  * PD_NONLINEAR: the state-based model of Section 2 without that approximation: Y = xi + u_j - u_i,
  *   e = |Y| - |xi| (Eq 1.10) and the force along the deformed bond M = Y / |Y| (Eq 1.13), with the
  *   force state of Eq 1.14 (as in the loop scheme of Appendix C).  Stretch for Eq 1.30: e / |xi|.
- *   PD_FP64 only. */
+ *   With PD_MIXED the bond arithmetic is FP32 (fixed-point xi and the FP32 shadow of u in units of
+ *   the quantum Q), the break test carries its own rounding band with the FP64 re-decision of
+ *   PD_MIXED, and the staged kernels always run (PD_OPT_SPLIT and PD_OPT_STAGE are ignored). */
 typedef enum { PD_LINEARIZED = 0, PD_NONLINEAR = 1 } pd_kinematics;
 
 /* Internal particle order (results do not depend on it beyond rounding).

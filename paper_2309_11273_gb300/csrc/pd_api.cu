@@ -159,7 +159,10 @@ pd_status alloc_state(pd_ctx* c) {
     PD_CUDA(cudaMemcpyAsync(c->pos32, hp.data(), sizeof(int4) * np, cudaMemcpyHostToDevice, s));
     PD_CUDA(cudaMemsetAsync(c->u32[0], 0, sizeof(float4) * np, s));
     PD_CUDA(cudaMemsetAsync(c->u32[1], 0, sizeof(float4) * np, s));
-    k_init_mixed<<<gb, tb, 0, s>>>(np, c->mu, c->aA, c->q, c->mu32, c->aA32, c->thm32, c->theta32);
+    // theta = aA32 sum: Q folded in once (linearized: xi in quanta, u in metres) or twice (nonlinear:
+    // both in quanta)
+    k_init_mixed<<<gb, tb, 0, s>>>(np, c->mu, c->aA, c->kin == PD_NONLINEAR ? c->q * c->q : c->q, c->mu32,
+                                   c->aA32, c->thm32, c->theta32);
     if ((st = prepare_staged_kernels(c)) != PD_OK) return st;
   }
   PD_CUDA(cudaGetLastError());

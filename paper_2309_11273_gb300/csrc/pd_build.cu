@@ -250,8 +250,6 @@ pd_status check_params(const pd_params& p, int dim) {
   if (!std::isfinite(p.s0)) return fail(PD_ERR_ARG, "s0 must be finite");
   if (p.ordering != PD_ORDER_BRICKS && p.ordering != PD_ORDER_MORTON) return fail(PD_ERR_ARG, "unknown ordering");
   if (p.kinematics != PD_LINEARIZED && p.kinematics != PD_NONLINEAR) return fail(PD_ERR_ARG, "unknown kinematics");
-  if (p.kinematics == PD_NONLINEAR && p.precision != PD_FP64)
-    return fail(PD_ERR_ARG, "PD_NONLINEAR runs in PD_FP64 only");
   return PD_OK;
 }
 
@@ -481,6 +479,8 @@ pd_status upload_body_params(pd_ctx* c) {
     d.rate = 0.0;
     d.Kp32 = (float)(d.Kp * c->q);
     d.G32 = (float)d.G;
+    d.G32q = (float)(d.G * c->q);
+    d.s0nl32 = (float)d.s0nl;
     d.inv_rho32 = (float)d.inv_rho;
     d.sigma_q = p.s0 * c->q;
     d.sigma32 = (float)d.sigma_q;

@@ -23,6 +23,8 @@ struct BodyDev {
   double s0nl;     // s0 (2 + s0): nonlinear break test |Y|^2 - |xi|^2 >= s0nl |xi|^2
   double rate;     // prescribed rotation rate
   float Kp32, G32, inv_rho32, sigma32;  // FP32 copies for the mixed path (sigma32 = s0 * Q)
+  float G32q;      // G * Q (mixed path, nonlinear bonds)
+  float s0nl32;    // s0 (2 + s0) in FP32 (mixed path, nonlinear bonds)
   double sigma_q;  // s0 * Q in double (Q = fixed-point quantum of the mixed coordinates)
   int32_t breaks;  // 1 if s0 > 0 (bond breaking on), else 0
   float xi1max;    // upper bound of |xi|_1 in quanta: sqrt(dim) (delta / Q + 2)
@@ -79,6 +81,7 @@ struct StepArgs {
   double* bd;              // tabled FP64 path: per slot xi.(u_j - u_i), written by pass 1
   double2* bE;             // tabled nonlinear path: per slot (e, 1 / |Y|), written by pass 1 (bA = (xi, |xi|))
   int expire;              // testing (PD_OPT_EXPIRE_WAITS): staged kernels skip their first copy
+  double uscale;           // mixed path: the FP32 shadow holds u * uscale (1, or 1/Q for nonlinear bonds)
   int adr;                 // PD_SOLVER_ADR: pass 2 stores g = f + b in gnew instead of updating
   double4* gnew;           // ADR: force density g^n of this iteration
 };

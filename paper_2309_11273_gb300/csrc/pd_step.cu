@@ -102,6 +102,12 @@ __device__ __noinline__ bool fp64_breaks(const StepArgs& a, int64_t i, int32_t j
   return d >= s0 * q;
 }
 
+// Nonlinear FP64 re-decision for the mixed path: |Y|^2 - |xi|^2 >= s0 (2 + s0) |xi|^2 with the
+// arithmetic of the FP64 nonlinear kernels (defined with them below).
+template <int DIM>
+__device__ __noinline__ bool fp64_breaks_nl(const StepArgs& a, int64_t i, int32_t j,
+                                            const double4* __restrict__ disp);
+
 // Explicit update (Eq 2.11) with the diagonal mass rho V_i (Eqs 2.1, 2.12) and the boundary
 // conditions at t_{n+1}; f = F_i / V_i.
 __device__ __forceinline__ void update(const StepArgs& a, int64_t i, int b, const double f[3],
@@ -291,6 +297,14 @@ __device__ __forceinline__ BondNL<DIM> bond_nl(const double4& pi, const double4&
     r.q = fma(ez, ez, r.q);
   }
   return r;
+}
+
+template <int DIM>
+__device__ __noinline__ bool fp64_breaks_nl(const StepArgs& a, int64_t i, int32_t j,
+                                            const double4* __restrict__ disp) {
+  const int b = a.body ? a.body[i] : 0;
+  const BondNL<DIM> r = bond_nl<DIM>(a.pos[i], a.pos[j], disp[i], disp[j]);
+  return r.p >= a.bp[b].s0nl * r.q;
 }
 
 template <int DIM, int SPLIT>
@@ -842,7 +856,8 @@ __global__ void __launch_bounds__(512) k_pass2_mixed(StepArgs a, const float4* _
     const double fd[3] = {(double)f[0], (double)f[1], (double)f[2]};
     double4 u;
     update(a, t.i, b, fd, disp, disp_out, u);
-    u32_out[t.i] = make_float4((float)u.x, (float)u.y, (float)u.z, 0.0f);
+    const double sc = a.uscale;
+    u32_out[t.i] = make_float4((float)(u.x * sc), (float)(u.y * sc), (float)(u.z * sc), 0.0f);
   }
 }
 
@@ -946,7 +961,7 @@ __device__ __forceinline__ void stage_drain(Stage& st, int from) {
   for (int c = from; c < st.issued; ++c) mbar_wait(&st.bar[c % kStageBuf], (unsigned)((c / kStageBuf) & 1));
 }
 
-template <int DIM>
+template <int DIM, int KIN>
 __global__ void __launch_bounds__(512) k_pass1_mixed_staged(StepArgs a, const float4* __restrict__ u32,
                                                              const double4* __restrict__ disp, int write_theta) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -969,6 +984,14 @@ __global__ void __launch_bounds__(512) k_pass1_mixed_staged(StepArgs a, const fl
   const float band_k2 = a.band_c * fmaf(sig, fmaf(2.01f, xim, 3.02f),
                                         5.9604645e-8f * fmaf(2.0f * xim, ui1, 6.0f * sig * qm));
   const float band_k3 = a.band_c * 5.9604645e-8f;
+  // Nonlinear bonds (KIN 1, u32 holds u / Q): g = eta.(2 xi + eta) - c |xi|^2, c = s0 (2 + s0), with
+  // |g32 - g| <= K0 + h1 (K1 + K2 h1) + eps |g32|, h1 = |eta|_1 (see the comment above
+  // fp64_breaks_nl): fixed-point coordinates (1 quantum per axis), the FP32 shadow of u and the
+  // rounding of xi, the products, the sums and the final FMA.
+  const float eps = 5.9604645e-8f, c32 = a.bp[b].s0nl32;
+  const float nl_k0 = a.band_c * (c32 * fmaf(2.0f, xim, 3.0f) + eps * (4.0f * ui1 * xim + 7.0f * c32 * qm));
+  const float nl_k1 = a.band_c * (2.0f + eps * (16.0f * xim + 4.0f * ui1));
+  const float nl_k2 = a.band_c * 10.0f * eps;
   uint32_t* __restrict__ bw = a.bits + (t.base >> 5);
   if (lane == 0)
     for (; st.issued < min(kStageBuf, st.nchunks); ++st.issued)
@@ -1010,8 +1033,14 @@ __global__ void __launch_bounds__(512) k_pass1_mixed_staged(StepArgs a, const fl
         const float ex = (float)(Pj[u].x - Pi.x), ey = (float)(Pj[u].y - Pi.y);
         const float ez = DIM == 3 ? (float)(Pj[u].z - Pi.z) : 0.0f;
         const float dx = Uj[u].x - Ui.x, dy = Uj[u].y - Ui.y, dz = DIM == 3 ? Uj[u].z - Ui.z : 0.0f;
-        float d = ex * dx + ey * dy;
-        if (DIM == 3) d = fmaf(ez, dz, d);
+        float d;
+        if (KIN == 0) {
+          d = ex * dx + ey * dy;
+          if (DIM == 3) d = fmaf(ez, dz, d);
+        } else {  // p = eta.(2 xi + eta) = |Y|^2 - |xi|^2 in quanta^2
+          d = dx * fmaf(2.0f, ex, dx) + dy * fmaf(2.0f, ey, dy);
+          if (DIM == 3) d = fmaf(dz, fmaf(2.0f, ez, dz), d);
+        }
         dv[u] = d;
         vj[u] = __int_as_float(Pj[u].w);
         intact[u] = (wd[u] >> lane) & 1u;
@@ -1019,10 +1048,26 @@ __global__ void __launch_bounds__(512) k_pass1_mixed_staged(StepArgs a, const fl
         if (a.check && can_break && intact[u]) {
           float q = ex * ex + ey * ey;
           if (DIM == 3) q = fmaf(ez, ez, q);
-          const float g = fmaf(-sig, q, d);
           const float du1 = fabsf(dx) + fabsf(dy) + fabsf(dz);
-          const float B = fmaf(du1, band_k1, fmaf(band_k3, fabsf(g), band_k2));
+          float g, B;
+          if (KIN == 0) {
+            g = fmaf(-sig, q, d);
+            B = fmaf(du1, band_k1, fmaf(band_k3, fabsf(g), band_k2));
+          } else {
+            g = fmaf(-c32, q, d);
+            B = fmaf(du1, fmaf(nl_k2, du1, nl_k1), fmaf(band_k3, fabsf(g), nl_k0));
+          }
           code[u] = fabsf(g) > B ? (g >= 0.0f ? 1 : 0) : 2;
+        }
+        if (KIN == 1) {  // theta term |xi| e with e = p / (|Y| + |xi|) (Eqs 1.6, 1.10)
+          const float yx = ex + dx, yy = ey + dy, yz = ez + dz;
+          float q = ex * ex + ey * ey, y2 = yx * yx + yy * yy;
+          if (DIM == 3) {
+            q = fmaf(ez, ez, q);
+            y2 = fmaf(yz, yz, y2);
+          }
+          const float xl = q * rsqrtf(q);
+          dv[u] = xl * __fdividef(d, fmaf(y2, rsqrtf(y2), xl));
         }
       }
       if (a.check) {
@@ -1032,13 +1077,16 @@ __global__ void __launch_bounds__(512) k_pass1_mixed_staged(StepArgs a, const fl
         if (__any_sync(kFull, band)) {
           for (int u = 0; u < U; ++u)
             if (code[u] == 2) {
-              code[u] = fp64_breaks<DIM>(a, t.i, j[u], disp, s0) ? 1 : 0;
+              code[u] = (KIN == 0 ? fp64_breaks<DIM>(a, t.i, j[u], disp, s0)
+                                  : fp64_breaks_nl<DIM>(a, t.i, j[u], disp)) ? 1 : 0;
               atomicAdd(&a.counters[0], 1ull);
             }
         }
         if (a.validate) {
           for (int u = 0; u < U; ++u)
-            if (can_break && intact[u] && (code[u] == 1) != fp64_breaks<DIM>(a, t.i, j[u], disp, s0))
+            if (can_break && intact[u] &&
+                (code[u] == 1) != (KIN == 0 ? fp64_breaks<DIM>(a, t.i, j[u], disp, s0)
+                                            : fp64_breaks_nl<DIM>(a, t.i, j[u], disp)))
               atomicAdd(&a.counters[1], 1ull);
         }
 #pragma unroll
@@ -1060,11 +1108,11 @@ __global__ void __launch_bounds__(512) k_pass1_mixed_staged(StepArgs a, const fl
     const float th = a.aA32[t.i] * acc;
     const float mu = a.mu32[t.i];
     a.theta32[t.i] = th;
-    a.thm32[t.i] = make_float2(a.bp[b].Kp32 * (th * mu), a.bp[b].G32 * mu);
+    a.thm32[t.i] = make_float2(a.bp[b].Kp32 * (th * mu), (KIN == 0 ? a.bp[b].G32 : a.bp[b].G32q) * mu);
   }
 }
 
-template <int DIM>
+template <int DIM, int KIN>
 __global__ void __launch_bounds__(512) k_pass2_mixed_staged(StepArgs a, const float4* __restrict__ u32,
                                                              float4* __restrict__ u32_out,
                                                              const double4* __restrict__ disp,
@@ -1112,17 +1160,36 @@ __global__ void __launch_bounds__(512) k_pass2_mixed_staged(StepArgs a, const fl
       for (int u = 0; u < U; ++u) {
         const float ex = (float)(Pj[u].x - Pi.x), ey = (float)(Pj[u].y - Pi.y);
         const float ez = DIM == 3 ? (float)(Pj[u].z - Pi.z) : 0.0f;
-        float d = ex * (Uj[u].x - Ui.x) + ey * (Uj[u].y - Ui.y);
-        float q = ex * ex + ey * ey;
-        if (DIM == 3) {
-          d = fmaf(ez, Uj[u].z - Ui.z, d);
-          q = fmaf(ez, ez, q);
+        if (KIN == 0) {
+          float d = ex * (Uj[u].x - Ui.x) + ey * (Uj[u].y - Ui.y);
+          float q = ex * ex + ey * ey;
+          if (DIM == 3) {
+            d = fmaf(ez, Uj[u].z - Ui.z, d);
+            q = fmaf(ez, ez, q);
+          }
+          float cf = fmaf(ti.y + tj[u].y, d * __frcp_rn(q), ti.x + tj[u].x);
+          cf = ((wd[u] >> lane) & 1u) ? cf * __int_as_float(Pj[u].w) : 0.0f;
+          f[0] = fmaf(cf, ex, f[0]);
+          f[1] = fmaf(cf, ey, f[1]);
+          if (DIM == 3) f[2] = fmaf(cf, ez, f[2]);
+        } else {  // Eq 1.14 for both ends along M = Y / |Y| (Eq 1.13), in quanta (Q folded into thm32)
+          const float hx = Uj[u].x - Ui.x, hy = Uj[u].y - Ui.y, hz = DIM == 3 ? Uj[u].z - Ui.z : 0.0f;
+          const float yx = ex + hx, yy = ey + hy, yz = ez + hz;
+          float pp = hx * (ex + yx) + hy * (ey + yy);
+          float q = ex * ex + ey * ey, y2 = yx * yx + yy * yy;
+          if (DIM == 3) {
+            pp = fmaf(hz, ez + yz, pp);
+            q = fmaf(ez, ez, q);
+            y2 = fmaf(yz, yz, y2);
+          }
+          const float xl = q * rsqrtf(q), ry = rsqrtf(y2);
+          const float e = __fdividef(pp, fmaf(y2, ry, xl));
+          float cf = fmaf(ti.x + tj[u].x, xl, (ti.y + tj[u].y) * e) * ry;
+          cf = ((wd[u] >> lane) & 1u) ? cf * __int_as_float(Pj[u].w) : 0.0f;
+          f[0] = fmaf(cf, yx, f[0]);
+          f[1] = fmaf(cf, yy, f[1]);
+          if (DIM == 3) f[2] = fmaf(cf, yz, f[2]);
         }
-        float cf = fmaf(ti.y + tj[u].y, d * __frcp_rn(q), ti.x + tj[u].x);
-        cf = ((wd[u] >> lane) & 1u) ? cf * __int_as_float(Pj[u].w) : 0.0f;
-        f[0] = fmaf(cf, ex, f[0]);
-        f[1] = fmaf(cf, ey, f[1]);
-        if (DIM == 3) f[2] = fmaf(cf, ez, f[2]);
       }
     }
     __syncwarp();
@@ -1132,7 +1199,8 @@ __global__ void __launch_bounds__(512) k_pass2_mixed_staged(StepArgs a, const fl
     const double fd[3] = {(double)f[0], (double)f[1], (double)f[2]};
     double4 u;
     update(a, t.i, b, fd, disp, disp_out, u);
-    u32_out[t.i] = make_float4((float)u.x, (float)u.y, (float)u.z, 0.0f);
+    const double sc = a.uscale;
+    u32_out[t.i] = make_float4((float)(u.x * sc), (float)(u.y * sc), (float)(u.z * sc), 0.0f);
   }
 }
 
@@ -1377,11 +1445,11 @@ __global__ void k_apply_bc(StepArgs a, double4* __restrict__ disp, int64_t step)
   a.vel[i] = make_double4(bp.rate * g.x, bp.rate * g.y, bp.rate * g.z, 0.0);
 }
 
-__global__ void k_shadow(int64_t n_pad, const double4* __restrict__ disp, float4* __restrict__ u32) {
+__global__ void k_shadow(int64_t n_pad, const double4* __restrict__ disp, float4* __restrict__ u32, double sc) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n_pad) return;
   const double4 u = disp[i];
-  u32[i] = make_float4((float)u.x, (float)u.y, (float)u.z, 0.0f);
+  u32[i] = make_float4((float)(u.x * sc), (float)(u.y * sc), (float)(u.z * sc), 0.0f);
 }
 
 // max |u_k| over all particles and components (order-independent: max of non-negative doubles as
@@ -1443,6 +1511,7 @@ StepArgs make_args(pd_ctx* c) {
   a.bd = c->bond_cache ? c->bd : nullptr;
   a.bE = c->bond_cache ? c->bE : nullptr;
   a.expire = c->expire_waits;
+  a.uscale = c->kin == PD_NONLINEAR ? 1.0 / c->q : 1.0;
   a.adr = c->solver == PD_SOLVER_ADR ? 1 : 0;
   a.gnew = c->gnew;
   return a;
@@ -1479,8 +1548,11 @@ void launch_pass2(pd_ctx* c, const StepArgs& a, unsigned grid, int block, size_t
 
 template <int DIM>
 void optin_staged() {
-  cudaFuncSetAttribute(k_pass1_mixed_staged<DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 16 * kStageWarpBytes);
-  cudaFuncSetAttribute(k_pass2_mixed_staged<DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 16 * kStageWarpBytes);
+  const int mx = 16 * kStageWarpBytes;
+  cudaFuncSetAttribute(k_pass1_mixed_staged<DIM, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_pass2_mixed_staged<DIM, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_pass1_mixed_staged<DIM, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_pass2_mixed_staged<DIM, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
 }
 
 }  // namespace
@@ -1502,13 +1574,23 @@ void dispatch_pass(pd_ctx* c, const StepArgs& a, int pass, int write_theta) {
   const int split = c->split;
   const int64_t threads = c->nslices * 32 * (int64_t)split;
   const unsigned grid = (unsigned)((threads + block - 1) / block);
-  if (c->precision == PD_MIXED && split == 1 && c->stage) {
+  if (c->precision == PD_MIXED && ((split == 1 && c->stage) || c->kin == PD_NONLINEAR)) {
+    // nonlinear bonds in the mixed form run the staged kernels only (one warp per slice)
+    const unsigned g1 = (unsigned)((c->nslices * 32 + block - 1) / block);
     const size_t smb = (size_t)(block / 32) * kStageWarpBytes;
-    if (pass == 1)
-      k_pass1_mixed_staged<DIM><<<grid, block, smb, c->stream>>>(a, c->u32[c->cur], c->disp[c->cur], write_theta);
-    else
-      k_pass2_mixed_staged<DIM><<<grid, block, smb, c->stream>>>(a, c->u32[c->cur], c->u32[c->cur ^ 1],
-                                                                 c->disp[c->cur], c->disp[c->cur ^ 1]);
+    if (c->kin == PD_NONLINEAR) {
+      if (pass == 1)
+        k_pass1_mixed_staged<DIM, 1><<<g1, block, smb, c->stream>>>(a, c->u32[c->cur], c->disp[c->cur], write_theta);
+      else
+        k_pass2_mixed_staged<DIM, 1><<<g1, block, smb, c->stream>>>(a, c->u32[c->cur], c->u32[c->cur ^ 1],
+                                                                    c->disp[c->cur], c->disp[c->cur ^ 1]);
+    } else {
+      if (pass == 1)
+        k_pass1_mixed_staged<DIM, 0><<<g1, block, smb, c->stream>>>(a, c->u32[c->cur], c->disp[c->cur], write_theta);
+      else
+        k_pass2_mixed_staged<DIM, 0><<<g1, block, smb, c->stream>>>(a, c->u32[c->cur], c->u32[c->cur ^ 1],
+                                                                    c->disp[c->cur], c->disp[c->cur ^ 1]);
+    }
     return;
   }
   const size_t sm = split > 1 ? (size_t)block * 3 * sizeof(double) : 0;
@@ -1745,7 +1827,8 @@ pd_status apply_bc_now(pd_ctx* c) {
 pd_status sync_shadow(pd_ctx* c) {
   if (c->precision != PD_MIXED) return PD_OK;
   const int tb = 256;
-  k_shadow<<<(unsigned)((c->n_pad + tb - 1) / tb), tb, 0, c->stream>>>(c->n_pad, c->disp[c->cur], c->u32[c->cur]);
+  k_shadow<<<(unsigned)((c->n_pad + tb - 1) / tb), tb, 0, c->stream>>>(c->n_pad, c->disp[c->cur], c->u32[c->cur],
+                                                                        c->kin == PD_NONLINEAR ? 1.0 / c->q : 1.0);
   PD_CUDA(cudaGetLastError());
   return PD_OK;
 }

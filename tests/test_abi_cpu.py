@@ -62,8 +62,7 @@ def _prm(**kw):
 @pytest.mark.parametrize("kw,msg", [(dict(E=-1.0), "E"), (dict(nu=0.5), "nu"), (dict(rho=0.0), "rho"),
                                     (dict(horizon=0.0), "horizon"), (dict(dt=float("nan")), "dt"),
                                     (dict(model=5), "model"), (dict(precision=3), "precision"),
-                                    (dict(kinematics=2), "kinematics"),
-                                    (dict(kinematics=B.PD_NONLINEAR, precision=B.PD_MIXED), "PD_FP64 only")])
+                                    (dict(kinematics=2), "kinematics")])
 def test_create_rejects_bad_parameters(lib, kw, msg):
     with pytest.raises(B.PDError) as e:
         B.pd_create_particles(_prm(**kw), np.zeros(4), np.arange(4.0), None, np.ones(4))

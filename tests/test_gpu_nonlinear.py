@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from paper_2309_11273_gb300 import PD_FP64, PD_NONLINEAR, BatchSimulation, Simulation
+from paper_2309_11273_gb300 import PD_FP64, PD_MIXED, PD_NONLINEAR, BatchSimulation, Simulation
 from paper_2309_11273_gb300 import _binding as B
 from paper_2309_11273_gb300 import workloads as W
 
@@ -63,7 +63,7 @@ def assert_parity(out, phi=None, ref=None, tol_v=TOL):
 @pytest.mark.parametrize("bond_cache", [1, 0])
 def test_cracked_plate_breaking_nonlinear(bond_cache):
     """Both kernel forms: per-slot tables (default) and recomputed geometry."""
-    w = W.cracked_plate(nx=60, ny=24, dx=2.5e-4, crack_cells=30.125, sigma=1.5e8, nsteps=400)
+    w = W.cracked_plate(nx=60, ny=24, dx=2.5e-4, crack_cells=30.125, sigma=2e6, nsteps=400)
     out, phi, ref = run_pair(w, 400, 100, bond_cache=bond_cache)
     assert out[-1]["broken"] > 0
     assert_parity(out, phi, ref)
@@ -71,8 +71,10 @@ def test_cracked_plate_breaking_nonlinear(bond_cache):
 
 @pytest.mark.parametrize("bond_cache", [1, 0])
 def test_notched_block_twist_nonlinear(bond_cache):
-    w = W.notched_block(nx=30, ny=14, nz=12, dx=1e-3, notch_cells=11.5, nsteps=60, seed=1, amp=2e-6)
-    out, phi, ref = run_pair(w, 60, 20, rate=5e3, bond_cache=bond_cache)
+    """Clamped + twisted notched block (24 s0 rad over the 300 steps): progressive fracture."""
+    w = W.notched_block(nx=24, ny=12, nz=10, dx=1e-3, notch_cells=9.5, nsteps=300, seed=3, amp=1e-7)
+    out, phi, ref = run_pair(w, 300, 100, bond_cache=bond_cache)
+    assert out[-1]["broken"] > 10000
     assert_parity(out, phi, ref)
 
 
@@ -168,3 +170,88 @@ def test_nonlinear_mapping_variants_agree(block, split):
         res.append(sim.state()[0])
         sim.close()
     assert rel(res[1], res[0]) <= 1e-13
+
+
+# ------------------------------------------------------------------ mixed precision, nonlinear bonds
+def _oracle_nl(w, s0, rate=0.0):
+    ref = O.OracleSim(w.model, w.E, w.nu, w.rho, w.delta, s0, w.dt, w.x, w.y, w.z, w.vol, w.cracks,
+                      kin=O.NONLINEAR)
+    ref.set_bc(w.flag, w.b, w.axis_point, w.axis_dir, rate)
+    ref.set_state(w.initial_u(), w.initial_v())
+    return ref
+
+
+def test_mixed_nonlinear_error_bound():
+    """FP32 nonlinear bonds with FP64 integration on the vibrating plate (configuration 1's
+    geometry): rel-L2(u) against the oracle's FP64 nonlinear run <= 2e-5 after 100 steps and <= 1e-4
+    over 1000 (the bounds of the linearized mixed form)."""
+    w = W.config1()
+    sim = Simulation(w, s0=0.0, precision=PD_MIXED, kinematics=PD_NONLINEAR)
+    ref = _oracle_nl(w, 0.0)
+    errs = []
+    for _ in range(10):
+        ref.step(100)
+        sim.step(100)
+        errs.append(rel(sim.state()[0], ref.u))
+    sim.close()
+    assert errs[0] <= 2e-5 and max(errs) <= 1e-4, errs
+
+
+def test_mixed_nonlinear_decisions_equal_fp64_on_own_state():
+    """Zero spurious breaks for nonlinear bonds: with validation on, every decision of the FP32 +
+    band path equals the FP64 nonlinear decision on the mixed run's own state; bonds do break."""
+    w = W.cracked_plate(nx=60, ny=24, dx=2.5e-4, crack_cells=30.125, sigma=2e6, nsteps=400)
+    sim = Simulation(w, s0=s0_of(w), precision=PD_MIXED, kinematics=PD_NONLINEAR)
+    sim.set_option(B.PD_OPT_VALIDATE, 1)
+    sim.step(400)
+    st = sim.stats()
+    u = sim.state()[0]
+    sim.close()
+    ref = _oracle_nl(w, s0_of(w))
+    ref.step(400)
+    assert st["broken_bonds"] > 0 and st["validate_mismatches"] == 0
+    assert rel(u, ref.u) <= 1e-4
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_mixed_nonlinear_turned_spinning_body(dim):
+    """Large rotation in FP32 bonds: the body turned by 35 degrees and spinning follows the FP64
+    oracle to 1e-5 in u (the rigid motion dominates u; the FP32 strain resolution, ~1e-7 of the bond
+    length, bounds the accuracy of the small elastic forces)."""
+    if dim == 2:
+        w = W.plate_vibration(nx=24, ny=20, nsteps=300, dt=2e-7, amp=0.0)
+    else:
+        x, y, z = W.grid_3d(12, 10, 8, 1e-3)
+        w = W.Workload("block", W.MODEL_3D, E=30e9, nu=0.2, rho=2400.0, dx=1e-3, delta=3.015e-3, dt=2e-7,
+                       nsteps=300, x=x, y=y, z=z, vol=np.full(x.size, 1e-9))
+    P = np.stack([w.x, w.y] + ([w.z] if dim == 3 else []))
+    c = P.mean(axis=1, keepdims=True)
+    r = _rotation(dim, np.deg2rad(35.0)) @ (P - c)
+    om = np.array([0.0, 0.0, 2e3]) if dim == 2 else np.array([300.0, -500.0, 800.0])
+    r3 = np.vstack([r, np.zeros((1, w.n))]) if dim == 2 else r
+    v0 = np.cross(om, r3.T).T[:dim]
+    w.u0, w.v0 = r + c - P, v0
+    sim = Simulation(w, s0=0.0, rate=0.0, precision=PD_MIXED, kinematics=PD_NONLINEAR)
+    ref = _oracle_nl(w, 0.0)
+    sim.step(300)
+    ref.step(300)
+    assert rel(sim.state()[0], ref.u) <= 1e-5
+    sim.close()
+
+
+def test_mixed_nonlinear_full_size_block():
+    """The 200 x 100 x 50 notched block under torsion with nonlinear bonds: the mixed form follows
+    the FP64 GPU path (itself held to the oracle at 1e-12 above) to 1e-3 over the first tenth of the
+    run, with zero decisions differing from FP64 on its own state."""
+    w = W.config3()
+    s0 = s0_of(w)
+    ref = Simulation(w, s0=s0, kinematics=PD_NONLINEAR)
+    sim = Simulation(w, s0=s0, precision=PD_MIXED, kinematics=PD_NONLINEAR)
+    sim.set_option(B.PD_OPT_VALIDATE, 1)
+    ref.step(200)
+    sim.step(200)
+    e = rel(sim.state()[0], ref.state()[0])
+    st = sim.stats()
+    ref.close()
+    sim.close()
+    assert e <= 1e-3 and st["validate_mismatches"] == 0, (e, st)

@@ -132,17 +132,21 @@ def test_config1_fp64_parity():
 
 
 def test_cracked_plate_breaking_parity():
-    """A small pre-cracked plate under a traction large enough to break bonds."""
-    w = W.cracked_plate(nx=60, ny=24, dx=2.5e-4, crack_cells=30.125, sigma=1.5e8, nsteps=400)
+    """A small pre-cracked plate under traction: the crack grows from the pre-crack tip (about 1,400
+    directed bonds break over 130 of the 400 steps, none in the loaded edge rows; the oracle's
+    smallest stretch margin stays near 1e-7, so bond status is compared exactly throughout)."""
+    w = W.cracked_plate(nx=60, ny=24, dx=2.5e-4, crack_cells=30.125, sigma=2e6, nsteps=400)
     out, stats, phi, ref = run_pair(w, w.nsteps, 50)
     assert out[-1]["broken"] > 0
     assert_fp64(out, ref.damage(), phi)
 
 
 def test_notched_block_twist_parity():
-    """3D notched block, clamped + twisted ends, random initial displacement, breaking on."""
-    w = W.notched_block(nx=24, ny=12, nz=10, dx=1e-3, notch_cells=9.5, nsteps=300, seed=3, amp=2e-6)
-    out, stats, phi, ref = run_pair(w, w.nsteps, 50, rate=5e3)
+    """3D notched block, clamped + twisted ends (24 s0 rad over the run), small random initial
+    displacement, breaking on: the fracture grows from step 23 on (about 50,000 of 263,000 directed
+    bonds over 260 of the 300 steps) with the oracle's stretch margin above 4e-6 throughout."""
+    w = W.notched_block(nx=24, ny=12, nz=10, dx=1e-3, notch_cells=9.5, nsteps=300, seed=3, amp=1e-7)
+    out, stats, phi, ref = run_pair(w, w.nsteps, 50)
     assert out[-1]["broken"] > 0
     assert_fp64(out, ref.damage(), phi)
     # prescribed particles follow the rigid rotation exactly
@@ -152,7 +156,7 @@ def test_notched_block_twist_parity():
 
 def test_plane_strain_breaking_parity():
     """Plane strain (Eq 1.8 / 1.15 / 1.28 plane-strain rows), steel-like material, breaking on."""
-    w = W.cracked_plate(nx=50, ny=20, dx=2.5e-4, crack_cells=25.125, sigma=4e8, nsteps=300, dt=4.5e-8)
+    w = W.cracked_plate(nx=50, ny=20, dx=2.5e-4, crack_cells=25.125, sigma=5e6, nsteps=300, dt=4.5e-8)
     w.model, w.E, w.nu, w.rho, w.Gc = W.MODEL_PLANE_STRAIN, 190e9, 0.25, 7800.0, 50.0
     out, stats, phi, ref = run_pair(w, w.nsteps, 50)
     assert out[-1]["broken"] > 0
@@ -356,7 +360,7 @@ def test_mixed_config1_error_bound():
 def test_mixed_decisions_equal_fp64_on_own_state():
     """Zero spurious breaks: with validation on, every bond decision of the FP32 + band path equals
     the pure FP64 decision on the mixed run's own state."""
-    w = W.cracked_plate(nx=60, ny=24, dx=2.5e-4, crack_cells=30.125, sigma=1.5e8, nsteps=400)
+    w = W.cracked_plate(nx=60, ny=24, dx=2.5e-4, crack_cells=30.125, sigma=2e6, nsteps=400)
     sim = Simulation(w, s0=s0_of(w), precision=PD_MIXED)
     sim.set_option(B.PD_OPT_VALIDATE, 1)
     sim.step(400)
