@@ -112,6 +112,15 @@ typedef struct {
   int64_t band_rechecks;  /* PD_MIXED: bonds re-decided in FP64 (cumulative) */
   int64_t validate_mismatches; /* PD_MIXED with PD_OPT_VALIDATE: FP32+band vs pure FP64 decisions */
   double max_abs_u;       /* max |u| component at the last refresh */
+  /* Diagnostics of the current state, evaluated in FP64 by pd_get_stats (two extra passes over the
+   * bonds): */
+  double min_rel_margin;  /* min |s - s0| / s0 over the intact breakable bonds (Eq 1.30; 1e300 if
+                             none): how close the nearest bond is to its failure decision */
+  double strain_energy;   /* sum_i V_i [(K - G/3)/(2A) theta_i^2 + G/(2 m_i) sum_j e_ij^2 V_j] over the
+                             intact bonds (the energy whose derivative is the force of Eq 1.14) */
+  double shadow_energy;   /* strain_energy + 1/2 sum_i rho V_i v_i^n . v_i^{n+1}, v^{n+1} the next
+                             velocity of Eq 2.11 (free particles); for the linearized model without
+                             loads, constraints or breaking it is conserved by the integrator */
 } pd_stats;
 
 /* Options for pd_set_option / pd_get_option. */

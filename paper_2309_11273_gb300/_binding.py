@@ -54,7 +54,8 @@ class pd_crack(ctypes.Structure):
 class pd_stats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int64), ("bonds", ctypes.c_int64), ("broken_bonds", ctypes.c_int64),
                 ("band_rechecks", ctypes.c_int64), ("validate_mismatches", ctypes.c_int64),
-                ("max_abs_u", ctypes.c_double)]
+                ("max_abs_u", ctypes.c_double), ("min_rel_margin", ctypes.c_double),
+                ("strain_energy", ctypes.c_double), ("shadow_energy", ctypes.c_double)]
 
 
 class PDError(RuntimeError):

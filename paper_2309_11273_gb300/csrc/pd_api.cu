@@ -61,6 +61,8 @@ void free_build(pd_ctx* c) {
   c->adr_part = c->adr_st = nullptr;
   c->adr_first = nullptr;
   c->adr_restart = true;
+  c->diag_theta = nullptr;
+  c->diag_part = nullptr;
   c->u32[0] = c->u32[1] = nullptr;
   c->thm32 = nullptr;
   c->mu32 = c->aA32 = c->theta32 = nullptr;
@@ -438,6 +440,9 @@ pd_status pd_get_stats(pd_ctx* c, pd_stats* s) {
   double m = 0.0;
   if ((st = max_abs_u(c, &m, &nonfinite)) != PD_OK) return st;
   s->max_abs_u = nonfinite ? NAN : m;
+  double kin = 0.0;
+  if ((st = diagnostics(c, &s->min_rel_margin, &s->strain_energy, &kin)) != PD_OK) return st;
+  s->shadow_energy = s->strain_energy + kin;
   return PD_OK;
 }
 

@@ -469,6 +469,7 @@ pd_status upload_body_params(pd_ctx* c) {
     double A, K, G;
     material_constants(p.model, p.E, p.nu, &A, &K, &G);
     BodyDev& d = h[b];
+    d.A = A;
     d.Kp = K - G / 3.0;
     d.G = G;
     d.inv_rho = 1.0 / p.rho;

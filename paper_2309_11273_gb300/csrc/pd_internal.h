@@ -15,6 +15,7 @@ constexpr int kSlice = 32;  // particles per SELL slice (one warp)
 
 // Per-body constants read by the step kernels (one entry per body; a single body otherwise).
 struct BodyDev {
+  double A;        // Eq 1.8
   double Kp;       // K - G/3 (Eqs 1.14, 2.2)
   double G;        // Eq 1.16
   double inv_rho;  // 1 / rho
@@ -155,6 +156,8 @@ struct pd_ctx {
   double2* adr_part = nullptr;    // ADR per-block partial sums (u.k.u, u.u)
   double2* adr_st = nullptr;      // ADR (c^n, start flag) of the current iteration
   int* adr_first = nullptr;       // ADR: 1 = the next iteration starts from rest
+  double* diag_theta = nullptr;   // pd_get_stats: theta at the current state
+  double4* diag_part = nullptr;   // pd_get_stats: per-block (strain energy, min margin, kinetic, 0)
   double q = 0.0;               // fixed-point quantum of the mixed coordinates [m]
   double qlo[3] = {0, 0, 0};     // origin of the fixed-point coordinates
   // state
@@ -205,6 +208,7 @@ pd_status launch_set_step(pd_ctx* c, int64_t value);
 pd_status init_disp_w(pd_ctx* c);
 pd_status ensure_bond_cache(pd_ctx* c);
 pd_status ensure_adr(pd_ctx* c);      // ADR arrays and lambda (once per build)
+pd_status diagnostics(pd_ctx* c, double* min_margin, double* strain, double* kinetic);
 pd_status prepare_staged_kernels(pd_ctx* c);  // shared-memory opt-in of the staged kernels
 pd_status upload_field(pd_ctx* c, const double* host_soa, double4* dst, int comps);
 pd_status download_field(pd_ctx* c, const double4* src, double* host_soa, int comps);

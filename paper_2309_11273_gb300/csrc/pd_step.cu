@@ -1367,6 +1367,122 @@ __global__ void __launch_bounds__(kAdrBlock) k_adr_update(StepArgs a, const doub
   gold[i] = g;
 }
 
+
+// ------------------------------------------------------------------------- state diagnostics
+// pd_get_stats: theta, the strain energy sum_i V_i [(K - G/3)/(2A) theta_i^2 + G/(2 m_i) sum_j e^2 V_j]
+// and the smallest relative stretch margin |s - s0| / s0 over the intact breakable bonds (pass A),
+// then the force at the same state and 1/2 rho V v^n . v^{n+1} (pass B), all in FP64 from the master
+// state and the current bond status; per-block sums in a fixed order.
+constexpr int kDiagBlock = 256;
+
+template <int DIM, int KIN>
+__device__ __forceinline__ void diag_bond(const double4& pi, const double4& pj, const double4& ui, const double4& uj,
+                                          double& xl, double& e, double& s, double dir[3]) {
+  if (KIN == 0) {
+    double ex, ey, ez, d, q;
+    bond_f64<DIM>(pi, pj, ui, uj, ex, ey, ez, d, q);
+    xl = sqrt(q);
+    e = d / xl;
+    s = d / q;
+    dir[0] = ex / xl;
+    dir[1] = ey / xl;
+    dir[2] = ez / xl;
+  } else {
+    const BondNL<DIM> r = bond_nl<DIM>(pi, pj, ui, uj);
+    double y2 = r.yx * r.yx + r.yy * r.yy;
+    if (DIM == 3) y2 = fma(r.yz, r.yz, y2);
+    const double yl = sqrt(y2);
+    xl = sqrt(r.q);
+    e = r.p / (yl + xl);
+    s = e / xl;
+    dir[0] = r.yx / yl;
+    dir[1] = r.yy / yl;
+    dir[2] = r.yz / yl;
+  }
+}
+
+template <int DIM, int KIN>
+__global__ void __launch_bounds__(kDiagBlock) k_diag_a(StepArgs a, const double4* __restrict__ disp,
+                                                        double* __restrict__ theta, double4* __restrict__ part) {
+  __shared__ double se[kDiagBlock], sm[kDiagBlock];
+  const SliceIdx t = slice_index<1>(a.n_pad, a.slice_ptr);
+  double energy = 0.0, margin = 1e300;
+  if (t.active) {
+    const int b = a.body ? a.body[t.i] : 0;
+    const BodyDev& bp = a.bp[b];
+    const double4 pi = a.pos[t.i], ui = disp[t.i];
+    double th = 0.0, ee = 0.0;
+    for (int k = 0; k < t.W; ++k) {
+      if (!((a.bits[(t.base >> 5) + k] >> t.lane) & 1u)) continue;
+      const int32_t j = a.col[t.base + t.lane + ((int64_t)k << 5)];
+      const double4 pj = a.pos[j];
+      double xl, e, sv, dir[3];
+      diag_bond<DIM, KIN>(pi, pj, ui, disp[j], xl, e, sv, dir);
+      th += xl * e * pj.w;
+      ee += e * e * pj.w;
+      if (bp.breaks) margin = fmin(margin, fabs(sv - bp.s0) / bp.s0);
+    }
+    const double theta_i = a.aA[t.i] * th;
+    theta[t.i] = theta_i;
+    energy = pi.w * (bp.Kp / (2.0 * bp.A) * theta_i * theta_i + 0.5 * bp.G * a.mu[t.i] * ee);
+  }
+  se[threadIdx.x] = energy;
+  sm[threadIdx.x] = margin;
+  __syncthreads();
+  for (int w = kDiagBlock / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      se[threadIdx.x] += se[threadIdx.x + w];
+      sm[threadIdx.x] = fmin(sm[threadIdx.x], sm[threadIdx.x + w]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = make_double4(se[0], sm[0], 0.0, 0.0);
+}
+
+template <int DIM, int KIN>
+__global__ void __launch_bounds__(kDiagBlock) k_diag_b(StepArgs a, const double4* __restrict__ disp,
+                                                        const double* __restrict__ theta, double4* __restrict__ part) {
+  __shared__ double sk[kDiagBlock];
+  const SliceIdx t = slice_index<1>(a.n_pad, a.slice_ptr);
+  double kin = 0.0;
+  if (t.active) {
+    const int b = a.body ? a.body[t.i] : 0;
+    const BodyDev& bp = a.bp[b];
+    const double4 pi = a.pos[t.i], ui = disp[t.i];
+    const double txi = bp.Kp * theta[t.i] * a.mu[t.i], tyi = bp.G * a.mu[t.i];
+    double f[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < t.W; ++k) {
+      if (!((a.bits[(t.base >> 5) + k] >> t.lane) & 1u)) continue;
+      const int32_t j = a.col[t.base + t.lane + ((int64_t)k << 5)];
+      const double4 pj = a.pos[j];
+      double xl, e, sv, dir[3];
+      diag_bond<DIM, KIN>(pi, pj, ui, disp[j], xl, e, sv, dir);
+      // Eq 1.14 for both ends (Eq 2.2 in the linearized model), force density on i
+      const double cf = ((txi + bp.Kp * theta[j] * a.mu[j]) * xl + (tyi + bp.G * a.mu[j]) * e) * pj.w;
+      f[0] = fma(cf, dir[0], f[0]);
+      f[1] = fma(cf, dir[1], f[1]);
+      f[2] = fma(cf, dir[2], f[2]);
+    }
+    const double4 v = a.vel[t.i];
+    const uint8_t fl = a.flag ? a.flag[t.i] : (uint8_t)0;
+    double vn[3] = {v.x, v.y, v.z};
+    if (fl == 0) {
+      const double4 bb = a.bacc ? a.bacc[t.i] : make_double4(0.0, 0.0, 0.0, 0.0);
+      vn[0] += bp.dt * ((f[0] + bb.x) * bp.inv_rho);
+      vn[1] += bp.dt * ((f[1] + bb.y) * bp.inv_rho);
+      vn[2] += bp.dt * ((f[2] + bb.z) * bp.inv_rho);
+    }
+    kin = 0.5 * (pi.w / bp.inv_rho) * (v.x * vn[0] + v.y * vn[1] + v.z * vn[2]);
+  }
+  sk[threadIdx.x] = kin;
+  __syncthreads();
+  for (int w = kDiagBlock / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sk[threadIdx.x] += sk[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x].z = sk[0];
+}
+
 // ----------------------------------------------------------------------------- auxiliary kernels
 __global__ void k_set_step(int64_t* d_step, int64_t v) { *d_step = v; }
 
@@ -1698,6 +1814,43 @@ pd_status ensure_adr(pd_ctx* c) {
     PD_CUDA(cudaGetLastError());
     c->adr_restart = false;
   }
+  return PD_OK;
+}
+
+pd_status diagnostics(pd_ctx* c, double* min_margin, double* strain, double* kinetic) {
+  const int64_t np = c->n_pad;
+  const unsigned nblk = (unsigned)((np + kDiagBlock - 1) / kDiagBlock);
+  pd_status st;
+  if (!c->diag_theta && (st = alloc(c, &c->diag_theta, np)) != PD_OK) return st;
+  if (!c->diag_part && (st = alloc(c, &c->diag_part, nblk)) != PD_OK) return st;
+  StepArgs a = make_args(c);
+  const double4* u = c->disp[c->cur];
+  if (c->dim == 3 && c->kin == PD_NONLINEAR) {
+    k_diag_a<3, 1><<<nblk, kDiagBlock, 0, c->stream>>>(a, u, c->diag_theta, c->diag_part);
+    k_diag_b<3, 1><<<nblk, kDiagBlock, 0, c->stream>>>(a, u, c->diag_theta, c->diag_part);
+  } else if (c->dim == 3) {
+    k_diag_a<3, 0><<<nblk, kDiagBlock, 0, c->stream>>>(a, u, c->diag_theta, c->diag_part);
+    k_diag_b<3, 0><<<nblk, kDiagBlock, 0, c->stream>>>(a, u, c->diag_theta, c->diag_part);
+  } else if (c->kin == PD_NONLINEAR) {
+    k_diag_a<2, 1><<<nblk, kDiagBlock, 0, c->stream>>>(a, u, c->diag_theta, c->diag_part);
+    k_diag_b<2, 1><<<nblk, kDiagBlock, 0, c->stream>>>(a, u, c->diag_theta, c->diag_part);
+  } else {
+    k_diag_a<2, 0><<<nblk, kDiagBlock, 0, c->stream>>>(a, u, c->diag_theta, c->diag_part);
+    k_diag_b<2, 0><<<nblk, kDiagBlock, 0, c->stream>>>(a, u, c->diag_theta, c->diag_part);
+  }
+  PD_CUDA(cudaGetLastError());
+  std::vector<double4> h(nblk);
+  PD_CUDA(cudaMemcpyAsync(h.data(), c->diag_part, sizeof(double4) * nblk, cudaMemcpyDeviceToHost, c->stream));
+  PD_CUDA(cudaStreamSynchronize(c->stream));
+  double e = 0.0, k = 0.0, m = 1e300;
+  for (const double4& p : h) {
+    e += p.x;
+    m = std::min(m, p.y);
+    k += p.z;
+  }
+  *min_margin = m;
+  *strain = e;
+  *kinetic = k;
   return PD_OK;
 }
 

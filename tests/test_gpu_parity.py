@@ -368,3 +368,56 @@ def test_mixed_decisions_equal_fp64_on_own_state():
     sim.close()
     assert st["broken_bonds"] > 0
     assert st["validate_mismatches"] == 0
+
+
+# ------------------------------------------------------------------------------- diagnostics
+def _strain_energy_np(ref, u, status):
+    """sum_i V_i [(K - G/3)/(2A) theta_i^2 + G/(2 m_i) sum_j e_ij^2 V_j], linearized e, from the
+    oracle's family and coordinates (written out here, independently of both implementations)."""
+    P = np.stack([ref.x, ref.y] + ([ref.z] if ref.dim == 3 else []))
+    rows = np.repeat(np.arange(ref.n), np.diff(ref.row_ptr))
+    xi = P[:, ref.col] - P[:, rows]
+    xl = np.sqrt((xi * xi).sum(0))
+    e = ((xi / xl) * (u[:, ref.col] - u[:, rows])).sum(0) * status
+    vj = ref.vol[ref.col]
+    th = ref.A / ref.m * np.bincount(rows, weights=xl * e * vj, minlength=ref.n)
+    es = np.bincount(rows, weights=e * e * vj, minlength=ref.n)
+    return float((ref.vol * ((ref.K - ref.G / 3) / (2 * ref.A) * th ** 2 + ref.G / (2 * ref.m) * es)).sum())
+
+
+def test_shadow_energy_is_conserved():
+    """Configuration 1 (no loads, constraints or breaking): pd_get_stats' shadow energy
+    U(u^n) + 1/2 sum rho V v^n . v^{n+1} stays constant to 1e-12 over 1000 steps while the strain
+    energy alone swings; the strain energy equals the one written out in the test to 1e-12."""
+    w = W.config1()
+    sim = Simulation(w, s0=0.0)
+    ref = oracle_for(w, 0.0)
+    H, Us = [], []
+    for _ in range(10):
+        sim.step(100)
+        ref.step(100)
+        st = sim.stats()
+        H.append(st["shadow_energy"])
+        Us.append(st["strain_energy"])
+        u = sim.state()[0]
+        assert st["strain_energy"] == pytest.approx(_strain_energy_np(ref, u, np.ones(ref.col.size)), rel=1e-12)
+    sim.close()
+    H = np.array(H)
+    assert np.abs(H - H[0]).max() <= 1e-12 * abs(H[0])
+    assert (max(Us) - min(Us)) > 1e-3 * max(Us)
+
+
+def test_min_margin_matches_oracle():
+    """The smallest relative stretch margin of pd_get_stats equals the oracle's after the same steps
+    (cracked plate with crack growth)."""
+    w = W.cracked_plate(nx=60, ny=24, dx=2.5e-4, crack_cells=30.125, sigma=2e6, nsteps=400)
+    s0 = s0_of(w)
+    sim = Simulation(w, s0=s0)
+    ref = oracle_for(w, s0)
+    for _ in range(4):
+        margins, _ = ref.step(100)
+        sim.step(100)
+        st = sim.stats()
+        assert st["min_rel_margin"] == pytest.approx(margins[-1], rel=1e-9)
+    assert st["broken_bonds"] > 0
+    sim.close()
