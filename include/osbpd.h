@@ -216,7 +216,9 @@ pd_status pd_set_state(pd_ctx* c, const double* u, const double* v);
 /* Advances nsteps >= 0 explicit time steps.  Per step: bond-status update on u^n (the failure block
  * that follows the previous update in Appendix B), dilatation, force, velocity / displacement
  * update with boundary conditions at t_{n+1}.  Runs as CUDA-graph chunks of PD_OPT_GRAPH_CHUNK
- * steps when graphs are enabled.  Enqueue only: returns before the GPU finishes. */
+ * steps when graphs are enabled.  Enqueue only: returns before the GPU finishes.  A state that
+ * became non-finite is reported by the next pd_sync / pd_get_* as PD_ERR_NUMERIC (a one-pass check
+ * over the particles is enqueued after the steps). */
 pd_status pd_step(pd_ctx* c, int64_t nsteps);
 
 /* Waits for all work of the context. */

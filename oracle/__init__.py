@@ -21,6 +21,8 @@ sequences the calls.  Equation references are to the paper:
 * Eq 2.11 + Appendix B  -> :class:`OracleSim`
 * adaptive dynamic relaxation (Section 4.4's quasi-static solver) -> :func:`adr_lambda`,
   :meth:`OracleSim.adr_step`
+* ``pdref_*``: the oracle behind the GPU library's call sequence (create, build, boundary
+  conditions, state, step, read back), so that one harness drives both
 
 Parity unpinned: none (every function is pinned by the ``-m "not gpu"`` tests).
 """
@@ -387,3 +389,110 @@ class OracleSim:
         self._adr_fresh = False
         self.steps_done += nsteps
         return damping[:nsteps], margins[:nsteps], broken[:nsteps]
+
+
+# ------------------------------------------------------------------------------------ pdref_*
+class _PdrefParams(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int32), ("precision", ctypes.c_int32), ("E", ctypes.c_double),
+                ("nu", ctypes.c_double), ("rho", ctypes.c_double), ("horizon", ctypes.c_double),
+                ("s0", ctypes.c_double), ("dt", ctypes.c_double), ("band_safety", ctypes.c_double),
+                ("device", ctypes.c_int32), ("ordering", ctypes.c_int32), ("stream", ctypes.c_void_p),
+                ("kinematics", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class _PdrefCrack(ctypes.Structure):
+    _fields_ = [("p0", ctypes.c_double * 3), ("p1", ctypes.c_double * 3), ("p2", ctypes.c_double * 3),
+                ("body", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+def _pdref_lib():
+    L = lib()
+    if not getattr(L, "_pdref_ready", False):
+        vp = ctypes.c_void_p
+        L.pdref_create_particles.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(_PdrefParams), ctypes.c_int64,
+                                             _d, _d, _d, _d]
+        L.pdref_build_neighbors.argtypes = [vp, ctypes.POINTER(_PdrefCrack), ctypes.c_int32]
+        L.pdref_set_bc.argtypes = [vp, _u8, _d, _d, _d, ctypes.c_double]
+        L.pdref_set_state.argtypes = [vp, _d, _d]
+        L.pdref_step.argtypes = [vp, ctypes.c_int64]
+        L.pdref_get_state.argtypes = [vp, _d, _d, _d]
+        L.pdref_get_damage.argtypes = [vp, _d]
+        L.pdref_num_bonds.argtypes = [vp, _i64]
+        L.pdref_get_neighbors.argtypes = [vp, _i64, _i32, _u8]
+        L.pdref_destroy.argtypes = [vp]
+        L.pdref_destroy.restype = None
+        L._pdref_ready = True
+    return L
+
+
+def _ok(st):
+    if st != 0:
+        raise RuntimeError("pdref call failed with status %d" % st)
+
+
+def pdref_create_particles(model, E, nu, rho, horizon, s0, dt, x, y, z=None, vol=None, kinematics=LINEARIZED):
+    """The oracle behind the GPU library's call sequence (``pdref_*`` in ``osb_oracle.c``)."""
+    prm = _PdrefParams(int(model), 0, float(E), float(nu), float(rho), float(horizon), float(s0), float(dt), 0.0,
+                       0, 0, None, int(kinematics), 0)
+    x, y, z, vol = _f64(x), _f64(y), _f64(z), _f64(vol)
+    h = ctypes.c_void_p()
+    _ok(_pdref_lib().pdref_create_particles(ctypes.byref(h), ctypes.byref(prm), x.size, _p(x, _d), _p(y, _d),
+                                            _p(z, _d), _p(vol, _d)))
+    return h
+
+
+def pdref_build_neighbors(h, cracks=()):
+    arr = (_PdrefCrack * max(len(cracks), 1))()
+    for k, c in enumerate(cracks):
+        pts = np.zeros(9)
+        q = np.asarray(c, dtype=np.float64).reshape(-1)
+        pts[:q.size] = q
+        arr[k].p0[:] = list(pts[0:3])
+        arr[k].p1[:] = list(pts[3:6])
+        arr[k].p2[:] = list(pts[6:9])
+        arr[k].body = -1
+    _ok(_pdref_lib().pdref_build_neighbors(h, arr, len(cracks)))
+
+
+def pdref_set_bc(h, dim, n, flag=None, b=None, axis_point=None, axis_dir=None, rate=0.0):
+    flag = None if flag is None else np.ascontiguousarray(flag, dtype=np.uint8)
+    b = None if b is None else np.ascontiguousarray(np.asarray(b, dtype=np.float64).reshape(dim, n))
+    ap = None if axis_point is None else np.ascontiguousarray(axis_point, dtype=np.float64)
+    ad = None if axis_dir is None else np.ascontiguousarray(axis_dir, dtype=np.float64)
+    _ok(_pdref_lib().pdref_set_bc(h, _p(flag, _u8), _p(b, _d), _p(ap, _d), _p(ad, _d), float(rate)))
+
+
+def pdref_set_state(h, dim, n, u, v=None):
+    u = np.ascontiguousarray(np.asarray(u, dtype=np.float64).reshape(dim, n))
+    v = None if v is None else np.ascontiguousarray(np.asarray(v, dtype=np.float64).reshape(dim, n))
+    _ok(_pdref_lib().pdref_set_state(h, _p(u, _d), _p(v, _d)))
+
+
+def pdref_step(h, nsteps):
+    _ok(_pdref_lib().pdref_step(h, int(nsteps)))
+
+
+def pdref_get_state(h, dim, n):
+    u, v, th = np.zeros((dim, n)), np.zeros((dim, n)), np.zeros(n)
+    _ok(_pdref_lib().pdref_get_state(h, _p(u, _d), _p(v, _d), _p(th, _d)))
+    return u, v, th
+
+
+def pdref_get_damage(h, n):
+    phi = np.zeros(n)
+    _ok(_pdref_lib().pdref_get_damage(h, _p(phi, _d)))
+    return phi
+
+
+def pdref_get_neighbors(h, n):
+    nb = ctypes.c_int64()
+    _ok(_pdref_lib().pdref_num_bonds(h, ctypes.byref(nb)))
+    rp = np.zeros(n + 1, dtype=np.int64)
+    col = np.zeros(max(nb.value, 1), dtype=np.int32)
+    intact = np.zeros(max(nb.value, 1), dtype=np.uint8)
+    _ok(_pdref_lib().pdref_get_neighbors(h, _p(rp, _i64), _p(col, _i32), _p(intact, _u8)))
+    return rp, col[:nb.value], intact[:nb.value]
+
+
+def pdref_destroy(h):
+    _pdref_lib().pdref_destroy(h)

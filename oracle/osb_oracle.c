@@ -706,3 +706,188 @@ void orc_adr_run(int kin, int64_t n, int dim, const double* x, const double* y, 
     if (broken) broken[s] = nb;
   }
 }
+
+/* ------------------------------------------------------------------------------------------------
+ * pdref_*: the oracle behind the same call sequence as the GPU library's C ABI (create, build the
+ * family, boundary conditions, state, step, read back), so one harness can drive both.  The
+ * parameter and crack blocks have the GPU library's field layout, declared here on their own.
+ * Single body, explicit solver; every computation is one of the functions above.  Status codes:
+ * 0 ok, -1 bad argument, -2 call out of order.
+ * ---------------------------------------------------------------------------------------------- */
+typedef struct {
+  int32_t model, precision;
+  double E, nu, rho, horizon, s0, dt, band_safety;
+  int32_t device, ordering;
+  void* stream;
+  int32_t kinematics, reserved;
+} pdref_params;
+
+typedef struct {
+  double p0[3], p1[3], p2[3];
+  int32_t body, reserved;
+} pdref_crack;
+
+typedef struct pdref_ctx {
+  int64_t n;
+  int dim, model, kin, built;
+  double rho, delta, s0, dt, A, K, G, kappa, mu;
+  double *x, *y, *z, *vol;
+  int64_t* row_ptr;
+  int32_t* col;
+  uint8_t* status;
+  double *m, *u[3], *v[3], *theta, *f[3], *b[3];
+  uint8_t* flag;
+  double axis_point[3], axis_dir[3], rate;
+  int64_t steps;
+} pdref_ctx;
+
+static double* pdref_copy(const double* a, int64_t n) {
+  double* p = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  if (a) memcpy(p, a, sizeof(double) * (size_t)n);
+  else memset(p, 0, sizeof(double) * (size_t)(n > 0 ? n : 1));
+  return p;
+}
+
+void pdref_destroy(pdref_ctx* c) {
+  if (!c) return;
+  free(c->x); free(c->y); free(c->z); free(c->vol);
+  free(c->row_ptr); free(c->col); free(c->status); free(c->m); free(c->theta); free(c->flag);
+  for (int k = 0; k < 3; ++k) {
+    free(c->u[k]); free(c->v[k]); free(c->f[k]); free(c->b[k]);
+  }
+  free(c);
+}
+
+int pdref_create_particles(pdref_ctx** out, const pdref_params* p, int64_t n, const double* x,
+                           const double* y, const double* z, const double* vol) {
+  if (!out || !p || !x || !y || !vol || n < 1) return -1;
+  if (p->model < 0 || p->model > 2 || (p->model == ORC_3D) != (z != NULL)) return -1;
+  pdref_ctx* c = (pdref_ctx*)calloc(1, sizeof(pdref_ctx));
+  c->n = n;
+  c->dim = z ? 3 : 2;
+  c->model = p->model;
+  c->kin = p->kinematics;
+  c->rho = p->rho;
+  c->delta = p->horizon;
+  c->s0 = p->s0;
+  c->dt = p->dt;
+  orc_constants(p->model, p->E, p->nu, &c->A, &c->K, &c->G, &c->kappa, &c->mu);
+  c->x = pdref_copy(x, n);
+  c->y = pdref_copy(y, n);
+  c->z = z ? pdref_copy(z, n) : NULL;
+  c->vol = pdref_copy(vol, n);
+  for (int k = 0; k < 3; ++k) {
+    c->u[k] = pdref_copy(NULL, n);
+    c->v[k] = pdref_copy(NULL, n);
+    c->f[k] = pdref_copy(NULL, n);
+  }
+  c->theta = pdref_copy(NULL, n);
+  *out = c;
+  return 0;
+}
+
+int pdref_build_neighbors(pdref_ctx* c, const pdref_crack* cracks, int32_t ncracks) {
+  if (!c || ncracks < 0 || (ncracks > 0 && !cracks)) return -1;
+  double* cr = (double*)malloc(sizeof(double) * 9 * (size_t)(ncracks > 0 ? ncracks : 1));
+  for (int32_t k = 0; k < ncracks; ++k)
+    for (int t = 0; t < 3; ++t) {
+      cr[9 * k + t] = cracks[k].p0[t];
+      cr[9 * k + 3 + t] = cracks[k].p1[t];
+      cr[9 * k + 6 + t] = cracks[k].p2[t];
+    }
+  int64_t* counts = (int64_t*)calloc((size_t)c->n, sizeof(int64_t));
+  orc_family_binned(c->n, c->dim, c->x, c->y, c->z ? c->z : c->x, c->delta, ncracks, cr, counts, NULL, NULL);
+  free(c->row_ptr); free(c->col); free(c->status); free(c->m);
+  c->row_ptr = (int64_t*)calloc((size_t)c->n + 1, sizeof(int64_t));
+  for (int64_t i = 0; i < c->n; ++i) c->row_ptr[i + 1] = c->row_ptr[i] + counts[i];
+  int64_t nb = c->row_ptr[c->n];
+  c->col = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nb > 0 ? nb : 1));
+  orc_family_binned(c->n, c->dim, c->x, c->y, c->z ? c->z : c->x, c->delta, ncracks, cr, counts, c->row_ptr,
+                    c->col);
+  c->status = (uint8_t*)malloc((size_t)(nb > 0 ? nb : 1));
+  memset(c->status, 1, (size_t)(nb > 0 ? nb : 1));
+  c->m = pdref_copy(NULL, c->n);
+  orc_weighted_volume(c->n, c->dim, c->x, c->y, c->z ? c->z : c->x, c->vol, c->row_ptr, c->col, c->m);
+  free(counts);
+  free(cr);
+  c->built = 1;
+  return 0;
+}
+
+int pdref_set_bc(pdref_ctx* c, const uint8_t* flag, const double* b, const double* axis_point,
+                 const double* axis_dir, double rate) {
+  if (!c) return -1;
+  if (!c->built) return -2;
+  free(c->flag);
+  c->flag = NULL;
+  if (flag) {
+    c->flag = (uint8_t*)malloc((size_t)c->n);
+    memcpy(c->flag, flag, (size_t)c->n);
+  }
+  for (int k = 0; k < 3; ++k) {
+    free(c->b[k]);
+    c->b[k] = (b && k < c->dim) ? pdref_copy(b + (int64_t)k * c->n, c->n) : NULL;
+    c->axis_point[k] = axis_point ? axis_point[k] : 0.0;
+    c->axis_dir[k] = axis_dir ? axis_dir[k] : 0.0;
+  }
+  c->rate = rate;
+  return 0;
+}
+
+int pdref_set_state(pdref_ctx* c, const double* u, const double* v) {
+  if (!c || !u) return -1;
+  if (!c->built) return -2;
+  for (int k = 0; k < c->dim; ++k) {
+    memcpy(c->u[k], u + (int64_t)k * c->n, sizeof(double) * (size_t)c->n);
+    if (v) memcpy(c->v[k], v + (int64_t)k * c->n, sizeof(double) * (size_t)c->n);
+    else memset(c->v[k], 0, sizeof(double) * (size_t)c->n);
+  }
+  return 0;
+}
+
+int pdref_step(pdref_ctx* c, int64_t nsteps) {
+  if (!c || nsteps < 0) return -1;
+  if (!c->built) return -2;
+  const double* zz = c->z ? c->z : c->x;
+  orc_run(c->kin, c->n, c->dim, c->x, c->y, zz, c->vol, c->row_ptr, c->col, c->status, c->m, c->A, c->K,
+          c->G, c->rho, c->dt, c->s0, c->flag, c->b[0], c->b[1], c->b[2], c->axis_point, c->axis_dir,
+          c->rate, c->steps, nsteps, c->u[0], c->u[1], c->u[2], c->v[0], c->v[1], c->v[2], c->theta,
+          c->f[0], c->f[1], c->f[2], NULL, NULL);
+  c->steps += nsteps;
+  return 0;
+}
+
+int pdref_get_state(pdref_ctx* c, double* u, double* v, double* theta) {
+  if (!c) return -1;
+  if (!c->built) return -2;
+  for (int k = 0; k < c->dim; ++k) {
+    if (u) memcpy(u + (int64_t)k * c->n, c->u[k], sizeof(double) * (size_t)c->n);
+    if (v) memcpy(v + (int64_t)k * c->n, c->v[k], sizeof(double) * (size_t)c->n);
+  }
+  if (theta) memcpy(theta, c->theta, sizeof(double) * (size_t)c->n);
+  return 0;
+}
+
+int pdref_get_damage(pdref_ctx* c, double* phi) {
+  if (!c || !phi) return -1;
+  if (!c->built) return -2;
+  orc_damage(c->n, c->vol, c->row_ptr, c->col, c->status, phi);
+  return 0;
+}
+
+int pdref_num_bonds(pdref_ctx* c, int64_t* nbonds) {
+  if (!c || !nbonds) return -1;
+  if (!c->built) return -2;
+  *nbonds = c->row_ptr[c->n];
+  return 0;
+}
+
+int pdref_get_neighbors(pdref_ctx* c, int64_t* row_ptr, int32_t* col, uint8_t* intact) {
+  if (!c || !row_ptr || !col) return -1;
+  if (!c->built) return -2;
+  int64_t nb = c->row_ptr[c->n];
+  memcpy(row_ptr, c->row_ptr, sizeof(int64_t) * (size_t)(c->n + 1));
+  memcpy(col, c->col, sizeof(int32_t) * (size_t)nb);
+  if (intact) memcpy(intact, c->status, (size_t)nb);
+  return 0;
+}

@@ -73,7 +73,8 @@ struct StepArgs {
   float* mu32;             // 1 / m_i in FP32
   float* aA32;             // A / m_i * Q in FP32 (Q folded in)
   float* theta32;          // theta_i in FP32
-  unsigned long long* counters;  // [0] band rechecks, [1] validate mismatches, [2..3] max |u|, [4] wait expired
+  unsigned long long* counters;  // [0] band rechecks, [1] validate mismatches, [2..3] max |u|, [4] wait expired,
+                                 // [5] non-finite displacement after a pd_step
   float band_c;            // safety factor of the band
   int validate;            // mixed: also decide every bond in FP64 and count mismatches
   int check;               // apply the failure criterion at the head of pass 1

@@ -1570,6 +1570,14 @@ __global__ void k_shadow(int64_t n_pad, const double4* __restrict__ disp, float4
 
 // max |u_k| over all particles and components (order-independent: max of non-negative doubles as
 // integers), plus a count of non-finite components.
+// Sets *flag when any displacement component is not finite (checked after each pd_step).
+__global__ void k_flag_nonfinite(int64_t n, const double4* __restrict__ disp, unsigned long long* flag) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double4 u = disp[i];
+  if (!isfinite(u.x) || !isfinite(u.y) || !isfinite(u.z)) atomicExch(flag, 1ull);
+}
+
 __global__ void k_max_abs(int64_t n, const double4* __restrict__ disp, unsigned long long* out) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double m = 0.0;
@@ -1989,12 +1997,18 @@ pd_status sync_shadow(pd_ctx* c) {
 // Error word of the staged kernels (a bounded wait expired); cleared after it is reported.
 pd_status check_device_error(pd_ctx* c) {
   unsigned long long flag = 0;
+  unsigned long long nonfinite = 0;
   PD_CUDA(cudaMemcpyAsync(&flag, c->counters + 4, sizeof(flag), cudaMemcpyDeviceToHost, c->stream));
+  PD_CUDA(cudaMemcpyAsync(&nonfinite, c->counters + 5, sizeof(nonfinite), cudaMemcpyDeviceToHost, c->stream));
   PD_CUDA(cudaStreamSynchronize(c->stream));
   if (flag) {
     PD_CUDA(cudaMemsetAsync(c->counters + 4, 0, sizeof(flag), c->stream));
     return fail(PD_ERR_TIMEOUT, "a staged neighbour-index copy did not complete within the wait limit; "
                                 "the step's results were not written");
+  }
+  if (nonfinite) {
+    PD_CUDA(cudaMemsetAsync(c->counters + 5, 0, sizeof(nonfinite), c->stream));
+    return fail(PD_ERR_NUMERIC, "the displacement became non-finite (the run diverged)");
   }
   return PD_OK;
 }
@@ -2072,6 +2086,10 @@ pd_status run_steps(pd_ctx* c, int64_t nsteps) {
     }
   }
   c->check_pending = true;
+  // divergence check, reported by the next pd_sync / pd_get_* (PD_ERR_NUMERIC)
+  const int tb = 256;
+  k_flag_nonfinite<<<(unsigned)((c->n + tb - 1) / tb), tb, 0, c->stream>>>(c->n, c->disp[c->cur], c->counters + 5);
+  PD_CUDA(cudaGetLastError());
   return PD_OK;
 }
 

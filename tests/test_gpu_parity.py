@@ -281,6 +281,11 @@ def test_unstable_time_step_trips_the_guard():
     sim = Simulation(w, s0=0.0)
     sim.step(600)
     assert B.pd_check_state(sim.h, 1e-3) == B.PD_ERR_NUMERIC
+    # run on until the state overflows: the next sync reports it without a device fault
+    sim.step(20000)
+    with pytest.raises(B.PDError) as e:
+        sim.sync()
+    assert e.value.status == B.PD_ERR_NUMERIC
     sim.close()
 
 
