@@ -202,9 +202,24 @@ def oracle_sample_rate(target_s=12.0, max_steps=1000):
     t0 = time.perf_counter()
     sim.step(steps)
     el = time.perf_counter() - t0
-    return {"value": sim.nbonds * steps / el, "unit": UNIT, "cores": O.get_threads(), "kind": "oracle",
+    # the same loop on one core, a few steps (a quarter of the time budget at most)
+    cores = O.get_threads()
+    O.set_threads(1)
+    try:
+        t0 = time.perf_counter()
+        sim.step(1)
+        one = time.perf_counter() - t0
+        s1 = int(max(1, min(20, 0.25 * target_s / max(one, 1e-6))))
+        t0 = time.perf_counter()
+        sim.step(s1)
+        el1 = time.perf_counter() - t0
+    finally:
+        O.set_threads(cores)
+    return {"value": sim.nbonds * steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "single_core_value": sim.nbonds * s1 / el1,
             "sample": "%d time steps of the oracle on a 100x50x25 sub-block of the workload (%d particles, "
-                      "%d directed bonds), %.1f s" % (steps, sim.n, sim.nbonds, el)}
+                      "%d directed bonds), %.1f s on %d threads; %d steps on one thread, %.1f s"
+                      % (steps, sim.n, sim.nbonds, el, cores, s1, el1)}
 
 
 def run_reference(args):
@@ -515,6 +530,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--profile-target", choices=["fp64", "mixed", "nonlinear"], default=None,
                     help="only build the workload and run 4 eager steps (the command profiled by ncu)")
+    ap.add_argument("--sweep", action="store_true",
+                    help="one JSON line per configuration (1-5): FP64 and mixed GPU rates and the oracle's "
+                         "rate on all host cores and on one (the per-configuration table of the baseline)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -524,7 +542,66 @@ def main():
     __graft_entry__.build()
     if args.profile_target:
         return profile_target(args.profile_target)
+    if args.sweep:
+        return run_sweep(args)
     return run_gpu(args)
+
+
+def run_sweep(args):
+    """Every configuration on the GPU (FP64 and mixed, CUDA-graph chunks, events on the library's
+    stream) and the oracle on the host (all cores and one core, a bounded number of steps)."""
+    import torch
+    import oracle as O
+    from paper_2309_11273_gb300 import PD_FP64, PD_MIXED, BatchSimulation, Simulation
+    from paper_2309_11273_gb300 import _binding as B
+    from paper_2309_11273_gb300 import workloads as W
+    stream = torch.cuda.Stream()
+    dev = torch.cuda.current_device()
+    cfgs = [("config1", W.config1, 1000, 1000, 200), ("config2", W.config2, 1000, 1000, 50),
+            ("config3", W.config3, 200, 10, 2), ("config4", W.config4, 200, 10, 2),
+            ("config5", W.config5, 50, 2, 1)]
+    for name, make, gpu_steps, cpu_steps, cpu1_steps in cfgs:
+        w = make()
+        batch = isinstance(w, W.BatchWorkload)
+        line = {"sweep": name, "unit": UNIT}
+        for prec, tag in ((PD_FP64, "fp64"), (PD_MIXED, "mixed")):
+            if batch:
+                sim = BatchSimulation(w, precision=prec, stream=stream.cuda_stream, device=dev)
+            else:
+                sim = Simulation(w, precision=prec, stream=stream.cuda_stream, device=dev)
+            B.pd_autotune(sim.h, 3)
+            sim.step(args.warmup)
+            ms = timed(sim, stream, gpu_steps, 1)
+            line[tag] = {"value": sim.nbonds * gpu_steps / (ms * 1e-3), "ms_per_step": ms / gpu_steps,
+                         "steps": gpu_steps, "bonds": sim.nbonds}
+            sim.close()
+            torch.cuda.empty_cache()
+        # the oracle: configuration 4 one plate after another (it has no batched form)
+        bodies = w.bodies if batch else [w]
+        refs = []
+        for b in bodies:
+            s0 = O.critical_stretch(b.model, b.E, b.nu, b.Gc, b.delta) if b.Gc else 0.0
+            r = O.OracleSim(b.model, b.E, b.nu, b.rho, b.delta, s0, b.dt, b.x, b.y, b.z, b.vol, b.cracks)
+            r.set_bc(b.flag, b.b, b.axis_point, b.axis_dir, b.rotation_rate(s0))
+            r.set_state(b.initial_u(), b.initial_v())
+            refs.append(r)
+        nb = sum(r.nbonds for r in refs)
+        res = {}
+        cores = O.get_threads()
+        for threads, steps in ((cores, cpu_steps), (1, cpu1_steps)):
+            O.set_threads(threads)
+            t0 = time.perf_counter()
+            for r in refs:
+                r.step(steps)
+            el = time.perf_counter() - t0
+            res[threads] = (nb * steps / el, steps, el)
+        O.set_threads(cores)
+        line["oracle"] = {"value": res[cores][0], "cores": cores, "steps": res[cores][1], "seconds": res[cores][2],
+                          "single_core_value": res[1][0], "single_core_steps": res[1][1],
+                          "single_core_seconds": res[1][2]}
+        print(json.dumps(line), flush=True)
+        del refs
+    return 0
 
 
 def profile_target(form):
