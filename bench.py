@@ -559,7 +559,7 @@ def run_sweep(args):
     dev = torch.cuda.current_device()
     cfgs = [("config1", W.config1, 1000, 1000, 200), ("config2", W.config2, 1000, 1000, 50),
             ("config3", W.config3, 200, 10, 2), ("config4", W.config4, 200, 10, 2),
-            ("config5", W.config5, 50, 2, 1)]
+            ("config5", W.config5, 50, 2, 1), ("kalthoff", W.kalthoff, 1000, 200, 20)]
     for name, make, gpu_steps, cpu_steps, cpu1_steps in cfgs:
         w = make()
         batch = isinstance(w, W.BatchWorkload)

@@ -208,6 +208,13 @@ pd_status pd_build_neighbors(pd_ctx* c, const pd_crack* cracks, int32_t ncracks)
 pd_status pd_set_bc(pd_ctx* c, const uint8_t* flag, const double* b, const double* axis_point,
                     const double* axis_dir, double rate);
 
+/* Prescribed velocity field: every particle with flag 2 (pd_set_bc) then moves as u = t vp_i,
+ * v = vp_i (t = step * dt) instead of the rotation of pd_set_bc: a constant velocity applied to
+ * impacted nodes (Section 4.3).  vp: dim * n SoA in caller order (entries of other particles are
+ * ignored).  PD_ERR_ARG for NULL or non-finite vp, PD_ERR_STATE before pd_set_bc marked prescribed
+ * particles. */
+pd_status pd_set_prescribed_velocity(pd_ctx* c, const double* vp);
+
 /* Sets the displacement u (dim * n SoA, required) and velocity v (dim * n SoA, NULL: zero) and
  * applies the boundary conditions at the current time.  The next step does not apply the failure
  * criterion before its force evaluation (the paper applies it after each update, Appendix B). */

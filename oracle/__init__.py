@@ -94,7 +94,7 @@ def lib():
             L.orc_damage.argtypes = [ctypes.c_int64, _d, _i64, _i32, _u8, _d]
             L.orc_run.argtypes = ([ctypes.c_int, ctypes.c_int64, ctypes.c_int, _d, _d, _d, _d, _i64, _i32, _u8, _d]
                                   + [ctypes.c_double] * 6
-                                  + [_u8, _d, _d, _d, _d, _d, ctypes.c_double, ctypes.c_int64,
+                                  + [_u8, _d, _d, _d, _d, _d, ctypes.c_double, _d, _d, _d, ctypes.c_int64,
                                      ctypes.c_int64]
                                   + [_d] * 10 + [_d, _i64])
             L.orc_adr_lambda.argtypes = [ctypes.c_int64, ctypes.c_int, _d, _d, _d, _d, _i64, _i32, _d, _d,
@@ -296,7 +296,10 @@ class OracleSim:
     def nbonds(self) -> int:
         return int(self.col.size)
 
-    def set_bc(self, flag=None, b=None, axis_point=None, axis_dir=None, rate=0.0):
+    def set_bc(self, flag=None, b=None, axis_point=None, axis_dir=None, rate=0.0, vp=None):
+        """vp (dim, n), optional: a prescribed velocity for the prescribed particles (u = t vp,
+        v = vp) in place of the rotation."""
+        self.vp = None if vp is None else np.ascontiguousarray(np.asarray(vp, dtype=np.float64).reshape(self.dim, -1))
         self.flag = None if flag is None else np.ascontiguousarray(flag, dtype=np.uint8)
         self.b = None if b is None else np.ascontiguousarray(b, dtype=np.float64).reshape(self.dim, -1)
         self.axis_point = np.zeros(3) if axis_point is None else np.asarray(axis_point, dtype=np.float64)
@@ -324,11 +327,16 @@ class OracleSim:
         bx = b[0].copy() if b is not None else None
         by = b[1].copy() if b is not None else None
         bz = b[2].copy() if (b is not None and self.dim == 3) else None
+        vp = getattr(self, "vp", None)
+        vpx = vp[0].copy() if vp is not None else None
+        vpy = vp[1].copy() if vp is not None else None
+        vpz = vp[2].copy() if (vp is not None and self.dim == 3) else (np.zeros(self.n) if vp is not None else None)
         lib().orc_run(self.kin, self.n, self.dim, _p(self.x, _d), _p(self.y, _d), _p(zz, _d), _p(self.vol, _d),
                       _p(self.row_ptr, _i64), _p(self.col, _i32), _p(self.status, _u8), _p(self.m, _d),
                       self.A, self.K, self.G, self.rho, self.dt, self.s0, _p(self.flag, _u8),
                       _p(bx, _d), _p(by, _d), _p(bz, _d), _p(self.axis_point, _d),
-                      _p(self.axis_dir, _d), self.rate, self.steps_done, nsteps, _p(ux, _d),
+                      _p(self.axis_dir, _d), self.rate, _p(vpx, _d), _p(vpy, _d), _p(vpz, _d),
+                      self.steps_done, nsteps, _p(ux, _d),
                       _p(uy, _d), _p(uz, _d), _p(vx, _d), _p(vy, _d), _p(vz, _d), _p(self.theta, _d),
                       _p(fx, _d), _p(fy, _d), _p(fz, _d), _p(margins, _d), _p(broken, _i64))
         self.u = np.stack([ux, uy, uz][:self.dim])

@@ -479,15 +479,23 @@ static void bc_value(int dim, const double* x, const double* y, const double* z,
   }
 }
 
+/* vp (may be NULL): a prescribed velocity per particle (3 arrays) that replaces the rotation:
+ * u = t vp_i, v = vp_i (a constant velocity applied to the impacted nodes, as in Section 4.3). */
 static void apply_bc(int64_t n, int dim, const double* x, const double* y, const double* z,
                      const uint8_t* flag, const double c[3], const double a[3], double rate, double t,
-                     double* ux, double* uy, double* uz, double* vx, double* vy, double* vz) {
+                     double* ux, double* uy, double* uz, double* vx, double* vy, double* vz,
+                     const double* const* vp) {
   if (!flag) return;
 #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) {
     if (flag[i] == ORC_FREE) continue;
     double u[3], v[3];
     bc_value(dim, x, y, z, i, flag[i], c, a, rate, t, u, v);
+    if (vp && flag[i] == ORC_PRESCRIBED)
+      for (int k = 0; k < 3; ++k) {
+        v[k] = vp[k] ? vp[k][i] : 0.0;
+        u[k] = t * v[k];
+      }
     ux[i] = u[0];
     uy[i] = u[1];
     vx[i] = v[0];
@@ -517,9 +525,12 @@ void orc_run(int kin, int64_t n, int dim, const double* x, const double* y, cons
              const double* vol, const int64_t* row_ptr, const int32_t* col, uint8_t* status,
              const double* m, double A, double K, double G, double rho, double dt, double s0,
              const uint8_t* flag, const double* bx, const double* by, const double* bz,
-             const double* axis_point, const double* axis_dir, double rate, int64_t step0,
-             int64_t nsteps, double* ux, double* uy, double* uz, double* vx, double* vy, double* vz,
-             double* theta, double* fx, double* fy, double* fz, double* margins, int64_t* broken) {
+             const double* axis_point, const double* axis_dir, double rate, const double* vpx,
+             const double* vpy, const double* vpz, int64_t step0, int64_t nsteps, double* ux,
+             double* uy, double* uz, double* vx, double* vy, double* vz, double* theta, double* fx,
+             double* fy, double* fz, double* margins, int64_t* broken) {
+  const double* vpa[3] = {vpx, vpy, vpz};
+  const double* const* vp = vpx ? vpa : NULL;
   double c[3] = {0, 0, 0}, a[3] = {0, 0, 0};
   if (axis_point)
     for (int k = 0; k < 3; ++k) c[k] = axis_point[k];
@@ -528,7 +539,7 @@ void orc_run(int kin, int64_t n, int dim, const double* x, const double* y, cons
   for (int64_t s = 0; s < nsteps; ++s) {
     int64_t step = step0 + s;
     double tn = (double)step * dt, tn1 = (double)(step + 1) * dt;
-    apply_bc(n, dim, x, y, z, flag, c, a, rate, tn, ux, uy, uz, vx, vy, vz);
+    apply_bc(n, dim, x, y, z, flag, c, a, rate, tn, ux, uy, uz, vx, vy, vz, vp);
     orc_dilatation(kin, n, dim, x, y, z, vol, row_ptr, col, status, m, A, ux, uy, uz, theta);
     orc_force(kin, n, dim, x, y, z, vol, row_ptr, col, status, m, theta, K, G, ux, uy, uz, fx, fy, fz);
 #pragma omp parallel for schedule(static)
@@ -544,7 +555,7 @@ void orc_run(int kin, int64_t n, int dim, const double* x, const double* y, cons
         u[k][i] = u[k][i] + dt * v[k][i];
       }
     }
-    apply_bc(n, dim, x, y, z, flag, c, a, rate, tn1, ux, uy, uz, vx, vy, vz);
+    apply_bc(n, dim, x, y, z, flag, c, a, rate, tn1, ux, uy, uz, vx, vy, vz, vp);
     double mm = 1e300;
     int64_t nb = 0;
     if (s0 > 0.0) nb = orc_failure(kin, n, dim, x, y, z, row_ptr, col, status, s0, ux, uy, uz, &mm);
@@ -636,7 +647,7 @@ void orc_adr_run(int kin, int64_t n, int dim, const double* x, const double* y, 
   for (int64_t s = 0; s < nsteps; ++s) {
     int64_t step = step0 + s;
     double tn = (double)step * dt, tn1 = (double)(step + 1) * dt;
-    apply_bc(n, dim, x, y, z, flag, c, a, rate, tn, ux, uy, uz, vx, vy, vz);
+    apply_bc(n, dim, x, y, z, flag, c, a, rate, tn, ux, uy, uz, vx, vy, vz, NULL);
     /* theta and internal forces with per-particle constants: one call per distinct (A, K, G) would
      * do, but bodies are independent, so the per-particle form below is the same sum. */
     for (int64_t i = 0; i < n; ++i) theta[i] = 0.0;
@@ -698,7 +709,7 @@ void orc_adr_run(int kin, int64_t n, int dim, const double* x, const double* y, 
     }
     for (int k = 0; k < dim; ++k)
       for (int64_t i = 0; i < n; ++i) gp[k][i] = f[k][i];
-    apply_bc(n, dim, x, y, z, flag, c, a, rate, tn1, ux, uy, uz, vx, vy, vz);
+    apply_bc(n, dim, x, y, z, flag, c, a, rate, tn1, ux, uy, uz, vx, vy, vz, NULL);
     double mm = 1e300;
     int64_t nb = 0;
     if (s0 > 0.0) nb = orc_failure(kin, n, dim, x, y, z, row_ptr, col, status, s0, ux, uy, uz, &mm);
@@ -851,7 +862,7 @@ int pdref_step(pdref_ctx* c, int64_t nsteps) {
   const double* zz = c->z ? c->z : c->x;
   orc_run(c->kin, c->n, c->dim, c->x, c->y, zz, c->vol, c->row_ptr, c->col, c->status, c->m, c->A, c->K,
           c->G, c->rho, c->dt, c->s0, c->flag, c->b[0], c->b[1], c->b[2], c->axis_point, c->axis_dir,
-          c->rate, c->steps, nsteps, c->u[0], c->u[1], c->u[2], c->v[0], c->v[1], c->v[2], c->theta,
+          c->rate, NULL, NULL, NULL, c->steps, nsteps, c->u[0], c->u[1], c->u[2], c->v[0], c->v[1], c->v[2], c->theta,
           c->f[0], c->f[1], c->f[2], NULL, NULL);
   c->steps += nsteps;
   return 0;

@@ -40,6 +40,8 @@ class Simulation:
             self.rate = w.rotation_rate(self.s0) if rate is None else float(rate)
             if w.flag is not None or w.b is not None:
                 B.pd_set_bc(self.h, self.dim, self.n, w.flag, w.b, w.axis_point, w.axis_dir, self.rate)
+            if getattr(w, "vp", None) is not None:
+                B.pd_set_prescribed_velocity(self.h, self.dim, self.n, w.vp)
             B.pd_set_state(self.h, self.dim, self.n, w.initial_u(), w.initial_v())
         except Exception:
             B.pd_destroy(self.h)

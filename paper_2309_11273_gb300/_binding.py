@@ -31,7 +31,7 @@ STATUS_NAMES = {0: "PD_OK", -1: "PD_ERR_ARG", -2: "PD_ERR_STATE", -3: "PD_ERR_OO
                 -5: "PD_ERR_NUMERIC", -6: "PD_ERR_TIMEOUT"}
 
 # Every function the header declares (checked against the shared object by the CPU tests).
-EXPORTED = ["pd_critical_stretch", "pd_material_constants", "pd_create_particles", "pd_create_batch", "pd_build_neighbors",
+EXPORTED = ["pd_critical_stretch", "pd_material_constants", "pd_set_prescribed_velocity", "pd_create_particles", "pd_create_batch", "pd_build_neighbors",
             "pd_set_bc", "pd_set_state", "pd_step", "pd_sync", "pd_get_damage", "pd_get_state",
             "pd_num_bonds", "pd_get_neighbors", "pd_get_stats", "pd_check_state", "pd_autotune",
             "pd_set_option", "pd_get_option", "pd_get_profile", "pd_get_info", "pd_step_noalloc",
@@ -84,6 +84,7 @@ def lib(path: str = LIB_PATH):
             L.pd_critical_stretch.argtypes = [ctypes.c_int32] + [ctypes.c_double] * 4
             L.pd_critical_stretch.restype = ctypes.c_double
             L.pd_material_constants.argtypes = [ctypes.c_int32, ctypes.c_double, ctypes.c_double] + [_d] * 3
+            L.pd_set_prescribed_velocity.argtypes = [_vp, _d]
             L.pd_create_particles.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(pd_params), ctypes.c_int64,
                                               _d, _d, _d, _d]
             L.pd_create_batch.argtypes = [ctypes.POINTER(_vp), ctypes.c_int32, ctypes.POINTER(pd_params), _i64,
@@ -201,6 +202,11 @@ def pd_set_bc(h, dim, n, flag=None, b=None, axis_point=None, axis_dir=None, rate
     ap = None if axis_point is None else np.ascontiguousarray(axis_point, dtype=np.float64)
     ad = None if axis_dir is None else np.ascontiguousarray(axis_dir, dtype=np.float64)
     _check(lib().pd_set_bc(h, _ptr(flag, _u8), _ptr(b, _d), _ptr(ap, _d), _ptr(ad, _d), float(rate)))
+
+
+def pd_set_prescribed_velocity(h, dim, n, vp):
+    vp = _soa(vp, dim, n)
+    _check(lib().pd_set_prescribed_velocity(h, _ptr(vp, _d)))
 
 
 def pd_set_state(h, dim, n, u, v=None):

@@ -301,6 +301,25 @@ pd_status pd_set_bc(pd_ctx* c, const uint8_t* flag, const double* b, const doubl
   return PD_OK;
 }
 
+pd_status pd_set_prescribed_velocity(pd_ctx* c, const double* vp) {
+  pd_status st = check_ctx(c, true);
+  if (st != PD_OK) return st;
+  if (!vp || !all_finite(vp, c->dim * c->n)) return fail(PD_ERR_ARG, "vp must be a finite dim * n array");
+  if (!c->has_prescribed) return fail(PD_ERR_STATE, "no particle is prescribed (pd_set_bc flag 2)");
+  drop_graphs(c);
+  // u = rate t g with rate 1 and g = vp (the prescribed particles' rows of gvec)
+  std::vector<double> g(3 * c->n, 0.0);
+  for (int t = 0; t < c->dim; ++t)
+    for (int64_t i = 0; i < c->n; ++i) g[(size_t)t * c->n + i] = vp[(size_t)t * c->n + i];
+  if ((st = upload_field(c, g.data(), c->gvec, 3)) != PD_OK) return st;
+  c->rate = 1.0;
+  if ((st = upload_body_params(c)) != PD_OK) return st;
+  if ((st = apply_bc_now(c)) != PD_OK) return st;
+  if ((st = sync_shadow(c)) != PD_OK) return st;
+  PD_CUDA(cudaStreamSynchronize(c->stream));
+  return PD_OK;
+}
+
 pd_status pd_set_state(pd_ctx* c, const double* u, const double* v) {
   pd_status st = check_ctx(c, true);
   if (st != PD_OK) return st;

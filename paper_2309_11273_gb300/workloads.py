@@ -46,6 +46,7 @@ class Workload:
     twist_in_s0: float = 0.0              # prescribed total rotation angle, in units of s0
     u0: Optional[np.ndarray] = None       # (dim, n)
     v0: Optional[np.ndarray] = None
+    vp: Optional[np.ndarray] = None       # (dim, n) prescribed velocity of the prescribed particles
 
     @property
     def n(self) -> int:
@@ -127,6 +128,34 @@ def cracked_plate(nx: int = 400, ny: int = 160, dx: float = 2.5e-4, ratio: float
     return Workload("cracked_plate_%dx%d" % (nx, ny), MODEL_PLANE_STRESS, dx=dx, delta=ratio * dx,
                     dt=dt, nsteps=nsteps, x=x, y=y, z=None, vol=np.full(n, dx * dx), Gc=Gc,
                     cracks=[crack], b=b, **GLASS)
+
+
+def kalthoff(nx: int = 402, ny: int = 201, dx: float = 5e-4, ratio: float = 3.015, v_imp: float = 22.0,
+             notch_cells: float = 100.125, gap_cells: int = 100, layers: int = 3, Gc: float = 6.9e4,
+             nsteps: int = 5000, dt: float = 2e-8) -> Workload:
+    """Kalthoff-Winkler-like plane-strain impact (Section 4.3's workload in shape; the figure with its
+    geometry is not in the text): steel (E 190 GPa, nu 0.25, rho 7800, G0 6.9e4 J/m^2), delta =
+    3.015 dx (the paper's 3 dx puts lattice points exactly on the horizon, where membership would
+    depend on rounding), nx x ny particles (402 x 201 = 80,802 for the defaults, the paper's node
+    count).  Two edge notches
+    run from outside the left edge to x = notch_cells * dx on the lattice lines y = yc +- gap_cells/2 dx
+    (yc the lattice line nearest the centre; particles sit at cell centres, so no particle lies on a
+    notch); the first `layers` columns between the notches move at the constant velocity v_imp along +x
+    from t = 0 (prescribed velocity); everything else is free.
+    """
+    x, y = grid_2d(nx, ny, dx)
+    n = x.size
+    jc = ny // 2
+    ylo, yhi = (jc - gap_cells // 2) * dx, (jc + gap_cells // 2) * dx
+    cracks = [(-dx, yl, 0.0, notch_cells * dx, yl, 0.0, 0.0, 0.0, 0.0) for yl in (ylo, yhi)]
+    i = np.arange(n) % nx
+    hit = (i < layers) & (y > ylo) & (y < yhi)
+    flag = np.where(hit, PRESCRIBED, FREE).astype(np.uint8)
+    vp = np.zeros((2, n))
+    vp[0, hit] = v_imp
+    return Workload("kalthoff_%dx%d" % (nx, ny), MODEL_PLANE_STRAIN, E=190e9, nu=0.25, rho=7800.0, dx=dx,
+                    delta=ratio * dx, dt=dt, nsteps=nsteps, x=x, y=y, z=None, vol=np.full(n, dx * dx), Gc=Gc,
+                    cracks=cracks, flag=flag, axis_point=np.zeros(3), axis_dir=np.array([0.0, 0.0, 1.0]), vp=vp)
 
 
 def notched_block(nx: int = 200, ny: int = 100, nz: int = 50, dx: float = 1e-3,
