@@ -4,12 +4,15 @@ Workload (one "step" = one explicit time step over every bond: failure check + d
 force + update pass): the 3D notched block of 200 x 100 x 50 particles (dx = 1 mm, delta = 3.015 dx,
 ~1.17e8 directed bonds, E = 30 GPa, nu = 0.2, clamp + twist, bond breaking at s0 from G0 = 50 J/m^2),
 plain FP64 (the paper's precision).  The same line reports the FP32-bond / FP64-integration form on
-the same workload and the batched form (256 uneven plates) as speed-ups over plain FP64.
+the same workload, the batched form (256 uneven plates) as speed-ups over plain FP64, the nonlinear
+bond model, adaptive dynamic relaxation and the paper's matrix scheme on the same GPU.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--no-forms] [--no-cpu]
 
-N > 1 runs under torchrun: every rank runs an independent replica of the workload (the method has no
-exchange step on one body), timed between barriers; the slowest rank's time counts.
+N > 1 runs under torchrun: every rank runs an independent replica of the workload (one body fits one
+GPU, so no data moves between ranks), timed between barriers; the slowest rank's time counts.
+--sweep prints one line per configuration (FP64, mixed and oracle rates); --profile-target builds one
+form of the workload and runs four eager steps (the command the ncu captures profile).
 """
 from __future__ import annotations
 
