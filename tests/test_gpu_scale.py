@@ -32,3 +32,45 @@ def test_config5_full_size_two_steps():
         assert rel(u, ref.u) <= tol and rel(v, ref.v) <= tol, (precision, rel(u, ref.u), rel(v, ref.v))
         if precision == PD_FP64:
             assert rel(th, ref.theta) <= 1e-11
+
+
+def _config5_small_amp():
+    return W.notched_block(nx=400, ny=200, nz=100, dx=5e-4, nsteps=1000, dt=1.895e-7, seed=11, amp=5e-7)
+
+
+def test_config5_full_size_nonlinear_two_steps():
+    """Nonlinear bonds (Eqs 1.10, 1.13) at full size: FP64 against the oracle's kin=NONLINEAR."""
+    from paper_2309_11273_gb300 import PD_NONLINEAR
+    w = _config5_small_amp()
+    s0 = O.critical_stretch(w.model, w.E, w.nu, w.Gc, w.delta)
+    ref = O.OracleSim(w.model, w.E, w.nu, w.rho, w.delta, s0, w.dt, w.x, w.y, w.z, w.vol, w.cracks, kin=O.NONLINEAR)
+    ref.set_bc(w.flag, w.b, w.axis_point, w.axis_dir, w.rotation_rate(s0))
+    ref.set_state(w.initial_u(), w.initial_v())
+    ref.step(2)
+    sim = Simulation(w, s0=s0, kinematics=PD_NONLINEAR)
+    sim.step(2)
+    u, v, _ = sim.state()
+    sim.close()
+    assert rel(u, ref.u) <= 1e-12 and rel(v, ref.v) <= 1e-12
+
+
+def test_config5_full_size_adr_three_iterations():
+    """Adaptive dynamic relaxation at full size (8M particles, one damping reduction over all of
+    them): three iterations against the oracle's from rest under the twist, without bond failure.
+    (A random start is not used: the local stiffness -(g^n - g^{n-1}) / (lambda v) divides by
+    velocity components that are tiny but not zero, so the damping's Rayleigh quotient becomes a
+    sum of huge terms of both signs whose rounding two correct evaluations do not share.)"""
+    from paper_2309_11273_gb300 import _binding as B
+    w = W.notched_block(nx=400, ny=200, nz=100, dx=5e-4, nsteps=1000, dt=1.895e-7)
+    s0 = 0.0
+    rate = w.rotation_rate(9.5292e-4)
+    ref = O.OracleSim(w.model, w.E, w.nu, w.rho, w.delta, s0, w.dt, w.x, w.y, w.z, w.vol, w.cracks)
+    ref.set_bc(w.flag, w.b, w.axis_point, w.axis_dir, rate)
+    ref.set_state(w.initial_u(), w.initial_v())
+    ref.adr_step(3)
+    sim = Simulation(w, s0=s0, rate=rate)
+    sim.set_option(B.PD_OPT_SOLVER, B.PD_SOLVER_ADR)
+    sim.step(3)
+    u, v, _ = sim.state()
+    sim.close()
+    assert rel(u, ref.u) <= 1e-12 and np.linalg.norm(v - ref.v) <= 1e-12 * np.linalg.norm(ref.u)
