@@ -156,8 +156,9 @@ typedef enum {
  *   iteration after selecting the solver or pd_set_state starts from rest (v^{1/2} = g / (2 lambda)).
  *   pd_params.dt then only advances the boundary-condition clock (t_n = n dt), so a prescribed
  *   rotation grows by rate * dt per iteration (load stepping); a particle without bonds is held in
- *   place.  Bond failure is checked after every iteration as in the explicit solver.  PD_FP64 and
- *   single-body contexts only (PD_ERR_ARG otherwise).  With PD_OPT_PROFILE, the reduction and update
+ *   place.  Bond failure is checked after every iteration as in the explicit solver.  With PD_MIXED
+ *   the forces come from the FP32 bond arithmetic and the relaxation runs in FP64.  Single-body
+ *   contexts only (PD_ERR_ARG otherwise).  With PD_OPT_PROFILE, the reduction and update
  *   kernels of an iteration are counted with PD_K_PASS2. */
 typedef enum { PD_SOLVER_EXPLICIT = 0, PD_SOLVER_ADR = 1 } pd_solver;
 

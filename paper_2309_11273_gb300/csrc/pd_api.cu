@@ -512,7 +512,6 @@ pd_status pd_set_option(pd_ctx* c, int32_t option, int64_t value) {
       break;
     case PD_OPT_SOLVER:
       if (value != PD_SOLVER_EXPLICIT && value != PD_SOLVER_ADR) return fail(PD_ERR_ARG, "unknown solver");
-      if (value == PD_SOLVER_ADR && c->precision != PD_FP64) return fail(PD_ERR_ARG, "PD_SOLVER_ADR runs in PD_FP64 only");
       if (value == PD_SOLVER_ADR && c->nbodies > 1)
         return fail(PD_ERR_ARG, "PD_SOLVER_ADR needs a single-body context (its damping is one Rayleigh quotient)");
       c->solver = (int)value;

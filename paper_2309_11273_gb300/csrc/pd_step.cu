@@ -1327,7 +1327,8 @@ __global__ void __launch_bounds__(kAdrBlock) k_adr_update(StepArgs a, const doub
                                                            double4* __restrict__ disp_out,
                                                            double4* __restrict__ gold,
                                                            const double* __restrict__ lam,
-                                                           const double2* __restrict__ st) {
+                                                           const double2* __restrict__ st,
+                                                           float4* __restrict__ u32_out) {
   const int64_t i = blockIdx.x * (int64_t)kAdrBlock + threadIdx.x;
   if (i >= a.n_pad) return;
   const int b = a.body ? a.body[i] : 0;
@@ -1365,6 +1366,10 @@ __global__ void __launch_bounds__(kAdrBlock) k_adr_update(StepArgs a, const doub
   disp_out[i] = u;
   a.vel[i] = v;
   gold[i] = g;
+  if (u32_out) {  // mixed form: the FP32 shadow of the new state
+    const double sc = a.uscale;
+    u32_out[i] = make_float4((float)(u.x * sc), (float)(u.y * sc), (float)(u.z * sc), 0.0f);
+  }
 }
 
 
@@ -1888,7 +1893,8 @@ pd_status launch_step(pd_ctx* c, bool check) {
     k_adr_sums<<<nblk, kAdrBlock, 0, c->stream>>>(a, c->disp[c->cur], c->gold, c->lam, c->adr_part);
     k_adr_coef<<<1, 1024, 0, c->stream>>>(c->adr_part, (int)nblk, c->adr_first, c->adr_st);
     k_adr_update<<<nblk, kAdrBlock, 0, c->stream>>>(a, c->disp[c->cur], c->disp[c->cur ^ 1], c->gold, c->lam,
-                                                    c->adr_st);
+                                                    c->adr_st,
+                                                    c->precision == PD_MIXED ? c->u32[c->cur ^ 1] : nullptr);
   }
   if (prof) {
     cudaEventRecord(e2, c->stream);

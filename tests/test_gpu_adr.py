@@ -131,8 +131,32 @@ def test_adr_restart_autotune_and_arguments():
     assert np.array_equal(b.state()[0], c.state()[0])
     for s in (a, b, c):
         s.close()
-    m = Simulation(w, s0=0.0, precision=PD_MIXED)
+    bw = W.plate_batch(nplates=2, seed=4, side_lo=10, side_hi=20, nsteps=10)
+    from paper_2309_11273_gb300 import BatchSimulation
+    m = BatchSimulation(bw)
     with pytest.raises(B.PDError) as e:
         m.set_option(B.PD_OPT_SOLVER, B.PD_SOLVER_ADR)
     assert e.value.status == B.PD_ERR_ARG
     m.close()
+
+
+def test_mixed_adr_converges_to_the_direct_solution():
+    """ADR over the FP32 bond arithmetic (FP64 relaxation): the clamped plate reaches the direct dense
+    solve to 1e-5 (the FP32 force accuracy), in 3000 iterations like the FP64 form."""
+    w = _clamped_plate(2, (12, 8))
+    ref = O.OracleSim(w.model, w.E, w.nu, w.rho, w.delta, 0.0, 1.0, w.x, w.y, None, w.vol)
+    n = w.n
+    S = np.zeros((2 * n, 2 * n))
+    for k in range(n):
+        for c in range(2):
+            u = np.zeros((2, n)); u[c, k] = 1.0
+            S[:, c * n + k] = -(ref.internal_force(u)[1] / w.vol).reshape(-1)
+    free = np.tile(w.flag == 0, 2)
+    ud = np.zeros(2 * n)
+    ud[free] = np.linalg.solve(S[np.ix_(free, free)], w.b.reshape(-1)[free])
+    sim = Simulation(w, s0=0.0, precision=PD_MIXED)
+    sim.set_option(B.PD_OPT_SOLVER, B.PD_SOLVER_ADR)
+    sim.step(3000)
+    u = sim.state()[0]
+    sim.close()
+    assert rel(u.reshape(-1), ud) <= 1e-5
