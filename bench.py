@@ -531,7 +531,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--profile-target", choices=["fp64", "mixed", "nonlinear"], default=None,
+    ap.add_argument("--profile-target", choices=["fp64", "mixed", "nonlinear", "mixed-nonlinear"], default=None,
                     help="only build the workload and run 4 eager steps (the command profiled by ncu)")
     ap.add_argument("--sweep", action="store_true",
                     help="one JSON line per configuration (1-5): FP64 and mixed GPU rates and the oracle's "
@@ -613,8 +613,8 @@ def profile_target(form):
     from paper_2309_11273_gb300 import workloads as W
     w = W.config3()
     s0 = pd_critical_stretch(w.model, w.E, w.nu, w.Gc, w.delta)
-    sim = Simulation(w, s0=s0, precision=PD_MIXED if form == "mixed" else PD_FP64, graph_chunk=0,
-                     kinematics=PD_NONLINEAR if form == "nonlinear" else PD_LINEARIZED)
+    sim = Simulation(w, s0=s0, precision=PD_MIXED if form.startswith("mixed") else PD_FP64, graph_chunk=0,
+                     kinematics=PD_NONLINEAR if form.endswith("nonlinear") else PD_LINEARIZED)
     sim.step(4)
     sim.sync()
     print(json.dumps({"profile_target": form, "stats": sim.stats()}))
