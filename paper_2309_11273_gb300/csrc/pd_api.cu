@@ -55,6 +55,8 @@ void free_build(pd_ctx* c) {
   c->bA = nullptr;
   c->bB = nullptr;
   c->bd = nullptr;
+  c->bS = nullptr;
+  c->bs_stale = true;
   c->bE = nullptr;
   c->lam = nullptr;
   c->gnew = c->gold = nullptr;
@@ -640,6 +642,7 @@ pd_status pd_autotune(pd_ctx* c, int32_t trial_steps, int32_t* block_out, int32_
       // an ADR run in progress continues from the restored v and g_prev; one that had not started
       // (or whose arrays were allocated by the trials) starts from rest
       c->adr_restart = adr_restart0 || !gold0;
+      c->bs_stale = true;  // the restored status bits
       c->steps = steps0;
       c->skip_next_check = skip0;
       c->check_pending = pend0;

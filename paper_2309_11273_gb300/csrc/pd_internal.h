@@ -79,8 +79,9 @@ struct StepArgs {
   int validate;            // mixed: also decide every bond in FP64 and count mismatches
   int check;               // apply the failure criterion at the head of pass 1
   const double4* bA;       // tabled FP64 path: per slot (xi, s0 |xi|^2), or nullptr
-  const double4* bB;       // tabled FP64 path: per slot (V_j xi, 1 / |xi|^2)
+  const double4* bB;       // tabled FP64 path: per slot (V_j xi, G (1/m_i + 1/m_j) / |xi|^2)
   double* bd;              // tabled FP64 path: per slot xi.(u_j - u_i), written by pass 1
+  double4* bS;             // tabled FP64 path: per particle sum of V_j xi over the intact slots
   double2* bE;             // tabled nonlinear path: per slot (e, 1 / |Y|), written by pass 1 (bA = (xi, |xi|))
   int expire;              // testing (PD_OPT_EXPIRE_WAITS): staged kernels skip their first copy
   double uscale;           // mixed path: the FP32 shadow holds u * uscale (1, or 1/Q for nonlinear bonds)
@@ -143,8 +144,10 @@ struct pd_ctx {
   float* theta32 = nullptr;
   unsigned long long* counters = nullptr;
   double4* bA = nullptr;          // FP64 per-slot table (xi, s0 |xi|^2)
-  double4* bB = nullptr;          // FP64 per-slot table (V_j xi, 1/|xi|^2)
+  double4* bB = nullptr;          // FP64 per-slot table (V_j xi, G (1/m_i + 1/m_j) / |xi|^2)
   double* bd = nullptr;           // FP64 per-slot xi.du of the current step
+  double4* bS = nullptr;          // FP64 per-particle sum of V_j xi over the intact slots
+  bool bs_stale = true;           // bS no longer matches the status bits (recomputed before a step)
   double2* bE = nullptr;          // nonlinear FP64: per-slot (e, 1/|Y|) of the current step
   int bond_cache = 1;             // use the table in the FP64 path
   int stage = 1;                  // mixed path: TMA-staged index streams (split 1)

@@ -557,17 +557,48 @@ __global__ void k_bond_tables_nl(StepArgs a, double4* __restrict__ bA) {
 
 // Tabled FP64 kernels.  GB300 issues FP64 at 1/64 of the FP32 rate, so everything that does not
 // depend on the displacement is computed once per family into per-slot tables:
-//   bA = (xi, s0 |xi|^2)            read by pass 1 (the break test xi.du >= s0 |xi|^2, Eq 1.30);
-//   bB = (V_j xi, 1 / |xi|^2)       read by pass 2;
-// and pass 1 stores each slot's xi.du (the per-bond extension times |xi|, the paper's E array of
-// Appendix B) in bd for pass 2, which then needs neither u_j nor a divide: per bond it issues
-// 7 FP64 instructions instead of 14, and pass 1 8 instead of 15.
+//   bA = (xi, s0 |xi|^2)                       read by pass 1 (the break test xi.du >= s0 |xi|^2, Eq 1.30);
+//   bB = (V_j xi, G (1/m_i + 1/m_j) / |xi|^2)  read by pass 2 (m is fixed once the family is built);
+// pass 1 stores each slot's xi.du (the per-bond extension times |xi|, the paper's E array of
+// Appendix B) in bd for pass 2, which then needs neither u_j nor a divide.  The i-end dilatation term
+// of Eq 2.2 is the same for every bond of particle i, so pass 2 multiplies it once by
+//   bS_i = sum of V_j xi over the intact slots of i
+// instead of adding it to every bond's coefficient; bS changes only when a bond breaks, and the pass
+// that breaks it recomputes bS for that slice.  Per bond pass 1 issues 7 FP64 instructions (the
+// difference, the dot product and the theta sum) and pass 2 4 (the bond coefficient and the force),
+// against 15 and 14 when everything is recomputed.  The break test compares the two doubles' bit
+// patterns as signed integers: for a positive threshold s0 |xi|^2 that order equals the FP64 order of
+// xi.du (negative values and -0 sort below every positive double), and it runs on the integer pipe
+// instead of the FP64 one.
+
+// bS_i from the status bits and bB, in slot order (so bS is a function of the bits alone).  The
+// words are read through L2: other warps of the block may have just written them.
+__device__ __forceinline__ void bond_sum_row(const StepArgs& a, const SliceIdx& t) {
+  const uint32_t* bw = a.bits + (t.base >> 5);
+  const double4* tb = a.bB + t.base + t.lane;
+  double sx = 0.0, sy = 0.0, sz = 0.0;
+  for (int k = 0; k < t.W; ++k) {
+    if ((__ldcg(bw + k) >> t.lane) & 1u) {
+      const double4 g = tb[(int64_t)k << 5];
+      sx += g.x;
+      sy += g.y;
+      sz += g.z;
+    }
+  }
+  a.bS[t.i] = make_double4(sx, sy, sz, 0.0);
+}
+
+__global__ void k_bond_sums(StepArgs a) {
+  const SliceIdx t = slice_index<1>(a.n_pad, a.slice_ptr);
+  if (t.active) bond_sum_row(a, t);
+}
+
 template <int DIM, int SPLIT>
 __global__ void __launch_bounds__(512) k_pass1_f64t(StepArgs a, const double4* __restrict__ disp,
                                                      int write_theta) {
   const SliceIdx t = slice_index<SPLIT>(a.n_pad, a.slice_ptr);
   if (write_theta && blockIdx.x == 0 && threadIdx.x == 0) *a.d_step += 1;
-  double acc[1] = {0.0};
+  double acc[2] = {0.0, 0.0};  // theta sum, and 1 if a bond of this warp's slots broke (warp-uniform)
   int b = 0;
   if (t.active) {
     b = a.body ? a.body[t.i] : 0;
@@ -600,23 +631,29 @@ __global__ void __launch_bounds__(512) k_pass1_f64t(StepArgs a, const double4* _
         if (k < t.W) td[(int64_t)k << 5] = d;
         bool intact = (wd[u] >> t.lane) & 1u;
         if (a.check) {
-          const bool brk = intact && can_break && d >= g[u].w;
+          const bool ge = __double_as_longlong(d) >= __double_as_longlong(g[u].w);  // d >= s0 |xi|^2
+          const bool brk = intact && can_break && ge;
           const unsigned m = __ballot_sync(kFull, brk);
           if (m) {
             intact = intact && !brk;
             if (t.lane == 0) bw[k] = wd[u] & ~m;
+            acc[1] = 1.0;
           }
         }
         acc[0] = fma(intact ? uj[u].w : 0.0, d, acc[0]);
       }
     }
   }
-  split_reduce<SPLIT, 1>(acc);
-  if (t.active && t.sub == 0 && write_theta) {
-    const double th = a.aA[t.i] * acc[0];
-    const double mu = a.mu[t.i];
-    a.theta[t.i] = th;
-    a.thm[t.i] = make_double2(a.bp[b].Kp * (th * mu), a.bp[b].G * mu);
+  if (SPLIT == 1) __syncwarp();  // lane 0's status words, for the bS recomputation below
+  split_reduce<SPLIT, 2>(acc);   // (SPLIT > 1: its block barrier orders the other warps' words)
+  if (t.active && t.sub == 0) {
+    if (write_theta) {
+      const double th = a.aA[t.i] * acc[0];
+      const double mu = a.mu[t.i];
+      a.theta[t.i] = th;
+      a.thm[t.i] = make_double2(a.bp[b].Kp * (th * mu), a.bp[b].G * mu);
+    }
+    if (acc[1] != 0.0) bond_sum_row(a, t);
   }
 }
 
@@ -628,7 +665,6 @@ __global__ void __launch_bounds__(512) k_pass2_f64t(StepArgs a, const double4* _
   int b = 0;
   if (t.active) {
     b = a.body ? a.body[t.i] : 0;
-    const double2 ti = a.thm[t.i];
     const uint32_t* __restrict__ bw = a.bits + (t.base >> 5);
     const int32_t* __restrict__ cl = a.col + t.base + t.lane;
     const double4* __restrict__ tb = a.bB + t.base + t.lane;
@@ -640,21 +676,22 @@ __global__ void __launch_bounds__(512) k_pass2_f64t(StepArgs a, const double4* _
     for (int k0 = t.sub; k0 < t.W; k0 += U * SPLIT) {
       uint32_t wd[U];
       double4 g[U];
-      double d[U];
-      double2 tj[U];
+      double d[U], tj[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int k = min(k0 + u * SPLIT, t.W - 1);
         wd[u] = wn[u];
         g[u] = tb[(int64_t)k << 5];
         d[u] = td[(int64_t)k << 5];
-        tj[u] = a.thm[jn[u]];
+        tj[u] = a.thm[jn[u]].x;
       }
       load_slots<U, SPLIT>(t, cl, bw, k0 + U * SPLIT, jn, wn);
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        // Eq 2.2 with V_j folded into the tabled xi: [(K - G/3) theta~ + G e~ / |xi|] (V_j xi)
-        double c = fma(ti.y + tj[u].y, d[u] * g[u].w, ti.x + tj[u].x);
+        // Eq 2.2 with V_j folded into the tabled xi, G (1/m_i + 1/m_j) / |xi|^2 tabled and the
+        // i-end term (K - G/3) theta_i / m_i applied to bS_i below:
+        // [(K - G/3) theta_j / m_j + G (1/m_i + 1/m_j) e / |xi|] (V_j xi)
+        double c = fma(g[u].w, d[u], tj[u]);
         c = ((wd[u] >> t.lane) & 1u) ? c : 0.0;
         f[0] = fma(c, g[u].x, f[0]);
         f[1] = fma(c, g[u].y, f[1]);
@@ -664,6 +701,11 @@ __global__ void __launch_bounds__(512) k_pass2_f64t(StepArgs a, const double4* _
   }
   split_reduce<SPLIT, 3>(f);
   if (t.active && t.sub == 0) {
+    const double ti = a.thm[t.i].x;
+    const double4 S = a.bS[t.i];
+    f[0] = fma(ti, S.x, f[0]);
+    f[1] = fma(ti, S.y, f[1]);
+    f[2] = fma(ti, S.z, f[2]);
     double4 u;
     update(a, t.i, b, f, disp, disp_out, u);
   }
@@ -676,8 +718,9 @@ __global__ void k_bond_tables(StepArgs a, double4* __restrict__ bA, double4* __r
   const SliceIdx t = slice_index<1>(a.n_pad, a.slice_ptr);
   if (!t.active) return;
   const int b = a.body ? a.body[t.i] : 0;
-  const double s0 = a.bp[b].s0;
+  const double s0 = a.bp[b].s0, G = a.bp[b].G;
   const double4 pi = a.pos[t.i];
+  const double mi = a.mu[t.i];
   const double4 zero = make_double4(0.0, 0.0, 0.0, 0.0);
   for (int k = 0; k < t.W; ++k) {
     const int64_t e = t.base + t.lane + ((int64_t)k << 5);
@@ -686,7 +729,7 @@ __global__ void k_bond_tables(StepArgs a, double4* __restrict__ bA, double4* __r
     double ex, ey, ez, d, q;
     bond_f64<DIM>(pi, pj, zero, zero, ex, ey, ez, d, q);
     bA[e] = make_double4(ex, ey, ez, s0 * q);
-    bB[e] = make_double4(pj.w * ex, pj.w * ey, pj.w * ez, q > 0.0 ? 1.0 / q : 0.0);
+    bB[e] = make_double4(pj.w * ex, pj.w * ey, pj.w * ez, q > 0.0 ? G * (mi + a.mu[j]) / q : 0.0);
   }
 }
 
@@ -1638,6 +1681,7 @@ StepArgs make_args(pd_ctx* c) {
   a.bA = c->bond_cache ? c->bA : nullptr;
   a.bB = c->bond_cache ? c->bB : nullptr;
   a.bd = c->bond_cache ? c->bd : nullptr;
+  a.bS = c->bond_cache ? c->bS : nullptr;
   a.bE = c->bond_cache ? c->bE : nullptr;
   a.expire = c->expire_waits;
   a.uscale = c->kin == PD_NONLINEAR ? 1.0 / c->q : 1.0;
@@ -1754,17 +1798,19 @@ pd_status init_disp_w(pd_ctx* c) {
   return PD_OK;
 }
 
-// Allocates and fills the per-slot tables of the tabled FP64 path (once per build).
+// Allocates and fills the per-slot tables of the tabled FP64 path (once per build), and brings the
+// per-particle intact sums up to date with the status bits.
 pd_status ensure_bond_cache(pd_ctx* c) {
-  if (!c->bond_cache || c->precision != PD_FP64 || c->bA) return PD_OK;
+  if (!c->bond_cache || c->precision != PD_FP64) return PD_OK;
   pd_status st;
   const size_t ne = (size_t)std::max<int64_t>(c->nentries, 32);
+  const int tb = 256;
+  const unsigned grid = (unsigned)((c->n_pad + tb - 1) / tb);
   if (c->kin == PD_NONLINEAR) {
+    if (c->bA) return PD_OK;
     if ((st = alloc(c, &c->bA, ne)) != PD_OK) return st;
     if ((st = alloc(c, &c->bE, ne)) != PD_OK) return st;
     StepArgs a = make_args(c);
-    const int tb = 256;
-    const unsigned grid = (unsigned)((c->n_pad + tb - 1) / tb);
     if (c->dim == 3)
       k_bond_tables_nl<3><<<grid, tb, 0, c->stream>>>(a, c->bA);
     else
@@ -1772,17 +1818,24 @@ pd_status ensure_bond_cache(pd_ctx* c) {
     PD_CUDA(cudaGetLastError());
     return PD_OK;
   }
-  if ((st = alloc(c, &c->bA, ne)) != PD_OK) return st;
-  if ((st = alloc(c, &c->bB, ne)) != PD_OK) return st;
-  if ((st = alloc(c, &c->bd, ne)) != PD_OK) return st;
-  StepArgs a = make_args(c);
-  const int tb = 256;
-  const unsigned grid = (unsigned)((c->n_pad + tb - 1) / tb);
-  if (c->dim == 3)
-    k_bond_tables<3><<<grid, tb, 0, c->stream>>>(a, c->bA, c->bB);
-  else
-    k_bond_tables<2><<<grid, tb, 0, c->stream>>>(a, c->bA, c->bB);
-  PD_CUDA(cudaGetLastError());
+  if (!c->bA) {
+    if ((st = alloc(c, &c->bA, ne)) != PD_OK) return st;
+    if ((st = alloc(c, &c->bB, ne)) != PD_OK) return st;
+    if ((st = alloc(c, &c->bd, ne)) != PD_OK) return st;
+    if ((st = alloc(c, &c->bS, (size_t)c->n_pad)) != PD_OK) return st;
+    StepArgs a = make_args(c);
+    if (c->dim == 3)
+      k_bond_tables<3><<<grid, tb, 0, c->stream>>>(a, c->bA, c->bB);
+    else
+      k_bond_tables<2><<<grid, tb, 0, c->stream>>>(a, c->bA, c->bB);
+    PD_CUDA(cudaGetLastError());
+    c->bs_stale = true;
+  }
+  if (c->bs_stale) {
+    k_bond_sums<<<grid, tb, 0, c->stream>>>(make_args(c));
+    PD_CUDA(cudaGetLastError());
+    c->bs_stale = false;
+  }
   return PD_OK;
 }
 
@@ -2042,6 +2095,7 @@ pd_status run_steps(pd_ctx* c, int64_t nsteps) {
   if (nsteps <= 0) return PD_OK;
   pd_status st = ensure_bond_cache(c);
   if (st != PD_OK) return st;
+  if (c->precision == PD_FP64 && !c->bond_cache) c->bs_stale = true;  // untabled kernels break bonds
   if ((st = ensure_adr(c)) != PD_OK) return st;
   st = launch_set_step(c, c->steps - 1);
   if (st != PD_OK) return st;

@@ -239,6 +239,36 @@ def test_orderings_and_bond_cache_agree(precision):
         assert rel(u, ref) <= tol, (k, rel(u, ref))
 
 
+def test_intact_sums_follow_the_status_bits():
+    """The tabled FP64 force pass applies the i-end dilatation term of Eq 2.2 to a per-particle sum
+    of V_j xi over the intact bonds, so that sum has to follow every change of the status bits: bonds
+    broken by the tabled kernels, bonds broken while the table is switched off (untabled kernels), and
+    bits restored by an autotune whose trial steps broke bonds.  Through all three the run equals the
+    oracle (the cracked plate breaks bonds from step 40 to 180)."""
+    w = W.cracked_plate(nx=60, ny=24, dx=2.5e-4, crack_cells=30.125, sigma=2e6, nsteps=400)
+    s0 = s0_of(w)
+    sim = Simulation(w, s0=s0)
+    ref = oracle_for(w, s0)
+    exact = True
+    for k, action in ((50, None), (40, "autotune"), (40, "untabled"), (270, "tabled")):
+        if action == "autotune":
+            B.pd_autotune(sim.h, 10)  # each trial advances 11 steps (breaking bonds), then restores
+        elif action == "untabled":
+            sim.set_option(B.PD_OPT_BOND_CACHE, 0)
+        elif action == "tabled":
+            sim.set_option(B.PD_OPT_BOND_CACHE, 1)
+        margins, _ = ref.step(k)
+        sim.step(k)
+        exact = exact and (not margins.size or margins.min() > 1e-9)
+    u, v, th = sim.state()
+    _, _, intact = sim.neighbors()
+    phi = sim.damage()
+    sim.close()
+    assert exact and (ref.status == 0).sum() > 1000
+    assert rel(u, ref.u) <= TOL and rel(v, ref.v) <= TOL
+    assert np.array_equal(intact, ref.status) and np.array_equal(phi, ref.damage())
+
+
 # --------------------------------------------------------------------------------- edge cases
 def test_single_particle_and_ragged_sizes():
     for nx, ny in ((1, 1), (33, 1), (7, 5)):
