@@ -40,12 +40,13 @@ WORKLOAD = "3D linearized OSB-PD notched block 200x100x50 (1M particles), dx=1 m
 # neighbour index per pass, status bit read each pass and written in pass 1; per particle the
 # coordinates, displacements, velocities, theta, 1/m, flag and row pointer of the model.  FLOPs
 # (FMA = 2): FLOPS_BOND is the sqrt-free form that recomputes the bond geometry every step;
-# FLOPS_BOND_TABLED the per-step part of the tabled FP64 form, whose geometry terms (xi, |xi|^2,
-# 1/|xi|^2, V_j xi, s0 |xi|^2) are computed once per family.
+# FLOPS_BOND_TABLED the per-step part of the tabled FP64 form, whose geometry terms (xi, V_j xi,
+# s0 |xi|^2, G (1/m_i + 1/m_j) / |xi|^2) are computed once per family and whose i-end dilatation
+# term is applied once per particle (pass 2: the bond coefficient and the force, 4 FMAs).
 BYTES_BOND = {1: 4.25, 2: 4.125}
 BYTES_PART = {1: 68.0, 2: 141.0}
 FLOPS_BOND = {1: 19.0, 2: 28.0}
-FLOPS_BOND_TABLED = {1: 10.0, 2: 11.0}
+FLOPS_BOND_TABLED = {1: 10.0, 2: 8.0}
 # Geometrically nonlinear bonds (Eqs 1.10, 1.13), FP64, square root and divide counted as one flop
 # each: pass 1 forms xi, eta, Y, |Y|^2 - |xi|^2, |xi|^2, |Y|^2, two roots, e and the theta term and
 # the break test; pass 2 the same geometry, the Eq 1.14 coefficient and the force along Y / |Y|.
@@ -84,9 +85,11 @@ def kernel_source_sha(kernel):
     return hashlib.sha256(src[m.start():end].encode()).hexdigest()[:16]
 
 
-def recorded_traffic(kernel):
+def recorded_traffic(kernel, nbonds=None):
     """DRAM bytes per launch recorded from an ncu capture (profiles/ncu_traffic.txt), or None when
-    the kernel source changed since the capture."""
+    the kernel source changed since the capture.  A capture taken on a smaller case of the same
+    geometry records its directed bonds (bonds=); its bytes are scaled to nbonds, as the per-slot
+    streams and the per-particle state both grow in proportion."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     try:
         lines = open(path).read().splitlines()
@@ -96,8 +99,26 @@ def recorded_traffic(kernel):
     for ln in lines:
         kv = dict(p.split("=", 1) for p in ln.split() if "=" in p)
         if kv.get("kernel") == kernel and kv.get("source_sha") == sha and "dram_bytes_per_launch" in kv:
-            return float(kv["dram_bytes_per_launch"])
+            t = float(kv["dram_bytes_per_launch"])
+            if "bonds" in kv and nbonds:
+                t *= nbonds / float(kv["bonds"])
+            return t
     return None
+
+
+def table_stream(tabled, kp, prof, nb, hbm):
+    """DRAM rate of the other FP64 pass from its recorded ncu traffic: the tabled pass 2 streams its
+    per-slot tables (V_j xi and the bond coefficient, 32 B; xi.du, 8 B; the index, 4 B), so it is
+    bound by HBM rather than by the FP64 pipe."""
+    kname = "k_pass%d_f64%s" % (kp, "t" if tabled else "")
+    ms = prof["pass%d_ms" % kp]
+    t = recorded_traffic(kname, nb)
+    out = {"kernel": kname, "ms": ms, "traffic": t}
+    if t is not None:
+        out.update({"dram_gbs": t / (ms * 1e-3) / 1e9, "dram_frac": t / (ms * 1e-3) / 1e9 / hbm,
+                    "note": "measured DRAM bytes (ncu) / CUDA-event time, of measured HBM peak; the bytes "
+                            "are the per-slot tables, not the model's algorithmic bytes"})
+    return out
 
 
 class ClockSampler:
@@ -316,12 +337,13 @@ def run_gpu(args):
     achieved = fl * nb / (kms * 1e-3) / 1e12
     kname = "k_pass%d_f64%s" % (kp, "t" if tabled else "")
     roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": recorded_traffic(kname),
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": recorded_traffic(kname, nb),
                 "peak_note": "FP64 peak from unit counts and clock: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz",
                 "algorithmic": "%g FP64 flop per directed bond (per-step part of the %s form) x %d bonds per launch"
                                % (fl, "tabled" if tabled else "recompute", nb),
                 "frac_recompute_model": FLOPS_BOND[kp] * nb / (kms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
                 "pass1_ms": prof["pass1_ms"], "pass2_ms": prof["pass2_ms"],
+                "other_pass": table_stream(tabled, 3 - kp, prof, nb, hbm),
                 "model_bytes_frac_of_hbm": (sum(BYTES_BOND.values()) * nb + sum(BYTES_PART.values()) * w.n)
                 / ((prof["pass1_ms"] + prof["pass2_ms"]) * 1e-3) / (hbm * 1e9)}
 
@@ -479,7 +501,7 @@ def run_forms(args, stream, dev, world, fp64_value, nb, hbm, hbm_note):
                         "vs_linearized_fp64": nval / fp64_value, "mapping": {"block": nmap[0], "split": nmap[1]},
                         "roofline": {"bound": "alu", "kernel": nkern, "achieved": ach,
                                      "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
-                                     "traffic": recorded_traffic(nkern),
+                                     "traffic": recorded_traffic(nkern, nb),
                                      "algorithmic": "%g FP64 flop per directed bond (%s form; root, divide = 1) x %d"
                                                     " bonds" % (nfl, "tabled" if ntab else "recompute", nb),
                                      "pass1_ms": prof["pass1_ms"], "pass2_ms": prof["pass2_ms"]}}
@@ -533,6 +555,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--profile-target", choices=["fp64", "mixed", "nonlinear", "mixed-nonlinear"], default=None,
                     help="only build the workload and run 4 eager steps (the command profiled by ncu)")
+    ap.add_argument("--profile-quarter", action="store_true",
+                    help="with --profile-target: configuration 3's geometry at a quarter of its particles "
+                         "(100x50x50, same dx and horizon), so that multi-pass ncu captures of the tabled "
+                         "FP64 kernels hold a few GB")
     ap.add_argument("--sweep", action="store_true",
                     help="one JSON line per configuration (1-5): FP64 and mixed GPU rates and the oracle's "
                          "rate on all host cores and on one (the per-configuration table of the baseline)")
@@ -544,7 +570,7 @@ def main():
     import __graft_entry__
     __graft_entry__.build()
     if args.profile_target:
-        return profile_target(args.profile_target)
+        return profile_target(args.profile_target, args.profile_quarter)
     if args.sweep:
         return run_sweep(args)
     return run_gpu(args)
@@ -607,17 +633,17 @@ def run_sweep(args):
     return 0
 
 
-def profile_target(form):
+def profile_target(form, quarter=False):
     """Workload of the benchmark in one precision, 4 eager time steps (ncu captures this command)."""
     from paper_2309_11273_gb300 import PD_FP64, PD_LINEARIZED, PD_MIXED, PD_NONLINEAR, Simulation, pd_critical_stretch
     from paper_2309_11273_gb300 import workloads as W
-    w = W.config3()
+    w = W.notched_block(nx=100, ny=50, nz=50) if quarter else W.config3()
     s0 = pd_critical_stretch(w.model, w.E, w.nu, w.Gc, w.delta)
     sim = Simulation(w, s0=s0, precision=PD_MIXED if form.startswith("mixed") else PD_FP64, graph_chunk=0,
                      kinematics=PD_NONLINEAR if form.endswith("nonlinear") else PD_LINEARIZED)
     sim.step(4)
     sim.sync()
-    print(json.dumps({"profile_target": form, "stats": sim.stats()}))
+    print(json.dumps({"profile_target": form, "particles": w.n, "directed_bonds": sim.nbonds, "stats": sim.stats()}))
     sim.close()
     return 0
 
