@@ -130,10 +130,12 @@ typedef enum {
   PD_OPT_VALIDATE = 3,     /* PD_MIXED: 1 = also decide every bond in FP64 and count mismatches */
   PD_OPT_BLOCK = 4,        /* threads per block of the step kernels (multiple of 32, <= 512) */
   PD_OPT_SPLIT = 5,        /* warps cooperating on one 32-particle slice: 1, 2 or 4 */
-  PD_OPT_BOND_CACHE = 6,   /* PD_FP64: 1 (default) = keep a per-bond table of the reference
-                              geometry (xi, 1/|xi|^2, s0 |xi|^2; 40 bytes per bond slot) so each
-                              step evaluates only displacement-dependent FP64 terms; 0 = recompute
-                              the geometry from the coordinates every step */
+  PD_OPT_BOND_CACHE = 6,   /* PD_FP64: 1 (default) = keep per-bond tables of the reference
+                              geometry and bond coefficients (xi, s0 |xi|^2, V_j xi,
+                              G (1/m_i + 1/m_j) / |xi|^2, and the step's xi.(u_j - u_i); 72 bytes per
+                              bond slot, plus a per-particle sum of V_j xi over the intact bonds) so
+                              each step evaluates only displacement-dependent FP64 terms; 0 =
+                              recompute the geometry from the coordinates every step */
   PD_OPT_STAGE = 7,        /* PD_MIXED with split 1: 1 (default) = stream each warp's neighbour
                               indices and status words into shared memory with bulk asynchronous
                               copies (bounded waits; an expired wait makes the next pd_sync /
