@@ -354,6 +354,10 @@ def run_gpu(args):
     u_out = torch.empty((dim, n), dtype=torch.float64, pin_memory=True).numpy()
     B.pd_get_state(sim.h, dim, n, u_h, v_h, False)
     e2e_steps = max(5, min(args.steps, 20))
+    for _ in range(2):  # untimed: the first calls load the transfer kernels
+        B.pd_set_state(sim.h, dim, n, u_h, v_h)
+        B.pd_step(sim.h, 1)
+        B.pd_get_state(sim.h, dim, n, u_out, False, False)
     barrier(world)
     torch.cuda.synchronize()
     t0 = time.perf_counter()

@@ -327,12 +327,24 @@ pd_status pd_set_state(pd_ctx* c, const double* u, const double* v) {
   if (st != PD_OK) return st;
   if (!u) return fail(PD_ERR_ARG, "u is required");
   const int dim = c->dim;
-  if (!all_finite(u, dim * c->n) || (v && !all_finite(v, dim * c->n)))
-    return fail(PD_ERR_ARG, "non-finite state");
-  st = upload_field(c, u, c->disp[c->cur], dim);
-  if (st != PD_OK) return st;
+  // Both arrays are copied to the device and checked there (a host scan of 6n doubles costs more
+  // than the copies); the state changes only once both are known to be finite.
+  const int64_t nd = (int64_t)dim * c->n;
+  unsigned long long* flag = c->counters + 6;
+  PD_CUDA(cudaMemsetAsync(flag, 0, sizeof(*flag), c->stream));
+  PD_CUDA(cudaMemcpyAsync(c->scratch, u, sizeof(double) * nd, cudaMemcpyHostToDevice, c->stream));
+  if ((st = launch_nonfinite(c, c->scratch, nd, flag)) != PD_OK) return st;
   if (v) {
-    st = upload_field(c, v, c->vel, dim);
+    PD_CUDA(cudaMemcpyAsync(c->scratch2, v, sizeof(double) * nd, cudaMemcpyHostToDevice, c->stream));
+    if ((st = launch_nonfinite(c, c->scratch2, nd, flag)) != PD_OK) return st;
+  }
+  unsigned long long bad = 0;
+  PD_CUDA(cudaMemcpyAsync(&bad, flag, sizeof(bad), cudaMemcpyDeviceToHost, c->stream));
+  PD_CUDA(cudaStreamSynchronize(c->stream));
+  if (bad) return fail(PD_ERR_ARG, "non-finite state");
+  if ((st = gather_field(c, c->scratch, c->disp[c->cur], dim)) != PD_OK) return st;
+  if (v) {
+    st = gather_field(c, c->scratch2, c->vel, dim);
   } else {
     PD_CUDA(cudaMemsetAsync(c->vel, 0, sizeof(double4) * c->n_pad, c->stream));
   }

@@ -421,6 +421,7 @@ pd_status create(pd_ctx** out, int32_t nbodies, const pd_params* prm, const int6
   PD_TRY(alloc(c, &c->d_step, 1));
   PD_TRY(alloc(c, &c->counters, 8));
   PD_TRY(alloc(c, &c->scratch, (size_t)c->n_pad * 3));
+  PD_TRY(alloc(c, &c->scratch2, (size_t)c->n_pad * 3));
   if (cudaMemcpyAsync(c->pos, hpos.data(), sizeof(double4) * c->n_pad, cudaMemcpyHostToDevice, c->stream) !=
           cudaSuccess ||
       cudaMemcpyAsync(c->body, body_int.data(), sizeof(int32_t) * c->n_pad, cudaMemcpyHostToDevice,

@@ -74,7 +74,7 @@ struct StepArgs {
   float* aA32;             // A / m_i * Q in FP32 (Q folded in)
   float* theta32;          // theta_i in FP32
   unsigned long long* counters;  // [0] band rechecks, [1] validate mismatches, [2..3] max |u|, [4] wait expired,
-                                 // [5] non-finite displacement after a pd_step
+                                 // [5] non-finite displacement after a pd_step, [6] non-finite pd_set_state input
   float band_c;            // safety factor of the band
   int validate;            // mixed: also decide every bond in FP64 and count mismatches
   int check;               // apply the failure criterion at the head of pass 1
@@ -135,6 +135,7 @@ struct pd_ctx {
   int64_t* d_step = nullptr;
   int64_t* perm_dev = nullptr;   // internal -> caller (n)
   double* scratch = nullptr;     // n_pad * 3 doubles for transfers
+  double* scratch2 = nullptr;    // a second n_pad * 3 (pd_set_state checks u and v before either lands)
   // mixed path
   int4* pos32 = nullptr;
   float4* u32[2] = {nullptr, nullptr};
@@ -215,6 +216,8 @@ pd_status ensure_adr(pd_ctx* c);      // ADR arrays and lambda (once per build)
 pd_status diagnostics(pd_ctx* c, double* min_margin, double* strain, double* kinetic);
 pd_status prepare_staged_kernels(pd_ctx* c);  // shared-memory opt-in of the staged kernels
 pd_status upload_field(pd_ctx* c, const double* host_soa, double4* dst, int comps);
+pd_status gather_field(pd_ctx* c, const double* dev_soa, double4* dst, int comps);
+pd_status launch_nonfinite(pd_ctx* c, const double* a, int64_t n, unsigned long long* flag);
 pd_status download_field(pd_ctx* c, const double4* src, double* host_soa, int comps);
 pd_status download_scalar(pd_ctx* c, const double* src, double* host);
 pd_status apply_bc_now(pd_ctx* c);

@@ -1562,6 +1562,14 @@ __global__ void k_gather_soa(int64_t n, int64_t n_pad, int comps, const double* 
   dst[k] = make_double4(src[u], src[n + u], comps == 3 ? src[2 * n + u] : 0.0, w);
 }
 
+// Any non-finite value among n doubles (grid-stride) -> *flag = 1.
+__global__ void k_nonfinite(int64_t n, const double* __restrict__ a, unsigned long long* flag) {
+  bool bad = false;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    bad = bad || !isfinite(a[i]);
+  if (__any_sync(kFull, bad) && (threadIdx.x & 31) == 0) atomicExch(flag, 1ull);
+}
+
 // disp[.].w = V (set once after allocation; every writer of disp keeps it).
 __global__ void k_set_w(int64_t n_pad, const double4* __restrict__ pos, double4* __restrict__ d0,
                         double4* __restrict__ d1) {
@@ -2005,12 +2013,26 @@ pd_status launch_damage(pd_ctx* c, double* phi_caller_dev) {
 }
 
 pd_status upload_field(pd_ctx* c, const double* host_soa, double4* dst, int comps) {
-  const int64_t n = c->n;
-  PD_CUDA(cudaMemcpyAsync(c->scratch, host_soa, sizeof(double) * comps * n, cudaMemcpyHostToDevice, c->stream));
+  PD_CUDA(cudaMemcpyAsync(c->scratch, host_soa, sizeof(double) * comps * c->n, cudaMemcpyHostToDevice, c->stream));
+  return gather_field(c, c->scratch, dst, comps);
+}
+
+// Caller-order SoA field already on the device -> internal order (double4; disp keeps V in .w).
+pd_status gather_field(pd_ctx* c, const double* dev_soa, double4* dst, int comps) {
   const int tb = 256;
   const bool is_disp = dst == c->disp[0] || dst == c->disp[1];
-  k_gather_soa<<<(unsigned)((c->n_pad + tb - 1) / tb), tb, 0, c->stream>>>(n, c->n_pad, comps, c->scratch,
+  k_gather_soa<<<(unsigned)((c->n_pad + tb - 1) / tb), tb, 0, c->stream>>>(c->n, c->n_pad, comps, dev_soa,
                                                                           c->perm_dev, is_disp ? c->pos : nullptr, dst);
+  PD_CUDA(cudaGetLastError());
+  return PD_OK;
+}
+
+// Sets *flag (device word) to 1 if any of the n doubles at a is not finite.
+pd_status launch_nonfinite(pd_ctx* c, const double* a, int64_t n, unsigned long long* flag) {
+  const int tb = 256;
+  const unsigned grid = (unsigned)std::min<int64_t>((n + tb - 1) / tb, 4096);
+  if (grid == 0) return PD_OK;
+  k_nonfinite<<<grid, tb, 0, c->stream>>>(n, a, flag);
   PD_CUDA(cudaGetLastError());
   return PD_OK;
 }

@@ -297,11 +297,21 @@ def test_state_errors_and_divergence_guard():
         B.pd_step(h, 1)
     assert e.value.status == B.PD_ERR_STATE
     B.pd_build_neighbors(h)
-    B.pd_set_state(h, 2, w.n, w.initial_u())
+    u0 = w.initial_u()
+    B.pd_set_state(h, 2, w.n, u0)
     assert B.pd_check_state(h, 1.0) == B.PD_OK
     assert B.pd_check_state(h, 1e-9) == B.PD_ERR_NUMERIC
-    with pytest.raises(B.PDError):
-        B.pd_set_state(h, 2, w.n, np.full((2, w.n), np.nan))
+    # a non-finite value anywhere in u or v is rejected and leaves the state as it was
+    bad_u = u0.copy()
+    bad_u[1, w.n - 1] = np.inf
+    bad_v = np.zeros((2, w.n))
+    bad_v[0, 3] = np.nan
+    for args in ((np.full((2, w.n), np.nan),), (bad_u,), (2.0 * u0, bad_v)):
+        with pytest.raises(B.PDError) as e:
+            B.pd_set_state(h, 2, w.n, *args)
+        assert e.value.status == B.PD_ERR_ARG
+    u, v, _ = B.pd_get_state(h, 2, w.n)
+    assert np.array_equal(u, u0) and np.all(v == 0.0)
     B.pd_destroy(h)
 
 
