@@ -593,7 +593,9 @@ __global__ void k_bond_sums(StepArgs a) {
   if (t.active) bond_sum_row(a, t);
 }
 
-template <int DIM, int SPLIT>
+// THETA = false: the failure check alone (applied to the current state before it is read), with no
+// theta sum and no xi.du store: 6 FP64 instructions per bond.
+template <int DIM, int SPLIT, bool THETA>
 __global__ void __launch_bounds__(512) k_pass1_f64t(StepArgs a, const double4* __restrict__ disp,
                                                      int write_theta) {
   const SliceIdx t = slice_index<SPLIT>(a.n_pad, a.slice_ptr);
@@ -628,7 +630,7 @@ __global__ void __launch_bounds__(512) k_pass1_f64t(StepArgs a, const double4* _
         double d = g[u].x * (uj[u].x - ui.x) + g[u].y * (uj[u].y - ui.y);
         if (DIM == 3) d = fma(g[u].z, uj[u].z - ui.z, d);
         const int k = k0 + u * SPLIT;
-        if (k < t.W) td[(int64_t)k << 5] = d;
+        if (THETA && k < t.W) td[(int64_t)k << 5] = d;
         bool intact = (wd[u] >> t.lane) & 1u;
         if (a.check) {
           const bool ge = __double_as_longlong(d) >= __double_as_longlong(g[u].w);  // d >= s0 |xi|^2
@@ -640,14 +642,14 @@ __global__ void __launch_bounds__(512) k_pass1_f64t(StepArgs a, const double4* _
             acc[1] = 1.0;
           }
         }
-        acc[0] = fma(intact ? uj[u].w : 0.0, d, acc[0]);
+        if (THETA) acc[0] = fma(intact ? uj[u].w : 0.0, d, acc[0]);
       }
     }
   }
   if (SPLIT == 1) __syncwarp();  // lane 0's status words, for the bS recomputation below
   split_reduce<SPLIT, 2>(acc);   // (SPLIT > 1: its block barrier orders the other warps' words)
   if (t.active && t.sub == 0) {
-    if (write_theta) {
+    if (THETA && write_theta) {
       const double th = a.aA[t.i] * acc[0];
       const double mu = a.mu[t.i];
       a.theta[t.i] = th;
@@ -1705,7 +1707,10 @@ void launch_pass1(pd_ctx* c, const StepArgs& a, int write_theta, unsigned grid, 
   else if (c->kin == PD_NONLINEAR)
     k_pass1_nl<DIM, SPLIT><<<grid, block, sm, c->stream>>>(a, c->disp[c->cur], write_theta);
   else if (c->precision == PD_FP64 && a.bA)
-    k_pass1_f64t<DIM, SPLIT><<<grid, block, sm, c->stream>>>(a, c->disp[c->cur], write_theta);
+    if (write_theta)
+      k_pass1_f64t<DIM, SPLIT, true><<<grid, block, sm, c->stream>>>(a, c->disp[c->cur], write_theta);
+    else
+      k_pass1_f64t<DIM, SPLIT, false><<<grid, block, sm, c->stream>>>(a, c->disp[c->cur], write_theta);
   else if (c->precision == PD_FP64)
     k_pass1_f64<DIM, SPLIT><<<grid, block, sm, c->stream>>>(a, c->disp[c->cur], write_theta);
   else
