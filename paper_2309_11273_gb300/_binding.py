@@ -24,6 +24,7 @@ PD_OPT_GRAPH_CHUNK, PD_OPT_PROFILE, PD_OPT_VALIDATE, PD_OPT_BLOCK, PD_OPT_SPLIT,
 PD_OPT_STAGE = 7
 PD_OPT_EXPIRE_WAITS = 8
 PD_OPT_SOLVER = 9
+PD_OPT_PAIRS = 10
 PD_SOLVER_EXPLICIT, PD_SOLVER_ADR = 0, 1
 PD_K_PASS1, PD_K_PASS2 = 0, 1
 

@@ -43,6 +43,10 @@ void free_build(pd_ctx* c) {
   c->allocs.resize(std::min(c->allocs.size(), c->n_create_allocs));
   c->alloc_bytes.resize(c->allocs.size());
   c->cnt = nullptr;
+  c->own0 = nullptr;
+  c->twin = nullptr;
+  c->dirty = nullptr;
+  c->pairs_ok = false;
   c->slice_ptr = nullptr;
   c->col = nullptr;
   c->bits = nullptr;
@@ -524,6 +528,9 @@ pd_status pd_set_option(pd_ctx* c, int32_t option, int64_t value) {
     case PD_OPT_EXPIRE_WAITS:
       c->expire_waits = value != 0;
       break;
+    case PD_OPT_PAIRS:
+      c->pairs = value != 0;
+      break;
     case PD_OPT_SOLVER:
       if (value != PD_SOLVER_EXPLICIT && value != PD_SOLVER_ADR) return fail(PD_ERR_ARG, "unknown solver");
       if (value == PD_SOLVER_ADR && c->nbodies > 1)
@@ -552,6 +559,7 @@ pd_status pd_get_option(pd_ctx* c, int32_t option, int64_t* value) {
     case PD_OPT_STAGE: *value = c->stage; break;
     case PD_OPT_EXPIRE_WAITS: *value = c->expire_waits; break;
     case PD_OPT_SOLVER: *value = c->solver; break;
+    case PD_OPT_PAIRS: *value = (c->pairs && c->pairs_ok && c->precision == PD_FP64) ? 1 : 0; break;
     default: return fail(PD_ERR_ARG, "unknown option");
   }
   return PD_OK;

@@ -40,6 +40,9 @@ struct BuildArgs {
   double* mu;
   double* aA;
   double* dden;
+  int32_t* own0;             // pair tables (FP64 linearized contexts), else nullptr
+  int32_t* twin;
+  unsigned long long* missing;
 };
 
 // A bond a-b is cut by a crack iff a and b lie strictly on opposite sides of the crack line (2D) or
@@ -210,6 +213,57 @@ __global__ void k_init_bonds(BuildArgs A) {
   const double mu = m > 0.0 ? 1.0 / m : 0.0;
   A.mu[i] = mu;
   A.aA[i] = (i < A.n) ? A.body_A[A.cellc[i].w] * mu : 0.0;
+}
+
+// Pair tables of the FP64 path.  Each undirected bond is evaluated once, by the end that owns it:
+// entry (i, k) with neighbour j is owned when its key is above the key of xi = 0, or equal to it with
+// j > i (so of the two entries of a pair exactly one is owned, the key of -xi being the mirror image
+// of the key of xi component by component).  Rows are sorted by (key, neighbour), so a particle's
+// owned entries are the tail of its row from own0[i]; twin[e] of an owned entry is the index of the
+// entry (j, k') whose neighbour is i, found by binary search of row j for (mirror key, i).  A pair
+// whose second entry is missing (a family that is not exactly symmetric) is counted in *missing.
+__device__ __forceinline__ unsigned long long mirror_key(unsigned long long k) {
+  const unsigned long long c = 1048576ull, m = 2097151ull;
+  return ((c - ((k >> 42) & m)) << 42) | ((c - ((k >> 21) & m)) << 21) | (c - (k & m));
+}
+
+__global__ void k_twins(BuildArgs A) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= A.n_pad) return;
+  const int lane = (int)(i & 31);
+  const int64_t base = A.slice_ptr[i >> 5] + lane;
+  const int cnt = A.cnt[i];
+  const unsigned long long key0 = (524288ull << 42) | (524288ull << 21) | 524288ull;
+  int own = cnt;
+  for (int k = 0; k < cnt; ++k) {
+    const unsigned long long key = A.keys[base + (int64_t)k * 32];
+    if (key > key0 || (key == key0 && A.col[base + (int64_t)k * 32] > i)) {
+      own = k;
+      break;
+    }
+  }
+  A.own0[i] = own;
+  for (int k = own; k < cnt; ++k) {
+    const int64_t e = base + (int64_t)k * 32;
+    const int32_t j = A.col[e];
+    const unsigned long long mk = mirror_key(A.keys[e]);
+    const int64_t bj = A.slice_ptr[j >> 5] + (j & 31);
+    int lo = 0, hi = A.cnt[j];  // first entry of row j not below (mk, i)
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      const unsigned long long km = A.keys[bj + (int64_t)mid * 32];
+      const int32_t jm = A.col[bj + (int64_t)mid * 32];
+      if (km < mk || (km == mk && jm < (int32_t)i)) lo = mid + 1;
+      else hi = mid;
+    }
+    const int64_t t = bj + (int64_t)lo * 32;
+    if (lo < A.cnt[j] && A.col[t] == (int32_t)i && A.keys[t] == mk) {
+      A.twin[e] = (int32_t)t;
+    } else {
+      A.twin[e] = -1;
+      atomicAdd(A.missing, 1ull);
+    }
+  }
 }
 
 // Morton key of 21-bit quantized coordinates.
@@ -696,6 +750,22 @@ pd_status build_neighbors(pd_ctx* c, const pd_crack* cracks, int32_t ncracks) {
       k_init_bonds<2><<<gb, tb, 0, s>>>(A);
     }
     PD_CUDA(cudaGetLastError());
+    c->pairs_ok = false;
+    if (c->precision == PD_FP64 && c->kin == PD_LINEARIZED && c->nentries < (int64_t)INT32_MAX) {
+      // pair tables of the FP64 path (entry indices fit in 32 bits)
+      PD_TRY2(alloc(c, &c->own0, (size_t)n_pad));
+      PD_TRY2(alloc(c, &c->twin, (size_t)std::max<int64_t>(c->nentries, 32)));
+      A.own0 = c->own0;
+      A.twin = c->twin;
+      A.missing = c->counters + 7;
+      PD_CUDA(cudaMemsetAsync(c->counters + 7, 0, sizeof(unsigned long long), s));
+      k_twins<<<gb, tb, 0, s>>>(A);
+      PD_CUDA(cudaGetLastError());
+      unsigned long long missing = 0;
+      PD_CUDA(cudaMemcpyAsync(&missing, c->counters + 7, sizeof(missing), cudaMemcpyDeviceToHost, s));
+      PD_CUDA(cudaStreamSynchronize(s));
+      c->pairs_ok = missing == 0;
+    }
     PD_CUDA(cudaStreamSynchronize(s));
   }
   cleanup();

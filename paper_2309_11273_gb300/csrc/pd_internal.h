@@ -74,7 +74,8 @@ struct StepArgs {
   float* aA32;             // A / m_i * Q in FP32 (Q folded in)
   float* theta32;          // theta_i in FP32
   unsigned long long* counters;  // [0] band rechecks, [1] validate mismatches, [2..3] max |u|, [4] wait expired,
-                                 // [5] non-finite displacement after a pd_step, [6] non-finite pd_set_state input
+                                 // [5] non-finite displacement after a pd_step, [6] non-finite pd_set_state input,
+                                 // [7] pair entries missing at the build
   float band_c;            // safety factor of the band
   int validate;            // mixed: also decide every bond in FP64 and count mismatches
   int check;               // apply the failure criterion at the head of pass 1
@@ -82,6 +83,10 @@ struct StepArgs {
   const double4* bB;       // tabled FP64 path: per slot (V_j xi, G (1/m_i + 1/m_j) / |xi|^2)
   double* bd;              // tabled FP64 path: per slot xi.(u_j - u_i), written by pass 1
   double4* bS;             // tabled FP64 path: per particle sum of V_j xi over the intact slots
+  const int32_t* cnt;      // family size of each row
+  const int32_t* own0;     // FP64 pair path (or nullptr): first owned slot of each row
+  const int32_t* twin;     // FP64 pair path: per owned slot, the entry index of the same bond at j
+  uint8_t* dirty;          // FP64 pair path: per slice, bS needs recomputing
   double2* bE;             // tabled nonlinear path: per slot (e, 1 / |Y|), written by pass 1 (bA = (xi, |xi|))
   int expire;              // testing (PD_OPT_EXPIRE_WAITS): staged kernels skip their first copy
   double uscale;           // mixed path: the FP32 shadow holds u * uscale (1, or 1/Q for nonlinear bonds)
@@ -121,6 +126,10 @@ struct pd_ctx {
   int32_t* col = nullptr;
   uint32_t* bits = nullptr;
   int32_t* cnt = nullptr;
+  int32_t* own0 = nullptr;       // FP64 pair path: first owned slot of each row
+  int32_t* twin = nullptr;       // FP64 pair path: per owned slot, the entry of the same bond at j
+  bool pairs_ok = false;         // the pair tables exist and every pair has both entries
+  uint8_t* dirty = nullptr;      // FP64 pair path: per slice, a bond of the slice broke (bS to redo)
   int64_t nentries = 0, nbonds = 0;
   double* mu = nullptr;
   double* aA = nullptr;
@@ -151,6 +160,7 @@ struct pd_ctx {
   bool bs_stale = true;           // bS no longer matches the status bits (recomputed before a step)
   double2* bE = nullptr;          // nonlinear FP64: per-slot (e, 1/|Y|) of the current step
   int bond_cache = 1;             // use the table in the FP64 path
+  int pairs = 1;                  // FP64 tabled path: evaluate each bond once per pair (needs pairs_ok)
   int stage = 1;                  // mixed path: TMA-staged index streams (split 1)
   int expire_waits = 0;           // testing: make the staged kernels' first wait expire
   int solver = 0;                 // pd_solver

@@ -269,6 +269,33 @@ def test_intact_sums_follow_the_status_bits():
     assert np.array_equal(intact, ref.status) and np.array_equal(phi, ref.damage())
 
 
+@pytest.mark.parametrize("case,split", [("block", 1), ("block", 2), ("block", 4), ("plate", 1), ("plate", 2)])
+def test_pair_form_is_bitwise_the_single_pass(case, split):
+    """The tabled FP64 path forms each bond's xi.(u_j - u_i) once for both directed entries (the
+    pair form, default) or once per entry: the two give bitwise the same u, v, bond status and
+    damage, through bond breaking, with a state read (and its failure check) half way."""
+    if case == "block":
+        w = W.notched_block(nx=24, ny=12, nz=10, dx=1e-3, notch_cells=9.5, nsteps=300, seed=3, amp=1e-7)
+    else:
+        w = W.cracked_plate(nx=60, ny=24, dx=2.5e-4, crack_cells=30.125, sigma=2e6, nsteps=400)
+    res = []
+    for pairs in (1, 0):
+        sim = Simulation(w, s0=s0_of(w))
+        assert B.pd_get_option(sim.h, B.PD_OPT_PAIRS) == 1
+        sim.set_option(B.PD_OPT_PAIRS, pairs)
+        sim.set_option(B.PD_OPT_BLOCK, 128)
+        sim.set_option(B.PD_OPT_SPLIT, split)
+        sim.step(w.nsteps // 2)
+        mid = sim.state()[0]
+        sim.step(w.nsteps - w.nsteps // 2)
+        u, v, _ = sim.state()
+        res.append((mid, u, v, sim.neighbors()[2], sim.damage(), sim.stats()["broken_bonds"]))
+        sim.close()
+    assert res[0][5] > 0
+    for a, b in zip(res[0], res[1]):
+        assert np.array_equal(a, b)
+
+
 # --------------------------------------------------------------------------------- edge cases
 def test_single_particle_and_ragged_sizes():
     for nx, ny in ((1, 1), (33, 1), (7, 5)):
