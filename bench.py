@@ -55,6 +55,9 @@ BYTES_BOND = {1: 4.25, 2: 4.125}
 BYTES_PART = {1: 68.0, 2: 141.0}
 FLOPS_BOND = {1: 19.0, 2: 28.0}
 FLOPS_BOND_TABLED = {1: 10.0, 2: 8.0}
+# ... and of the pair form, per directed bond: pass 1a forms the difference and dot product once per
+# bond (8 flop per pair), pass 1b the theta FMA, pass 2 as in the tabled form.
+FLOPS_BOND_PAIRS = {"k_pass1a_f64p": 4.0, "k_pass1b_f64p": 2.0, "k_pass2_f64t": 8.0}
 # Geometrically nonlinear bonds (Eqs 1.10, 1.13), FP64, square root and divide counted as one flop
 # each: pass 1 forms xi, eta, Y, |Y|^2 - |xi|^2, |xi|^2, |Y|^2, two roots, e and the theta term and
 # the break test; pass 2 the same geometry, the Eq 1.14 coefficient and the force along Y / |Y|.
@@ -114,18 +117,16 @@ def recorded_traffic(kernel, nbonds=None):
     return None
 
 
-def table_stream(tabled, kp, prof, nb, hbm):
-    """DRAM rate of the other FP64 pass from its recorded ncu traffic: the tabled pass 2 streams its
-    per-slot tables (V_j xi and the bond coefficient, 32 B; xi.du, 8 B; the index, 4 B), so it is
-    bound by HBM rather than by the FP64 pipe."""
-    kname = "k_pass%d_f64%s" % (kp, "t" if tabled else "")
-    ms = prof["pass%d_ms" % kp]
+def kernel_entry(kname, ms, flops, nb, hbm):
+    """One FP64 kernel of the step: its CUDA-event time, flop rate against the FP64 peak, and its
+    DRAM rate from the recorded ncu traffic (the tabled kernels stream per-slot tables, so their
+    bytes are the tables, not the model's algorithmic bytes)."""
+    out = {"ms": ms, "flop_per_bond": flops, "achieved_tflops": flops * nb / (ms * 1e-3) / 1e12,
+           "frac": flops * nb / (ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS}
     t = recorded_traffic(kname, nb)
-    out = {"kernel": kname, "ms": ms, "traffic": t}
+    out["traffic"] = t
     if t is not None:
-        out.update({"dram_gbs": t / (ms * 1e-3) / 1e9, "dram_frac": t / (ms * 1e-3) / 1e9 / hbm,
-                    "note": "measured DRAM bytes (ncu) / CUDA-event time, of measured HBM peak; the bytes "
-                            "are the per-slot tables, not the model's algorithmic bytes"})
+        out.update({"dram_gbs": t / (ms * 1e-3) / 1e9, "dram_frac": t / (ms * 1e-3) / 1e9 / hbm})
     return out
 
 
@@ -307,9 +308,11 @@ def profiled(sim, steps):
     sim.step(steps)
     sim.sync()
     p1 = B.pd_get_profile(sim.h, B.PD_K_PASS1)
+    p1b = B.pd_get_profile(sim.h, B.PD_K_PASS1B)
     p2 = B.pd_get_profile(sim.h, B.PD_K_PASS2, reset=True)
     sim.set_option(B.PD_OPT_PROFILE, 0)
-    return {"pass1_ms": p1[0] / max(p1[1], 1), "pass2_ms": p2[0] / max(p2[1], 1), "launches": p1[1] + p2[1]}
+    return {"pass1_ms": p1[0] / max(p1[1], 1), "pass1b_ms": p1b[0] / max(p1b[1], 1),
+            "pass2_ms": p2[0] / max(p2[1], 1), "launches": p1[1] + p1b[1] + p2[1]}
 
 
 def run_gpu(args):
@@ -339,21 +342,31 @@ def run_gpu(args):
     value = world * nb * args.steps / (ms * 1e-3)
     prof = profiled(sim, max(10, min(args.steps, 50)))
     tabled = B.pd_get_option(sim.h, B.PD_OPT_BOND_CACHE) == 1
-    kp = 1 if prof["pass1_ms"] >= prof["pass2_ms"] else 2  # the dominant kernel
-    kms = prof["pass%d_ms" % kp]
-    fl = (FLOPS_BOND_TABLED if tabled else FLOPS_BOND)[kp]
-    achieved = fl * nb / (kms * 1e-3) / 1e12
-    kname = "k_pass%d_f64%s" % (kp, "t" if tabled else "")
+    pairs = tabled and B.pd_get_option(sim.h, B.PD_OPT_PAIRS) == 1
+    if pairs:
+        kern = {"k_pass1a_f64p": prof["pass1_ms"], "k_pass1b_f64p": prof["pass1b_ms"], "k_pass2_f64t": prof["pass2_ms"]}
+        fl = FLOPS_BOND_PAIRS
+        form = "pair"
+    else:
+        sfx = "t" if tabled else ""
+        kern = {"k_pass1_f64" + sfx: prof["pass1_ms"], "k_pass2_f64" + sfx: prof["pass2_ms"]}
+        table = FLOPS_BOND_TABLED if tabled else FLOPS_BOND
+        fl = {"k_pass1_f64" + sfx: table[1], "k_pass2_f64" + sfx: table[2]}
+        form = "tabled" if tabled else "recompute"
+    kname = max(kern, key=kern.get)  # the dominant kernel
+    kms = kern[kname]
+    achieved = fl[kname] * nb / (kms * 1e-3) / 1e12
+    step_ms = sum(kern.values())
     roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": recorded_traffic(kname, nb),
                 "peak_note": "FP64 peak from unit counts and clock: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz",
                 "algorithmic": "%g FP64 flop per directed bond (per-step part of the %s form) x %d bonds per launch"
-                               % (fl, "tabled" if tabled else "recompute", nb),
-                "frac_recompute_model": FLOPS_BOND[kp] * nb / (kms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
-                "pass1_ms": prof["pass1_ms"], "pass2_ms": prof["pass2_ms"],
-                "other_pass": table_stream(tabled, 3 - kp, prof, nb, hbm),
+                               % (fl[kname], form, nb),
+                "kernels": {k: kernel_entry(k, v, fl[k], nb, hbm) for k, v in kern.items()},
+                "frac_recompute_model": (FLOPS_BOND[1] + FLOPS_BOND[2]) * nb / (step_ms * 1e-3) / 1e12
+                / FP64_PEAK_TFLOPS,
                 "model_bytes_frac_of_hbm": (sum(BYTES_BOND.values()) * nb + sum(BYTES_PART.values()) * w.n)
-                / ((prof["pass1_ms"] + prof["pass2_ms"]) * 1e-3) / (hbm * 1e9)}
+                / (step_ms * 1e-3) / (hbm * 1e9)}
 
     # end to end through the C ABI with pinned host buffers: H2D of (u, v), one step, D2H of u
     n, dim = w.n, w.dim
@@ -392,7 +405,7 @@ def run_gpu(args):
                        "graph_chunk": 100, "mapping": {"block": mapping[0], "split": mapping[1]}, "l2": "inputs larger than L2 (neighbour indices %.0f MB)" % (nb * 4 / 1e6),
                        "replicas": world},
             "roofline": roofline, "e2e": e2e, "clocks": clocks,
-            "gpu_launches": 2 * args.steps + 1,
+            "gpu_launches": (3 if pairs else 2) * args.steps + 2,  # step kernels + k_set_step + k_flag_nonfinite
             "paper_context": dict(PAPER_CONTEXT, ratio=value / PAPER_CONTEXT["derived_value"])}
     line.update(forms)
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -169,8 +169,10 @@ typedef enum {
  *   kernels of an iteration are counted with PD_K_PASS2. */
 typedef enum { PD_SOLVER_EXPLICIT = 0, PD_SOLVER_ADR = 1 } pd_solver;
 
-/* Kernel identifiers for pd_get_profile. */
-typedef enum { PD_K_PASS1 = 0, PD_K_PASS2 = 1, PD_K_COUNT = 2 } pd_kernel;
+/* Kernel identifiers for pd_get_profile.  With the FP64 pair form (PD_OPT_PAIRS) pass 1 is two
+ * kernels: PD_K_PASS1 times the first (extension and failure check per pair), PD_K_PASS1B the
+ * second (dilatation sum); otherwise PD_K_PASS1B records nothing. */
+typedef enum { PD_K_PASS1 = 0, PD_K_PASS2 = 1, PD_K_PASS1B = 2, PD_K_COUNT = 3 } pd_kernel;
 
 /* Critical stretch s_c from the critical energy release rate Gc [J/m^2] and the horizon (w = 1).
  *   3D: Eq 1.26 with beta = 125 delta / 1848 and beta' = 5 delta / 24.  Eq 1.27 prints

@@ -26,7 +26,7 @@ PD_OPT_EXPIRE_WAITS = 8
 PD_OPT_SOLVER = 9
 PD_OPT_PAIRS = 10
 PD_SOLVER_EXPLICIT, PD_SOLVER_ADR = 0, 1
-PD_K_PASS1, PD_K_PASS2 = 0, 1
+PD_K_PASS1, PD_K_PASS2, PD_K_PASS1B = 0, 1, 2
 
 STATUS_NAMES = {0: "PD_OK", -1: "PD_ERR_ARG", -2: "PD_ERR_STATE", -3: "PD_ERR_OOM", -4: "PD_ERR_CUDA",
                 -5: "PD_ERR_NUMERIC", -6: "PD_ERR_TIMEOUT"}

@@ -97,8 +97,9 @@ struct StepArgs {
 struct KernelTimes {
   std::vector<cudaEvent_t> ev;  // pairs (start, stop) per launch
   std::vector<int> which;       // kernel id per pair
-  double ms[PD_K_COUNT] = {0, 0};
-  int64_t launches[PD_K_COUNT] = {0, 0};
+  double ms[PD_K_COUNT] = {};
+  int64_t launches[PD_K_COUNT] = {};
+  cudaEvent_t mid = nullptr;    // pair form: recorded between the two pass-1 kernels of a step
 };
 
 }  // namespace pd

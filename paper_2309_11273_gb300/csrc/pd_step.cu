@@ -1809,6 +1809,12 @@ StepArgs make_args(pd_ctx* c) {
   return a;
 }
 
+cudaEvent_t take_event(pd_ctx* c) {
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
 template <int DIM, int SPLIT>
 void launch_pass1(pd_ctx* c, const StepArgs& a, int write_theta, unsigned grid, int block, size_t sm) {
   if (c->kin == PD_NONLINEAR && a.bA)
@@ -1817,7 +1823,13 @@ void launch_pass1(pd_ctx* c, const StepArgs& a, int write_theta, unsigned grid, 
     k_pass1_nl<DIM, SPLIT><<<grid, block, sm, c->stream>>>(a, c->disp[c->cur], write_theta);
   else if (c->precision == PD_FP64 && a.bA && a.own0) {
     k_pass1a_f64p<DIM, SPLIT><<<grid, block, 0, c->stream>>>(a, c->disp[c->cur]);
-    if (write_theta) k_pass1b_f64p<DIM, SPLIT><<<grid, block, sm, c->stream>>>(a, c->disp[c->cur], write_theta);
+    if (write_theta) {
+      if (c->profile) {
+        c->times.mid = take_event(c);
+        cudaEventRecord(c->times.mid, c->stream);
+      }
+      k_pass1b_f64p<DIM, SPLIT><<<grid, block, sm, c->stream>>>(a, c->disp[c->cur], write_theta);
+    }
   } else if (c->precision == PD_FP64 && a.bA) {
     if (write_theta)
       k_pass1_f64t<DIM, SPLIT, true><<<grid, block, sm, c->stream>>>(a, c->disp[c->cur], write_theta);
@@ -1909,11 +1921,6 @@ void dispatch(pd_ctx* c, const StepArgs& a, int pass, int write_theta) {
   else dispatch_pass<2>(c, a, pass, write_theta);
 }
 
-cudaEvent_t take_event(pd_ctx* c) {
-  cudaEvent_t e = nullptr;
-  cudaEventCreate(&e);
-  return e;
-}
 
 }  // namespace
 
@@ -2082,9 +2089,19 @@ pd_status launch_step(pd_ctx* c, bool check) {
   }
   if (prof) {
     cudaEventRecord(e2, c->stream);
-    c->times.ev.push_back(e0);
-    c->times.ev.push_back(e1);
-    c->times.which.push_back(PD_K_PASS1);
+    if (c->times.mid) {  // pair form: two pass-1 kernels
+      c->times.ev.push_back(e0);
+      c->times.ev.push_back(c->times.mid);
+      c->times.which.push_back(PD_K_PASS1);
+      c->times.ev.push_back(c->times.mid);
+      c->times.ev.push_back(e1);
+      c->times.which.push_back(PD_K_PASS1B);
+      c->times.mid = nullptr;
+    } else {
+      c->times.ev.push_back(e0);
+      c->times.ev.push_back(e1);
+      c->times.which.push_back(PD_K_PASS1);
+    }
     c->times.ev.push_back(e1);
     c->times.ev.push_back(e2);
     c->times.which.push_back(PD_K_PASS2);
