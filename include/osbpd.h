@@ -145,11 +145,13 @@ typedef enum {
                               of the GPU's global timer) expires; the warps skip their outputs
                               and the next pd_sync / pd_get_* returns PD_ERR_TIMEOUT.  Default 0. */
   PD_OPT_SOLVER = 9,       /* pd_solver: PD_SOLVER_EXPLICIT (0, default) or PD_SOLVER_ADR (1) */
-  PD_OPT_PAIRS = 10        /* PD_FP64, linearized bonds, bond cache on: 1 (default) = form each
-                              bond's xi.(u_j - u_i) once for its two directed entries (the failure
-                              check and dilatation pass then runs as two kernels); 0 = once per
-                              entry.  Results are bitwise the same.  Has no effect when the build
-                              could not pair every entry (pd_get_option then reports 0). */
+  PD_OPT_PAIRS = 10        /* PD_FP64 with the bond cache on: 1 (default) = form each bond's
+                              extension (linearized: xi.(u_j - u_i); nonlinear: e and 1/|Y|) and
+                              failure test once for its two directed entries (the failure check and
+                              dilatation pass then runs as two kernels); 0 = once per entry.
+                              Linearized results are bitwise the same; nonlinear theta sums differ
+                              in rounding order only.  Has no effect when the build could not pair
+                              every entry (pd_get_option then reports 0). */
 } pd_option;
 
 /* Solvers (PD_OPT_SOLVER).

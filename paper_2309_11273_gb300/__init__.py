@@ -22,7 +22,7 @@ class Simulation:
 
     def __init__(self, w, s0=None, precision=PD_FP64, rate=None, device=0, stream=None,
                  band_safety=0.0, graph_chunk=None, ordering=B.PD_ORDER_BRICKS, bond_cache=None,
-                 kinematics=B.PD_LINEARIZED):
+                 kinematics=B.PD_LINEARIZED, pairs=None):
         self.w = w
         self.n, self.dim = w.n, w.dim
         if s0 is None:
@@ -36,6 +36,8 @@ class Simulation:
                 B.pd_set_option(self.h, B.PD_OPT_GRAPH_CHUNK, graph_chunk)
             if bond_cache is not None:
                 B.pd_set_option(self.h, B.PD_OPT_BOND_CACHE, int(bond_cache))
+            if pairs is not None:
+                B.pd_set_option(self.h, B.PD_OPT_PAIRS, int(pairs))
             B.pd_build_neighbors(self.h, w.cracks)
             self.rate = w.rotation_rate(self.s0) if rate is None else float(rate)
             if w.flag is not None or w.b is not None:

@@ -62,6 +62,7 @@ void free_build(pd_ctx* c) {
   c->bS = nullptr;
   c->bs_stale = true;
   c->bE = nullptr;
+  c->bt = nullptr;
   c->lam = nullptr;
   c->gnew = c->gold = nullptr;
   c->adr_part = c->adr_st = nullptr;

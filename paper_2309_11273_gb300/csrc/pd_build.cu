@@ -751,7 +751,7 @@ pd_status build_neighbors(pd_ctx* c, const pd_crack* cracks, int32_t ncracks) {
     }
     PD_CUDA(cudaGetLastError());
     c->pairs_ok = false;
-    if (c->precision == PD_FP64 && c->kin == PD_LINEARIZED && c->nentries < (int64_t)INT32_MAX) {
+    if (c->precision == PD_FP64 && c->nentries < (int64_t)INT32_MAX) {
       // pair tables of the FP64 path (entry indices fit in 32 bits)
       PD_TRY2(alloc(c, &c->own0, (size_t)n_pad));
       PD_TRY2(alloc(c, &c->twin, (size_t)std::max<int64_t>(c->nentries, 32)));

@@ -88,6 +88,7 @@ struct StepArgs {
   const int32_t* twin;     // FP64 pair path: per owned slot, the entry index of the same bond at j
   uint8_t* dirty;          // FP64 pair path: per slice, bS needs recomputing
   double2* bE;             // tabled nonlinear path: per slot (e, 1 / |Y|), written by pass 1 (bA = (xi, |xi|))
+  double* bt;              // tabled nonlinear pair form: per slot V_j |xi| e, written by pass 1a
   int expire;              // testing (PD_OPT_EXPIRE_WAITS): staged kernels skip their first copy
   double uscale;           // mixed path: the FP32 shadow holds u * uscale (1, or 1/Q for nonlinear bonds)
   int adr;                 // PD_SOLVER_ADR: pass 2 stores g = f + b in gnew instead of updating
@@ -160,6 +161,7 @@ struct pd_ctx {
   double4* bS = nullptr;          // FP64 per-particle sum of V_j xi over the intact slots
   bool bs_stale = true;           // bS no longer matches the status bits (recomputed before a step)
   double2* bE = nullptr;          // nonlinear FP64: per-slot (e, 1/|Y|) of the current step
+  double* bt = nullptr;           // nonlinear FP64 pair form: per-slot theta term V_j |xi| e
   int bond_cache = 1;             // use the table in the FP64 path
   int pairs = 1;                  // FP64 tabled path: evaluate each bond once per pair (needs pairs_ok)
   int stage = 1;                  // mixed path: TMA-staged index streams (split 1)

@@ -540,6 +540,88 @@ __global__ void __launch_bounds__(512) k_pass2_nlt(StepArgs a, const double4* __
   }
 }
 
+// Pair form of the tabled nonlinear pass 1.  Y and u_j - u_i change sign between the two entries of a
+// bond and |Y|^2 - |xi|^2 does not, so the failure test, e and 1/|Y| are the same numbers at both
+// ends: pass 1a forms them once, at the owned entry, clears both bits of a broken bond, and writes
+// (e, 1/|Y|) and the theta terms V_j |xi| e and V_i |xi| e of both entries; pass 1b sums theta.  The
+// root and the divide, most of the FP64 work of the single pass, run once per bond.
+template <int DIM, int SPLIT>
+__global__ void __launch_bounds__(512) k_pass1a_nlp(StepArgs a, const double4* __restrict__ disp) {
+  const SliceIdx t = slice_index<SPLIT>(a.n_pad, a.slice_ptr);
+  if (!t.active) return;  // whole warps; no block-wide barrier below
+  const int b = a.body ? a.body[t.i] : 0;
+  const double s0nl = a.bp[b].s0nl;
+  const bool can_break = a.bp[b].breaks != 0;
+  const int own = a.own0[t.i], cnt = a.cnt[t.i];
+  const int k_lo = __reduce_min_sync(kFull, (unsigned)own);
+  const int k_hi = __reduce_max_sync(kFull, (unsigned)cnt);
+  const double4 ui = disp[t.i];
+  uint32_t* bw = a.bits + (t.base >> 5);
+  const int32_t* __restrict__ cl = a.col + t.base + t.lane;
+  const int32_t* __restrict__ tw = a.twin + t.base + t.lane;
+  const double4* __restrict__ ta = a.bA + t.base + t.lane;
+  for (int k = k_lo + t.sub; k < k_hi; k += SPLIT) {
+    const bool mine = k >= own && k < cnt;
+    const int64_t e = t.base + t.lane + ((int64_t)k << 5);
+    double p = 0.0, yl2 = 0.0, xl = 0.0, vj = 0.0;
+    int32_t te = 0;
+    if (mine) {
+      const int32_t j = cl[(int64_t)k << 5];
+      const double4 g = ta[(int64_t)k << 5];
+      const double4 uj = disp[j];
+      te = tw[(int64_t)k << 5];
+      const double hx = uj.x - ui.x, hy = uj.y - ui.y, hz = DIM == 3 ? uj.z - ui.z : 0.0;
+      const double yx = g.x + hx, yy = g.y + hy, yz = g.z + hz;
+      p = hx * (g.x + yx) + hy * (g.y + yy);
+      if (DIM == 3) p = fma(hz, g.z + yz, p);
+      yl2 = yx * yx + yy * yy;
+      if (DIM == 3) yl2 = fma(yz, yz, yl2);
+      xl = g.w;
+      vj = uj.w;
+    }
+    bool intact = mine && ((bw[k] >> t.lane) & 1u);  // this warp's owned bits change only here
+    if (a.check) {
+      const bool brk = intact && can_break && p >= s0nl * (xl * xl);
+      const unsigned m = __ballot_sync(kFull, brk);
+      if (m) {
+        if (t.lane == 0) atomicAnd(&bw[k], ~m);
+        if (brk) atomicAnd(a.bits + (te >> 5), ~(1u << (te & 31)));
+        intact = intact && !brk;
+      }
+    }
+    if (intact) {
+      const double ry = rsqrt(yl2);
+      const double ev = p / fma(yl2, ry, xl);
+      a.bE[e] = make_double2(ev, ry);
+      a.bE[te] = make_double2(ev, ry);
+      a.bt[e] = (vj * xl) * ev;       // Eq 1.6 term of entry (i, j): w |xi| e V_j
+      a.bt[te] = (ui.w * xl) * ev;    // and of entry (j, i): w |xi| e V_i
+    }
+  }
+}
+
+template <int DIM, int SPLIT>
+__global__ void __launch_bounds__(512) k_pass1b_nlp(StepArgs a, int write_theta) {
+  const SliceIdx t = slice_index<SPLIT>(a.n_pad, a.slice_ptr);
+  if (write_theta && blockIdx.x == 0 && threadIdx.x == 0) *a.d_step += 1;
+  double acc[1] = {0.0};
+  int b = 0;
+  if (t.active) {
+    b = a.body ? a.body[t.i] : 0;
+    const uint32_t* __restrict__ bw = a.bits + (t.base >> 5);
+    const double* __restrict__ tt = a.bt + t.base + t.lane;
+    for (int k = t.sub; k < t.W; k += SPLIT)
+      if ((bw[k] >> t.lane) & 1u) acc[0] += tt[(int64_t)k << 5];
+  }
+  split_reduce<SPLIT, 1>(acc);
+  if (t.active && t.sub == 0 && write_theta) {
+    const double th = a.aA[t.i] * acc[0];
+    const double mu = a.mu[t.i];
+    a.theta[t.i] = th;
+    a.thm[t.i] = make_double2(a.bp[b].Kp * (th * mu), a.bp[b].G * mu);
+  }
+}
+
 template <int DIM>
 __global__ void k_bond_tables_nl(StepArgs a, double4* __restrict__ bA) {
   const SliceIdx t = slice_index<1>(a.n_pad, a.slice_ptr);
@@ -1798,7 +1880,9 @@ StepArgs make_args(pd_ctx* c) {
   a.bd = c->bond_cache ? c->bd : nullptr;
   a.bS = c->bond_cache ? c->bS : nullptr;
   a.cnt = c->cnt;
-  a.own0 = (c->bond_cache && c->pairs && c->pairs_ok && c->dirty) ? c->own0 : nullptr;
+  const bool pairs_ready = c->kin == PD_NONLINEAR ? c->bt != nullptr : c->dirty != nullptr;
+  a.own0 = (c->bond_cache && c->pairs && c->pairs_ok && pairs_ready) ? c->own0 : nullptr;
+  a.bt = c->bt;
   a.twin = c->twin;
   a.dirty = c->dirty;
   a.bE = c->bond_cache ? c->bE : nullptr;
@@ -1817,7 +1901,16 @@ cudaEvent_t take_event(pd_ctx* c) {
 
 template <int DIM, int SPLIT>
 void launch_pass1(pd_ctx* c, const StepArgs& a, int write_theta, unsigned grid, int block, size_t sm) {
-  if (c->kin == PD_NONLINEAR && a.bA)
+  if (c->kin == PD_NONLINEAR && a.bA && a.own0) {
+    k_pass1a_nlp<DIM, SPLIT><<<grid, block, 0, c->stream>>>(a, c->disp[c->cur]);
+    if (write_theta) {
+      if (c->profile) {
+        c->times.mid = take_event(c);
+        cudaEventRecord(c->times.mid, c->stream);
+      }
+      k_pass1b_nlp<DIM, SPLIT><<<grid, block, sm, c->stream>>>(a, write_theta);
+    }
+  } else if (c->kin == PD_NONLINEAR && a.bA)
     k_pass1_nlt<DIM, SPLIT><<<grid, block, sm, c->stream>>>(a, c->disp[c->cur], write_theta);
   else if (c->kin == PD_NONLINEAR)
     k_pass1_nl<DIM, SPLIT><<<grid, block, sm, c->stream>>>(a, c->disp[c->cur], write_theta);
@@ -1943,6 +2036,11 @@ pd_status ensure_bond_cache(pd_ctx* c) {
     if (c->bA) return PD_OK;
     if ((st = alloc(c, &c->bA, ne)) != PD_OK) return st;
     if ((st = alloc(c, &c->bE, ne)) != PD_OK) return st;
+    PD_CUDA(cudaMemsetAsync(c->bE, 0, sizeof(double2) * ne, c->stream));
+    if (c->pairs_ok) {
+      if ((st = alloc(c, &c->bt, ne)) != PD_OK) return st;
+      PD_CUDA(cudaMemsetAsync(c->bt, 0, sizeof(double) * ne, c->stream));
+    }
     StepArgs a = make_args(c);
     if (c->dim == 3)
       k_bond_tables_nl<3><<<grid, tb, 0, c->stream>>>(a, c->bA);

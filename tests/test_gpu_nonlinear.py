@@ -60,20 +60,24 @@ def assert_parity(out, phi=None, ref=None, tol_v=TOL):
         assert np.array_equal(phi, ref.damage())
 
 
-@pytest.mark.parametrize("bond_cache", [1, 0])
-def test_cracked_plate_breaking_nonlinear(bond_cache):
-    """Both kernel forms: per-slot tables (default) and recomputed geometry."""
+FORMS = {"pairs": dict(bond_cache=1, pairs=1), "tabled": dict(bond_cache=1, pairs=0), "recompute": dict(bond_cache=0)}
+
+
+@pytest.mark.parametrize("form", sorted(FORMS))
+def test_cracked_plate_breaking_nonlinear(form):
+    """All kernel forms: per-slot tables with each bond's e and 1/|Y| formed once per pair (default)
+    or once per entry, and recomputed geometry."""
     w = W.cracked_plate(nx=60, ny=24, dx=2.5e-4, crack_cells=30.125, sigma=2e6, nsteps=400)
-    out, phi, ref = run_pair(w, 400, 100, bond_cache=bond_cache)
+    out, phi, ref = run_pair(w, 400, 100, **FORMS[form])
     assert out[-1]["broken"] > 0
     assert_parity(out, phi, ref)
 
 
-@pytest.mark.parametrize("bond_cache", [1, 0])
-def test_notched_block_twist_nonlinear(bond_cache):
+@pytest.mark.parametrize("form", sorted(FORMS))
+def test_notched_block_twist_nonlinear(form):
     """Clamped + twisted notched block (24 s0 rad over the 300 steps): progressive fracture."""
     w = W.notched_block(nx=24, ny=12, nz=10, dx=1e-3, notch_cells=9.5, nsteps=300, seed=3, amp=1e-7)
-    out, phi, ref = run_pair(w, 300, 100, bond_cache=bond_cache)
+    out, phi, ref = run_pair(w, 300, 100, **FORMS[form])
     assert out[-1]["broken"] > 10000
     assert_parity(out, phi, ref)
 
