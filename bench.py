@@ -406,7 +406,7 @@ def run_gpu(args):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "particles": w.n, "directed_bonds": nb, "precision": "fp64",
-                       "graph_chunk": 100, "mapping": {"block": mapping[0], "split": mapping[1]}, "l2": "inputs larger than L2 (neighbour indices %.0f MB)" % (nb * 4 / 1e6),
+                       "graph_chunk": 100, "mapping": {"block": mapping[0], "split": mapping[1], "pairs": int(pairs)}, "l2": "inputs larger than L2 (neighbour indices %.0f MB)" % (nb * 4 / 1e6),
                        "replicas": world},
             "roofline": roofline, "e2e": e2e, "clocks": clocks,
             "gpu_launches": (3 if pairs else 2) * args.steps + 2,  # step kernels + k_set_step + k_flag_nonfinite

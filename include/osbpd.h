@@ -269,9 +269,11 @@ pd_status pd_check_state(pd_ctx* c, double max_abs_u);
 
 /* Picks the launch mapping (threads per block, warps per 32-particle slice) of the step kernels by
  * timing trial_steps steps of every candidate on the context's own data, keeps the fastest, and
- * restores the state, bond status and step count afterwards.  If the environment variable
- * PD_AUTOTUNE_CACHE names a file, results are looked up / appended there under a key made of the
- * problem sizes, precision and device name.  *block / *split (may be NULL) receive the choice. */
+ * restores the state, bond status and step count afterwards.  PD_FP64 contexts with the bond cache
+ * also try both settings of PD_OPT_PAIRS for every mapping and keep the faster (read it back with
+ * pd_get_option).  If the environment variable PD_AUTOTUNE_CACHE names a file, results are looked
+ * up / appended there under a key made of the problem sizes, precision and device name.
+ * *block / *split (may be NULL) receive the choice. */
 pd_status pd_autotune(pd_ctx* c, int32_t trial_steps, int32_t* block, int32_t* split);
 
 pd_status pd_set_option(pd_ctx* c, int32_t option, int64_t value);

@@ -604,7 +604,7 @@ pd_status pd_autotune(pd_ctx* c, int32_t trial_steps, int32_t* block_out, int32_
   for (char* p = key; *p; ++p)
     if (*p == '\n' || *p == '|') *p = ' ';
   const char* cache = std::getenv("PD_AUTOTUNE_CACHE");
-  int best_block = -1, best_split = -1;
+  int best_block = -1, best_split = -1, best_pairs = -1;
   if (cache) {
     if (FILE* f = std::fopen(cache, "r")) {
       char line[700];
@@ -612,10 +612,11 @@ pd_status pd_autotune(pd_ctx* c, int32_t trial_steps, int32_t* block_out, int32_
         char* bar = std::strchr(line, '|');
         if (!bar) continue;
         *bar = 0;
-        int b = 0, s = 0;
-        if (std::strcmp(line, key) == 0 && std::sscanf(bar + 1, "%d %d", &b, &s) == 2) {
+        int b = 0, s = 0, pr = -1;
+        if (std::strcmp(line, key) == 0 && std::sscanf(bar + 1, "%d %d %d", &b, &s, &pr) >= 2) {
           best_block = b;
           best_split = s;
+          best_pairs = pr;
         }
       }
       std::fclose(f);
@@ -674,34 +675,45 @@ pd_status pd_autotune(pd_ctx* c, int32_t trial_steps, int32_t* block_out, int32_
     double best_ms = 1e300;
     const int blocks[] = {64, 128, 256, 512};
     const int splits[] = {1, 2, 4};
+    // FP64 with the pair tables: the pair form (one more launch per step, fewer FP64 instructions)
+    // against the single pass, which wins on small bodies where launches dominate
+    const int pairs0 = c->pairs;
+    const bool try_pairs = c->precision == PD_FP64 && c->pairs_ok && c->bond_cache;
+    const int pair_opts[2] = {1, 0};
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     for (int bl : blocks) {
       for (int sp : splits) {
         if ((bl / 32) % sp) continue;
-        c->block = bl;
-        c->split = sp;
-        if ((st = restore()) != PD_OK) break;
-        run_steps(c, 1);  // warm-up
-        cudaEventRecord(e0, s);
-        st = run_steps(c, trial_steps);
-        cudaEventRecord(e1, s);
+        for (int po = 0; po < (try_pairs ? 2 : 1); ++po) {
+          c->block = bl;
+          c->split = sp;
+          c->pairs = try_pairs ? pair_opts[po] : pairs0;
+          if ((st = restore()) != PD_OK) break;
+          run_steps(c, 1);  // warm-up
+          cudaEventRecord(e0, s);
+          st = run_steps(c, trial_steps);
+          cudaEventRecord(e1, s);
+          if (st != PD_OK) break;
+          if (cudaEventSynchronize(e1) != cudaSuccess) {
+            st = cuda_fail(cudaGetLastError(), "autotune trial");
+            break;
+          }
+          float ms = 0.0f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (ms < best_ms) {
+            best_ms = ms;
+            best_block = bl;
+            best_split = sp;
+            best_pairs = c->pairs;
+          }
+        }
         if (st != PD_OK) break;
-        if (cudaEventSynchronize(e1) != cudaSuccess) {
-          st = cuda_fail(cudaGetLastError(), "autotune trial");
-          break;
-        }
-        float ms = 0.0f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best_ms) {
-          best_ms = ms;
-          best_block = bl;
-          best_split = sp;
-        }
       }
       if (st != PD_OK) break;
     }
+    c->pairs = pairs0;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     pd_status st2 = restore();
@@ -718,13 +730,14 @@ pd_status pd_autotune(pd_ctx* c, int32_t trial_steps, int32_t* block_out, int32_
     if (st2 != PD_OK) return st2;
     if (cache && best_block > 0) {
       if (FILE* f = std::fopen(cache, "a")) {
-        std::fprintf(f, "%s|%d %d\n", key, best_block, best_split);
+        std::fprintf(f, "%s|%d %d %d\n", key, best_block, best_split, best_pairs);
         std::fclose(f);
       }
     }
   }
   c->block = best_block;
   c->split = best_split;
+  if (best_pairs >= 0) c->pairs = best_pairs;
   drop_graphs(c);
   if (block_out) *block_out = best_block;
   if (split_out) *split_out = best_split;
