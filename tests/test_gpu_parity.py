@@ -401,6 +401,27 @@ def test_batch_equals_separate_runs_bitwise():
         assert np.array_equal(u, ub[:, bw.offsets[k]:bw.offsets[k + 1]]), k
 
 
+def test_batch_pair_form_and_option_reporting():
+    """A batch of uneven plates with breaking: the pair form (pairs never cross bodies) equals the
+    single pass bitwise; PD_OPT_PAIRS reads back 1 for FP64 contexts and 0 for mixed ones."""
+    bw = _small_batch(n=6, seed=11)
+    s0s = [s0_of(b) for b in bw.bodies]
+    res = []
+    for pairs in (1, 0):
+        bs = BatchSimulation(bw, s0s)
+        assert B.pd_get_option(bs.h, B.PD_OPT_PAIRS) == 1
+        B.pd_set_option(bs.h, B.PD_OPT_PAIRS, pairs)
+        assert B.pd_get_option(bs.h, B.PD_OPT_PAIRS) == pairs
+        bs.step(200)
+        res.append((bs.state()[0], bs.neighbors()[2], bs.stats()["broken_bonds"]))
+        bs.close()
+    assert res[0][2] > 0 and res[0][2] == res[1][2]
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+    bm = BatchSimulation(bw, s0s, precision=PD_MIXED)
+    assert B.pd_get_option(bm.h, B.PD_OPT_PAIRS) == 0
+    bm.close()
+
+
 def test_batch_vs_oracle():
     bw = _small_batch(n=3, seed=9)
     s0s = [s0_of(b) for b in bw.bodies]
