@@ -764,26 +764,40 @@ __global__ void __launch_bounds__(512) k_pass1a_f64p(StepArgs a, const double4* 
   const int32_t* __restrict__ tw = a.twin + t.base + t.lane;
   const double4* __restrict__ ta = a.bA + t.base + t.lane;
   double* td = a.bd;
-  for (int k = k_lo + t.sub; k < k_hi; k += SPLIT) {
-    const bool mine = k >= own && k < cnt;
+  // the owned-slot streams (index, table row, twin entry) of the next slot are loaded while the
+  // current slot's displacement gather and arithmetic run
+  int k = k_lo + t.sub;
+  bool mn = k < k_hi && k >= own && k < cnt;
+  int32_t jn = (int32_t)t.i, ten = 0;
+  double4 gn = make_double4(0.0, 0.0, 0.0, 0.0);
+  if (mn) {
+    jn = cl[(int64_t)k << 5];
+    gn = ta[(int64_t)k << 5];
+    ten = tw[(int64_t)k << 5];
+  }
+  for (; k < k_hi; k += SPLIT) {
+    const bool mine = mn;
+    const int32_t j = jn, te = ten;
+    const double4 g = gn;
+    const double4 uj = disp[j];
+    const int kn = k + SPLIT;
+    mn = kn < k_hi && kn >= own && kn < cnt;
+    if (mn) {
+      jn = cl[(int64_t)kn << 5];
+      gn = ta[(int64_t)kn << 5];
+      ten = tw[(int64_t)kn << 5];
+    }
     const int64_t e = t.base + t.lane + ((int64_t)k << 5);
-    double d = 0.0, thr = 0.0;
-    int32_t te = 0;
+    double d = g.x * (uj.x - ui.x) + g.y * (uj.y - ui.y);
+    if (DIM == 3) d = fma(g.z, uj.z - ui.z, d);
     if (mine) {
-      const int32_t j = cl[(int64_t)k << 5];
-      const double4 g = ta[(int64_t)k << 5];
-      const double4 uj = disp[j];
-      te = tw[(int64_t)k << 5];
-      d = g.x * (uj.x - ui.x) + g.y * (uj.y - ui.y);
-      if (DIM == 3) d = fma(g.z, uj.z - ui.z, d);
-      thr = g.w;
       td[e] = d;
       td[te] = d;
     }
     if (a.check) {
       const uint32_t wd = bw[k];  // this warp's owned bits change only here
       const bool brk = mine && can_break && ((wd >> t.lane) & 1u) &&
-                       __double_as_longlong(d) >= __double_as_longlong(thr);  // d >= s0 |xi|^2
+                       __double_as_longlong(d) >= __double_as_longlong(g.w);  // d >= s0 |xi|^2
       const unsigned m = __ballot_sync(kFull, brk);
       if (m) {
         if (t.lane == 0) {
@@ -792,7 +806,7 @@ __global__ void __launch_bounds__(512) k_pass1a_f64p(StepArgs a, const double4* 
         }
         if (brk) {
           atomicAnd(a.bits + (te >> 5), ~(1u << (te & 31)));
-          a.dirty[a.col[e] >> 5] = 1;
+          a.dirty[j >> 5] = 1;
         }
       }
     }
@@ -814,17 +828,21 @@ __global__ void __launch_bounds__(512) k_pass1b_f64p(StepArgs a, const double4* 
     int32_t jn[U];
     uint32_t wn[U];
     load_slots<U, SPLIT>(t, cl, bw, t.sub, jn, wn);
+    double dn[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) dn[u] = td[(int64_t)min(t.sub + u * SPLIT, t.W - 1) << 5];
     for (int k0 = t.sub; k0 < t.W; k0 += U * SPLIT) {
       uint32_t wd[U];
       double d[U], v[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const int k = min(k0 + u * SPLIT, t.W - 1);
         wd[u] = wn[u];
-        d[u] = td[(int64_t)k << 5];
+        d[u] = dn[u];
         v[u] = disp[jn[u]].w;
       }
       load_slots<U, SPLIT>(t, cl, bw, k0 + U * SPLIT, jn, wn);
+#pragma unroll
+      for (int u = 0; u < U; ++u) dn[u] = td[(int64_t)min(k0 + (U + u) * SPLIT, t.W - 1) << 5];
 #pragma unroll
       for (int u = 0; u < U; ++u)
         if ((wd[u] >> t.lane) & 1u) acc[0] = fma(v[u], d[u], acc[0]);
