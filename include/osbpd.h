@@ -287,6 +287,19 @@ pd_status pd_get_profile(pd_ctx* c, int32_t kernel, double* total_ms, int64_t* l
 /* Number of particles, dimension and storage of the context (for sizing host buffers). */
 pd_status pd_get_info(pd_ctx* c, int64_t* n, int32_t* dim, int64_t* device_bytes);
 
+/* Checkpoint / resume (the paper has no counterpart; a library convenience for long runs).
+ * pd_save_state writes the dynamic state -- u, v, the bond status, the step count and whether the
+ * failure check on the current state is still pending -- to the file `path` (created or truncated),
+ * with a header identifying the problem (a hash of the parameters, the particle positions and the
+ * built family) and a checksum.  pd_load_state reads such a file into a context built the same way
+ * (same particles, parameters and cracks; it may be a different context or process) and continues
+ * exactly: N steps equal k steps, save, load, N - k steps, bit for bit.  The relaxation solver
+ * restarts from rest after a load, as after pd_set_state.  Errors: PD_ERR_ARG for a path that cannot
+ * be opened, a file that is not a checkpoint, a checksum mismatch or a problem that differs (the
+ * context is then unchanged); PD_ERR_CUDA for device failures.  Both synchronize. */
+pd_status pd_save_state(pd_ctx* c, const char* path);
+pd_status pd_load_state(pd_ctx* c, const char* path);
+
 /* pd_step_noalloc -- one explicit time step that allocates no memory at all.
  *
  * The paper has no counterpart; this is a library convenience for callers that cannot allocate

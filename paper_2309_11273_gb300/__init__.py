@@ -81,6 +81,14 @@ class Simulation:
     def get_option(self, opt) -> int:
         return B.pd_get_option(self.h, opt)
 
+    def save_state(self, path):
+        """Checkpoint (u, v, bond status, step count) to a file; see pd_save_state."""
+        B.pd_save_state(self.h, path)
+
+    def load_state(self, path):
+        """Resume from a checkpoint of the same problem; see pd_load_state."""
+        B.pd_load_state(self.h, path)
+
     def close(self):
         if self.h:
             B.pd_destroy(self.h)

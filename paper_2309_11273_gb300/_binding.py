@@ -35,8 +35,8 @@ STATUS_NAMES = {0: "PD_OK", -1: "PD_ERR_ARG", -2: "PD_ERR_STATE", -3: "PD_ERR_OO
 EXPORTED = ["pd_critical_stretch", "pd_material_constants", "pd_set_prescribed_velocity", "pd_create_particles", "pd_create_batch", "pd_build_neighbors",
             "pd_set_bc", "pd_set_state", "pd_step", "pd_sync", "pd_get_damage", "pd_get_state",
             "pd_num_bonds", "pd_get_neighbors", "pd_get_stats", "pd_check_state", "pd_autotune",
-            "pd_set_option", "pd_get_option", "pd_get_profile", "pd_get_info", "pd_step_noalloc",
-            "pd_last_error", "pd_destroy"]
+            "pd_set_option", "pd_get_option", "pd_get_profile", "pd_get_info", "pd_save_state",
+            "pd_load_state", "pd_step_noalloc", "pd_last_error", "pd_destroy"]
 
 
 class pd_params(ctypes.Structure):
@@ -106,6 +106,8 @@ def lib(path: str = LIB_PATH):
             L.pd_get_option.argtypes = [_vp, ctypes.c_int32, _i64]
             L.pd_get_profile.argtypes = [_vp, ctypes.c_int32, _d, _i64, ctypes.c_int32]
             L.pd_get_info.argtypes = [_vp, _i64, _i32, _i64]
+            L.pd_save_state.argtypes = [_vp, ctypes.c_char_p]
+            L.pd_load_state.argtypes = [_vp, ctypes.c_char_p]
             L.pd_step_noalloc.argtypes = ([ctypes.c_int32] + [ctypes.c_double] * 4 + [ctypes.c_int64]
                                           + [_vp] * 12 + [_vp])
             L.pd_last_error.restype = ctypes.c_char_p
@@ -283,6 +285,14 @@ def pd_get_profile(h, kernel, reset=False):
     ms, cnt = ctypes.c_double(), ctypes.c_int64()
     _check(lib().pd_get_profile(h, int(kernel), ctypes.byref(ms), ctypes.byref(cnt), int(bool(reset))))
     return ms.value, int(cnt.value)
+
+
+def pd_save_state(h, path):
+    _check(lib().pd_save_state(h, os.fsencode(path)))
+
+
+def pd_load_state(h, path):
+    _check(lib().pd_load_state(h, os.fsencode(path)))
 
 
 def pd_get_info(h):

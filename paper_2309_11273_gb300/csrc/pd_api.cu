@@ -582,6 +582,146 @@ pd_status pd_get_profile(pd_ctx* c, int32_t kernel, double* total_ms, int64_t* l
   return PD_OK;
 }
 
+namespace {
+
+// 64-bit FNV-1a (Fowler, Noll and Vo): the checkpoint's checksum and problem hash.
+constexpr uint64_t kFnvBasis = 14695981039346656037ull;
+uint64_t fnv1a(uint64_t h, const void* p, size_t bytes) {
+  const unsigned char* b = static_cast<const unsigned char*>(p);
+  for (size_t k = 0; k < bytes; ++k) {
+    h ^= b[k];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+struct CheckpointHeader {
+  char magic[8];  // "OSBPDCK1"
+  uint32_t version;
+  int32_t dim;
+  int64_t n, n_pad, nentries, nbonds, steps;
+  int32_t precision, kinematics, nbodies, flags;  // flags: 1 check pending, 2 skip next check
+  uint64_t problem;  // hash of the parameters, positions and family
+};
+const char kCkptMagic[8] = {'O', 'S', 'B', 'P', 'D', 'C', 'K', '1'};
+
+// Hash of everything that fixes the meaning of a state: sizes, per-body parameters (not the device
+// or stream), and the device copies of the positions and of the built family.
+pd_status problem_hash(pd_ctx* c, uint64_t* out) {
+  uint64_t h = kFnvBasis;
+  const int64_t sizes[4] = {c->n, c->n_pad, c->nentries, c->nbonds};
+  h = fnv1a(h, sizes, sizeof(sizes));
+  const int32_t kinds[3] = {c->dim, c->precision, c->kin};
+  h = fnv1a(h, kinds, sizeof(kinds));
+  for (const pd_params& p : c->prm) {
+    const double v[8] = {p.E, p.nu, p.rho, p.horizon, p.s0, p.dt, p.band_safety, 0.0};
+    const int32_t k[4] = {p.model, p.precision, p.ordering, p.kinematics};
+    h = fnv1a(h, v, sizeof(v));
+    h = fnv1a(h, k, sizeof(k));
+  }
+  std::vector<double4> pos(c->n_pad);
+  std::vector<int32_t> col(c->nentries);
+  PD_CUDA(cudaMemcpyAsync(pos.data(), c->pos, sizeof(double4) * c->n_pad, cudaMemcpyDeviceToHost, c->stream));
+  PD_CUDA(cudaMemcpyAsync(col.data(), c->col, sizeof(int32_t) * c->nentries, cudaMemcpyDeviceToHost, c->stream));
+  PD_CUDA(cudaStreamSynchronize(c->stream));
+  h = fnv1a(h, pos.data(), sizeof(double4) * pos.size());
+  h = fnv1a(h, col.data(), sizeof(int32_t) * col.size());
+  *out = h;
+  return PD_OK;
+}
+
+}  // namespace
+
+pd_status pd_save_state(pd_ctx* c, const char* path) {
+  pd_status st = check_ctx(c, true);
+  if (st != PD_OK) return st;
+  if (!path) return fail(PD_ERR_ARG, "path is NULL");
+  if ((st = check_device_error(c)) != PD_OK) return st;
+  CheckpointHeader hd{};
+  std::memcpy(hd.magic, kCkptMagic, 8);
+  hd.version = 1;
+  hd.dim = c->dim;
+  hd.n = c->n;
+  hd.n_pad = c->n_pad;
+  hd.nentries = c->nentries;
+  hd.nbonds = c->nbonds;
+  hd.steps = c->steps;
+  hd.precision = c->precision;
+  hd.kinematics = c->kin;
+  hd.nbodies = c->nbodies;
+  hd.flags = (c->check_pending ? 1 : 0) | (c->skip_next_check ? 2 : 0);
+  if ((st = problem_hash(c, &hd.problem)) != PD_OK) return st;
+  const size_t nw = (size_t)std::max<int64_t>(c->nentries / 32, 1);
+  std::vector<double4> u(c->n_pad), v(c->n_pad);
+  std::vector<uint32_t> bits(nw);
+  PD_CUDA(cudaMemcpyAsync(u.data(), c->disp[c->cur], sizeof(double4) * c->n_pad, cudaMemcpyDeviceToHost, c->stream));
+  PD_CUDA(cudaMemcpyAsync(v.data(), c->vel, sizeof(double4) * c->n_pad, cudaMemcpyDeviceToHost, c->stream));
+  PD_CUDA(cudaMemcpyAsync(bits.data(), c->bits, sizeof(uint32_t) * nw, cudaMemcpyDeviceToHost, c->stream));
+  PD_CUDA(cudaStreamSynchronize(c->stream));
+  uint64_t sum = kFnvBasis;
+  sum = fnv1a(sum, &hd, sizeof(hd));
+  sum = fnv1a(sum, u.data(), sizeof(double4) * u.size());
+  sum = fnv1a(sum, v.data(), sizeof(double4) * v.size());
+  sum = fnv1a(sum, bits.data(), sizeof(uint32_t) * bits.size());
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(PD_ERR_ARG, std::string("cannot open ") + path + " for writing");
+  bool ok = std::fwrite(&hd, sizeof(hd), 1, f) == 1 && std::fwrite(u.data(), sizeof(double4), u.size(), f) == u.size() &&
+            std::fwrite(v.data(), sizeof(double4), v.size(), f) == v.size() &&
+            std::fwrite(bits.data(), sizeof(uint32_t), bits.size(), f) == bits.size() &&
+            std::fwrite(&sum, sizeof(sum), 1, f) == 1;
+  ok = (std::fclose(f) == 0) && ok;
+  if (!ok) return fail(PD_ERR_ARG, std::string("write to ") + path + " failed");
+  return PD_OK;
+}
+
+pd_status pd_load_state(pd_ctx* c, const char* path) {
+  pd_status st = check_ctx(c, true);
+  if (st != PD_OK) return st;
+  if (!path) return fail(PD_ERR_ARG, "path is NULL");
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(PD_ERR_ARG, std::string("cannot open ") + path);
+  CheckpointHeader hd{};
+  const size_t nw = (size_t)std::max<int64_t>(c->nentries / 32, 1);
+  std::vector<double4> u(c->n_pad), v(c->n_pad);
+  std::vector<uint32_t> bits(nw);
+  uint64_t sum_file = 0;
+  bool ok = std::fread(&hd, sizeof(hd), 1, f) == 1 && std::memcmp(hd.magic, kCkptMagic, 8) == 0 && hd.version == 1 &&
+            hd.dim == c->dim && hd.n == c->n && hd.n_pad == c->n_pad && hd.nentries == c->nentries &&
+            hd.nbonds == c->nbonds && hd.precision == c->precision && hd.kinematics == c->kin &&
+            hd.nbodies == c->nbodies;
+  if (ok)
+    ok = std::fread(u.data(), sizeof(double4), u.size(), f) == u.size() &&
+         std::fread(v.data(), sizeof(double4), v.size(), f) == v.size() &&
+         std::fread(bits.data(), sizeof(uint32_t), bits.size(), f) == bits.size() &&
+         std::fread(&sum_file, sizeof(sum_file), 1, f) == 1;
+  std::fclose(f);
+  if (!ok) return fail(PD_ERR_ARG, std::string(path) + " is not a checkpoint of this problem");
+  uint64_t sum = kFnvBasis;
+  sum = fnv1a(sum, &hd, sizeof(hd));
+  sum = fnv1a(sum, u.data(), sizeof(double4) * u.size());
+  sum = fnv1a(sum, v.data(), sizeof(double4) * v.size());
+  sum = fnv1a(sum, bits.data(), sizeof(uint32_t) * bits.size());
+  if (sum != sum_file) return fail(PD_ERR_ARG, std::string(path) + ": checksum mismatch");
+  uint64_t problem = 0;
+  if ((st = problem_hash(c, &problem)) != PD_OK) return st;
+  if (problem != hd.problem)
+    return fail(PD_ERR_ARG, std::string(path) + " was written for different particles, parameters or family");
+  if ((st = check_device_error(c)) != PD_OK) return st;
+  PD_CUDA(cudaMemcpyAsync(c->disp[c->cur], u.data(), sizeof(double4) * c->n_pad, cudaMemcpyHostToDevice, c->stream));
+  PD_CUDA(cudaMemcpyAsync(c->vel, v.data(), sizeof(double4) * c->n_pad, cudaMemcpyHostToDevice, c->stream));
+  PD_CUDA(cudaMemcpyAsync(c->bits, bits.data(), sizeof(uint32_t) * nw, cudaMemcpyHostToDevice, c->stream));
+  if ((st = sync_shadow(c)) != PD_OK) return st;
+  if (c->dirty) PD_CUDA(cudaMemsetAsync(c->dirty, 0, (size_t)c->nslices, c->stream));
+  PD_CUDA(cudaStreamSynchronize(c->stream));
+  c->steps = hd.steps;
+  c->check_pending = (hd.flags & 1) != 0;
+  c->skip_next_check = (hd.flags & 2) != 0;
+  c->bs_stale = true;  // the loaded status bits
+  c->adr_restart = true;
+  drop_graphs(c);
+  return PD_OK;
+}
+
 pd_status pd_get_info(pd_ctx* c, int64_t* n, int32_t* dim, int64_t* device_bytes) {
   pd_status st = check_ctx(c, false);
   if (st != PD_OK) return st;
