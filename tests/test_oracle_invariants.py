@@ -200,3 +200,20 @@ def test_thread_count_does_not_change_results():
         res.append(sim.u.copy())
     O.set_threads(orig)
     assert np.array_equal(res[0], res[1])
+
+
+def test_edge_traction_response_is_mirror_symmetric():
+    """The edge traction of the plate workloads (body force +-sigma/dx on the top and bottom rows)
+    loads the uncracked plate symmetrically about its mid-plane: u_x(x, y) = u_x(x, -y) and
+    u_y(x, y) = -u_y(x, -y) to rounding (mirrored particles sum their bonds in mirrored order).  A
+    traction applied to one row only, on the wrong row or with one sign flipped breaks it."""
+    w = W.cracked_plate(nx=40, ny=16, dx=2.5e-4, crack_cells=20.125, sigma=5e6)
+    sim = O.OracleSim(w.model, w.E, w.nu, w.rho, w.delta, 0.0, w.dt, w.x, w.y, None, w.vol)
+    sim.set_bc(None, w.b)
+    sim.step(300)
+    u = sim.u.reshape(2, 16, 40)  # [component, row j, column i], rows at y = (j + 1/2) dx
+    scale = np.abs(u).max()
+    assert scale > 0.0
+    assert np.abs(u[0] - u[0, ::-1]).max() <= 1e-12 * scale
+    assert np.abs(u[1] + u[1, ::-1]).max() <= 1e-12 * scale
+    assert u[1, -1].mean() > 0.0 > u[1, 0].mean()  # the top row moves up, the bottom row down
