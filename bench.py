@@ -66,9 +66,11 @@ FLOPS_BOND_NL = {1: 36.0, 2: 44.0}
 # for pass 2 (rsqrt counted as one flop).
 FLOPS_BOND_NL_TABLED = {1: 29.0, 2: 19.0}
 # ... and its pair form, per directed bond: pass 1a forms the geometry, root, divide and failure test
-# once per bond and both entries' theta terms (26 flop per pair without the theta sum, + 2 x 2 for
-# the two terms: 15 per directed bond), 1b adds the terms (1), pass 2 as above.
-FLOPS_BOND_NL_PAIRS = {"k_pass1a_nlp": 15.0, "k_pass1b_nlp": 1.0, "k_pass2_nlt": 19.0}
+# once per bond, both entries' theta terms and the direction Y/|Y| (26 flop per pair without the
+# theta sum, + 2 x 2 for the two terms, + 3 for the direction: 16.5 per directed bond), 1b adds the
+# terms (1), pass 2 forms the coefficient from the tables and the force along the stored direction
+# (12).
+FLOPS_BOND_NL_PAIRS = {"k_pass1a_nlp": 16.5, "k_pass1b_nlp": 1.0, "k_pass2_nlp": 12.0}
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12  # 2 DFMA/clk/SM x 2 flop x 152 SMs x 2.07 GHz
 
 
@@ -514,7 +516,7 @@ def run_forms(args, stream, dev, world, fp64_value, nb, hbm, hbm_note):
     npairs = ntab and B.pd_get_option(sim.h, B.PD_OPT_PAIRS) == 1
     sim.close()
     if npairs:
-        nkerns = {"k_pass1a_nlp": prof["pass1_ms"], "k_pass1b_nlp": prof["pass1b_ms"], "k_pass2_nlt": prof["pass2_ms"]}
+        nkerns = {"k_pass1a_nlp": prof["pass1_ms"], "k_pass1b_nlp": prof["pass1b_ms"], "k_pass2_nlp": prof["pass2_ms"]}
         nfls = FLOPS_BOND_NL_PAIRS
         nform = "pair"
     else:

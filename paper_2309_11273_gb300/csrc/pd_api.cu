@@ -63,6 +63,8 @@ void free_build(pd_ctx* c) {
   c->bs_stale = true;
   c->bE = nullptr;
   c->bt = nullptr;
+  c->bY = nullptr;
+  c->bX = nullptr;
   c->lam = nullptr;
   c->gnew = c->gold = nullptr;
   c->adr_part = c->adr_st = nullptr;

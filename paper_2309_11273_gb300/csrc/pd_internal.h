@@ -89,6 +89,8 @@ struct StepArgs {
   uint8_t* dirty;          // FP64 pair path: per slice, bS needs recomputing
   double2* bE;             // tabled nonlinear path: per slot (e, 1 / |Y|), written by pass 1 (bA = (xi, |xi|))
   double* bt;              // tabled nonlinear pair form: per slot V_j |xi| e, written by pass 1a
+  double4* bY;             // tabled nonlinear pair form: per slot (Y/|Y|, e), written by pass 1a
+  const double2* bX;       // tabled nonlinear pair form: per slot (|xi| V_j, V_j), built once
   int expire;              // testing (PD_OPT_EXPIRE_WAITS): staged kernels skip their first copy
   double uscale;           // mixed path: the FP32 shadow holds u * uscale (1, or 1/Q for nonlinear bonds)
   int adr;                 // PD_SOLVER_ADR: pass 2 stores g = f + b in gnew instead of updating
@@ -162,6 +164,8 @@ struct pd_ctx {
   bool bs_stale = true;           // bS no longer matches the status bits (recomputed before a step)
   double2* bE = nullptr;          // nonlinear FP64: per-slot (e, 1/|Y|) of the current step
   double* bt = nullptr;           // nonlinear FP64 pair form: per-slot theta term V_j |xi| e
+  double4* bY = nullptr;          // nonlinear FP64 pair form: per-slot (Y/|Y|, e)
+  double2* bX = nullptr;          // nonlinear FP64 pair form: per-slot (|xi| V_j, V_j)
   int bond_cache = 1;             // use the table in the FP64 path
   int pairs = 1;                  // FP64 tabled path: evaluate each bond once per pair (needs pairs_ok)
   int stage = 1;                  // mixed path: TMA-staged index streams (split 1)

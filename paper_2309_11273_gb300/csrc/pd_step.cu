@@ -543,8 +543,10 @@ __global__ void __launch_bounds__(512) k_pass2_nlt(StepArgs a, const double4* __
 // Pair form of the tabled nonlinear pass 1.  Y and u_j - u_i change sign between the two entries of a
 // bond and |Y|^2 - |xi|^2 does not, so the failure test, e and 1/|Y| are the same numbers at both
 // ends: pass 1a forms them once, at the owned entry, clears both bits of a broken bond, and writes
-// (e, 1/|Y|) and the theta terms V_j |xi| e and V_i |xi| e of both entries; pass 1b sums theta.  The
-// root and the divide, most of the FP64 work of the single pass, run once per bond.
+// (M = Y/|Y|, e) and the theta terms V_j |xi| e and V_i |xi| e of both entries (M changes sign);
+// pass 1b sums theta, and pass 2 takes the bond's direction and extension from the table instead of
+// recomputing Y from the displacements.  The root and the divide, most of the FP64 work of the
+// single pass, run once per bond.
 template <int DIM, int SPLIT>
 __global__ void __launch_bounds__(512) k_pass1a_nlp(StepArgs a, const double4* __restrict__ disp) {
   const SliceIdx t = slice_index<SPLIT>(a.n_pad, a.slice_ptr);
@@ -563,7 +565,7 @@ __global__ void __launch_bounds__(512) k_pass1a_nlp(StepArgs a, const double4* _
   for (int k = k_lo + t.sub; k < k_hi; k += SPLIT) {
     const bool mine = k >= own && k < cnt;
     const int64_t e = t.base + t.lane + ((int64_t)k << 5);
-    double p = 0.0, yl2 = 0.0, xl = 0.0, vj = 0.0;
+    double p = 0.0, yl2 = 0.0, xl = 0.0, vj = 0.0, yx = 0.0, yy = 0.0, yz = 0.0;
     int32_t te = 0;
     if (mine) {
       const int32_t j = cl[(int64_t)k << 5];
@@ -571,7 +573,9 @@ __global__ void __launch_bounds__(512) k_pass1a_nlp(StepArgs a, const double4* _
       const double4 uj = disp[j];
       te = tw[(int64_t)k << 5];
       const double hx = uj.x - ui.x, hy = uj.y - ui.y, hz = DIM == 3 ? uj.z - ui.z : 0.0;
-      const double yx = g.x + hx, yy = g.y + hy, yz = g.z + hz;
+      yx = g.x + hx;
+      yy = g.y + hy;
+      yz = g.z + hz;
       p = hx * (g.x + yx) + hy * (g.y + yy);
       if (DIM == 3) p = fma(hz, g.z + yz, p);
       yl2 = yx * yx + yy * yy;
@@ -592,8 +596,9 @@ __global__ void __launch_bounds__(512) k_pass1a_nlp(StepArgs a, const double4* _
     if (intact) {
       const double ry = rsqrt(yl2);
       const double ev = p / fma(yl2, ry, xl);
-      a.bE[e] = make_double2(ev, ry);
-      a.bE[te] = make_double2(ev, ry);
+      const double mx = ry * yx, my = ry * yy, mz = ry * yz;  // M = Y / |Y| (Eq 1.13), -M at j
+      a.bY[e] = make_double4(mx, my, mz, ev);
+      a.bY[te] = make_double4(-mx, -my, -mz, ev);
       a.bt[e] = (vj * xl) * ev;       // Eq 1.6 term of entry (i, j): w |xi| e V_j
       a.bt[te] = (ui.w * xl) * ev;    // and of entry (j, i): w |xi| e V_i
     }
@@ -619,6 +624,72 @@ __global__ void __launch_bounds__(512) k_pass1b_nlp(StepArgs a, int write_theta)
     const double mu = a.mu[t.i];
     a.theta[t.i] = th;
     a.thm[t.i] = make_double2(a.bp[b].Kp * (th * mu), a.bp[b].G * mu);
+  }
+}
+
+// Pass 2 of the nonlinear pair form: Eq 1.14 for both ends along M (Eq 1.13),
+// f_i = sum_j [(K - G/3)(theta_i/m_i + theta_j/m_j) |xi| V_j + G (1/m_i + 1/m_j) e V_j] M, with
+// (M, e) from pass 1a and (|xi| V_j, V_j) from a per-slot table built once.
+template <int DIM, int SPLIT>
+__global__ void __launch_bounds__(512) k_pass2_nlp(StepArgs a, const double4* __restrict__ disp,
+                                                    double4* __restrict__ disp_out) {
+  const SliceIdx t = slice_index<SPLIT>(a.n_pad, a.slice_ptr);
+  double f[3] = {0.0, 0.0, 0.0};
+  int b = 0;
+  if (t.active) {
+    b = a.body ? a.body[t.i] : 0;
+    const double2 ti = a.thm[t.i];
+    const uint32_t* __restrict__ bw = a.bits + (t.base >> 5);
+    const int32_t* __restrict__ cl = a.col + t.base + t.lane;
+    const double4* __restrict__ ty = a.bY + t.base + t.lane;
+    const double2* __restrict__ tx = a.bX + t.base + t.lane;
+    constexpr int U = 4;
+    int32_t jn[U];
+    uint32_t wn[U];
+    load_slots<U, SPLIT>(t, cl, bw, t.sub, jn, wn);
+    for (int k0 = t.sub; k0 < t.W; k0 += U * SPLIT) {
+      uint32_t wd[U];
+      double4 y[U];
+      double2 x[U], tj[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int k = min(k0 + u * SPLIT, t.W - 1);
+        wd[u] = wn[u];
+        y[u] = ty[(int64_t)k << 5];
+        x[u] = tx[(int64_t)k << 5];
+        tj[u] = a.thm[jn[u]];
+      }
+      load_slots<U, SPLIT>(t, cl, bw, k0 + U * SPLIT, jn, wn);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        double c = fma(ti.x + tj[u].x, x[u].x, (ti.y + tj[u].y) * (y[u].w * x[u].y));
+        c = ((wd[u] >> t.lane) & 1u) ? c : 0.0;  // broken and unused slots
+        f[0] = fma(c, y[u].x, f[0]);
+        f[1] = fma(c, y[u].y, f[1]);
+        if (DIM == 3) f[2] = fma(c, y[u].z, f[2]);
+      }
+    }
+  }
+  split_reduce<SPLIT, 3>(f);
+  if (t.active && t.sub == 0) {
+    double4 u;
+    update(a, t.i, b, f, disp, disp_out, u);
+  }
+}
+
+// (|xi| V_j, V_j) per slot for k_pass2_nlp, |xi| as in k_bond_tables_nl.
+template <int DIM>
+__global__ void k_bond_tables_nlp(StepArgs a, double2* __restrict__ bX) {
+  const SliceIdx t = slice_index<1>(a.n_pad, a.slice_ptr);
+  if (!t.active) return;
+  const double4 pi = a.pos[t.i];
+  const double4 zero = make_double4(0.0, 0.0, 0.0, 0.0);
+  for (int k = 0; k < t.W; ++k) {
+    const int64_t e = t.base + t.lane + ((int64_t)k << 5);
+    const double4 pj = a.pos[a.col[e]];
+    double ex, ey, ez, d, q;
+    bond_f64<DIM>(pi, pj, zero, zero, ex, ey, ez, d, q);
+    bX[e] = make_double2(sqrt(q) * pj.w, pj.w);
   }
 }
 
@@ -1898,9 +1969,11 @@ StepArgs make_args(pd_ctx* c) {
   a.bd = c->bond_cache ? c->bd : nullptr;
   a.bS = c->bond_cache ? c->bS : nullptr;
   a.cnt = c->cnt;
-  const bool pairs_ready = c->kin == PD_NONLINEAR ? c->bt != nullptr : c->dirty != nullptr;
+  const bool pairs_ready = c->kin == PD_NONLINEAR ? c->bX != nullptr : c->dirty != nullptr;
   a.own0 = (c->bond_cache && c->pairs && c->pairs_ok && pairs_ready) ? c->own0 : nullptr;
   a.bt = c->bt;
+  a.bY = c->bY;
+  a.bX = c->bX;
   a.twin = c->twin;
   a.dirty = c->dirty;
   a.bE = c->bond_cache ? c->bE : nullptr;
@@ -1955,7 +2028,9 @@ void launch_pass1(pd_ctx* c, const StepArgs& a, int write_theta, unsigned grid, 
 
 template <int DIM, int SPLIT>
 void launch_pass2(pd_ctx* c, const StepArgs& a, unsigned grid, int block, size_t sm) {
-  if (c->kin == PD_NONLINEAR && a.bA)
+  if (c->kin == PD_NONLINEAR && a.bA && a.own0)
+    k_pass2_nlp<DIM, SPLIT><<<grid, block, sm, c->stream>>>(a, c->disp[c->cur], c->disp[c->cur ^ 1]);
+  else if (c->kin == PD_NONLINEAR && a.bA)
     k_pass2_nlt<DIM, SPLIT><<<grid, block, sm, c->stream>>>(a, c->disp[c->cur], c->disp[c->cur ^ 1]);
   else if (c->kin == PD_NONLINEAR)
     k_pass2_nl<DIM, SPLIT><<<grid, block, sm, c->stream>>>(a, c->disp[c->cur], c->disp[c->cur ^ 1]);
@@ -2058,6 +2133,15 @@ pd_status ensure_bond_cache(pd_ctx* c) {
     if (c->pairs_ok) {
       if ((st = alloc(c, &c->bt, ne)) != PD_OK) return st;
       PD_CUDA(cudaMemsetAsync(c->bt, 0, sizeof(double) * ne, c->stream));
+      if ((st = alloc(c, &c->bY, ne)) != PD_OK) return st;
+      PD_CUDA(cudaMemsetAsync(c->bY, 0, sizeof(double4) * ne, c->stream));
+      if ((st = alloc(c, &c->bX, ne)) != PD_OK) return st;
+      StepArgs ax = make_args(c);
+      if (c->dim == 3)
+        k_bond_tables_nlp<3><<<grid, tb, 0, c->stream>>>(ax, c->bX);
+      else
+        k_bond_tables_nlp<2><<<grid, tb, 0, c->stream>>>(ax, c->bX);
+      PD_CUDA(cudaGetLastError());
     }
     StepArgs a = make_args(c);
     if (c->dim == 3)
