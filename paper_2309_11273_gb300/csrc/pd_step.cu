@@ -540,6 +540,11 @@ __global__ void __launch_bounds__(512) k_pass2_nlt(StepArgs a, const double4* __
   }
 }
 
+// -x exactly, by the sign bit (on the integer pipe rather than the FP64 one).
+__device__ __forceinline__ double flip_sign(double x) {
+  return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull);
+}
+
 // Pair form of the tabled nonlinear pass 1.  Y and u_j - u_i change sign between the two entries of a
 // bond and |Y|^2 - |xi|^2 does not, so the failure test, e and 1/|Y| are the same numbers at both
 // ends: pass 1a forms them once, at the owned entry, clears both bits of a broken bond, and writes
@@ -598,7 +603,7 @@ __global__ void __launch_bounds__(512) k_pass1a_nlp(StepArgs a, const double4* _
       const double ev = p / fma(yl2, ry, xl);
       const double mx = ry * yx, my = ry * yy, mz = ry * yz;  // M = Y / |Y| (Eq 1.13), -M at j
       a.bY[e] = make_double4(mx, my, mz, ev);
-      a.bY[te] = make_double4(-mx, -my, -mz, ev);
+      a.bY[te] = make_double4(flip_sign(mx), flip_sign(my), flip_sign(mz), ev);
       a.bt[e] = (vj * xl) * ev;       // Eq 1.6 term of entry (i, j): w |xi| e V_j
       a.bt[te] = (ui.w * xl) * ev;    // and of entry (j, i): w |xi| e V_i
     }
