@@ -8,10 +8,13 @@
 //           F_i / V_i = sum_j rho_ij V_j [ (K - G/3)(theta_i/m_i + theta_j/m_j)
 //                                         + G (1/m_i + 1/m_j) xi.(u_j - u_i) / |xi|^2 ] xi,
 //           followed by the explicit update of Eq 2.11 and the boundary conditions (Appendix B).
-// Both passes gather: every directed bond is visited from its own particle, so no atomics are
-// needed and every sum runs in a fixed order.  A warp owns one 32-particle slice (one particle
+// Both passes gather: every directed bond is visited from its own particle and every sum runs in a
+// fixed order, with no floating-point atomics.  A warp owns one 32-particle slice (one particle
 // per lane); with SPLIT > 1 several warps share a slice, each taking every SPLIT-th slot, and
-// their partial sums are combined in shared memory in a fixed order.
+// their partial sums are combined in shared memory in a fixed order.  The tabled FP64 kernels run
+// pass 1 in a pair form by default: its first kernel forms each bond's extension once, at the entry
+// that owns the bond, and writes it to both entries (the other entry's status bit is cleared with
+// an atomic AND); its second kernel forms the dilatation sums.
 //
 // The break test is evaluated without square roots: s = e/|xi| >= s0  <=>  xi.du >= s0 |xi|^2.
 #include <algorithm>
