@@ -586,11 +586,20 @@ pd_status pd_get_profile(pd_ctx* c, int32_t kernel, double* total_ms, int64_t* l
 
 namespace {
 
-// 64-bit FNV-1a (Fowler, Noll and Vo): the checkpoint's checksum and problem hash.
+// The checkpoint's checksum and problem hash: the 64-bit FNV-1a scheme (Fowler, Noll and Vo) applied
+// to 8-byte words (then to the trailing bytes), which hashes the gigabytes of a large family eight
+// times faster than byte by byte.
 constexpr uint64_t kFnvBasis = 14695981039346656037ull;
 uint64_t fnv1a(uint64_t h, const void* p, size_t bytes) {
   const unsigned char* b = static_cast<const unsigned char*>(p);
-  for (size_t k = 0; k < bytes; ++k) {
+  size_t k = 0;
+  for (; k + 8 <= bytes; k += 8) {
+    uint64_t w;
+    std::memcpy(&w, b + k, 8);
+    h ^= w;
+    h *= 1099511628211ull;
+  }
+  for (; k < bytes; ++k) {
     h ^= b[k];
     h *= 1099511628211ull;
   }
