@@ -149,8 +149,9 @@ typedef enum {
                               extension (linearized: xi.(u_j - u_i); nonlinear: e and 1/|Y|) and
                               failure test once for its two directed entries (the failure check and
                               dilatation pass then runs as two kernels); 0 = once per entry.
-                              Linearized results are bitwise the same; nonlinear theta sums differ
-                              in rounding order only.  Has no effect when the build could not pair
+                              Linearized results are bitwise the same, also when the option is
+                              switched between steps; nonlinear theta sums differ in rounding
+                              order only.  Has no effect when the build could not pair
                               every entry (pd_get_option then reports 0). */
 } pd_option;
 
@@ -229,7 +230,9 @@ pd_status pd_set_prescribed_velocity(pd_ctx* c, const double* vp);
 
 /* Sets the displacement u (dim * n SoA, required) and velocity v (dim * n SoA, NULL: zero) and
  * applies the boundary conditions at the current time.  The next step does not apply the failure
- * criterion before its force evaluation (the paper applies it after each update, Appendix B). */
+ * criterion before its force evaluation (the paper applies it after each update, Appendix B).
+ * PD_ERR_ARG (state unchanged) if u or v holds a non-finite value.  The new state replaces the old
+ * after all work enqueued before the call; u and v may be reused when the call returns. */
 pd_status pd_set_state(pd_ctx* c, const double* u, const double* v);
 
 /* Advances nsteps >= 0 explicit time steps.  Per step: bond-status update on u^n (the failure block
@@ -247,9 +250,10 @@ pd_status pd_sync(pd_ctx* c);
  * writes phi_i of Eq 1.31 in caller order (n doubles).  A particle without bonds gets 0. */
 pd_status pd_get_damage(pd_ctx* c, double* phi);
 
-/* Applies the pending failure check, then copies the state in caller order: u and v as dim * n SoA
- * (FP64 master copies in PD_MIXED), theta (n) = the dilatation evaluated by the last step.  Any of
- * the three may be NULL. */
+/* Copies the state in caller order: u and v as dim * n SoA (FP64 master copies in PD_MIXED),
+ * theta (n) = the dilatation evaluated by the last step.  Any of the three may be NULL.  Also
+ * enqueues the pending failure check of the current state (none of the three depends on it); the
+ * call returns when the copies are done, and later calls are ordered after the check. */
 pd_status pd_get_state(pd_ctx* c, double* u, double* v, double* theta);
 
 /* Number of directed bonds of the built family. */

@@ -106,6 +106,20 @@ __global__ void k_init_thm(int64_t n_pad, const double* __restrict__ mu, double2
   thm[i] = make_double2(0.0, mu[i]);
 }
 
+// The transfer stream of pd_get_state / pd_set_state, on the context's device.
+pd_status ensure_xfer(pd_ctx* c) {
+  if (c->xfer) return PD_OK;
+  PD_CUDA(cudaStreamCreateWithFlags(&c->xfer, cudaStreamNonBlocking));
+  cudaError_t e = cudaEventCreateWithFlags(&c->xfer_ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(c->xfer);
+    c->xfer = nullptr;
+    c->xfer_ev = nullptr;
+    return cuda_fail(e, "cudaEventCreateWithFlags");
+  }
+  return PD_OK;
+}
+
 pd_status check_ctx(pd_ctx* c, bool need_built) {
   clear_error();
   if (!c) return fail(PD_ERR_ARG, "context is NULL");
@@ -333,21 +347,26 @@ pd_status pd_set_state(pd_ctx* c, const double* u, const double* v) {
   pd_status st = check_ctx(c, true);
   if (st != PD_OK) return st;
   if (!u) return fail(PD_ERR_ARG, "u is required");
+  if ((st = ensure_xfer(c)) != PD_OK) return st;
   const int dim = c->dim;
   // Both arrays are copied to the device and checked there (a host scan of 6n doubles costs more
-  // than the copies); the state changes only once both are known to be finite.
+  // than the copies); the state changes only once both are known to be finite.  The copies and
+  // checks run on the transfer stream: they use only the staging buffers and one flag word, which
+  // no main-stream work still in flight uses, so a failure check that pd_get_state left running
+  // overlaps them; the state itself changes on the main stream, after that check.
   const int64_t nd = (int64_t)dim * c->n;
   unsigned long long* flag = c->counters + 6;
-  PD_CUDA(cudaMemsetAsync(flag, 0, sizeof(*flag), c->stream));
-  PD_CUDA(cudaMemcpyAsync(c->scratch, u, sizeof(double) * nd, cudaMemcpyHostToDevice, c->stream));
-  if ((st = launch_nonfinite(c, c->scratch, nd, flag)) != PD_OK) return st;
+  cudaStream_t s = c->xfer;
+  PD_CUDA(cudaMemsetAsync(flag, 0, sizeof(*flag), s));
+  PD_CUDA(cudaMemcpyAsync(c->scratch, u, sizeof(double) * nd, cudaMemcpyHostToDevice, s));
+  if ((st = launch_nonfinite(c->scratch, nd, flag, s)) != PD_OK) return st;
   if (v) {
-    PD_CUDA(cudaMemcpyAsync(c->scratch2, v, sizeof(double) * nd, cudaMemcpyHostToDevice, c->stream));
-    if ((st = launch_nonfinite(c, c->scratch2, nd, flag)) != PD_OK) return st;
+    PD_CUDA(cudaMemcpyAsync(c->scratch2, v, sizeof(double) * nd, cudaMemcpyHostToDevice, s));
+    if ((st = launch_nonfinite(c->scratch2, nd, flag, s)) != PD_OK) return st;
   }
   unsigned long long bad = 0;
-  PD_CUDA(cudaMemcpyAsync(&bad, flag, sizeof(bad), cudaMemcpyDeviceToHost, c->stream));
-  PD_CUDA(cudaStreamSynchronize(c->stream));
+  PD_CUDA(cudaMemcpyAsync(&bad, flag, sizeof(bad), cudaMemcpyDeviceToHost, s));
+  PD_CUDA(cudaStreamSynchronize(s));
   if (bad) return fail(PD_ERR_ARG, "non-finite state");
   if ((st = gather_field(c, c->scratch, c->disp[c->cur], dim)) != PD_OK) return st;
   if (v) {
@@ -396,20 +415,18 @@ pd_status pd_get_damage(pd_ctx* c, double* phi) {
 pd_status pd_get_state(pd_ctx* c, double* u, double* v, double* theta) {
   pd_status st = check_ctx(c, true);
   if (st != PD_OK) return st;
-  if ((st = launch_refresh_check(c)) != PD_OK) return st;
   if ((st = check_device_error(c)) != PD_OK) return st;
-  if (u) {
-    if ((st = download_field(c, c->disp[c->cur], u, c->dim)) != PD_OK) return st;
-    PD_CUDA(cudaStreamSynchronize(c->stream));
-  }
-  if (v) {
-    if ((st = download_field(c, c->vel, v, c->dim)) != PD_OK) return st;
-    PD_CUDA(cudaStreamSynchronize(c->stream));
-  }
-  if (theta) {
-    if ((st = download_scalar(c, c->theta, theta)) != PD_OK) return st;
-    PD_CUDA(cudaStreamSynchronize(c->stream));
-  }
+  if ((st = ensure_xfer(c)) != PD_OK) return st;
+  // u, v and theta do not depend on the bond status, so their copies run on the transfer stream,
+  // after the work enqueued so far, while the pending failure check runs on the main stream (it
+  // writes only bond status); the call returns once the copies are done.
+  PD_CUDA(cudaEventRecord(c->xfer_ev, c->stream));
+  PD_CUDA(cudaStreamWaitEvent(c->xfer, c->xfer_ev, 0));
+  if (u && (st = download_field(c, c->disp[c->cur], u, c->dim, c->xfer)) != PD_OK) return st;
+  if (v && (st = download_field(c, c->vel, v, c->dim, c->xfer)) != PD_OK) return st;
+  if (theta && (st = download_scalar(c, c->theta, theta, c->xfer)) != PD_OK) return st;
+  if ((st = launch_refresh_check(c)) != PD_OK) return st;
+  PD_CUDA(cudaStreamSynchronize(c->xfer));
   return PD_OK;
 }
 
@@ -532,6 +549,9 @@ pd_status pd_set_option(pd_ctx* c, int32_t option, int64_t value) {
       c->expire_waits = value != 0;
       break;
     case PD_OPT_PAIRS:
+      // A failure check of the pair form marks slices whose bS its next pass 1b recomputes; the
+      // other form never reads those marks, so a switch recomputes every bS before the next step.
+      if ((value != 0) != (c->pairs != 0)) c->bs_stale = true;
       c->pairs = value != 0;
       break;
     case PD_OPT_SOLVER:
@@ -888,7 +908,10 @@ pd_status pd_autotune(pd_ctx* c, int32_t trial_steps, int32_t* block_out, int32_
   }
   c->block = best_block;
   c->split = best_split;
-  if (best_pairs >= 0) c->pairs = best_pairs;
+  if (best_pairs >= 0) {
+    if ((best_pairs != 0) != (c->pairs != 0)) c->bs_stale = true;  // as a PD_OPT_PAIRS switch
+    c->pairs = best_pairs;
+  }
   drop_graphs(c);
   if (block_out) *block_out = best_block;
   if (split_out) *split_out = best_split;
@@ -899,7 +922,10 @@ void pd_destroy(pd_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
   read_profile(c);
+  if (c->xfer) cudaStreamSynchronize(c->xfer);
   free_all(c);
+  if (c->xfer_ev) cudaEventDestroy(c->xfer_ev);
+  if (c->xfer) cudaStreamDestroy(c->xfer);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }

@@ -111,6 +111,11 @@ struct pd_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  // Host transfers of pd_get_state / pd_set_state (created at first use).  Its work touches only
+  // the scratch buffers, one flag word and state that the main stream's work in flight does not
+  // write, and it is always synchronized before the call that used it returns.
+  cudaStream_t xfer = nullptr;
+  cudaEvent_t xfer_ev = nullptr;
   int dim = 3;
   int model = 0;
   int precision = 0;
@@ -234,9 +239,9 @@ pd_status diagnostics(pd_ctx* c, double* min_margin, double* strain, double* kin
 pd_status prepare_staged_kernels(pd_ctx* c);  // shared-memory opt-in of the staged kernels
 pd_status upload_field(pd_ctx* c, const double* host_soa, double4* dst, int comps);
 pd_status gather_field(pd_ctx* c, const double* dev_soa, double4* dst, int comps);
-pd_status launch_nonfinite(pd_ctx* c, const double* a, int64_t n, unsigned long long* flag);
-pd_status download_field(pd_ctx* c, const double4* src, double* host_soa, int comps);
-pd_status download_scalar(pd_ctx* c, const double* src, double* host);
+pd_status launch_nonfinite(const double* a, int64_t n, unsigned long long* flag, cudaStream_t s);
+pd_status download_field(pd_ctx* c, const double4* src, double* host_soa, int comps, cudaStream_t s);
+pd_status download_scalar(pd_ctx* c, const double* src, double* host, cudaStream_t s);
 pd_status apply_bc_now(pd_ctx* c);
 pd_status sync_shadow(pd_ctx* c);
 pd_status max_abs_u(pd_ctx* c, double* out, int* nonfinite);

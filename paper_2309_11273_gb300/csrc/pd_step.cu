@@ -943,6 +943,66 @@ __global__ void __launch_bounds__(512) k_pass1b_f64p(StepArgs a, const double4* 
   }
 }
 
+// The failure check alone in the pair form, applied to the current state before its bond status is
+// read between steps: ξ·(u_j − u_i) once per intact bond at its owned entry, as in pass 1a, but
+// with no bd store (the next step's pass 1a stores it) and the twin entry's index loaded only
+// for a bond that breaks.  Slices with broken bonds are marked for the next pass 1b.
+template <int DIM, int SPLIT>
+__global__ void __launch_bounds__(512) k_check_f64p(StepArgs a, const double4* __restrict__ disp) {
+  const SliceIdx t = slice_index<SPLIT>(a.n_pad, a.slice_ptr);
+  if (!t.active) return;  // whole warps; no block-wide barrier below
+  const int b = a.body ? a.body[t.i] : 0;
+  const bool can_break = a.bp[b].breaks != 0;
+  if (!__any_sync(kFull, can_break)) return;
+  const int own = a.own0[t.i], cnt = a.cnt[t.i];
+  const int k_lo = __reduce_min_sync(kFull, (unsigned)own);
+  const int k_hi = __reduce_max_sync(kFull, (unsigned)cnt);
+  const double4 ui = disp[t.i];
+  uint32_t* bw = a.bits + (t.base >> 5);
+  const int32_t* __restrict__ cl = a.col + t.base + t.lane;
+  const double4* __restrict__ ta = a.bA + t.base + t.lane;
+  // the next slot's index and table row are loaded while the current slot's gather runs
+  int k = k_lo + t.sub;
+  bool mn = k < k_hi && k >= own && k < cnt && can_break;
+  int32_t jn = (int32_t)t.i;
+  double4 gn = make_double4(0.0, 0.0, 0.0, 0.0);
+  if (mn) {
+    jn = cl[(int64_t)k << 5];
+    gn = ta[(int64_t)k << 5];
+  }
+  for (; k < k_hi; k += SPLIT) {
+    const uint32_t wd = bw[k];  // this warp's owned bits change only here
+    const bool mine = mn && ((wd >> t.lane) & 1u);
+    const int32_t j = jn;
+    const double4 g = gn;
+    const int kn = k + SPLIT;
+    mn = kn < k_hi && kn >= own && kn < cnt && can_break;
+    if (mn) {
+      jn = cl[(int64_t)kn << 5];
+      gn = ta[(int64_t)kn << 5];
+    }
+    bool brk = false;
+    if (mine) {
+      const double4 uj = disp[j];
+      double d = g.x * (uj.x - ui.x) + g.y * (uj.y - ui.y);
+      if (DIM == 3) d = fma(g.z, uj.z - ui.z, d);
+      brk = __double_as_longlong(d) >= __double_as_longlong(g.w);  // d >= s0 |xi|^2
+    }
+    const unsigned m = __ballot_sync(kFull, brk);
+    if (m) {
+      if (t.lane == 0) {
+        atomicAnd(&bw[k], ~m);
+        a.dirty[t.i >> 5] = 1;
+      }
+      if (brk) {
+        const int32_t te = a.twin[t.base + t.lane + ((int64_t)k << 5)];
+        atomicAnd(a.bits + (te >> 5), ~(1u << (te & 31)));
+        a.dirty[j >> 5] = 1;
+      }
+    }
+  }
+}
+
 template <int DIM, int SPLIT>
 __global__ void __launch_bounds__(512) k_pass2_f64t(StepArgs a, const double4* __restrict__ disp,
                                                      double4* __restrict__ disp_out) {
@@ -2013,15 +2073,15 @@ void launch_pass1(pd_ctx* c, const StepArgs& a, int write_theta, unsigned grid, 
     k_pass1_nlt<DIM, SPLIT><<<grid, block, sm, c->stream>>>(a, c->disp[c->cur], write_theta);
   else if (c->kin == PD_NONLINEAR)
     k_pass1_nl<DIM, SPLIT><<<grid, block, sm, c->stream>>>(a, c->disp[c->cur], write_theta);
-  else if (c->precision == PD_FP64 && a.bA && a.own0) {
+  else if (c->precision == PD_FP64 && a.bA && a.own0 && !write_theta) {
+    if (a.check) k_check_f64p<DIM, SPLIT><<<grid, block, 0, c->stream>>>(a, c->disp[c->cur]);
+  } else if (c->precision == PD_FP64 && a.bA && a.own0) {
     k_pass1a_f64p<DIM, SPLIT><<<grid, block, 0, c->stream>>>(a, c->disp[c->cur]);
-    if (write_theta) {
-      if (c->profile) {
-        c->times.mid = take_event(c);
-        cudaEventRecord(c->times.mid, c->stream);
-      }
-      k_pass1b_f64p<DIM, SPLIT><<<grid, block, sm, c->stream>>>(a, c->disp[c->cur], write_theta);
+    if (c->profile) {
+      c->times.mid = take_event(c);
+      cudaEventRecord(c->times.mid, c->stream);
     }
+    k_pass1b_f64p<DIM, SPLIT><<<grid, block, sm, c->stream>>>(a, c->disp[c->cur], write_theta);
   } else if (c->precision == PD_FP64 && a.bA) {
     if (write_theta)
       k_pass1_f64t<DIM, SPLIT, true><<<grid, block, sm, c->stream>>>(a, c->disp[c->cur], write_theta);
@@ -2376,32 +2436,32 @@ pd_status gather_field(pd_ctx* c, const double* dev_soa, double4* dst, int comps
 }
 
 // Sets *flag (device word) to 1 if any of the n doubles at a is not finite.
-pd_status launch_nonfinite(pd_ctx* c, const double* a, int64_t n, unsigned long long* flag) {
+pd_status launch_nonfinite(const double* a, int64_t n, unsigned long long* flag, cudaStream_t s) {
   const int tb = 256;
   const unsigned grid = (unsigned)std::min<int64_t>((n + tb - 1) / tb, 4096);
   if (grid == 0) return PD_OK;
-  k_nonfinite<<<grid, tb, 0, c->stream>>>(n, a, flag);
+  k_nonfinite<<<grid, tb, 0, s>>>(n, a, flag);
   PD_CUDA(cudaGetLastError());
   return PD_OK;
 }
 
-pd_status download_field(pd_ctx* c, const double4* src, double* host_soa, int comps) {
+pd_status download_field(pd_ctx* c, const double4* src, double* host_soa, int comps, cudaStream_t s) {
   const int64_t n = c->n;
   const int tb = 256;
-  k_scatter_soa<<<(unsigned)((n + tb - 1) / tb), tb, 0, c->stream>>>(n, comps, src, c->perm_dev, c->scratch);
+  k_scatter_soa<<<(unsigned)((n + tb - 1) / tb), tb, 0, s>>>(n, comps, src, c->perm_dev, c->scratch);
   PD_CUDA(cudaGetLastError());
-  PD_CUDA(cudaMemcpyAsync(host_soa, c->scratch, sizeof(double) * comps * n, cudaMemcpyDeviceToHost, c->stream));
+  PD_CUDA(cudaMemcpyAsync(host_soa, c->scratch, sizeof(double) * comps * n, cudaMemcpyDeviceToHost, s));
   return PD_OK;
 }
 
-pd_status download_scalar(pd_ctx* c, const double* src, double* host) {
+pd_status download_scalar(pd_ctx* c, const double* src, double* host, cudaStream_t s) {
   const int64_t n = c->n;
   const int tb = 256;
   const bool mixed = c->precision == PD_MIXED && src == c->theta;
-  k_scatter_scalar<<<(unsigned)((n + tb - 1) / tb), tb, 0, c->stream>>>(
+  k_scatter_scalar<<<(unsigned)((n + tb - 1) / tb), tb, 0, s>>>(
       n, mixed ? nullptr : src, mixed ? c->theta32 : nullptr, c->perm_dev, c->scratch);
   PD_CUDA(cudaGetLastError());
-  PD_CUDA(cudaMemcpyAsync(host, c->scratch, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+  PD_CUDA(cudaMemcpyAsync(host, c->scratch, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
   return PD_OK;
 }
 

@@ -296,6 +296,69 @@ def test_pair_form_is_bitwise_the_single_pass(case, split):
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("split", [1, 2])
+def test_checks_between_steps_with_form_switches_keep_the_trajectory(split):
+    """A read between steps applies the pending failure check itself (the pair form by its own
+    check kernel, the single pass by its check-only form) and the next step skips it.  Reading
+    after every step, and switching between the pair form and the single pass after every read,
+    gives bitwise the run that reads only at the end: bonds broken by a pair-form check and
+    followed by a single-pass step leave no stale intact sum behind."""
+    w = W.notched_block(nx=24, ny=12, nz=10, dx=1e-3, notch_cells=9.5, nsteps=300, seed=3, amp=1e-7)
+    ref = Simulation(w, s0=s0_of(w))
+    ref.set_option(B.PD_OPT_BLOCK, 128)
+    ref.set_option(B.PD_OPT_SPLIT, split)
+    ref.step(w.nsteps)
+    want = ref.state()[:2] + (ref.neighbors()[2], ref.damage())
+    ref.close()
+    sim = Simulation(w, s0=s0_of(w))
+    sim.set_option(B.PD_OPT_BLOCK, 128)
+    sim.set_option(B.PD_OPT_SPLIT, split)
+    broken, pair_checks_broke = 0, 0
+    for k in range(w.nsteps):
+        pairs = B.pd_get_option(sim.h, B.PD_OPT_PAIRS)
+        sim.step(1)
+        now = sim.stats()["broken_bonds"]
+        pair_checks_broke += pairs == 1 and now > broken
+        broken = now
+        sim.set_option(B.PD_OPT_PAIRS, 1 - pairs)
+    got = sim.state()[:2] + (sim.neighbors()[2], sim.damage())
+    sim.close()
+    assert pair_checks_broke > 0
+    for a, b in zip(got, want):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("precision", [PD_FP64, PD_MIXED])
+def test_state_round_trip_after_every_step_is_the_plain_run(precision):
+    """Reading u and v after every step and writing them back before the next gives bitwise the
+    run that never leaves the device, while bonds break throughout: the read's copies (and the
+    write's upload and finiteness check) run on the library's transfer stream beside the failure
+    check that the read leaves running, and the written state lands only after that check.  Host
+    buffers alternate between pageable and pinned memory."""
+    import torch
+    w = W.notched_block(nx=24, ny=12, nz=10, dx=1e-3, notch_cells=9.5, nsteps=300, seed=3, amp=1e-7)
+    ref = Simulation(w, s0=s0_of(w), precision=precision)
+    ref.step(w.nsteps)
+    want = ref.state()[:2] + (ref.neighbors()[2],)
+    ref.close()
+    sim = Simulation(w, s0=s0_of(w), precision=precision)
+    dim, n = 3, w.n
+    pinned = [torch.empty((dim, n), dtype=torch.float64, pin_memory=True).numpy() for _ in range(2)]
+    for k in range(w.nsteps):
+        sim.step(1)
+        if k % 2:
+            u, v = pinned
+            B.pd_get_state(sim.h, dim, n, u, v, False)
+        else:
+            u, v, _ = B.pd_get_state(sim.h, dim, n, True, True, False)
+        B.pd_set_state(sim.h, dim, n, u, v)
+    got = sim.state()[:2] + (sim.neighbors()[2],)
+    sim.close()
+    assert not want[2].all()  # bonds broke
+    for a, b in zip(got, want):
+        assert np.array_equal(a, b)
+
+
 # --------------------------------------------------------------------------------- edge cases
 def test_single_particle_and_ragged_sizes():
     for nx, ny in ((1, 1), (33, 1), (7, 5)):
