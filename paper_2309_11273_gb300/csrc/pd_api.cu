@@ -46,6 +46,8 @@ void free_build(pd_ctx* c) {
   c->own0 = nullptr;
   c->twin = nullptr;
   c->dirty = nullptr;
+  c->cA32 = nullptr;
+  c->cu32 = nullptr;
   c->pairs_ok = false;
   c->slice_ptr = nullptr;
   c->col = nullptr;

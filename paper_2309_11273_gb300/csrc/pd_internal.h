@@ -139,6 +139,8 @@ struct pd_ctx {
   int32_t* twin = nullptr;       // FP64 pair path: per owned slot, the entry of the same bond at j
   bool pairs_ok = false;         // the pair tables exist and every pair has both entries
   uint8_t* dirty = nullptr;      // FP64 pair path: per slice, a bond of the slice broke (bS to redo)
+  float4* cA32 = nullptr;        // FP64 pair path, check before a read: per slot FP32 (xi, s0 |xi|^2 rounded down)
+  float4* cu32 = nullptr;        // ... and its FP32 copy of u
   int64_t nentries = 0, nbonds = 0;
   double* mu = nullptr;
   double* aA = nullptr;

@@ -947,8 +947,20 @@ __global__ void __launch_bounds__(512) k_pass1b_f64p(StepArgs a, const double4* 
 // read between steps: ξ·(u_j − u_i) once per intact bond at its owned entry, as in pass 1a, but
 // with no bd store (the next step's pass 1a stores it) and the twin entry's index loaded only
 // for a bond that breaks.  Slices with broken bonds are marked for the next pass 1b.
-template <int DIM, int SPLIT>
-__global__ void __launch_bounds__(512) k_check_f64p(StepArgs a, const double4* __restrict__ disp) {
+//
+// SCREEN: each bond is first evaluated in FP32, from FP32 copies of u (cu) and of the slot's ξ with
+// its threshold rounded down (cA).  With M = Σ_c |ξ_c| (|u_jc| + |u_ic|), the FP32 value differs
+// from the FP64 one by at most 6.01 u₃₂ M (u₃₂ = 2⁻²⁴: the roundings of ξ, of both u and of their
+// difference, and three for the products and sums; the FP64 rounding is below 2⁻⁵⁰ M), and the
+// FP32-evaluated M by a few u₃₂ M.  A bond whose FP32 value plus 2⁻¹⁹ (M + |value|) (five times
+// that bound, so the final FP32 addition cannot close the gap) is still below the rounded-down
+// threshold is below the FP64 threshold in FP64 too, and stays intact; the small absolute terms
+// cover gradual underflow.  Every other bond, and every non-finite value (its comparisons are
+// false), is evaluated in FP64 exactly as pass 1a does, so each decision is pass 1a's.
+template <int DIM, int SPLIT, bool SCREEN>
+__global__ void __launch_bounds__(512) k_check_f64p(StepArgs a, const double4* __restrict__ disp,
+                                                     const float4* __restrict__ cu,
+                                                     const float4* __restrict__ cA) {
   const SliceIdx t = slice_index<SPLIT>(a.n_pad, a.slice_ptr);
   if (!t.active) return;  // whole warps; no block-wide barrier below
   const int b = a.body ? a.body[t.i] : 0;
@@ -958,35 +970,63 @@ __global__ void __launch_bounds__(512) k_check_f64p(StepArgs a, const double4* _
   const int k_lo = __reduce_min_sync(kFull, (unsigned)own);
   const int k_hi = __reduce_max_sync(kFull, (unsigned)cnt);
   const double4 ui = disp[t.i];
+  const float4 ui32 = SCREEN ? cu[t.i] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   uint32_t* bw = a.bits + (t.base >> 5);
   const int32_t* __restrict__ cl = a.col + t.base + t.lane;
   const double4* __restrict__ ta = a.bA + t.base + t.lane;
+  const float4* __restrict__ ts = SCREEN ? cA + t.base + t.lane : nullptr;
   // the next slot's index and table row are loaded while the current slot's gather runs
   int k = k_lo + t.sub;
   bool mn = k < k_hi && k >= own && k < cnt && can_break;
   int32_t jn = (int32_t)t.i;
   double4 gn = make_double4(0.0, 0.0, 0.0, 0.0);
+  float4 sn = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   if (mn) {
     jn = cl[(int64_t)k << 5];
-    gn = ta[(int64_t)k << 5];
+    if (SCREEN)
+      sn = ts[(int64_t)k << 5];
+    else
+      gn = ta[(int64_t)k << 5];
   }
   for (; k < k_hi; k += SPLIT) {
     const uint32_t wd = bw[k];  // this warp's owned bits change only here
     const bool mine = mn && ((wd >> t.lane) & 1u);
     const int32_t j = jn;
-    const double4 g = gn;
+    const double4 g0 = gn;
+    const float4 sc = sn;
     const int kn = k + SPLIT;
     mn = kn < k_hi && kn >= own && kn < cnt && can_break;
     if (mn) {
       jn = cl[(int64_t)kn << 5];
-      gn = ta[(int64_t)kn << 5];
+      if (SCREEN)
+        sn = ts[(int64_t)kn << 5];
+      else
+        gn = ta[(int64_t)kn << 5];
     }
     bool brk = false;
     if (mine) {
-      const double4 uj = disp[j];
-      double d = g.x * (uj.x - ui.x) + g.y * (uj.y - ui.y);
-      if (DIM == 3) d = fma(g.z, uj.z - ui.z, d);
-      brk = __double_as_longlong(d) >= __double_as_longlong(g.w);  // d >= s0 |xi|^2
+      bool exact = true;
+      if (SCREEN) {
+        const float4 uj = cu[j];
+        const float dx = uj.x - ui32.x, dy = uj.y - ui32.y;
+        float d = fmaf(sc.x, dx, sc.y * dy);
+        float m = fmaf(fabsf(sc.x), fabsf(uj.x) + fabsf(ui32.x), fabsf(sc.y) * (fabsf(uj.y) + fabsf(ui32.y)));
+        float l1 = fabsf(sc.x) + fabsf(sc.y);
+        if (DIM == 3) {
+          d = fmaf(sc.z, uj.z - ui32.z, d);
+          m = fmaf(fabsf(sc.z), fabsf(uj.z) + fabsf(ui32.z), m);
+          l1 += fabsf(sc.z);
+        }
+        const float bound = fmaf(0x1p-19f, m + fabsf(d), fmaf(0x1p-120f, l1, 0x1p-140f));
+        exact = !(d + bound < sc.w);
+      }
+      if (exact) {
+        const double4 g = SCREEN ? ta[(int64_t)k << 5] : g0;
+        const double4 uj = disp[j];
+        double d = g.x * (uj.x - ui.x) + g.y * (uj.y - ui.y);
+        if (DIM == 3) d = fma(g.z, uj.z - ui.z, d);
+        brk = __double_as_longlong(d) >= __double_as_longlong(g.w);  // d >= s0 |xi|^2
+      }
     }
     const unsigned m = __ballot_sync(kFull, brk);
     if (m) {
@@ -1001,6 +1041,24 @@ __global__ void __launch_bounds__(512) k_check_f64p(StepArgs a, const double4* _
       }
     }
   }
+}
+
+// FP32 tables of the screened check: per slot ξ rounded to nearest and s0|ξ|² rounded down.
+__global__ void k_check_tables(int64_t nentries, const double4* __restrict__ bA, float4* __restrict__ cA) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nentries;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const double4 g = bA[e];
+    cA[e] = make_float4(__double2float_rn(g.x), __double2float_rn(g.y), __double2float_rn(g.z),
+                        __double2float_rd(g.w));
+  }
+}
+
+// u rounded to FP32 for the screened check.
+__global__ void k_check_u32(int64_t n_pad, const double4* __restrict__ disp, float4* __restrict__ cu) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n_pad) return;
+  const double4 u = disp[i];
+  cu[i] = make_float4(__double2float_rn(u.x), __double2float_rn(u.y), __double2float_rn(u.z), 0.0f);
 }
 
 template <int DIM, int SPLIT>
@@ -2074,7 +2132,13 @@ void launch_pass1(pd_ctx* c, const StepArgs& a, int write_theta, unsigned grid, 
   else if (c->kin == PD_NONLINEAR)
     k_pass1_nl<DIM, SPLIT><<<grid, block, sm, c->stream>>>(a, c->disp[c->cur], write_theta);
   else if (c->precision == PD_FP64 && a.bA && a.own0 && !write_theta) {
-    if (a.check) k_check_f64p<DIM, SPLIT><<<grid, block, 0, c->stream>>>(a, c->disp[c->cur]);
+    if (a.check && c->cA32) {
+      const int tb = 256;
+      k_check_u32<<<(unsigned)((c->n_pad + tb - 1) / tb), tb, 0, c->stream>>>(c->n_pad, c->disp[c->cur], c->cu32);
+      k_check_f64p<DIM, SPLIT, true><<<grid, block, 0, c->stream>>>(a, c->disp[c->cur], c->cu32, c->cA32);
+    } else if (a.check) {
+      k_check_f64p<DIM, SPLIT, false><<<grid, block, 0, c->stream>>>(a, c->disp[c->cur], nullptr, nullptr);
+    }
   } else if (c->precision == PD_FP64 && a.bA && a.own0) {
     k_pass1a_f64p<DIM, SPLIT><<<grid, block, 0, c->stream>>>(a, c->disp[c->cur]);
     if (c->profile) {
@@ -2400,8 +2464,29 @@ pd_status read_profile(pd_ctx* c) {
 
 // The failure criterion on the current state, without advancing (used before reading damage,
 // status or state, so that they equal the paper's end-of-iteration failure block).
+// FP32 tables of the screened check before a read (FP64 pair form), built at the first such check;
+// without them (another form, or no device memory left) the check runs in FP64 alone.
+static void ensure_check_tables(pd_ctx* c) {
+  if (c->cA32 || c->precision != PD_FP64 || c->kin == PD_NONLINEAR || !c->bond_cache || !c->pairs ||
+      !c->pairs_ok || !c->bA || c->nentries <= 0)
+    return;
+  float4* cA = nullptr;
+  float4* cu = nullptr;
+  if (alloc(c, &cA, (size_t)c->nentries) != PD_OK || alloc(c, &cu, (size_t)c->n_pad) != PD_OK) {
+    clear_error();
+    return;
+  }
+  const int tb = 256;
+  const unsigned grid = (unsigned)std::min<int64_t>((c->nentries + tb - 1) / tb, 152 * 64);
+  k_check_tables<<<grid, tb, 0, c->stream>>>(c->nentries, c->bA, cA);
+  if (cudaGetLastError() != cudaSuccess) return;
+  c->cA32 = cA;
+  c->cu32 = cu;
+}
+
 pd_status launch_refresh_check(pd_ctx* c) {
   if (!c->check_pending) return PD_OK;
+  ensure_check_tables(c);
   StepArgs a = make_args(c);
   a.check = 1;
   dispatch(c, a, 1, 0);

@@ -328,6 +328,38 @@ def test_checks_between_steps_with_form_switches_keep_the_trajectory(split):
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("shape", ["plate", "block"])
+def test_screened_check_decides_near_threshold_bonds_in_fp64(shape):
+    """The pair form's check before a read first decides each bond in FP32, with a bound on its
+    distance from the FP64 value, and evaluates in FP64 only the bonds that bound cannot settle.
+    Under a uniform stretch equal to the critical stretch every bond along x sits on its threshold
+    (FP64 rounding decides it) and every other bond lies below: the screened check and the single
+    pass's FP64 check break the same bonds, and the runs stay bitwise equal from there."""
+    s0 = 1e-3
+    if shape == "plate":
+        w = W.plate_vibration(nx=40, ny=12, nsteps=10)
+    else:
+        w = W.notched_block(nx=24, ny=12, nz=10, dx=1e-3, notch_cells=9.5, nsteps=10)
+    u0 = np.zeros((w.dim, w.n))
+    u0[0] = s0 * w.x
+    w.u0 = u0
+    res = []
+    for pairs in (1, 0):
+        sim = Simulation(w, s0=s0)
+        sim.set_option(B.PD_OPT_PAIRS, pairs)
+        assert B.pd_get_option(sim.h, B.PD_OPT_PAIRS) == pairs
+        sim.step(1)
+        phi = sim.damage()  # the check of u^1, by the screened kernel in the pair form
+        bits = sim.neighbors()[2]
+        broken = sim.stats()["broken_bonds"]
+        sim.step(5)
+        res.append((phi, bits, broken) + sim.state()[:2] + (sim.neighbors()[2],))
+        sim.close()
+    assert 0 < res[0][2] < res[0][1].size
+    for a, b in zip(res[0], res[1]):
+        assert np.array_equal(a, b)
+
+
 @pytest.mark.parametrize("precision", [PD_FP64, PD_MIXED])
 def test_state_round_trip_after_every_step_is_the_plain_run(precision):
     """Reading u and v after every step and writing them back before the next gives bitwise the
