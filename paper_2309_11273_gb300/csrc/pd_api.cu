@@ -359,16 +359,19 @@ pd_status pd_set_state(pd_ctx* c, const double* u, const double* v) {
   const int64_t nd = (int64_t)dim * c->n;
   unsigned long long* flag = c->counters + 6;
   cudaStream_t s = c->xfer;
-  PD_CUDA(cudaMemsetAsync(flag, 0, sizeof(*flag), s));
-  PD_CUDA(cudaMemcpyAsync(c->scratch, u, sizeof(double) * nd, cudaMemcpyHostToDevice, s));
-  if ((st = launch_nonfinite(c->scratch, nd, flag, s)) != PD_OK) return st;
-  if (v) {
-    PD_CUDA(cudaMemcpyAsync(c->scratch2, v, sizeof(double) * nd, cudaMemcpyHostToDevice, s));
-    if ((st = launch_nonfinite(c->scratch2, nd, flag, s)) != PD_OK) return st;
-  }
   unsigned long long bad = 0;
-  PD_CUDA(cudaMemcpyAsync(&bad, flag, sizeof(bad), cudaMemcpyDeviceToHost, s));
-  PD_CUDA(cudaStreamSynchronize(s));
+  cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(*flag), s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->scratch, u, sizeof(double) * nd, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) st = launch_nonfinite(c->scratch, nd, flag, s);
+  if (e == cudaSuccess && st == PD_OK && v) {
+    e = cudaMemcpyAsync(c->scratch2, v, sizeof(double) * nd, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) st = launch_nonfinite(c->scratch2, nd, flag, s);
+  }
+  if (e == cudaSuccess && st == PD_OK) e = cudaMemcpyAsync(&bad, flag, sizeof(bad), cudaMemcpyDeviceToHost, s);
+  const cudaError_t es = cudaStreamSynchronize(s);  // also on an error: nothing stays in flight
+  if (e == cudaSuccess) e = es;
+  if (e != cudaSuccess) return cuda_fail(e, "pd_set_state upload");
+  if (st != PD_OK) return st;
   if (bad) return fail(PD_ERR_ARG, "non-finite state");
   if ((st = gather_field(c, c->scratch, c->disp[c->cur], dim)) != PD_OK) return st;
   if (v) {
@@ -424,11 +427,13 @@ pd_status pd_get_state(pd_ctx* c, double* u, double* v, double* theta) {
   // writes only bond status); the call returns once the copies are done.
   PD_CUDA(cudaEventRecord(c->xfer_ev, c->stream));
   PD_CUDA(cudaStreamWaitEvent(c->xfer, c->xfer_ev, 0));
-  if (u && (st = download_field(c, c->disp[c->cur], u, c->dim, c->xfer)) != PD_OK) return st;
-  if (v && (st = download_field(c, c->vel, v, c->dim, c->xfer)) != PD_OK) return st;
-  if (theta && (st = download_scalar(c, c->theta, theta, c->xfer)) != PD_OK) return st;
-  if ((st = launch_refresh_check(c)) != PD_OK) return st;
-  PD_CUDA(cudaStreamSynchronize(c->xfer));
+  if (u) st = download_field(c, c->disp[c->cur], u, c->dim, c->xfer);
+  if (st == PD_OK && v) st = download_field(c, c->vel, v, c->dim, c->xfer);
+  if (st == PD_OK && theta) st = download_scalar(c, c->theta, theta, c->xfer);
+  if (st == PD_OK) st = launch_refresh_check(c);
+  const cudaError_t e = cudaStreamSynchronize(c->xfer);  // also on an error: nothing stays in flight
+  if (st != PD_OK) return st;
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
   return PD_OK;
 }
 
