@@ -603,7 +603,7 @@ def main():
                          "FP64 kernels hold a few GB")
     ap.add_argument("--sweep", action="store_true",
                     help="one JSON line per configuration (1-5): FP64 and mixed GPU rates and the oracle's "
-                         "rate on all host cores and on one (the per-configuration table of the baseline)")
+                         "rate on all host cores and on one")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
