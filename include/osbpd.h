@@ -135,7 +135,10 @@ typedef enum {
                               G (1/m_i + 1/m_j) / |xi|^2, and the step's xi.(u_j - u_i); 72 bytes per
                               bond slot, plus a per-particle sum of V_j xi over the intact bonds) so
                               each step evaluates only displacement-dependent FP64 terms; 0 =
-                              recompute the geometry from the coordinates every step */
+                              recompute the geometry from the coordinates every step.  With the
+                              pair form, the first failure check before a read also keeps FP32
+                              copies of xi and s0 |xi|^2 (16 bytes per slot) and of u (16 bytes
+                              per particle) for its FP32 screen */
   PD_OPT_STAGE = 7,        /* PD_MIXED with split 1: 1 (default) = stream each warp's neighbour
                               indices and status words into shared memory with bulk asynchronous
                               copies (bounded waits; an expired wait makes the next pd_sync /
