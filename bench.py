@@ -71,7 +71,14 @@ FLOPS_BOND_NL_TABLED = {1: 29.0, 2: 19.0}
 # terms (1), pass 2 forms the coefficient from the tables and the force along the stored direction
 # (12).
 FLOPS_BOND_NL_PAIRS = {"k_pass1a_nlp": 16.5, "k_pass1b_nlp": 1.0, "k_pass2_nlp": 12.0}
-FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12  # 2 DFMA/clk/SM x 2 flop x 152 SMs x 2.07 GHz
+# Algorithmic bytes per directed bond and per particle of each step kernel (the model above, 3D,
+# no body force): the pair form's pass 1 is split between its two kernels (1a: index, status read and
+# write, x and u; 1b: 1/m, theta and the row pointer), pass 2 is one kernel.
+BYTES_KERNEL = {"k_pass1a_f64p": (4.25, 48.0), "k_pass1b_f64p": (0.0, 20.0), "k_pass2_f64t": (4.125, 141.0),
+                "k_pass1_f64t": (4.25, 68.0), "k_pass2_f64": (4.125, 141.0), "k_pass1_f64": (4.25, 68.0)}
+# The same per-particle model in 2D (x, u, v, b of 2 components; configuration 4 has a body force,
+# the edge traction): pass 1 16 + 16 + 8 + 8 + 4, pass 2 48 + 16 + 16 + 1 + 32 + 4.
+BYTES_PART_2D = {1: 52.0, 2: 117.0}
 
 
 def env_int(name, default):
@@ -123,16 +130,38 @@ def recorded_traffic(kernel, nbonds=None):
     return None
 
 
-def kernel_entry(kname, ms, flops, nb, hbm):
-    """One FP64 kernel of the step: its CUDA-event time, flop rate against the FP64 peak, and its
-    DRAM rate from the recorded ncu traffic (the tabled kernels stream per-slot tables, so their
-    bytes are the tables, not the model's algorithmic bytes)."""
-    out = {"ms": ms, "flop_per_bond": flops, "achieved_tflops": flops * nb / (ms * 1e-3) / 1e12,
-           "frac": flops * nb / (ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS}
+def kernel_entry(kname, ms, flops, nb, n, hbm, fp64_peak):
+    """One FP64 kernel of the step: its CUDA-event time, its algorithmic bytes per launch and their
+    rate against the measured HBM bandwidth, its DRAM rate from the recorded ncu traffic (the tabled
+    kernels stream per-slot tables, so their DRAM bytes exceed the algorithmic ones), and its FP64
+    flop rate against the measured FP64 FMA rate."""
+    bb, bp = BYTES_KERNEL[kname]
+    alg = bb * nb + bp * n
+    out = {"ms": ms, "algorithmic_bytes": alg, "achieved_gbs": alg / (ms * 1e-3) / 1e9,
+           "frac": alg / (ms * 1e-3) / 1e9 / hbm,
+           "flop_per_bond": flops, "achieved_tflops": flops * nb / (ms * 1e-3) / 1e12}
+    if fp64_peak:
+        out["alu_frac"] = out["achieved_tflops"] / fp64_peak
     t = recorded_traffic(kname, nb)
     out["traffic"] = t
     if t is not None:
         out.update({"dram_gbs": t / (ms * 1e-3) / 1e9, "dram_frac": t / (ms * 1e-3) / 1e9 / hbm})
+    return out
+
+
+def measure_fp64_peak(dev):
+    """FP64 FMA throughput measured on this GPU (register-only probe in the library), with the SM
+    clocks sampled while it runs."""
+    from paper_2309_11273_gb300 import _binding as B
+    B.pd_probe_fp64(dev, 2)
+    with ClockSampler(dev) as clk:
+        rate, ms = B.pd_probe_fp64(dev, 20)
+    c = clk.summary()
+    out = {"tflops": rate / 1e12, "ms_per_launch": ms, "clocks": c,
+           "how": "pd_probe_fp64: 8 independent FP64 FMA chains per thread, 2048 threads per SM, 20 launches"}
+    if c.get("sm_mhz") and c.get("sm_max_mhz"):
+        out["tflops_at_max_clock"] = rate / 1e12 * c["sm_max_mhz"] / c["sm_mhz"]
+        out["flop_per_clk_per_sm"] = rate / (c["sm_mhz"] * 1e6) / 152.0
     return out
 
 
@@ -333,6 +362,11 @@ def run_gpu(args):
     peaks = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     hbm_note = "measured" if "hbm_gbs" in peaks else "fallback"
+    try:
+        fp64_peak = measure_fp64_peak(dev)
+    except Exception as exc:  # the probe is context for the alu fraction only
+        fp64_peak = None
+        sys.stderr.write("FP64 probe failed: %s\n" % exc)
 
     w = W.config3()
     s0 = pd_critical_stretch(w.model, w.E, w.nu, w.Gc, w.delta)
@@ -361,18 +395,28 @@ def run_gpu(args):
         form = "tabled" if tabled else "recompute"
     kname = max(kern, key=kern.get)  # the dominant kernel
     kms = kern[kname]
-    achieved = fl[kname] * nb / (kms * 1e-3) / 1e12
     step_ms = sum(kern.values())
-    roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": recorded_traffic(kname, nb),
-                "peak_note": "FP64 peak from unit counts and clock: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz",
-                "algorithmic": "%g FP64 flop per directed bond (per-step part of the %s form) x %d bonds per launch"
-                               % (fl[kname], form, nb),
-                "kernels": {k: kernel_entry(k, v, fl[k], nb, hbm) for k, v in kern.items()},
-                "frac_recompute_model": (FLOPS_BOND[1] + FLOPS_BOND[2]) * nb / (step_ms * 1e-3) / 1e12
-                / FP64_PEAK_TFLOPS,
-                "model_bytes_frac_of_hbm": (sum(BYTES_BOND.values()) * nb + sum(BYTES_PART.values()) * w.n)
-                / (step_ms * 1e-3) / (hbm * 1e9)}
+    n_part = w.n
+    peak64 = fp64_peak["tflops"] if fp64_peak else None
+    kernels = {k: kernel_entry(k, v, fl[k], nb, n_part, hbm, peak64) for k, v in kern.items()}
+    kd = kernels[kname]
+    step_bytes = sum(BYTES_KERNEL[k][0] * nb + BYTES_KERNEL[k][1] * n_part for k in kern)
+    bb, bp = BYTES_KERNEL[kname]
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": kd["achieved_gbs"], "peak": hbm, "unit": "GB/s",
+                "frac": kd["frac"], "traffic": kd["traffic"],
+                "peak_note": "%s HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" % hbm_note,
+                "algorithmic": "%.3f B per directed bond x %d bonds + %g B per particle x %d particles per launch "
+                               "(neighbour index, status bits, particle state)" % (bb, nb, bp, n_part),
+                "step_frac": step_bytes / (step_ms * 1e-3) / 1e9 / hbm, "step_ms": step_ms,
+                "step_algorithmic_bytes": step_bytes, "kernels": kernels}
+    if fp64_peak:
+        ach64 = fl[kname] * nb / (kms * 1e-3) / 1e12
+        roofline["alu"] = {"bound": "alu", "kernel": kname, "achieved": ach64, "peak": peak64, "unit": "TFLOP/s",
+                           "frac": ach64 / peak64, "peak_measured": fp64_peak,
+                           "algorithmic": "%g FP64 flop per directed bond (per-step part of the %s form) x %d "
+                                          "bonds per launch" % (fl[kname], form, nb),
+                           "frac_recompute_model": (FLOPS_BOND[1] + FLOPS_BOND[2]) * nb / (step_ms * 1e-3) / 1e12
+                           / peak64}
 
     # end to end through the C ABI with pinned host buffers: H2D of (u, v), one step, D2H of u
     n, dim = w.n, w.dim
@@ -402,7 +446,8 @@ def run_gpu(args):
 
     forms = {}
     if not args.no_forms:
-        forms = run_forms(args, stream, dev, world, value, nb, hbm, hbm_note)
+        forms = run_forms(args, stream, dev, world, value, nb, hbm, hbm_note,
+                          fp64_peak["tflops"] if fp64_peak else None)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -434,6 +479,34 @@ def mixed_roofline(prof, a1, a2, bytes1, bytes2, hbm, hbm_note, staged):
                            "ms": prof["pass%d_ms" % other]},
             "pass1_ms": prof["pass1_ms"], "pass2_ms": prof["pass2_ms"],
             "step_frac": (bytes1 + bytes2) / ((prof["pass1_ms"] + prof["pass2_ms"]) * 1e-3) / 1e9 / hbm}
+
+
+def mixed_error_on_workload(w, s0, stream, dev, nsteps):
+    """The mixed form against the plain FP64 GPU path on the benchmark's own workload: both run
+    nsteps from the same initial state (the FP64 path is held to 1e-12 of the oracle by the parity
+    tests); rel-L2(u), the largest per-particle error, and the directed bonds whose status differs,
+    beside the FP64 run's broken count.  The mixed run also decides every bond in FP64 on its own
+    state (validation mode) and counts the decisions that differ."""
+    from paper_2309_11273_gb300 import PD_FP64, PD_MIXED, Simulation
+    from paper_2309_11273_gb300 import _binding as B
+    res = {}
+    for prec in (PD_FP64, PD_MIXED):
+        sim = Simulation(w, s0=s0, precision=prec, stream=stream.cuda_stream, device=dev)
+        if prec == PD_MIXED:
+            sim.set_option(B.PD_OPT_VALIDATE, 1)
+        sim.step(nsteps)
+        u = sim.state()[0]
+        intact = sim.neighbors()[2]
+        res[prec] = (u, intact, sim.stats())
+        sim.close()
+    u64, s64, _ = res[PD_FP64]
+    u32, s32, st32 = res[PD_MIXED]
+    return {"workload": "this workload, first %d steps from the same state" % nsteps,
+            "reference": "plain FP64 GPU path",
+            "rel_l2_u": float(np.linalg.norm(u32 - u64) / np.linalg.norm(u64)),
+            "max_particle_err_rel": float(np.abs(u32 - u64).max() / np.abs(u64).max()),
+            "status_mismatches": int((s32 != s64).sum()), "broken_fp64": int((s64 == 0).sum()),
+            "validate_mismatches": int(st32["validate_mismatches"]), "band_rechecks": int(st32["band_rechecks"])}
 
 
 def run_matrix_scheme(args, stream, dev, world, w):
@@ -476,7 +549,7 @@ def run_matrix_scheme(args, stream, dev, world, w):
     return res
 
 
-def run_forms(args, stream, dev, world, fp64_value, nb, hbm, hbm_note):
+def run_forms(args, stream, dev, world, fp64_value, nb, hbm, hbm_note, fp64_tflops=None):
     """Mixed precision on the same workload and the batched form, as speed-ups over plain FP64."""
     from paper_2309_11273_gb300 import PD_FP64, PD_MIXED, PD_NONLINEAR, BatchSimulation, Simulation, pd_critical_stretch
     from paper_2309_11273_gb300 import _binding as B
@@ -500,8 +573,7 @@ def run_forms(args, stream, dev, world, fp64_value, nb, hbm, hbm_note):
     a1 = bytes1 / (prof["pass1_ms"] * 1e-3) / 1e9
     out["mixed"] = {"value": mval, "unit": UNIT, "speedup_vs_fp64": mval / fp64_value,
                     "ms_per_step": ms / steps, "dtype": "f32 bond arithmetic, f64 integration",
-                    "stated_error": "rel-L2(u) vs FP64 oracle <= 2e-5 after 100 steps and <= 1e-4 after 1000 "
-                                    "(configuration 1); zero bond decisions differing from FP64 on its own state",
+                    "stated_error": mixed_error_on_workload(w, s0, stream, dev, 200),
                     "band_rechecks": st["band_rechecks"], "mapping": {"block": mmap[0], "split": mmap[1]},
                     "roofline": mixed_roofline(prof, a1, a2, bytes1, bytes2, hbm, hbm_note, staged)}
     # geometrically nonlinear bonds (Eqs 1.10, 1.13, 1.14) in FP64 on the same workload
@@ -542,11 +614,15 @@ def run_forms(args, stream, dev, world, fp64_value, nb, hbm, hbm_note):
                         "kinematics": "e = |Y| - |xi|, force along Y/|Y| (Eqs 1.10, 1.13, 1.14)",
                         "vs_linearized_fp64": nval / fp64_value, "mapping": {"block": nmap[0], "split": nmap[1]},
                         "roofline": {"bound": "alu", "kernel": nkern, "achieved": ach,
-                                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                                     "peak": fp64_tflops, "unit": "TFLOP/s",
+                                     "frac": ach / fp64_tflops if fp64_tflops else None,
+                                     "peak_note": "measured FP64 FMA rate (pd_probe_fp64)",
                                      "traffic": recorded_traffic(nkern, nb),
                                      "algorithmic": "%g FP64 flop per directed bond (%s form; root, divide = 1) x %d"
                                                     " bonds" % (nfl, nform, nb),
-                                     "kernels": {kk: kernel_entry(kk, v, nfls[kk], nb, hbm) for kk, v in nkerns.items()}}}
+                                     "kernels": {kk: {"ms": v, "flop_per_bond": nfls[kk],
+                                                      "traffic": recorded_traffic(kk, nb)}
+                                                 for kk, v in nkerns.items()}}}
     # adaptive dynamic relaxation (the quasi-static solver) on the same block, FP64: per iteration
     # the two passes plus a damping reduction and the relaxation update
     sim = Simulation(w, s0=s0, precision=PD_FP64, stream=stream.cuda_stream, device=dev)
@@ -579,11 +655,20 @@ def run_forms(args, stream, dev, world, fp64_value, nb, hbm, hbm_note):
         res[name] = world * bnb * k / (ms * 1e-3)
         res["bonds"] = bnb
         bs.close()
+    bms = world * res["bonds"] / res["mixed"] * 1e3  # ms per step of the mixed batch (per replica)
+    bbytes = (BYTES_BOND[1] + BYTES_BOND[2]) * res["bonds"] + (BYTES_PART_2D[1] + BYTES_PART_2D[2]) * bw.n
     out["batched"] = {"value": res["mixed"], "unit": UNIT, "workload": "256 independent plane-stress plates, "
                       "sides U{20..200}, delta in {3.015, 4.015} dx, one context, 100-step CUDA graphs",
                       "particles": int(bw.n), "directed_bonds": res["bonds"], "fp64_value": res["fp64"],
                       "speedup_vs_fp64": res["mixed"] / res["fp64"], "dtype": "f32 bond arithmetic, f64 integration",
-                      "mapping": {"fp64": res["mapping_fp64"], "mixed": res["mapping_mixed"]}}
+                      "mapping": {"fp64": res["mapping_fp64"], "mixed": res["mapping_mixed"]},
+                      "roofline": {"bound": "hbm", "kernel": "mixed step (both passes)",
+                                   "achieved": bbytes / (bms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                                   "frac": bbytes / (bms * 1e-3) / 1e9 / hbm, "peak_note": hbm_note,
+                                   "traffic": None,
+                                   "algorithmic": "%.3f B per directed bond + %g B per particle per step (2D, with "
+                                                  "the edge-traction body force)"
+                                                  % (BYTES_BOND[1] + BYTES_BOND[2], BYTES_PART_2D[1] + BYTES_PART_2D[2])}}
     return out
 
 
@@ -601,6 +686,8 @@ def main():
                     help="with --profile-target: configuration 3's geometry at a quarter of its particles "
                          "(100x50x50, same dx and horizon), so that multi-pass ncu captures of the tabled "
                          "FP64 kernels hold a few GB")
+    ap.add_argument("--profile-pairs", type=int, choices=[0, 1], default=1,
+                    help="with --profile-target fp64: 0 runs the single-pass FP64 pass 1 (PD_OPT_PAIRS = 0)")
     ap.add_argument("--sweep", action="store_true",
                     help="one JSON line per configuration (1-5): FP64 and mixed GPU rates and the oracle's "
                          "rate on all host cores and on one")
@@ -612,7 +699,7 @@ def main():
     import __graft_entry__
     __graft_entry__.build()
     if args.profile_target:
-        return profile_target(args.profile_target, args.profile_quarter)
+        return profile_target(args.profile_target, args.profile_quarter, args.profile_pairs)
     if args.sweep:
         return run_sweep(args)
     return run_gpu(args)
@@ -675,14 +762,15 @@ def run_sweep(args):
     return 0
 
 
-def profile_target(form, quarter=False):
+def profile_target(form, quarter=False, pairs=1):
     """Workload of the benchmark in one precision, 4 eager time steps (ncu captures this command)."""
     from paper_2309_11273_gb300 import PD_FP64, PD_LINEARIZED, PD_MIXED, PD_NONLINEAR, Simulation, pd_critical_stretch
     from paper_2309_11273_gb300 import workloads as W
     w = W.notched_block(nx=100, ny=50, nz=50) if quarter else W.config3()
     s0 = pd_critical_stretch(w.model, w.E, w.nu, w.Gc, w.delta)
     sim = Simulation(w, s0=s0, precision=PD_MIXED if form.startswith("mixed") else PD_FP64, graph_chunk=0,
-                     kinematics=PD_NONLINEAR if form.endswith("nonlinear") else PD_LINEARIZED)
+                     kinematics=PD_NONLINEAR if form.endswith("nonlinear") else PD_LINEARIZED,
+                     pairs=None if pairs else 0)
     sim.step(4)
     sim.sync()
     print(json.dumps({"profile_target": form, "particles": w.n, "directed_bonds": sim.nbonds, "stats": sim.stats()}))

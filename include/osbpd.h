@@ -291,6 +291,13 @@ pd_status pd_get_option(pd_ctx* c, int32_t option, int64_t* value);
 pd_status pd_get_profile(pd_ctx* c, int32_t kernel, double* total_ms, int64_t* launches,
                          int32_t reset);
 
+/* Measured FP64 fused multiply-add throughput of device `device` (not part of the method: the
+ * denominator of the FP64 kernels' arithmetic roofline).  Runs `repeats` launches of a register-only
+ * kernel (8 independent FMA chains per thread, 2048 threads per SM) and returns the rate in flop/s
+ * (FMA = 2 flop) in *flops_per_s and the mean launch time in *ms_per_launch (may be NULL).  It
+ * synchronizes, and allocates and frees 8 bytes of device memory.  Errors: PD_ERR_ARG, PD_ERR_CUDA. */
+pd_status pd_probe_fp64(int32_t device, int32_t repeats, double* flops_per_s, double* ms_per_launch);
+
 /* Number of particles, dimension and storage of the context (for sizing host buffers). */
 pd_status pd_get_info(pd_ctx* c, int64_t* n, int32_t* dim, int64_t* device_bytes);
 
@@ -314,17 +321,22 @@ pd_status pd_load_state(pd_ctx* c, const char* path);
  * fixed buffers, real-time loops that must never enter the allocator, or callers recording work
  * while allocation is forbidden.  Such callers cannot create a pd_ctx (which cudaMallocs its arrays).
  *
- * What it computes (on the calling thread's current device, on `stream`, enqueue only): for a body
- * with no constraints, no body force and no bond breaking, m_i over the given family (Eq 1.9),
- * theta_i over its intact bonds (Eq 1.6), the forces of Eq 2.2 and the update of Eq 2.11:
+ * What it computes (on the calling thread's current device, on `stream`, enqueue only), for a body
+ * with no constraints, no body force and no bond breaking: each particle's weighted volume over the
+ * given family, its dilatation over the intact bonds, the linearized bond forces summed over the
+ * intact bonds, and one explicit update of velocity then displacement:
  * v_out = v + dt F / (rho V), u_out = u + dt v_out.  Same model constants as pd_params.
- * Arguments (all arrays DEVICE memory owned by the caller, in the caller's particle order):
+ * Arguments (all arrays DEVICE memory of the current device, owned by the caller, in the caller's
+ * particle order):
  *   x_dev, y_dev, z_dev (NULL unless PD_3D), vol_dev: n doubles each;
  *   row_ptr_dev (n + 1 int64), col_dev (row_ptr[n] int32): the family as CSR (e.g. from
  *   pd_get_neighbors); intact_dev: one byte per CSR entry (1 intact), or NULL for all intact;
- *   u_dev, v_dev -> u_out_dev, v_out_dev: dim * n SoA doubles (outputs must not alias inputs);
- *   theta_dev: n doubles or NULL.  stream: cudaStream_t or NULL (legacy default stream).
- * Limits: n <= 1,048,576.  Larger n returns PD_ERR_ARG with a message; so do NULL or host pointers.
+ *   u_dev, v_dev -> u_out_dev, v_out_dev: dim * n SoA doubles; theta_dev: n doubles or NULL.
+ *   No output (u_out, v_out, theta) may overlap another output or an input.
+ *   stream: cudaStream_t or NULL (legacy default stream).
+ * Limits: n <= 1,048,576.  Larger n returns PD_ERR_ARG with a message; so do NULL pointers, host
+ * pointers, pointers to another GPU's memory and overlapping outputs (col and intact, whose length
+ * the call does not read on the host, are checked at their first entry only).
  * Scratch: its one intermediate (2 doubles per particle) lives in a fixed 16 MiB device array that
  * every GPU loading the library holds until the process exits.  All calls share it and it keeps
  * the last call's contents (each call rewrites every entry it reads); calls that overlap on the GPU

@@ -36,7 +36,7 @@ EXPORTED = ["pd_critical_stretch", "pd_material_constants", "pd_set_prescribed_v
             "pd_set_bc", "pd_set_state", "pd_step", "pd_sync", "pd_get_damage", "pd_get_state",
             "pd_num_bonds", "pd_get_neighbors", "pd_get_stats", "pd_check_state", "pd_autotune",
             "pd_set_option", "pd_get_option", "pd_get_profile", "pd_get_info", "pd_save_state",
-            "pd_load_state", "pd_step_noalloc", "pd_last_error", "pd_destroy"]
+            "pd_load_state", "pd_step_noalloc", "pd_probe_fp64", "pd_last_error", "pd_destroy"]
 
 
 class pd_params(ctypes.Structure):
@@ -110,6 +110,7 @@ def lib(path: str = LIB_PATH):
             L.pd_load_state.argtypes = [_vp, ctypes.c_char_p]
             L.pd_step_noalloc.argtypes = ([ctypes.c_int32] + [ctypes.c_double] * 4 + [ctypes.c_int64]
                                           + [_vp] * 12 + [_vp])
+            L.pd_probe_fp64.argtypes = [ctypes.c_int32, ctypes.c_int32, _d, _d]
             L.pd_last_error.restype = ctypes.c_char_p
             L.pd_destroy.argtypes = [_vp]
             L.pd_destroy.restype = None
@@ -293,6 +294,13 @@ def pd_save_state(h, path):
 
 def pd_load_state(h, path):
     _check(lib().pd_load_state(h, os.fsencode(path)))
+
+
+def pd_probe_fp64(device=0, repeats=20):
+    """Measured FP64 FMA throughput of a device: (flop/s, ms per launch)."""
+    f, ms = ctypes.c_double(), ctypes.c_double()
+    _check(lib().pd_probe_fp64(int(device), int(repeats), ctypes.byref(f), ctypes.byref(ms)))
+    return f.value, ms.value
 
 
 def pd_get_info(h):

@@ -760,6 +760,63 @@ pd_status pd_load_state(pd_ctx* c, const char* path) {
   return PD_OK;
 }
 
+}  // extern "C"
+
+namespace pd_probe {
+// FP64 fused multiply-add throughput, registers only: 8 independent chains per thread, so that the
+// FP64 pipe, not the dependency latency, sets the rate.  Iterates x <- x a + b with |a| < 1 (bounded).
+__global__ void __launch_bounds__(256) k_probe_dfma(double* out, int iters, double a, double b) {
+  double x[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) x[k] = (threadIdx.x + 1) * 1e-9 * (k + 1);
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = fma(x[k], a, b);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += x[k];
+  if (s == -1.0) out[0] = s;  // never true: keeps the chains live without a store per thread
+}
+}  // namespace pd_probe
+
+extern "C" {
+
+pd_status pd_probe_fp64(int32_t device, int32_t repeats, double* flops_per_s, double* ms_per_launch) {
+  clear_error();
+  if (!flops_per_s || repeats < 1) return fail(PD_ERR_ARG, "flops_per_s is required and repeats must be >= 1");
+  PD_CUDA(cudaSetDevice(device));
+  int sms = 0;
+  PD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+  double* out = nullptr;
+  PD_CUDA(cudaMalloc(&out, sizeof(double)));
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  const int iters = 1 << 14, tb = 256;
+  const unsigned grid = (unsigned)sms * 8;  // 2048 resident threads per SM
+  float ms = 0.0f;
+  if (e == cudaSuccess) {
+    pd_probe::k_probe_dfma<<<grid, tb, 0, s>>>(out, 64, 0.999999, 1e-9);  // warm-up
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < repeats; ++r) pd_probe::k_probe_dfma<<<grid, tb, 0, s>>>(out, iters, 0.999999, 1e-9);
+    cudaEventRecord(e1, s);
+    e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (s) cudaStreamDestroy(s);
+  cudaFree(out);
+  if (e != cudaSuccess) return cuda_fail(e, "FP64 probe");
+  const double flops = 2.0 * 8.0 * iters * (double)grid * tb * repeats;
+  *flops_per_s = flops / (ms * 1e-3);
+  if (ms_per_launch) *ms_per_launch = ms / repeats;
+  return PD_OK;
+}
+
 pd_status pd_get_info(pd_ctx* c, int64_t* n, int32_t* dim, int64_t* device_bytes) {
   pd_status st = check_ctx(c, false);
   if (st != PD_OK) return st;

@@ -46,13 +46,22 @@ pd_status scratch_for_current_device(double2** out) {
   return PD_OK;
 }
 
-bool on_device(const void* p) {
+// Device (or managed) memory that the current device can address: a host array, or device memory
+// of another GPU, would reach the kernels as an address they cannot use.
+bool on_device(const void* p, int dev) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  if (at.type == cudaMemoryTypeManaged) return true;
+  return at.type == cudaMemoryTypeDevice && at.device == dev;
+}
+
+// Byte ranges [p, p + bytes) of two arrays overlap.
+bool overlap(const void* p, size_t pb, const void* q, size_t qb) {
+  const uintptr_t a = (uintptr_t)p, b = (uintptr_t)q;
+  return a < b + qb && b < a + pb;
 }
 
 struct NoAllocArgs {
@@ -109,7 +118,8 @@ __global__ void k_noalloc_force_update(NoAllocArgs a) {
       d = fma(ez, a.u[2 * n + j] - a.u[2 * n + i], d);
     }
     const double2 tj = a.scratch[j];
-    const double c = fma(ti.y + tj.y, d / q, ti.x + tj.x) * a.vol[j];
+    // a coincident pair (q = 0) carries no bond direction: no force, as in the context path's tables
+    const double c = fma(ti.y + tj.y, q > 0.0 ? d / q : 0.0, ti.x + tj.x) * a.vol[j];
     f[0] = fma(c, ex, f[0]);
     f[1] = fma(c, ey, f[1]);
     f[2] = fma(c, ez, f[2]);
@@ -143,11 +153,39 @@ extern "C" pd_status pd_step_noalloc(int32_t model, double E, double nu, double 
   if (!x_dev || !y_dev || (dim == 3) != (z_dev != nullptr) || !vol_dev || !row_ptr_dev || !col_dev || !u_dev ||
       !v_dev || !u_out_dev || !v_out_dev)
     return fail(PD_ERR_ARG, "a required device pointer is NULL (z must be given exactly for PD_3D)");
-  if (u_out_dev == u_dev || v_out_dev == v_dev || u_out_dev == v_dev)
-    return fail(PD_ERR_ARG, "outputs must not alias the inputs");
-  const void* ptrs[] = {x_dev, y_dev, vol_dev, row_ptr_dev, col_dev, u_dev, v_dev, u_out_dev, v_out_dev};
+  int dev = -1;
+  cudaError_t e0 = cudaGetDevice(&dev);
+  if (e0 != cudaSuccess) return cuda_fail(e0, "cudaGetDevice");
+  // every array the kernels touch must be addressable by the current device
+  const size_t nb = (size_t)n * sizeof(double), vb = (size_t)dim * nb;
+  const void* ptrs[] = {x_dev, y_dev, z_dev, vol_dev, row_ptr_dev, col_dev, intact_dev,
+                        u_dev, v_dev, u_out_dev, v_out_dev, theta_dev};
   for (const void* p : ptrs)
-    if (!on_device(p)) return fail(PD_ERR_ARG, "every array must be device (or managed) memory");
+    if (p && !on_device(p, dev))
+      return fail(PD_ERR_ARG, "every array must be device (or managed) memory of the current device");
+  // The kernels write u_out, v_out and theta while other threads still read u, v (and the rest):
+  // no output may share a byte with an input of known length or with another output.  The lengths
+  // of col and intact (row_ptr[n] entries) are not read on the host (that would synchronize), so for
+  // those two only their first entry is checked against the outputs.
+  {
+    const size_t rp_b = (size_t)(n + 1) * sizeof(int64_t);
+    struct Range {
+      const void* p;
+      size_t b;
+    };
+    const Range in[] = {{x_dev, nb}, {y_dev, nb}, {z_dev, z_dev ? nb : 0}, {vol_dev, nb}, {row_ptr_dev, rp_b},
+                        {col_dev, sizeof(int32_t)}, {intact_dev, intact_dev ? 1 : 0}, {u_dev, vb}, {v_dev, vb}};
+    const Range out[] = {{u_out_dev, vb}, {v_out_dev, vb}, {theta_dev, theta_dev ? nb : 0}};
+    for (int o = 0; o < 3; ++o) {
+      if (!out[o].p) continue;
+      for (const Range& r : in)
+        if (r.p && r.b && overlap(out[o].p, out[o].b, r.p, r.b))
+          return fail(PD_ERR_ARG, "an output array overlaps an input array");
+      for (int o2 = o + 1; o2 < 3; ++o2)
+        if (out[o2].p && overlap(out[o].p, out[o].b, out[o2].p, out[o2].b))
+          return fail(PD_ERR_ARG, "two output arrays overlap");
+    }
+  }
   double2* scratch = nullptr;
   pd_status st = scratch_for_current_device(&scratch);
   if (st != PD_OK) return st;

@@ -21,6 +21,7 @@
 #include <cmath>
 
 #include "pd_internal.h"
+#include "pd_order.h"
 
 namespace pd {
 namespace {
@@ -794,7 +795,7 @@ __global__ void __launch_bounds__(512) k_pass1_f64t(StepArgs a, const double4* _
         if (THETA && k < t.W) td[(int64_t)k << 5] = d;
         bool intact = (wd[u] >> t.lane) & 1u;
         if (a.check) {
-          const bool ge = __double_as_longlong(d) >= __double_as_longlong(g[u].w);  // d >= s0 |xi|^2
+          const bool ge = pd_ge_threshold(d, g[u].w);  // d >= s0 |xi|^2
           const bool brk = intact && can_break && ge;
           const unsigned m = __ballot_sync(kFull, brk);
           if (m) {
@@ -876,7 +877,7 @@ __global__ void __launch_bounds__(512) k_pass1a_f64p(StepArgs a, const double4* 
     if (a.check) {
       const uint32_t wd = bw[k];  // this warp's owned bits change only here
       const bool brk = mine && can_break && ((wd >> t.lane) & 1u) &&
-                       __double_as_longlong(d) >= __double_as_longlong(g.w);  // d >= s0 |xi|^2
+                       pd_ge_threshold(d, g.w);  // d >= s0 |xi|^2
       const unsigned m = __ballot_sync(kFull, brk);
       if (m) {
         if (t.lane == 0) {
@@ -1025,7 +1026,7 @@ __global__ void __launch_bounds__(512) k_check_f64p(StepArgs a, const double4* _
         const double4 uj = disp[j];
         double d = g.x * (uj.x - ui.x) + g.y * (uj.y - ui.y);
         if (DIM == 3) d = fma(g.z, uj.z - ui.z, d);
-        brk = __double_as_longlong(d) >= __double_as_longlong(g.w);  // d >= s0 |xi|^2
+        brk = pd_ge_threshold(d, g.w);  // d >= s0 |xi|^2
       }
     }
     const unsigned m = __ballot_sync(kFull, brk);

@@ -23,7 +23,7 @@ def lib():
 def declared_functions():
     src = open(os.path.join(ROOT, "include", "osbpd.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(pd_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(pd_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_header_declarations_match_binding():
@@ -32,7 +32,7 @@ def test_header_declarations_match_binding():
 
 def test_library_exports_every_declared_symbol(lib):
     out = subprocess.run(["nm", "-D", "--defined-only", BL.LIB], capture_output=True, text=True, check=True).stdout
-    exported = set(re.findall(r"\bT\s+(pd_[a-z_]+)\b", out))
+    exported = set(re.findall(r"\bT\s+(pd_[a-z0-9_]+)\b", out))
     for name in declared_functions():
         assert name in exported, name
         assert hasattr(lib, name)

@@ -13,6 +13,7 @@ import oracle as O
 from paper_2309_11273_gb300 import PD_FP64, PD_MIXED, PD_NONLINEAR, PD_LINEARIZED, Simulation
 from paper_2309_11273_gb300 import _binding as B
 from paper_2309_11273_gb300 import workloads as W
+from parity import elem
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-12
@@ -59,6 +60,7 @@ def test_adr_matches_oracle(dim, shape, kin):
         u, v, _ = sim.state()
         dv = np.linalg.norm(v - ref.v) / np.linalg.norm(ref.u)
         assert rel(u, ref.u) <= TOL and dv <= TOL, (rel(u, ref.u), dv)
+        assert elem(u, ref.u) <= TOL and np.abs(v - ref.v).max() <= TOL * np.abs(ref.u).max()
     sim.close()
 
 
@@ -96,7 +98,7 @@ def test_adr_notched_block_load_stepping_with_breaking():
     _, margins, _ = ref.adr_step(10)
     sim.step(10)
     u = sim.state()[0]
-    assert rel(u, ref.u) <= TOL and margins.min() > 1e-9
+    assert rel(u, ref.u) <= TOL and elem(u, ref.u) <= TOL and margins.min() > 1e-9
     assert np.array_equal(sim.neighbors()[2], ref.status) and (ref.status == 0).sum() > 1000
     ref.adr_step(190)
     sim.step(190)
