@@ -148,7 +148,7 @@ typedef enum {
                               of the GPU's global timer) expires; the warps skip their outputs
                               and the next pd_sync / pd_get_* returns PD_ERR_TIMEOUT.  Default 0. */
   PD_OPT_SOLVER = 9,       /* pd_solver: PD_SOLVER_EXPLICIT (0, default) or PD_SOLVER_ADR (1) */
-  PD_OPT_PAIRS = 10        /* PD_FP64 with the bond cache on: 1 (default) = form each bond's
+  PD_OPT_PAIRS = 10,       /* PD_FP64 with the bond cache on: 1 (default) = form each bond's
                               extension (linearized: xi.(u_j - u_i); nonlinear: e and 1/|Y|) and
                               failure test once for its two directed entries (the failure check and
                               dilatation pass then runs as two kernels); 0 = once per entry.
@@ -156,6 +156,15 @@ typedef enum {
                               switched between steps; nonlinear theta sums differ in rounding
                               order only.  Has no effect when the build could not pair
                               every entry (pd_get_option then reports 0). */
+  PD_OPT_LATTICE = 11      /* PD_MIXED with linearized bonds: 1 (default) = when every body's
+                              particles lie on a regular lattice (bond vectors h n with integer n to
+                              within 2^-30 h, uniform volumes, horizon up to 5 h in 3D and 8 h in
+                              2D), pd_build_neighbors lays the family out by lattice direction (slot
+                              k of every slice = direction k for every lane) and the step kernels
+                              take each slot's bond vector from a table instead of gathering
+                              coordinates; 0 = the general layout and kernels.  Set before
+                              pd_build_neighbors; after it, pd_get_option reports whether the built
+                              layout is the lattice one. */
 } pd_option;
 
 /* Solvers (PD_OPT_SOLVER).

@@ -77,6 +77,21 @@ void free_build(pd_ctx* c) {
   c->u32[0] = c->u32[1] = nullptr;
   c->thm32 = nullptr;
   c->mu32 = c->aA32 = c->theta32 = nullptr;
+  c->lattice = false;
+  c->lat_f = nullptr;
+}
+
+void release(pd_ctx* c, void* p) {
+  if (!p) return;
+  for (size_t k = 0; k < c->allocs.size(); ++k) {
+    if (c->allocs[k] != p) continue;
+    cudaFree(p);
+    c->device_bytes -= (int64_t)c->alloc_bytes[k];
+    c->allocs.erase(c->allocs.begin() + k);
+    c->alloc_bytes.erase(c->alloc_bytes.begin() + k);
+    if (k < c->n_create_allocs) --c->n_create_allocs;
+    return;
+  }
 }
 
 void free_all(pd_ctx* c) {
@@ -469,11 +484,14 @@ pd_status pd_get_neighbors(pd_ctx* c, int64_t* row_ptr, int32_t* col, uint8_t* i
     const int64_t k = inv[u];
     const int64_t s = k >> 5, lane = k & 31;
     row.clear();
-    for (int t = 0; t < hcnt[k]; ++t) {
+    const int W = (int)((sptr[s + 1] - sptr[s]) >> 5);
+    for (int t = 0; t < W; ++t) {  // a slot holds a bond unless it points at the particle itself
       const int64_t e = sptr[s] + 32 * (int64_t)t + lane;
+      if (hcol[e] == (int32_t)k) continue;
       const uint8_t ok = (hbits[(sptr[s] >> 5) + t] >> lane) & 1u;
       row.emplace_back((int32_t)c->perm[hcol[e]], ok);
     }
+    if ((int64_t)row.size() != hcnt[k]) return fail(PD_ERR_STATE, "neighbour layout does not match the family sizes");
     std::sort(row.begin(), row.end());
     for (size_t t = 0; t < row.size(); ++t) {
       col[row_ptr[u] + t] = row[t].first;
@@ -555,6 +573,9 @@ pd_status pd_set_option(pd_ctx* c, int32_t option, int64_t value) {
     case PD_OPT_EXPIRE_WAITS:
       c->expire_waits = value != 0;
       break;
+    case PD_OPT_LATTICE:
+      c->lattice_opt = value != 0;  // read by the next pd_build_neighbors
+      break;
     case PD_OPT_PAIRS:
       // A failure check of the pair form marks slices whose bS its next pass 1b recomputes; the
       // other form never reads those marks, so a switch recomputes every bS before the next step.
@@ -590,6 +611,7 @@ pd_status pd_get_option(pd_ctx* c, int32_t option, int64_t* value) {
     case PD_OPT_EXPIRE_WAITS: *value = c->expire_waits; break;
     case PD_OPT_SOLVER: *value = c->solver; break;
     case PD_OPT_PAIRS: *value = (c->pairs && c->pairs_ok && c->precision == PD_FP64) ? 1 : 0; break;
+    case PD_OPT_LATTICE: *value = c->built ? (c->lattice ? 1 : 0) : c->lattice_opt; break;
     default: return fail(PD_ERR_ARG, "unknown option");
   }
   return PD_OK;
@@ -833,9 +855,9 @@ pd_status pd_autotune(pd_ctx* c, int32_t trial_steps, int32_t* block_out, int32_
   cudaDeviceProp prop;
   PD_CUDA(cudaGetDeviceProperties(&prop, c->device));
   char key[512];
-  std::snprintf(key, sizeof(key), "osbpd n=%lld bonds=%lld entries=%lld dim=%d prec=%d bodies=%d dev=%s",
+  std::snprintf(key, sizeof(key), "osbpd n=%lld bonds=%lld entries=%lld dim=%d prec=%d bodies=%d lattice=%d dev=%s",
                 (long long)c->n, (long long)c->nbonds, (long long)c->nentries, c->dim, c->precision,
-                c->nbodies, prop.name);
+                c->nbodies, c->lattice ? 1 : 0, prop.name);
   for (char* p = key; *p; ++p)
     if (*p == '\n' || *p == '|') *p = ' ';
   const char* cache = std::getenv("PD_AUTOTUNE_CACHE");
@@ -921,6 +943,7 @@ pd_status pd_autotune(pd_ctx* c, int32_t trial_steps, int32_t* block_out, int32_
     for (int bl : blocks) {
       for (int sp : splits) {
         if ((bl / 32) % sp) continue;
+        if (c->lattice && sp != 1) continue;  // the lattice kernels run one warp per slice
         for (int po = 0; po < (try_pairs ? 2 : 1); ++po) {
           c->block = bl;
           c->split = sp;

@@ -17,6 +17,7 @@
 #include <numeric>
 
 #include "pd_internal.h"
+#include "pd_lattice.h"
 
 namespace pd {
 namespace {
@@ -183,7 +184,9 @@ __global__ void k_slice_width(int64_t nslices, const int32_t* cnt, int32_t* widt
 }
 
 // Initial status words (every built bond intact) and the per-particle sums m_i (Eq 1.9) and
-// D_i = sum_j V_j (Eq 1.31 denominator), both in FP64 over the built family.
+// D_i = sum_j V_j (Eq 1.31 denominator), both in FP64 over the built family.  A slot holds a bond
+// when its neighbour is not the particle itself (unused slots point at the particle), in both the
+// sorted and the lattice layout.
 template <int DIM>
 __global__ void k_init_bonds(BuildArgs A) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -192,14 +195,15 @@ __global__ void k_init_bonds(BuildArgs A) {
   const int64_t s = i >> 5;
   const int64_t base = A.slice_ptr[s];
   const int W = (int)((A.slice_ptr[s + 1] - base) >> 5);
-  const int cnt = A.cnt[i];
   const double4 pi = A.pos[i];
   double m = 0.0, d = 0.0;
   for (int k = 0; k < W; ++k) {
-    const unsigned word = __ballot_sync(0xffffffffu, k < cnt);
+    const int32_t jk = A.col[base + (int64_t)k * 32 + lane];
+    const bool built = jk != (int32_t)i;
+    const unsigned word = __ballot_sync(0xffffffffu, built);
     if (lane == 0) A.bits[(base >> 5) + k] = word;
-    if (k < cnt) {
-      const int32_t j = A.col[base + (int64_t)k * 32 + lane];
+    if (built) {
+      const int32_t j = jk;
       const double4 pj = A.pos[j];
       const double ex = pj.x - pi.x, ey = pj.y - pi.y, ez = pj.z - pi.z;
       double q = ex * ex + ey * ey;
@@ -264,6 +268,328 @@ __global__ void k_twins(BuildArgs A) {
       atomicAdd(A.missing, 1ull);
     }
   }
+}
+
+// ----------------------------------------------------------------------------- lattice layout
+// A body whose particles sit on a regular lattice of spacing h has every bond vector equal to h n,
+// n an integer vector, and its family (the closed ball of Section 2.1) is the set of lattice
+// directions with |n|^2 <= (delta / h)^2, a prefix of the direction table of pd_lattice.h.  The three
+// kernels below find each body's shortest bond (its spacing), check every bond vector of the sorted
+// layout against h n, and move each bond to the slot of its direction in the lattice layout, where
+// slot k of every slice holds direction k for every lane (unused slots point at the particle).
+struct LatArgs {
+  int64_t n_pad;
+  const double4* pos;
+  const int32_t* body;        // per particle, internal order
+  const int64_t* slice_ptr;   // sorted layout
+  const int32_t* col;
+  const int32_t* cnt;
+  const double* inv_h;        // per body: 1 / h
+  unsigned long long* minq;   // per body: shortest |xi|^2 (bits of a positive double)
+  int* stats;                 // per body: [0] not a lattice, [1] largest |n|^2, [2] largest |n|_1
+  int* emit_fail;             // a bond without a free slot of its direction (duplicate direction)
+  const short* lookup;        // direction index of n (lattice_lookup)
+  int R;                      // component bound of the table
+  const int64_t* slice_ptr2;  // lattice layout
+  int32_t* col2;
+  int32_t* nsum;              // per particle: sum of |n|^2 over its bonds (m_i = V h^2 nsum_i)
+};
+
+template <int DIM>
+__global__ void k_lat_minq(LatArgs L) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= L.n_pad) return;
+  const int cnt = L.cnt[i];
+  if (cnt == 0) return;
+  const int64_t base = L.slice_ptr[i >> 5] + (i & 31);
+  const double4 pi = L.pos[i];
+  double mq = 1e300;
+  for (int k = 0; k < cnt; ++k) {
+    const double4 pj = L.pos[L.col[base + (int64_t)k * 32]];
+    const double ex = pj.x - pi.x, ey = pj.y - pi.y, ez = DIM == 3 ? pj.z - pi.z : 0.0;
+    mq = fmin(mq, ex * ex + ey * ey + ez * ez);
+  }
+  atomicMin(&L.minq[L.body[i]], (unsigned long long)__double_as_longlong(mq));
+}
+
+// n of a bond vector in units of h, with its largest deviation from the integers.
+template <int DIM>
+__device__ __forceinline__ void lat_n(const double4& pi, const double4& pj, double inv_h, int (&n)[3], double& dev) {
+  const double f[3] = {(pj.x - pi.x) * inv_h, (pj.y - pi.y) * inv_h, DIM == 3 ? (pj.z - pi.z) * inv_h : 0.0};
+  dev = 0.0;
+  for (int c = 0; c < 3; ++c) {
+    const double r = rint(f[c]);
+    dev = fmax(dev, fabs(f[c] - r));
+    n[c] = fabs(r) < 1e6 ? (int)r : 1000000;
+  }
+}
+
+template <int DIM>
+__device__ __forceinline__ int lat_dir(const LatArgs& L, const int (&n)[3]) {
+  if (abs(n[0]) > L.R || abs(n[1]) > L.R || abs(n[2]) > (DIM == 3 ? L.R : 0)) return -1;
+  const int s = 2 * L.R + 1;
+  const int idx = DIM == 3 ? ((n[2] + L.R) * s + (n[1] + L.R)) * s + (n[0] + L.R) : (n[1] + L.R) * s + (n[0] + L.R);
+  return L.lookup[idx];
+}
+
+template <int DIM>
+__global__ void k_lat_classify(LatArgs L) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= L.n_pad) return;
+  const int cnt = L.cnt[i];
+  if (cnt == 0) return;
+  const int b = L.body[i];
+  const double inv_h = L.inv_h[b];
+  const int64_t base = L.slice_ptr[i >> 5] + (i & 31);
+  const double4 pi = L.pos[i];
+  int q1 = 0, n1m = 0;
+  bool bad = false;
+  for (int k = 0; k < cnt; ++k) {
+    const double4 pj = L.pos[L.col[base + (int64_t)k * 32]];
+    int n[3];
+    double dev;
+    lat_n<DIM>(pi, pj, inv_h, n, dev);
+    // bond vectors within 2^-30 h of h n (the positions of a lattice, rounded), inside the table
+    if (!(dev <= 9.313225746154785e-10) || lat_dir<DIM>(L, n) < 0) {
+      bad = true;
+      break;
+    }
+    q1 = max(q1, n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    n1m = max(n1m, abs(n[0]) + abs(n[1]) + abs(n[2]));
+  }
+  if (bad) {
+    atomicOr(&L.stats[3 * b], 1);
+    return;
+  }
+  atomicMax(&L.stats[3 * b + 1], q1);
+  atomicMax(&L.stats[3 * b + 2], n1m);
+}
+
+template <int DIM>
+__global__ void k_lat_emit(LatArgs L) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= L.n_pad) return;
+  const int64_t s = i >> 5;
+  const int64_t base2 = L.slice_ptr2[s] + (i & 31);
+  const int W2 = (int)((L.slice_ptr2[s + 1] - L.slice_ptr2[s]) >> 5);
+  for (int k = 0; k < W2; ++k) L.col2[base2 + (int64_t)k * 32] = (int32_t)i;
+  const int cnt = L.cnt[i];
+  const int64_t base = L.slice_ptr[s] + (i & 31);
+  const double4 pi = L.pos[i];
+  const double inv_h = L.inv_h[L.body[i]];
+  int nsum = 0;
+  for (int k = 0; k < cnt; ++k) {
+    const int32_t j = L.col[base + (int64_t)k * 32];
+    int n[3];
+    double dev;
+    lat_n<DIM>(pi, L.pos[j], inv_h, n, dev);
+    const int d = lat_dir<DIM>(L, n);
+    if (d < 0 || d >= W2 || L.col2[base2 + (int64_t)d * 32] != (int32_t)i) {
+      atomicOr(L.emit_fail, 1);
+      continue;
+    }
+    L.col2[base2 + (int64_t)d * 32] = j;
+    nsum += n[0] * n[0] + n[1] * n[1] + n[2] * n[2];
+  }
+  L.nsum[i] = nsum;
+}
+
+// Tries the lattice layout for a mixed-precision context with linearized bonds (called after the
+// sorted layout and its status words are built).  Every body must have uniform volumes and bond
+// vectors within 2^-30 h of h n with n inside the direction table; otherwise the sorted layout stays
+// and *done is false.  On success the context's col, bits and slice_ptr are replaced, m_i and D_i
+// are recomputed over the new slots, and the per-particle factors of the lattice kernels are set.
+pd_status build_lattice(pd_ctx* c, BuildArgs& A, bool* done) {
+  *done = false;
+  const int dim = c->dim, nb = c->nbodies;
+  const int64_t n = c->n, n_pad = c->n_pad;
+  for (int b = 0; b < nb; ++b) {
+    const double v0 = c->hvol[c->body_off[b]];
+    for (int64_t u = c->body_off[b]; u < c->body_off[b + 1]; ++u)
+      if (c->hvol[u] != v0) return PD_OK;  // non-uniform volumes: sorted layout
+  }
+  cudaStream_t s = c->stream;
+  const std::vector<short> cube = lattice_lookup(dim);
+  double* d_inv_h = nullptr;
+  unsigned long long* d_minq = nullptr;
+  int* d_stats = nullptr;
+  short* d_lookup = nullptr;
+  int32_t* d_nsum = nullptr;
+  int64_t* sptr2_dev = nullptr;
+  int32_t* col2 = nullptr;
+  uint32_t* bits2 = nullptr;
+  auto cleanup = [&]() {
+    cudaFree(d_inv_h);
+    cudaFree(d_minq);
+    cudaFree(d_stats);
+    cudaFree(d_lookup);
+    cudaFree(d_nsum);
+  };
+  auto tmp = [&](void** p, size_t bytes) -> bool {
+    if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    return true;
+  };
+  if (!tmp((void**)&d_inv_h, sizeof(double) * nb) || !tmp((void**)&d_minq, sizeof(unsigned long long) * nb) ||
+      !tmp((void**)&d_stats, sizeof(int) * (3 * nb + 1)) || !tmp((void**)&d_lookup, sizeof(short) * cube.size()) ||
+      !tmp((void**)&d_nsum, sizeof(int32_t) * n_pad)) {
+    cleanup();
+    return fail(PD_ERR_OOM, "cudaMalloc of lattice build temporaries failed");
+  }
+  const unsigned long long big = 0x7fefffffffffffffull;  // bits of the largest finite double
+  std::vector<unsigned long long> hminq(nb, big);
+  std::vector<int> hstats(3 * nb + 1, 0);
+  LatArgs L{};
+  L.n_pad = n_pad;
+  L.pos = c->pos;
+  L.body = c->body;
+  L.slice_ptr = c->slice_ptr;
+  L.col = c->col;
+  L.cnt = c->cnt;
+  L.inv_h = d_inv_h;
+  L.minq = d_minq;
+  L.stats = d_stats;
+  L.emit_fail = d_stats + 3 * nb;
+  L.lookup = d_lookup;
+  L.R = dim == 3 ? kLatR3 : kLatR2;
+  L.nsum = d_nsum;
+  const int tb = 128;
+  const unsigned gb = (unsigned)((n_pad + tb - 1) / tb);
+  cudaError_t e = cudaMemcpyAsync(d_minq, hminq.data(), sizeof(unsigned long long) * nb, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_stats, hstats.data(), sizeof(int) * hstats.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_lookup, cube.data(), sizeof(short) * cube.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    if (dim == 3) k_lat_minq<3><<<gb, tb, 0, s>>>(L);
+    else k_lat_minq<2><<<gb, tb, 0, s>>>(L);
+    e = cudaMemcpyAsync(hminq.data(), d_minq, sizeof(unsigned long long) * nb, cudaMemcpyDeviceToHost, s);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    cleanup();
+    return cuda_fail(e, "lattice spacing");
+  }
+  std::vector<double> h(nb), inv_h(nb);
+  for (int b = 0; b < nb; ++b) {
+    double q;
+    std::memcpy(&q, &hminq[b], sizeof(q));
+    if (hminq[b] == big || !(q > 0.0)) {  // a body without bonds
+      cleanup();
+      return PD_OK;
+    }
+    h[b] = std::sqrt(q);
+    inv_h[b] = 1.0 / h[b];
+  }
+  e = cudaMemcpyAsync(d_inv_h, inv_h.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    if (dim == 3) k_lat_classify<3><<<gb, tb, 0, s>>>(L);
+    else k_lat_classify<2><<<gb, tb, 0, s>>>(L);
+    e = cudaMemcpyAsync(hstats.data(), d_stats, sizeof(int) * hstats.size(), cudaMemcpyDeviceToHost, s);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    cleanup();
+    return cuda_fail(e, "lattice check");
+  }
+  std::vector<int> S(nb);
+  for (int b = 0; b < nb; ++b) {
+    if (hstats[3 * b] != 0 || hstats[3 * b + 1] < 1) {
+      cleanup();
+      return PD_OK;
+    }
+    S[b] = lattice_prefix(dim, hstats[3 * b + 1]);
+  }
+  // slice widths of the lattice layout: the largest family prefix among the slice's bodies, rounded
+  // up to a multiple of 4 (16-byte aligned status words for the bulk copies)
+  std::vector<int64_t> sptr2(c->nslices + 1, 0);
+  for (int64_t t = 0; t < c->nslices; ++t) {
+    int w = 0;
+    for (int l = 0; l < 32; ++l) {
+      const int64_t k = t * 32 + l;
+      if (k < n) w = std::max(w, S[c->body_of[k]]);
+    }
+    sptr2[t + 1] = sptr2[t] + 32 * (((int64_t)w + 3) & ~3LL);
+  }
+  const int64_t ne2 = sptr2[c->nslices];
+  pd_status st = PD_OK;
+  if ((st = alloc(c, &sptr2_dev, (size_t)c->nslices + 1)) != PD_OK ||
+      (st = alloc(c, &col2, (size_t)std::max<int64_t>(ne2, 32))) != PD_OK ||
+      (st = alloc(c, &bits2, (size_t)std::max<int64_t>(ne2 / 32, 1))) != PD_OK) {
+    release(c, sptr2_dev);
+    release(c, col2);
+    release(c, bits2);
+    cleanup();
+    if (st == PD_ERR_OOM) {  // not enough memory for a second layout: keep the sorted one
+      clear_error();
+      return PD_OK;
+    }
+    return st;
+  }
+  L.slice_ptr2 = sptr2_dev;
+  L.col2 = col2;
+  int efail = 0;
+  e = cudaMemcpyAsync(sptr2_dev, sptr2.data(), sizeof(int64_t) * sptr2.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    if (dim == 3) k_lat_emit<3><<<gb, tb, 0, s>>>(L);
+    else k_lat_emit<2><<<gb, tb, 0, s>>>(L);
+    e = cudaMemcpyAsync(&efail, d_stats + 3 * nb, sizeof(int), cudaMemcpyDeviceToHost, s);
+  }
+  std::vector<int32_t> hnsum(n_pad);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(hnsum.data(), d_nsum, sizeof(int32_t) * n_pad, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess || efail) {
+    release(c, sptr2_dev);
+    release(c, col2);
+    release(c, bits2);
+    cleanup();
+    return e != cudaSuccess ? cuda_fail(e, "lattice layout") : PD_OK;
+  }
+  // the lattice layout replaces the sorted one; m_i, D_i and the status words over the new slots
+  release(c, c->col);
+  release(c, c->bits);
+  release(c, c->slice_ptr);
+  c->col = col2;
+  c->bits = bits2;
+  c->slice_ptr = sptr2_dev;
+  c->nentries = ne2;
+  A.slice_ptr = c->slice_ptr;
+  A.col = c->col;
+  A.bits = c->bits;
+  if (dim == 3) k_init_bonds<3><<<gb, tb, 0, s>>>(A);
+  else k_init_bonds<2><<<gb, tb, 0, s>>>(A);
+  // per particle (N_ref / N_i, A / N_i), N_ref the largest N_i of the body (its interior value)
+  c->lat_h = h;
+  c->lat_nref.assign(nb, 0);
+  c->lat_qmax.assign(nb, 0);
+  c->lat_n1.assign(nb, 0);
+  for (int64_t k = 0; k < n; ++k) c->lat_nref[c->body_of[k]] = std::max(c->lat_nref[c->body_of[k]], hnsum[k]);
+  for (int b = 0; b < nb; ++b) {
+    c->lat_qmax[b] = hstats[3 * b + 1];
+    c->lat_n1[b] = hstats[3 * b + 2];
+  }
+  std::vector<float2> hf(n_pad, make_float2(0.0f, 0.0f));
+  for (int64_t k = 0; k < n; ++k) {
+    const int b = c->body_of[k];
+    double A_b, K_b, G_b;
+    material_constants(c->prm[b].model, c->prm[b].E, c->prm[b].nu, &A_b, &K_b, &G_b);
+    if (hnsum[k] > 0)
+      hf[k] = make_float2((float)((double)c->lat_nref[b] / hnsum[k]), (float)(A_b / hnsum[k]));
+  }
+  if ((st = alloc(c, &c->lat_f, (size_t)n_pad)) != PD_OK) {
+    cleanup();
+    return st;
+  }
+  e = cudaMemcpyAsync(c->lat_f, hf.data(), sizeof(float2) * n_pad, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cleanup();
+  if (e != cudaSuccess) return cuda_fail(e, "lattice factors");
+  c->lattice = true;
+  *done = true;
+  return upload_body_params(c);
 }
 
 // Morton key of 21-bit quantized coordinates.
@@ -544,6 +870,31 @@ pd_status upload_body_params(pd_ctx* c) {
     const double lq = p.horizon / c->q + 2.0;
     d.xi1max = (float)(std::sqrt((double)c->dim) * lq * 1.0001);
     d.qmax = (float)(lq * lq * 1.0001);
+    d.lat_h = d.lat_inv_h = d.lat_C = 0.0;
+    d.lat_lam_hi = d.lat_lam_lo = d.lat_s0 = 0.0f;
+    d.lat_Kf = d.lat_sq = d.lat_eps_c = d.lat_s0n1 = d.lat_Kfast = d.lat_Kcfast = 0.0f;
+    if (c->lattice) {
+      // FP32 sums in lattice units (u' = u / h, xi = h n, m_i = V h^2 N_i): F_i / V_i = G / (h N_ref) x
+      // sum_j rho_ij n [P_i + P_j + (N_ref/N_i + N_ref/N_j) n.(u'_j - u'_i) / |n|^2] with
+      // P_i = lambda sigma_i (N_ref/N_i)^2, sigma_i = sum_j rho_ij n.(u'_j - u'_i), theta_i = A sigma_i / N_i
+      const double h = c->lat_h[b];
+      const int nref = c->lat_nref[b], n1 = c->lat_n1[b], qm = c->lat_qmax[b];
+      d.lat_h = h;
+      d.lat_inv_h = 1.0 / h;
+      d.lat_C = G / (h * nref);
+      const double lam = (K - G / 3.0) * A / (G * nref);
+      d.lat_lam_hi = (float)lam;
+      d.lat_lam_lo = (float)(lam - (double)d.lat_lam_hi);
+      d.lat_s0 = (float)p.s0;
+      // rounding band of the FP32 break test (pd_lattice.h)
+      const LatBand lb = lattice_band(p.band_safety, p.s0, n1, qm);
+      d.lat_Kf = lb.Kf;
+      d.lat_sq = lb.sq;
+      d.lat_eps_c = lb.eps_c;
+      d.lat_s0n1 = lb.s0n1;
+      d.lat_Kfast = lb.Kfast;
+      d.lat_Kcfast = lb.Kcfast;
+    }
   }
   for (int b = 0; b < c->nbodies; ++b) h[b].rate = c->rate;
   PD_CUDA(cudaMemcpyAsync(c->bp, h.data(), sizeof(BodyDev) * c->nbodies, cudaMemcpyHostToDevice, c->stream));
@@ -750,6 +1101,13 @@ pd_status build_neighbors(pd_ctx* c, const pd_crack* cracks, int32_t ncracks) {
       k_init_bonds<2><<<gb, tb, 0, s>>>(A);
     }
     PD_CUDA(cudaGetLastError());
+    c->lattice = false;
+    c->lat_f = nullptr;
+    if (c->precision == PD_MIXED && c->kin == PD_LINEARIZED && c->lattice_opt) {
+      PD_CUDA(cudaStreamSynchronize(s));
+      bool lat = false;
+      PD_TRY2(build_lattice(c, A, &lat));
+    }
     c->pairs_ok = false;
     if (c->precision == PD_FP64 && c->nentries < (int64_t)INT32_MAX) {
       // pair tables of the FP64 path (entry indices fit in 32 bits)

@@ -30,6 +30,24 @@ struct BodyDev {
   int32_t breaks;  // 1 if s0 > 0 (bond breaking on), else 0
   float xi1max;    // upper bound of |xi|_1 in quanta: sqrt(dim) (delta / Q + 2)
   float qmax;      // upper bound of |xi|^2 in quanta^2: (delta / Q + 2)^2
+  // Lattice layout (mixed path, linearized bonds): bond vectors xi = h n with integer n, weighted
+  // volumes m_i = V h^2 N_i with integer N_i, N_ref = the largest N_i of the body.  The FP32 sums run
+  // in lattice units (u' = u / h) and are scaled back in FP64 by lat_C.
+  double lat_h;       // lattice spacing h
+  double lat_inv_h;   // 1 / h
+  double lat_C;       // G / (h N_ref): F_i / V_i = lat_C * (FP32 force sum)
+  float lat_lam_hi;   // lambda = (K - G/3) A / (G N_ref), split hi + lo (P_i = lambda sigma_i rho_i^2)
+  float lat_lam_lo;
+  float lat_s0;       // s0 in FP32
+  // Rounding band of the FP32 break test g = n.(u'_j - u'_i) - s0 |n|^2 (see k_pass1_lat):
+  // |g - g_FP64| <= Kf (U_i + U_j) + sq s0 |n|^2 + eps_c |g| + s0n1, U = |u'|_inf of each end.
+  float lat_Kf;
+  float lat_sq;
+  float lat_eps_c;
+  float lat_s0n1;
+  // ... and the screen that settles most bonds: g < -(Kfast (U_i + U_j) + Kcfast) implies intact.
+  float lat_Kfast;
+  float lat_Kcfast;
 };
 
 // Per-body neighbour-search grid (cells of edge >= delta).
@@ -95,6 +113,8 @@ struct StepArgs {
   double uscale;           // mixed path: the FP32 shadow holds u * uscale (1, or 1/Q for nonlinear bonds)
   int adr;                 // PD_SOLVER_ADR: pass 2 stores g = f + b in gnew instead of updating
   double4* gnew;           // ADR: force density g^n of this iteration
+  int lattice;             // mixed path: the lattice layout and its FP32 shadow u / h (with |u / h|_inf in .w)
+  const float2* lat_f;     // lattice layout: per particle (rho_i = N_ref / N_i, A / N_i)
 };
 
 struct KernelTimes {
@@ -187,6 +207,13 @@ struct pd_ctx {
   int* adr_first = nullptr;       // ADR: 1 = the next iteration starts from rest
   double* diag_theta = nullptr;   // pd_get_stats: theta at the current state
   double4* diag_part = nullptr;   // pd_get_stats: per-block (strain energy, min margin, kinetic, 0)
+  int lattice_opt = 1;            // PD_OPT_LATTICE: build the lattice layout when the bodies qualify
+  bool lattice = false;           // the built layout is the lattice layout (mixed, linearized bonds)
+  float2* lat_f = nullptr;        // lattice layout: per particle (N_ref / N_i, A / N_i)
+  std::vector<double> lat_h;      // lattice layout: spacing per body
+  std::vector<int> lat_nref;      // lattice layout: N_ref per body
+  std::vector<int> lat_n1;        // lattice layout: largest |n|_1 of the body's family
+  std::vector<int> lat_qmax;      // lattice layout: largest |n|^2 of the body's family
   double q = 0.0;               // fixed-point quantum of the mixed coordinates [m]
   double qlo[3] = {0, 0, 0};     // origin of the fixed-point coordinates
   // state
@@ -221,6 +248,7 @@ void clear_error();
 template <class T>
 pd_status alloc(pd_ctx* c, T** p, size_t count);
 void free_all(pd_ctx* c);
+void release(pd_ctx* c, void* p);  // frees one allocation of the context (nullptr: nothing)
 void free_build(pd_ctx* c);
 void material_constants(int model, double E, double nu, double* A, double* K, double* G);
 pd_status upload_body_params(pd_ctx* c);
@@ -239,6 +267,7 @@ pd_status ensure_bond_cache(pd_ctx* c);
 pd_status ensure_adr(pd_ctx* c);      // ADR arrays and lambda (once per build)
 pd_status diagnostics(pd_ctx* c, double* min_margin, double* strain, double* kinetic);
 pd_status prepare_staged_kernels(pd_ctx* c);  // shared-memory opt-in of the staged kernels
+pd_status upload_lattice_tables(int device);   // direction tables of the lattice kernels (once per device)
 pd_status upload_field(pd_ctx* c, const double* host_soa, double4* dst, int comps);
 pd_status gather_field(pd_ctx* c, const double* dev_soa, double4* dst, int comps);
 pd_status launch_nonfinite(const double* a, int64_t n, unsigned long long* flag, cudaStream_t s);

@@ -1,0 +1,153 @@
+// Lattice direction table shared by the family build (pd_build.cu) and the lattice step kernels
+// (pd_step.cu), and the FP32 break decision of those kernels with its rounding band (host and
+// device, so that a host test replays the same code).
+//
+// On a body whose particles sit on a regular lattice of spacing h, every bond vector is xi = h n with
+// n an integer vector, and the family (Section 2.1: the closed ball |xi| <= delta) is the set of
+// lattice directions with |n|^2 <= (delta / h)^2.  The table lists the non-zero integer vectors with
+// |n|^2 <= kLatQmax[dim] in a fixed order: by |n|^2, then each direction n whose first non-zero
+// component from z down to x is positive, immediately followed by its opposite -n.  So
+//   * every ball |n|^2 <= q is a prefix of the table (one family = the first S directions);
+//   * entry k and entry k ^ 1 are the two directions of one bond (xi_ji = -xi_ij).
+// In the lattice layout, slot k of every slice holds the neighbour in direction k of the table for
+// every lane, so the bond vector of a slot is one value for the whole warp.
+#pragma once
+
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#if defined(__CUDACC__)
+#define PD_LHD __host__ __device__ __forceinline__
+#else
+#define PD_LHD inline
+#endif
+
+namespace pd {
+
+constexpr int kLatQmax3 = 25;  // 3D: |n|^2 <= 25 (horizons up to 5 h): 514 directions
+constexpr int kLatQmax2 = 64;  // 2D: |n|^2 <= 64 (horizons up to 8 h): 196 directions
+constexpr int kLatDirs3 = 514;
+constexpr int kLatDirs2 = 196;
+constexpr int kLatR3 = 5;      // component bound of the 3D table
+constexpr int kLatR2 = 8;      // component bound of the 2D table
+
+struct LatDir {
+  int n[3];
+  int q;  // |n|^2
+};
+
+inline std::vector<LatDir> lattice_directions(int dim) {
+  const int qmax = dim == 3 ? kLatQmax3 : kLatQmax2;
+  const int R = dim == 3 ? kLatR3 : kLatR2;
+  std::vector<LatDir> pos;
+  for (int z = (dim == 3 ? -R : 0); z <= (dim == 3 ? R : 0); ++z)
+    for (int y = -R; y <= R; ++y)
+      for (int x = -R; x <= R; ++x) {
+        const int q = x * x + y * y + z * z;
+        if (q == 0 || q > qmax) continue;
+        const bool positive = z > 0 || (z == 0 && (y > 0 || (y == 0 && x > 0)));
+        if (positive) pos.push_back(LatDir{{x, y, z}, q});
+      }
+  std::sort(pos.begin(), pos.end(), [](const LatDir& a, const LatDir& b) {
+    if (a.q != b.q) return a.q < b.q;
+    if (a.n[2] != b.n[2]) return a.n[2] < b.n[2];
+    if (a.n[1] != b.n[1]) return a.n[1] < b.n[1];
+    return a.n[0] < b.n[0];
+  });
+  std::vector<LatDir> out;
+  out.reserve(2 * pos.size());
+  for (const LatDir& d : pos) {
+    out.push_back(d);
+    out.push_back(LatDir{{-d.n[0], -d.n[1], -d.n[2]}, d.q});
+  }
+  return out;
+}
+
+// Index into the lookup cube of side 2R + 1 (z ignored in 2D).
+inline int lattice_cube_index(int dim, int x, int y, int z) {
+  const int R = dim == 3 ? kLatR3 : kLatR2, s = 2 * R + 1;
+  return dim == 3 ? ((z + R) * s + (y + R)) * s + (x + R) : (y + R) * s + (x + R);
+}
+
+// Cube of side 2R + 1 mapping a direction to its table index (-1 outside the table).
+inline std::vector<short> lattice_lookup(int dim) {
+  const int R = dim == 3 ? kLatR3 : kLatR2, s = 2 * R + 1;
+  std::vector<short> cube((size_t)(dim == 3 ? s * s * s : s * s), (short)-1);
+  const std::vector<LatDir> t = lattice_directions(dim);
+  for (size_t k = 0; k < t.size(); ++k)
+    cube[lattice_cube_index(dim, t[k].n[0], t[k].n[1], t[k].n[2])] = (short)k;
+  return cube;
+}
+
+// Number of table directions with |n|^2 <= q (the family of a ball of radius sqrt(q) h).
+inline int lattice_prefix(int dim, int q) {
+  const std::vector<LatDir> t = lattice_directions(dim);
+  int k = 0;
+  while (k < (int)t.size() && t[k].q <= q) ++k;
+  return k;
+}
+
+// ------------------------------------------------------------- FP32 break decision and its band
+// In lattice units (u' = u / h in FP32, xi = h n) the failure criterion of Eq 1.30 in its sqrt-free
+// form xi.(u_j - u_i) >= s0 |xi|^2 reads d' >= s0 |n|^2 with d' = n.(u'_j - u'_i).  The kernels
+// evaluate g = d' - s0 |n|^2 in FP32 (the operations of lat_dprime and lat_g) and bound its
+// distance from the FP64 evaluation of the same criterion from the master state and the FP64
+// positions (eps = 2^-24; U_i, U_j = |u'|_inf of the two ends, N1 = the largest |n|_1 of the
+// family, c = the safety factor pd_params.band_safety):
+//   * the FP32 copies of u at both ends: eps |n|_1 (U_i + U_j) (relative rounding of each component);
+//   * the differences u'_j - u'_i: eps |n|_1 (U_i + U_j);
+//   * the product and the two FMAs of the dot product: 3 eps |n|_1 (U_i + U_j);
+//   * the FP64 side: bond vectors within 2^-30 h of h n (checked when the layout is built) and the
+//     FP64 rounding of its own dot product and threshold: 0.06 eps (U_i + U_j) + 0.034 eps s0 N1;
+//   * s0 rounded to FP32: eps s0 |n|^2; the final FMA: eps |g|;
+// so |g - g_FP64| <= B = c (1 + 8 eps) eps [(5.0003 N1 + 0.06)(U_i + U_j) + s0 (|n|^2 + 0.034 N1) + |g|]
+// (the 8 eps covers the FP32 evaluation of B itself, for c >= 1).  Outside +-B the FP32 sign is the
+// FP64 decision; inside, the bond is re-decided in FP64.  The screen g < -(Kfast (U_i + U_j) +
+// Kcfast), with |g| = -g folded in (division by 1 - c eps) and |n|^2 bounded by the family's
+// largest, implies g < -B: it settles the bonds far from their threshold in two instructions.
+struct LatBand {
+  float Kf, sq, eps_c, s0n1, Kfast, Kcfast;
+};
+
+inline LatBand lattice_band(double band_safety, double s0, int n1, int qmax) {
+  const double bc = band_safety > 0 ? band_safety : 4.0;
+  const double eps = 5.9604644775390625e-8, infl = 1.0 + 8.0 * eps;
+  const double k1 = 5.0003 * n1 + 0.06;
+  LatBand b;
+  b.Kf = (float)(bc * eps * k1 * infl);
+  b.sq = (float)(bc * eps * (1.0 + 1.5e-8) * infl);
+  b.eps_c = (float)(bc * eps * infl);
+  b.s0n1 = (float)(bc * eps * s0 * 0.034 * n1 * infl);
+  const double fast = infl / (1.0 - bc * eps);
+  b.Kfast = (float)(bc * eps * k1 * fast);
+  b.Kcfast = (float)(bc * eps * s0 * (qmax * (1.0 + 1.5e-8) + 0.034 * n1) * fast);
+  return b;
+}
+
+// d' = n.(u'_j - u'_i): one product and two FMAs (two in 2D).
+template <int DIM>
+PD_LHD float lat_dprime(float nx, float ny, float nz, float ujx, float ujy, float ujz, float uix, float uiy,
+                        float uiz) {
+  float d = nx * (ujx - uix);
+  d = fmaf(ny, ujy - uiy, d);
+  if (DIM == 3) d = fmaf(nz, ujz - uiz, d);
+  return d;
+}
+
+// g = d' - s0 |n|^2 in one FMA.
+PD_LHD float lat_g(float d, float s0f, float q) { return fmaf(-s0f, q, d); }
+
+// The screen: true settles the bond as intact.  scr_i = fmaf(Kfast, U_i, Kcfast), once per particle.
+PD_LHD bool lat_screen_intact(float g, float Kfast, float Uj, float scr_i) { return fmaf(Kfast, Uj, g) < -scr_i; }
+
+// Full band: 0 intact, 1 broken (FP32 decision), 2 inside the band (decide in FP64).  A NaN g is
+// inside (both comparisons false).
+PD_LHD int lat_code(float g, float Ui, float Uj, float s0f, float q, float Kf, float sq, float eps_c,
+                    float s0n1) {
+  const float B = fmaf(Kf, Ui + Uj, fmaf(sq, s0f * q, fmaf(eps_c, fabsf(g), s0n1)));
+  return g > B ? 1 : (g < -B ? 0 : 2);
+}
+
+}  // namespace pd

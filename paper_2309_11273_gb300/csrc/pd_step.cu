@@ -19,9 +19,12 @@
 // The break test is evaluated without square roots: s = e/|xi| >= s0  <=>  xi.du >= s0 |xi|^2.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
+#include <vector>
 
 #include "pd_internal.h"
 #include "pd_order.h"
+#include "pd_lattice.h"
 
 namespace pd {
 namespace {
@@ -1653,6 +1656,223 @@ __global__ void __launch_bounds__(512) k_pass2_mixed_staged(StepArgs a, const fl
 }
 
 
+// ------------------------------------------------------------------- lattice layout, mixed form
+// On a lattice body (pd_build.cu: every bond vector is h n with an integer n; slot k of every slice
+// holds direction k of the table for every lane) the bond vector of a slot is one value for the
+// whole warp, read from constant memory, and the FP32 arithmetic runs in lattice units:
+//   u' = u / h (the FP32 shadow, written by the FP64 update, with |u'|_inf in its 4th word),
+//   d'_ij = n.(u'_j - u'_i) = xi.(u_j - u_i) / h^2 (Eqs 2.4, 2.7: x e),
+//   pass 1: sigma_i = sum_j rho_ij d'_ij, theta_i = A sigma_i / N_i (Eq 1.6 with m_i = V h^2 N_i),
+//   pass 2: F_i / V_i = G / (h N_ref) sum_j rho_ij n [P_i + P_j + (N_ref/N_i + N_ref/N_j) d'_ij / |n|^2]
+//           (Eq 2.2), P_i = (K - G/3) / G theta_i N_ref / N_i,
+// so that no coordinate is gathered and the per-bond work is the displacement gather, the dot
+// product and the force FMAs.  The constants that multiply every bond (1 / |n|^2 per direction,
+// (K - G/3) A / (G N_ref) per body) are carried as FP32 hi + lo pairs, and the interior factors
+// N_ref / N_i are exactly 1, so no rounding of a constant is shared by all bonds of a direction or
+// of the body (such a shared rounding would shift every vibration frequency by the same amount and
+// grow as a phase error).  The failure check (Eq 1.30, d' >= s0 |n|^2) is decided in FP32 where its
+// rounding band (see BodyDev) cannot reach the threshold, and in FP64 from the master state
+// otherwise: a screen against the band with |n|^2 and |u'| bounded per body and per end settles
+// nearly every bond in two instructions; a warp with any bond the screen does not settle evaluates
+// the full band and re-decides the bonds inside it with the FP64 path's arithmetic.
+__constant__ float4 c_lat3[kLatDirs3];   // (n_x, n_y, n_z, |n|^2)
+__constant__ float2 c_latr3[kLatDirs3];  // 1 / |n|^2 as hi + lo
+__constant__ float4 c_lat2[kLatDirs2];
+__constant__ float2 c_latr2[kLatDirs2];
+
+template <int DIM>
+__device__ __forceinline__ float4 lat_dir(int k) {
+  return DIM == 3 ? c_lat3[k] : c_lat2[k];
+}
+template <int DIM>
+__device__ __forceinline__ float2 lat_rcp(int k) {
+  return DIM == 3 ? c_latr3[k] : c_latr2[k];
+}
+
+// The FP32 shadow of a displacement in the context's format.
+__device__ __forceinline__ float4 shadow_of(const StepArgs& a, int b, const double4& u) {
+  if (a.lattice) {
+    const double s = a.bp[b].lat_inv_h;
+    const float x = (float)(u.x * s), y = (float)(u.y * s), z = (float)(u.z * s);
+    return make_float4(x, y, z, fmaxf(fabsf(x), fmaxf(fabsf(y), fabsf(z))));
+  }
+  const double sc = a.uscale;
+  return make_float4((float)(u.x * sc), (float)(u.y * sc), (float)(u.z * sc), 0.0f);
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(512) k_pass1_lat(StepArgs a, const float4* __restrict__ u32,
+                                                    const double4* __restrict__ disp, int write_theta) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const SliceIdx t = slice_index<1>(a.n_pad, a.slice_ptr);
+  if (write_theta && blockIdx.x == 0 && threadIdx.x == 0) *a.d_step += 1;
+  if (!t.active) return;  // whole warps: the staging below is per warp
+  Stage st = stage_init(smem, t, a);
+  const int lane = t.lane;
+  const int b = a.body ? a.body[t.i] : 0;
+  const BodyDev& bp = a.bp[b];
+  const double s0 = bp.s0;
+  const float s0f = bp.lat_s0;
+  const bool can_break = bp.breaks != 0;
+  const float4 Ui = u32[t.i];
+  const float Kfast = bp.lat_Kfast;
+  const float scr_i = fmaf(Kfast, Ui.w, bp.lat_Kcfast);  // the screen's bound less its U_j term (pd_lattice.h)
+  uint32_t* __restrict__ bw = a.bits + (t.base >> 5);
+  if (lane == 0)
+    for (; st.issued < min(kStageBuf, st.nchunks); ++st.issued)
+      if (!(a.expire && st.issued == 0)) stage_issue(st, st.issued);  // testing: chunk 0 never arrives
+  float acc = 0.0f;
+  bool ok = true;
+  const bool checking = a.check != 0;  // warp-uniform (can_break is per body: per lane in a batch)
+  for (int c = 0; c < st.nchunks; ++c) {
+    const int buf = c % kStageBuf;
+    if (!mbar_wait(&st.bar[buf], (unsigned)((c / kStageBuf) & 1))) {
+      ok = false;
+      if (lane == 0) atomicExch(&a.counters[4], 1ull);
+      stage_drain(st, c + 1);
+      break;
+    }
+    const int32_t* cs = st.col + buf * kStageCh * 32 + lane;
+    const uint32_t* ws = st.words + buf * kStageCh;
+    const int k0 = c * kStageCh;
+    const int n = min(kStageCh, st.W - k0);
+    constexpr int U = kU32;
+    for (int kk = 0; kk < n; kk += U) {  // n is a multiple of 4 = U
+      uint32_t wd[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) wd[u] = ws[kk + u];
+      if ((wd[0] | wd[1] | wd[2] | wd[3]) == 0u) continue;  // warp-uniform: no intact bond in the batch
+      int32_t j[U];
+      float4 Uj[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        j[u] = cs[(kk + u) * 32];
+        Uj[u] = u32[j[u]];
+      }
+      float dv[U];
+      bool intact[U], near = false;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const float4 dn = lat_dir<DIM>(k0 + kk + u);
+        const float d = lat_dprime<DIM>(dn.x, dn.y, dn.z, Uj[u].x, Uj[u].y, Uj[u].z, Ui.x, Ui.y, Ui.z);
+        dv[u] = d;
+        intact[u] = (wd[u] >> lane) & 1u;
+        if (checking)
+          near = near || (can_break && intact[u] && !lat_screen_intact(lat_g(d, s0f, dn.w), Kfast, Uj[u].w, scr_i));
+      }
+      if (checking && (__any_sync(kFull, near) || a.validate)) {
+        // full band for the bonds the screen did not settle; FP64 inside it
+        int code[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const float4 dn = lat_dir<DIM>(k0 + kk + u);
+          code[u] = !(intact[u] && can_break)
+                        ? 0
+                        : lat_code(lat_g(dv[u], s0f, dn.w), Ui.w, Uj[u].w, s0f, dn.w, bp.lat_Kf, bp.lat_sq,
+                                   bp.lat_eps_c, bp.lat_s0n1);
+        }
+        for (int u = 0; u < U; ++u)
+          if (code[u] == 2) {
+            code[u] = fp64_breaks<DIM>(a, t.i, j[u], disp, s0) ? 1 : 0;
+            atomicAdd(&a.counters[0], 1ull);
+          }
+        if (a.validate) {
+          for (int u = 0; u < U; ++u)
+            if (can_break && intact[u] && (code[u] == 1) != fp64_breaks<DIM>(a, t.i, j[u], disp, s0))
+              atomicAdd(&a.counters[1], 1ull);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const unsigned m = __ballot_sync(kFull, code[u] == 1);
+          if (m) {
+            intact[u] = intact[u] && code[u] != 1;
+            if (lane == 0) bw[k0 + kk + u] = wd[u] & ~m;
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) acc += intact[u] ? dv[u] : 0.0f;
+    }
+    __syncwarp();  // every lane is done with this buffer before it is refilled
+    if (lane == 0 && st.issued < st.nchunks) stage_issue(st, st.issued++);
+  }
+  if (ok && write_theta) {
+    const float2 f = a.lat_f[t.i];  // (N_ref / N_i, A / N_i)
+    a.theta32[t.i] = f.y * acc;
+    const float x = acc * (f.x * f.x);
+    a.thm32[t.i] = make_float2(fmaf(bp.lat_lam_hi, x, bp.lat_lam_lo * x), f.x);
+  }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(512) k_pass2_lat(StepArgs a, const float4* __restrict__ u32,
+                                                    float4* __restrict__ u32_out,
+                                                    const double4* __restrict__ disp,
+                                                    double4* __restrict__ disp_out) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const SliceIdx t = slice_index<1>(a.n_pad, a.slice_ptr);
+  if (!t.active) return;
+  Stage st = stage_init(smem, t, a);
+  const int lane = t.lane;
+  const int b = a.body ? a.body[t.i] : 0;
+  const float4 Ui = u32[t.i];
+  const float2 ti = a.thm32[t.i];  // (P_i, N_ref / N_i)
+  if (lane == 0)
+    for (; st.issued < min(kStageBuf, st.nchunks); ++st.issued)
+      if (!(a.expire && st.issued == 0)) stage_issue(st, st.issued);  // testing: chunk 0 never arrives
+  float f[3] = {0.0f, 0.0f, 0.0f};
+  bool ok = true;
+  for (int c = 0; c < st.nchunks; ++c) {
+    const int buf = c % kStageBuf;
+    if (!mbar_wait(&st.bar[buf], (unsigned)((c / kStageBuf) & 1))) {
+      ok = false;
+      if (lane == 0) atomicExch(&a.counters[4], 1ull);
+      stage_drain(st, c + 1);
+      break;
+    }
+    const int32_t* cs = st.col + buf * kStageCh * 32 + lane;
+    const uint32_t* ws = st.words + buf * kStageCh;
+    const int k0 = c * kStageCh;
+    const int n = min(kStageCh, st.W - k0);
+    constexpr int U = kU32;
+    for (int kk = 0; kk < n; kk += U) {
+      uint32_t wd[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) wd[u] = ws[kk + u];
+      if ((wd[0] | wd[1] | wd[2] | wd[3]) == 0u) continue;
+      float4 Uj[U];
+      float2 tj[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int32_t j = cs[(kk + u) * 32];
+        Uj[u] = u32[j];
+        tj[u] = a.thm32[j];
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const float4 dn = lat_dir<DIM>(k0 + kk + u);
+        const float2 r = lat_rcp<DIM>(k0 + kk + u);
+        const float d = lat_dprime<DIM>(dn.x, dn.y, dn.z, Uj[u].x, Uj[u].y, Uj[u].z, Ui.x, Ui.y, Ui.z);
+        const float dr = fmaf(d, r.x, d * r.y);  // d / |n|^2 with 1 / |n|^2 carried as hi + lo
+        float cf = fmaf(ti.y + tj[u].y, dr, ti.x + tj[u].x);
+        cf = ((wd[u] >> lane) & 1u) ? cf : 0.0f;
+        f[0] = fmaf(cf, dn.x, f[0]);
+        f[1] = fmaf(cf, dn.y, f[1]);
+        if (DIM == 3) f[2] = fmaf(cf, dn.z, f[2]);
+      }
+    }
+    __syncwarp();
+    if (lane == 0 && st.issued < st.nchunks) stage_issue(st, st.issued++);
+  }
+  if (ok) {
+    const double C = a.bp[b].lat_C;
+    const double fd[3] = {C * (double)f[0], C * (double)f[1], C * (double)f[2]};
+    double4 u;
+    update(a, t.i, b, fd, disp, disp_out, u);
+    u32_out[t.i] = shadow_of(a, b, u);
+  }
+}
+
 // ---------------------------------------------------------------- adaptive dynamic relaxation
 // The quasi-static solver of Section 4.4 (cited there from the literature): fictitious dynamics
 // L u'' + c L u' = g(u), g = f + b, unit fictitious step.  Pass 1 and pass 2 run as in the explicit
@@ -1814,10 +2034,7 @@ __global__ void __launch_bounds__(kAdrBlock) k_adr_update(StepArgs a, const doub
   disp_out[i] = u;
   a.vel[i] = v;
   gold[i] = g;
-  if (u32_out) {  // mixed form: the FP32 shadow of the new state
-    const double sc = a.uscale;
-    u32_out[i] = make_float4((float)(u.x * sc), (float)(u.y * sc), (float)(u.z * sc), 0.0f);
-  }
+  if (u32_out) u32_out[i] = shadow_of(a, b, u);  // mixed form: the FP32 shadow of the new state
 }
 
 
@@ -2022,11 +2239,10 @@ __global__ void k_apply_bc(StepArgs a, double4* __restrict__ disp, int64_t step)
   a.vel[i] = make_double4(bp.rate * g.x, bp.rate * g.y, bp.rate * g.z, 0.0);
 }
 
-__global__ void k_shadow(int64_t n_pad, const double4* __restrict__ disp, float4* __restrict__ u32, double sc) {
+__global__ void k_shadow(StepArgs a, const double4* __restrict__ disp, float4* __restrict__ u32) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n_pad) return;
-  const double4 u = disp[i];
-  u32[i] = make_float4((float)(u.x * sc), (float)(u.y * sc), (float)(u.z * sc), 0.0f);
+  if (i >= a.n_pad) return;
+  u32[i] = shadow_of(a, a.body ? a.body[i] : 0, disp[i]);
 }
 
 // max |u_k| over all particles and components (order-independent: max of non-negative doubles as
@@ -2108,6 +2324,8 @@ StepArgs make_args(pd_ctx* c) {
   a.uscale = c->kin == PD_NONLINEAR ? 1.0 / c->q : 1.0;
   a.adr = c->solver == PD_SOLVER_ADR ? 1 : 0;
   a.gnew = c->gnew;
+  a.lattice = c->lattice ? 1 : 0;
+  a.lat_f = c->lat_f;
   return a;
 }
 
@@ -2179,6 +2397,8 @@ void launch_pass2(pd_ctx* c, const StepArgs& a, unsigned grid, int block, size_t
 template <int DIM>
 void optin_staged() {
   const int mx = 16 * kStageWarpBytes;
+  cudaFuncSetAttribute(k_pass1_lat<DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_pass2_lat<DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_pass1_mixed_staged<DIM, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_pass2_mixed_staged<DIM, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_pass1_mixed_staged<DIM, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
@@ -2193,6 +2413,36 @@ pd_status prepare_staged_kernels(pd_ctx* c) {
   if (c->dim == 3) optin_staged<3>();
   else optin_staged<2>();
   PD_CUDA(cudaGetLastError());
+  if (c->lattice) return upload_lattice_tables(c->device);
+  return PD_OK;
+}
+
+// The direction tables of the lattice kernels, once per device (every context uses the same
+// tables, so later uploads would write the same values).
+pd_status upload_lattice_tables(int device) {
+  static std::mutex mu;
+  static std::vector<int> done;
+  std::lock_guard<std::mutex> lock(mu);
+  if (std::find(done.begin(), done.end(), device) != done.end()) return PD_OK;
+  for (int dim = 2; dim <= 3; ++dim) {
+    const std::vector<LatDir> t = lattice_directions(dim);
+    std::vector<float4> dn(t.size());
+    std::vector<float2> rc(t.size());
+    for (size_t k = 0; k < t.size(); ++k) {
+      dn[k] = make_float4((float)t[k].n[0], (float)t[k].n[1], (float)t[k].n[2], (float)t[k].q);
+      const double r = 1.0 / t[k].q;
+      const float hi = (float)r;
+      rc[k] = make_float2(hi, (float)(r - (double)hi));
+    }
+    if (dim == 3) {
+      PD_CUDA(cudaMemcpyToSymbol(c_lat3, dn.data(), sizeof(float4) * dn.size()));
+      PD_CUDA(cudaMemcpyToSymbol(c_latr3, rc.data(), sizeof(float2) * rc.size()));
+    } else {
+      PD_CUDA(cudaMemcpyToSymbol(c_lat2, dn.data(), sizeof(float4) * dn.size()));
+      PD_CUDA(cudaMemcpyToSymbol(c_latr2, rc.data(), sizeof(float2) * rc.size()));
+    }
+  }
+  done.push_back(device);
   return PD_OK;
 }
 
@@ -2204,6 +2454,17 @@ void dispatch_pass(pd_ctx* c, const StepArgs& a, int pass, int write_theta) {
   const int split = c->split;
   const int64_t threads = c->nslices * 32 * (int64_t)split;
   const unsigned grid = (unsigned)((threads + block - 1) / block);
+  if (c->precision == PD_MIXED && c->lattice) {
+    // lattice layout (linearized bonds): one warp per slice, whatever the split and stage options
+    const unsigned g1 = (unsigned)((c->nslices * 32 + block - 1) / block);
+    const size_t smb = (size_t)(block / 32) * kStageWarpBytes;
+    if (pass == 1)
+      k_pass1_lat<DIM><<<g1, block, smb, c->stream>>>(a, c->u32[c->cur], c->disp[c->cur], write_theta);
+    else
+      k_pass2_lat<DIM><<<g1, block, smb, c->stream>>>(a, c->u32[c->cur], c->u32[c->cur ^ 1], c->disp[c->cur],
+                                                      c->disp[c->cur ^ 1]);
+    return;
+  }
   if (c->precision == PD_MIXED && ((split == 1 && c->stage) || c->kin == PD_NONLINEAR)) {
     // nonlinear bonds in the mixed form run the staged kernels only (one warp per slice)
     const unsigned g1 = (unsigned)((c->nslices * 32 + block - 1) / block);
@@ -2563,8 +2824,7 @@ pd_status apply_bc_now(pd_ctx* c) {
 pd_status sync_shadow(pd_ctx* c) {
   if (c->precision != PD_MIXED) return PD_OK;
   const int tb = 256;
-  k_shadow<<<(unsigned)((c->n_pad + tb - 1) / tb), tb, 0, c->stream>>>(c->n_pad, c->disp[c->cur], c->u32[c->cur],
-                                                                        c->kin == PD_NONLINEAR ? 1.0 / c->q : 1.0);
+  k_shadow<<<(unsigned)((c->n_pad + tb - 1) / tb), tb, 0, c->stream>>>(make_args(c), c->disp[c->cur], c->u32[c->cur]);
   PD_CUDA(cudaGetLastError());
   return PD_OK;
 }

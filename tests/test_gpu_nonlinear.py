@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-12
 
 
-from parity import elem, rel, theta_elem
+from parity import elem, elem_v, rel, theta_elem
 
 
 def s0_of(w):
@@ -42,7 +42,7 @@ def run_pair(w, nsteps, every, rate=None, s0=None, u0=None, v0=None, **kw):
             exact = False
         u, v, th = sim.state()
         rp, col, intact = sim.neighbors()
-        out.append(dict(step=done, ru=rel(u, ref.u), rv=rel(v, ref.v), eu=elem(u, ref.u), ev=elem(v, ref.v),
+        out.append(dict(step=done, ru=rel(u, ref.u), rv=rel(v, ref.v), eu=elem(u, ref.u), ev=elem_v(v, ref),
                         et=theta_elem(th, ref),
                         status_equal=np.array_equal(intact, ref.status), exact=exact,
                         broken=int((ref.status == 0).sum())))
