@@ -466,9 +466,9 @@ def run_gpu(args):
     return 0
 
 
-def mixed_roofline(prof, a1, a2, bytes1, bytes2, hbm, hbm_note, staged):
+def mixed_roofline(prof, a1, a2, bytes1, bytes2, hbm, hbm_note, staged, lattice=False):
     kp = 1 if prof["pass1_ms"] >= prof["pass2_ms"] else 2  # the dominant kernel
-    name = "k_pass%d_mixed%s" % (kp, "_staged" if staged else "")
+    name = ("k_pass%d_lat" % kp) if lattice else "k_pass%d_mixed%s" % (kp, "_staged" if staged else "")
     ach = a1 if kp == 1 else a2
     other = 2 if kp == 1 else 1
     return {"bound": "hbm", "kernel": name, "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
@@ -565,6 +565,7 @@ def run_forms(args, stream, dev, world, fp64_value, nb, hbm, hbm_note, fp64_tflo
     mval = world * nb * steps / (ms * 1e-3)
     prof = profiled(sim, 50)
     st = sim.stats()
+    lattice = sim.get_option(B.PD_OPT_LATTICE) == 1
     sim.close()
     staged = mmap[1] == 1  # the staged kernels run whenever the mapping has one warp per slice
     bytes2 = BYTES_BOND[2] * nb + BYTES_PART[2] * w.n
@@ -575,7 +576,8 @@ def run_forms(args, stream, dev, world, fp64_value, nb, hbm, hbm_note, fp64_tflo
                     "ms_per_step": ms / steps, "dtype": "f32 bond arithmetic, f64 integration",
                     "stated_error": mixed_error_on_workload(w, s0, stream, dev, 200),
                     "band_rechecks": st["band_rechecks"], "mapping": {"block": mmap[0], "split": mmap[1]},
-                    "roofline": mixed_roofline(prof, a1, a2, bytes1, bytes2, hbm, hbm_note, staged)}
+                    "layout": "lattice" if lattice else "general",
+                    "roofline": mixed_roofline(prof, a1, a2, bytes1, bytes2, hbm, hbm_note, staged, lattice)}
     # geometrically nonlinear bonds (Eqs 1.10, 1.13, 1.14) in FP64 on the same workload
     sim = Simulation(w, s0=s0, precision=PD_FP64, kinematics=PD_NONLINEAR, stream=stream.cuda_stream, device=dev)
     nmap = B.pd_autotune(sim.h, 2)

@@ -70,6 +70,17 @@ typedef enum { PD_FP64 = 0, PD_MIXED = 1 } pd_precision;
  *   PD_MIXED, and the staged kernels always run (PD_OPT_SPLIT and PD_OPT_STAGE are ignored). */
 typedef enum { PD_LINEARIZED = 0, PD_NONLINEAR = 1 } pd_kinematics;
 
+/* Influence function w(|xi|) of the weighted volume (Eq 1.9), the dilatation (Eq 1.6), the force
+ * state (Eq 1.14, so the bond force of Eq 2.2) and the damage (Eq 1.31).
+ * PD_W_ONE: w = 1, the paper's choice (Section 2.3).
+ * PD_W_INV: w = delta / |xi|, a form of the published catalogue the paper refers to at Eq 1.9.
+ *   Supported with linearized bonds and the explicit solver: in FP64 with the bond cache on (the
+ *   default; w is folded into the per-slot tables) and in PD_MIXED on the lattice layout
+ *   (PD_OPT_LATTICE; w is a per-direction factor).  Other combinations return PD_ERR_ARG.  The
+ *   critical stretch of Eqs 1.26-1.29 (pd_critical_stretch) is derived for w = 1; s0 remains an
+ *   input. */
+typedef enum { PD_W_ONE = 0, PD_W_INV = 1 } pd_influence;
+
 /* Internal particle order (results do not depend on it beyond rounding).
  * PD_ORDER_BRICKS: bricks of 32 x 4 x 4 (3D) or 32 x 8 (2D) points of the typical spacing
  *   (mean V)^(1/dim), x fastest inside a brick, bricks along a Morton curve: a warp's 32 particles
@@ -91,7 +102,7 @@ typedef struct {
   int32_t ordering;    /* internal particle order: PD_ORDER_BRICKS (0, default) or PD_ORDER_MORTON */
   void* stream;        /* cudaStream_t to run on, or NULL for a library-owned stream */
   int32_t kinematics;  /* pd_kinematics; every body of a batch takes the same */
-  int32_t reserved;    /* 0 */
+  int32_t influence;   /* pd_influence (0: w = 1); every body of a batch takes the same */
 } pd_params;
 
 /* A pre-crack / notch: bonds whose segment crosses it are never created (Section 4.2 / 4.4).

@@ -18,6 +18,8 @@ sequences the calls.  Equation references are to the paper:
 * Eqs 1.10, 1.13, 1.14  -> the same functions with ``kin=NONLINEAR`` (geometrically exact bonds)
 * Eqs 1.17, 1.30        -> :func:`failure`
 * Eq 1.31               -> :func:`damage`
+* Eq 1.9's influence function w: 1 (the paper's choice, Section 2.3) or ``infl=W_INV``, w = delta / |xi|
+  (a form of the published catalogue the paper cites at Eq 1.9), in every function above
 * Eq 2.11 + Appendix B  -> :class:`OracleSim`
 * adaptive dynamic relaxation (Section 4.4's quasi-static solver) -> :func:`adr_lambda`,
   :meth:`OracleSim.adr_step`
@@ -45,6 +47,7 @@ _lib = None
 MODEL_3D, MODEL_PLANE_STRESS, MODEL_PLANE_STRAIN = 0, 1, 2
 FREE, FIXED, PRESCRIBED = 0, 1, 2
 LINEARIZED, NONLINEAR = 0, 1  # bond kinematics: Eqs 2.4/2.7 (the paper's method) or Eqs 1.10/1.13
+W_ONE, W_INV = 0, 1  # influence function w of Eqs 1.6, 1.9, 1.14, 1.31: 1 (the paper's) or delta / |xi|
 
 _d = ctypes.POINTER(ctypes.c_double)
 _i64 = ctypes.POINTER(ctypes.c_int64)
@@ -82,17 +85,21 @@ def lib():
             L.orc_family_binned.argtypes = fam
             L.orc_family_binned.restype = ctypes.c_int64
             L.orc_weighted_volume.argtypes = [ctypes.c_int64, ctypes.c_int, _d, _d, _d, _d, _i64, _i32,
-                                              _d]
-            L.orc_damage_denominator.argtypes = [ctypes.c_int64, _d, _i64, _i32, _d]
+                                              ctypes.c_int, ctypes.c_double, _d]
+            L.orc_damage_denominator.argtypes = [ctypes.c_int64, ctypes.c_int, _d, _d, _d, _d, _i64, _i32,
+                                                 ctypes.c_int, ctypes.c_double, _d]
             L.orc_dilatation.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int, _d, _d, _d, _d, _i64, _i32, _u8,
-                                         _d, ctypes.c_double, _d, _d, _d, _d]
+                                         _d, ctypes.c_double, ctypes.c_int, ctypes.c_double, _d, _d, _d, _d]
             L.orc_force.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int, _d, _d, _d, _d, _i64, _i32, _u8, _d,
-                                    _d, ctypes.c_double, ctypes.c_double, _d, _d, _d, _d, _d, _d]
+                                    _d, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                                    _d, _d, _d, _d, _d, _d]
             L.orc_failure.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int, _d, _d, _d, _i64, _i32, _u8,
                                       ctypes.c_double, _d, _d, _d, _d]
             L.orc_failure.restype = ctypes.c_int64
-            L.orc_damage.argtypes = [ctypes.c_int64, _d, _i64, _i32, _u8, _d]
-            L.orc_run.argtypes = ([ctypes.c_int, ctypes.c_int64, ctypes.c_int, _d, _d, _d, _d, _i64, _i32, _u8, _d]
+            L.orc_damage.argtypes = [ctypes.c_int64, ctypes.c_int, _d, _d, _d, _d, _i64, _i32, _u8, ctypes.c_int,
+                                     ctypes.c_double, _d]
+            L.orc_run.argtypes = ([ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int64, ctypes.c_int, _d, _d,
+                                   _d, _d, _i64, _i32, _u8, _d]
                                   + [ctypes.c_double] * 6
                                   + [_u8, _d, _d, _d, _d, _d, ctypes.c_double, _d, _d, _d, ctypes.c_int64,
                                      ctypes.c_int64]
@@ -170,25 +177,32 @@ def family(x, y, z, delta, cracks=(), method="binned"):
     return row_ptr, col
 
 
-def weighted_volume(x, y, z, vol, row_ptr, col):
-    """m_i = sum_j x_ij^2 V_j (Eq 1.9, w = 1)."""
+def weighted_volume(x, y, z, vol, row_ptr, col, infl=W_ONE, delta=0.0):
+    """m_i = sum_j w x_ij^2 V_j (Eq 1.9; w = 1, or delta / |xi| with infl=W_INV)."""
     x, y, z, vol = _f64(x), _f64(y), _f64(z), _f64(vol)
     n = x.size
     dim = 3 if z is not None else 2
     m = np.zeros(n)
     lib().orc_weighted_volume(n, dim, _p(x, _d), _p(y, _d), _p(z if z is not None else x, _d),
-                              _p(vol, _d), _p(row_ptr, _i64), _p(col, _i32), _p(m, _d))
+                              _p(vol, _d), _p(row_ptr, _i64), _p(col, _i32), int(infl), float(delta), _p(m, _d))
     return m
 
 
-def damage_denominator(vol, row_ptr, col):
+def damage_denominator(vol, row_ptr, col, x=None, y=None, z=None, infl=W_ONE, delta=0.0):
+    """D_i = sum_j w V_j over the built family (denominator of Eq 1.31)."""
     vol = _f64(vol)
-    D = np.zeros(vol.size)
-    lib().orc_damage_denominator(vol.size, _p(vol, _d), _p(row_ptr, _i64), _p(col, _i32), _p(D, _d))
+    n = vol.size
+    if x is None:  # w = 1 needs no geometry
+        x = y = np.zeros(n)
+    x, y, z = _f64(x), _f64(y), _f64(z)
+    dim = 3 if z is not None else 2
+    D = np.zeros(n)
+    lib().orc_damage_denominator(n, dim, _p(x, _d), _p(y, _d), _p(z if z is not None else x, _d), _p(vol, _d),
+                                 _p(row_ptr, _i64), _p(col, _i32), int(infl), float(delta), _p(D, _d))
     return D
 
 
-def dilatation(x, y, z, vol, row_ptr, col, status, m, A, u, kin=LINEARIZED):
+def dilatation(x, y, z, vol, row_ptr, col, status, m, A, u, kin=LINEARIZED, infl=W_ONE, delta=0.0):
     """theta_i (Eq 1.6 / 2.3) for displacement ``u`` of shape (dim, n)."""
     x, y, z, vol, m = _f64(x), _f64(y), _f64(z), _f64(vol), _f64(m)
     u = np.ascontiguousarray(u, dtype=np.float64)
@@ -197,13 +211,13 @@ def dilatation(x, y, z, vol, row_ptr, col, status, m, A, u, kin=LINEARIZED):
     zz = z if z is not None else x
     uz = u[2] if dim == 3 else u[0]
     lib().orc_dilatation(int(kin), n, dim, _p(x, _d), _p(y, _d), _p(zz, _d), _p(vol, _d), _p(row_ptr, _i64),
-                         _p(col, _i32), _p(status, _u8), _p(m, _d), float(A),
+                         _p(col, _i32), _p(status, _u8), _p(m, _d), float(A), int(infl), float(delta),
                          _p(np.ascontiguousarray(u[0]), _d), _p(np.ascontiguousarray(u[1]), _d),
                          _p(np.ascontiguousarray(uz), _d), _p(th, _d))
     return th
 
 
-def force(x, y, z, vol, row_ptr, col, status, m, theta, K, G, u, kin=LINEARIZED):
+def force(x, y, z, vol, row_ptr, col, status, m, theta, K, G, u, kin=LINEARIZED, infl=W_ONE, delta=0.0):
     """Internal force F_i = sum_j F_i^{xi_ij} (Eq 2.2; Eqs 1.11-1.14 with kin=NONLINEAR), shape (dim, n)."""
     x, y, z, vol, m, theta = _f64(x), _f64(y), _f64(z), _f64(vol), _f64(m), _f64(theta)
     u = np.ascontiguousarray(u, dtype=np.float64)
@@ -213,7 +227,7 @@ def force(x, y, z, vol, row_ptr, col, status, m, theta, K, G, u, kin=LINEARIZED)
     uz = u[2] if dim == 3 else u[0]
     lib().orc_force(int(kin), n, dim, _p(x, _d), _p(y, _d), _p(zz, _d), _p(vol, _d), _p(row_ptr, _i64),
                     _p(col, _i32), _p(status, _u8), _p(m, _d), _p(theta, _d), float(K), float(G),
-                    _p(np.ascontiguousarray(u[0]), _d), _p(np.ascontiguousarray(u[1]), _d),
+                    int(infl), float(delta), _p(np.ascontiguousarray(u[0]), _d), _p(np.ascontiguousarray(u[1]), _d),
                     _p(np.ascontiguousarray(uz), _d), _p(f[0], _d), _p(f[1], _d), _p(f[2], _d))
     return f[:dim].copy()
 
@@ -247,12 +261,17 @@ def adr_lambda(x, y, z, vol, row_ptr, col, m, A, K, G):
     return lam
 
 
-def damage(vol, row_ptr, col, status):
+def damage(vol, row_ptr, col, status, x=None, y=None, z=None, infl=W_ONE, delta=0.0):
     """phi_i (Eq 1.31)."""
     vol = _f64(vol)
-    phi = np.zeros(vol.size)
-    lib().orc_damage(vol.size, _p(vol, _d), _p(row_ptr, _i64), _p(col, _i32), _p(status, _u8),
-                     _p(phi, _d))
+    n = vol.size
+    if x is None:  # w = 1 needs no geometry
+        x = y = np.zeros(n)
+    x, y, z = _f64(x), _f64(y), _f64(z)
+    dim = 3 if z is not None else 2
+    phi = np.zeros(n)
+    lib().orc_damage(n, dim, _p(x, _d), _p(y, _d), _p(z if z is not None else x, _d), _p(vol, _d),
+                     _p(row_ptr, _i64), _p(col, _i32), _p(status, _u8), int(infl), float(delta), _p(phi, _d))
     return phi
 
 
@@ -264,9 +283,10 @@ class OracleSim:
     """
 
     def __init__(self, model, E, nu, rho, delta, s0, dt, x, y, z=None, vol=None, cracks=(),
-                 family_method="binned", kin=LINEARIZED):
+                 family_method="binned", kin=LINEARIZED, infl=W_ONE):
         self.model = int(model)
         self.kin = int(kin)
+        self.infl = int(infl)
         self.dim = 3 if z is not None else 2
         self.x, self.y = _f64(x), _f64(y)
         self.z = _f64(z) if z is not None else None
@@ -278,8 +298,8 @@ class OracleSim:
         c = constants(model, E, nu)
         self.A, self.K, self.G = c["A"], c["K"], c["G"]
         self.row_ptr, self.col = family(self.x, self.y, self.z, delta, cracks, family_method)
-        self.m = weighted_volume(self.x, self.y, self.z, self.vol, self.row_ptr, self.col)
-        self.D = damage_denominator(self.vol, self.row_ptr, self.col)
+        self.m = weighted_volume(self.x, self.y, self.z, self.vol, self.row_ptr, self.col, self.infl, self.delta)
+        self.D = damage_denominator(self.vol, self.row_ptr, self.col, self.x, self.y, self.z, self.infl, self.delta)
         self.status = np.ones(self.col.size, dtype=np.uint8)
         self.u = np.zeros((self.dim, self.n))
         self.v = np.zeros((self.dim, self.n))
@@ -331,7 +351,8 @@ class OracleSim:
         vpx = vp[0].copy() if vp is not None else None
         vpy = vp[1].copy() if vp is not None else None
         vpz = vp[2].copy() if (vp is not None and self.dim == 3) else (np.zeros(self.n) if vp is not None else None)
-        lib().orc_run(self.kin, self.n, self.dim, _p(self.x, _d), _p(self.y, _d), _p(zz, _d), _p(self.vol, _d),
+        lib().orc_run(self.kin, self.infl, self.delta, self.n, self.dim, _p(self.x, _d), _p(self.y, _d), _p(zz, _d),
+                      _p(self.vol, _d),
                       _p(self.row_ptr, _i64), _p(self.col, _i32), _p(self.status, _u8), _p(self.m, _d),
                       self.A, self.K, self.G, self.rho, self.dt, self.s0, _p(self.flag, _u8),
                       _p(bx, _d), _p(by, _d), _p(bz, _d), _p(self.axis_point, _d),
@@ -349,18 +370,20 @@ class OracleSim:
         """theta and F for displacement u (default: current state) with the current bond status."""
         u = self.u if u is None else np.asarray(u, dtype=np.float64).reshape(self.dim, self.n)
         th = dilatation(self.x, self.y, self.z, self.vol, self.row_ptr, self.col, self.status, self.m,
-                        self.A, u, self.kin)
+                        self.A, u, self.kin, self.infl, self.delta)
         f = force(self.x, self.y, self.z, self.vol, self.row_ptr, self.col, self.status, self.m, th,
-                  self.K, self.G, u, self.kin)
+                  self.K, self.G, u, self.kin, self.infl, self.delta)
         return th, f
 
     def damage(self):
-        return damage(self.vol, self.row_ptr, self.col, self.status)
+        return damage(self.vol, self.row_ptr, self.col, self.status, self.x, self.y, self.z, self.infl, self.delta)
 
     def adr_step(self, nsteps: int):
         """Adaptive dynamic relaxation iterations (``orc_adr_run``) from the current state.  The first
         call after ``set_state`` starts from rest (v = 0); returns (damping c per iteration, min
         margin per iteration, broken count per iteration).  ``self.v`` holds v^{n-1/2}."""
+        if self.infl != W_ONE:
+            raise ValueError("adaptive dynamic relaxation is restated for w = 1 only")
         nsteps = int(nsteps)
         if getattr(self, "lam", None) is None:
             self.lam = adr_lambda(self.x, self.y, self.z, self.vol, self.row_ptr, self.col, self.m,

@@ -340,28 +340,42 @@ static double bond_kinematics(int kin, int dim, const double xi[3], double xlen,
   return p / (ylen + xlen);
 }
 
-/* Weighted volume m_i = sum_j w x_ij^2 V_j over the built family (Eq 1.9, discretized, w = 1). */
+/* Influence function w(|xi|) of Eqs 1.6, 1.9, 1.14 and 1.31.  The paper uses w = 1 (Section 2.3, where
+ * the critical stretch is derived) and refers at Eq 1.9 to the published catalogue of other forms;
+ * ORC_W_INV is the form w = delta / |xi| from that catalogue. */
+enum { ORC_W_ONE = 0, ORC_W_INV = 1 };
+static double influence(int infl, double delta, double xlen) {
+  return infl == ORC_W_INV ? delta / xlen : 1.0;
+}
+
+/* Weighted volume m_i = sum_j w x_ij^2 V_j over the built family (Eq 1.9, discretized). */
 void orc_weighted_volume(int64_t n, int dim, const double* x, const double* y, const double* z,
-                         const double* vol, const int64_t* row_ptr, const int32_t* col, double* m) {
+                         const double* vol, const int64_t* row_ptr, const int32_t* col, int infl,
+                         double delta, double* m) {
 #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) {
     double s = 0.0;
     for (int64_t b = row_ptr[i]; b < row_ptr[i + 1]; ++b) {
       double xi[3];
       double xl = bond_vector(dim, x, y, z, i, col[b], xi);
-      s += xl * xl * vol[col[b]];
+      s += influence(infl, delta, xl) * xl * xl * vol[col[b]];
     }
     m[i] = s;
   }
 }
 
-/* Denominator of Eq 1.31: D_i = sum_j w V_j over the built family (w = 1). */
-void orc_damage_denominator(int64_t n, const double* vol, const int64_t* row_ptr, const int32_t* col,
-                            double* D) {
+/* Denominator of Eq 1.31: D_i = sum_j w V_j over the built family. */
+void orc_damage_denominator(int64_t n, int dim, const double* x, const double* y, const double* z,
+                            const double* vol, const int64_t* row_ptr, const int32_t* col, int infl,
+                            double delta, double* D) {
 #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) {
     double s = 0.0;
-    for (int64_t b = row_ptr[i]; b < row_ptr[i + 1]; ++b) s += vol[col[b]];
+    for (int64_t b = row_ptr[i]; b < row_ptr[i + 1]; ++b) {
+      double xi[3];
+      double xl = bond_vector(dim, x, y, z, i, col[b], xi);
+      s += influence(infl, delta, xl) * vol[col[b]];
+    }
     D[i] = s;
   }
 }
@@ -370,8 +384,8 @@ void orc_damage_denominator(int64_t n, const double* vol, const int64_t* row_ptr
  * bonds of the per-bond contributions of Eq 2.3).  A particle with m_i = 0 has no bonds: theta_i = 0. */
 void orc_dilatation(int kin, int64_t n, int dim, const double* x, const double* y, const double* z,
                     const double* vol, const int64_t* row_ptr, const int32_t* col,
-                    const uint8_t* status, const double* m, double A, const double* ux,
-                    const double* uy, const double* uz, double* theta) {
+                    const uint8_t* status, const double* m, double A, int infl, double delta,
+                    const double* ux, const double* uy, const double* uz, double* theta) {
 #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) {
     double s = 0.0;
@@ -382,7 +396,7 @@ void orc_dilatation(int kin, int64_t n, int dim, const double* x, const double* 
       double M[3];
       double xl = bond_vector(dim, x, y, z, i, j, xi);
       double e = bond_kinematics(kin, dim, xi, xl, ux, uy, uz, i, j, M);
-      s += xl * e * vol[j];
+      s += influence(infl, delta, xl) * xl * e * vol[j];
     }
     theta[i] = (m[i] > 0.0) ? A * s / m[i] : 0.0;
   }
@@ -395,8 +409,8 @@ void orc_dilatation(int kin, int64_t n, int dim, const double* x, const double* 
 void orc_force(int kin, int64_t n, int dim, const double* x, const double* y, const double* z,
                const double* vol, const int64_t* row_ptr, const int32_t* col,
                const uint8_t* status, const double* m, const double* theta, double K, double G,
-               const double* ux, const double* uy, const double* uz, double* fx, double* fy,
-               double* fz) {
+               int infl, double delta, const double* ux, const double* uy, const double* uz,
+               double* fx, double* fy, double* fz) {
 #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) {
     double f[3] = {0.0, 0.0, 0.0};
@@ -409,7 +423,7 @@ void orc_force(int kin, int64_t n, int dim, const double* x, const double* y, co
       double e = bond_kinematics(kin, dim, xi, xl, ux, uy, uz, i, j, M);
       double th = theta[i] / m[i] + theta[j] / m[j];
       double et = e / m[i] + e / m[j];
-      double mag = ((K - G / 3.0) * th * xl + G * et) * vol[i] * vol[j];
+      double mag = ((K - G / 3.0) * th * xl + G * et) * influence(infl, delta, xl) * vol[i] * vol[j];
       for (int k = 0; k < dim; ++k) f[k] += mag * M[k];
     }
     fx[i] = f[0];
@@ -449,14 +463,18 @@ int64_t orc_failure(int kin, int64_t n, int dim, const double* x, const double* 
 }
 
 /* Damage phi_i = 1 - sum_j w rho_ij V_j / sum_j w V_j over the built family (Eq 1.31); 0 without bonds. */
-void orc_damage(int64_t n, const double* vol, const int64_t* row_ptr, const int32_t* col,
-                const uint8_t* status, double* phi) {
+void orc_damage(int64_t n, int dim, const double* x, const double* y, const double* z,
+                const double* vol, const int64_t* row_ptr, const int32_t* col,
+                const uint8_t* status, int infl, double delta, double* phi) {
 #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) {
     double num = 0.0, den = 0.0;
     for (int64_t b = row_ptr[i]; b < row_ptr[i + 1]; ++b) {
-      den += vol[col[b]];
-      if (status[b]) num += vol[col[b]];
+      double xi[3];
+      double xl = bond_vector(dim, x, y, z, i, col[b], xi);
+      double wv = influence(infl, delta, xl) * vol[col[b]];
+      den += wv;
+      if (status[b]) num += wv;
     }
     phi[i] = (den > 0.0) ? 1.0 - num / den : 0.0;
   }
@@ -521,8 +539,8 @@ static void apply_bc(int64_t n, int dim, const double* x, const double* y, const
  * broken[k] (may be NULL) the number of bonds broken in it.  theta holds the last iteration's
  * dilatation on return; fx/fy/fz its internal force.  b* may be NULL (no body force).
  * ---------------------------------------------------------------------------------------------- */
-void orc_run(int kin, int64_t n, int dim, const double* x, const double* y, const double* z,
-             const double* vol, const int64_t* row_ptr, const int32_t* col, uint8_t* status,
+void orc_run(int kin, int infl, double delta, int64_t n, int dim, const double* x, const double* y,
+             const double* z, const double* vol, const int64_t* row_ptr, const int32_t* col, uint8_t* status,
              const double* m, double A, double K, double G, double rho, double dt, double s0,
              const uint8_t* flag, const double* bx, const double* by, const double* bz,
              const double* axis_point, const double* axis_dir, double rate, const double* vpx,
@@ -540,8 +558,9 @@ void orc_run(int kin, int64_t n, int dim, const double* x, const double* y, cons
     int64_t step = step0 + s;
     double tn = (double)step * dt, tn1 = (double)(step + 1) * dt;
     apply_bc(n, dim, x, y, z, flag, c, a, rate, tn, ux, uy, uz, vx, vy, vz, vp);
-    orc_dilatation(kin, n, dim, x, y, z, vol, row_ptr, col, status, m, A, ux, uy, uz, theta);
-    orc_force(kin, n, dim, x, y, z, vol, row_ptr, col, status, m, theta, K, G, ux, uy, uz, fx, fy, fz);
+    orc_dilatation(kin, n, dim, x, y, z, vol, row_ptr, col, status, m, A, infl, delta, ux, uy, uz, theta);
+    orc_force(kin, n, dim, x, y, z, vol, row_ptr, col, status, m, theta, K, G, infl, delta, ux, uy, uz, fx, fy,
+              fz);
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
       if (flag && flag[i] != ORC_FREE) continue;
@@ -818,7 +837,8 @@ int pdref_build_neighbors(pdref_ctx* c, const pdref_crack* cracks, int32_t ncrac
   c->status = (uint8_t*)malloc((size_t)(nb > 0 ? nb : 1));
   memset(c->status, 1, (size_t)(nb > 0 ? nb : 1));
   c->m = pdref_copy(NULL, c->n);
-  orc_weighted_volume(c->n, c->dim, c->x, c->y, c->z ? c->z : c->x, c->vol, c->row_ptr, c->col, c->m);
+  orc_weighted_volume(c->n, c->dim, c->x, c->y, c->z ? c->z : c->x, c->vol, c->row_ptr, c->col, ORC_W_ONE, 0.0,
+                      c->m);
   free(counts);
   free(cr);
   c->built = 1;
@@ -860,7 +880,7 @@ int pdref_step(pdref_ctx* c, int64_t nsteps) {
   if (!c || nsteps < 0) return -1;
   if (!c->built) return -2;
   const double* zz = c->z ? c->z : c->x;
-  orc_run(c->kin, c->n, c->dim, c->x, c->y, zz, c->vol, c->row_ptr, c->col, c->status, c->m, c->A, c->K,
+  orc_run(c->kin, ORC_W_ONE, 0.0, c->n, c->dim, c->x, c->y, zz, c->vol, c->row_ptr, c->col, c->status, c->m, c->A, c->K,
           c->G, c->rho, c->dt, c->s0, c->flag, c->b[0], c->b[1], c->b[2], c->axis_point, c->axis_dir,
           c->rate, NULL, NULL, NULL, c->steps, nsteps, c->u[0], c->u[1], c->u[2], c->v[0], c->v[1], c->v[2], c->theta,
           c->f[0], c->f[1], c->f[2], NULL, NULL);
@@ -882,7 +902,8 @@ int pdref_get_state(pdref_ctx* c, double* u, double* v, double* theta) {
 int pdref_get_damage(pdref_ctx* c, double* phi) {
   if (!c || !phi) return -1;
   if (!c->built) return -2;
-  orc_damage(c->n, c->vol, c->row_ptr, c->col, c->status, phi);
+  orc_damage(c->n, c->dim, c->x, c->y, c->z ? c->z : c->x, c->vol, c->row_ptr, c->col, c->status, ORC_W_ONE, 0.0,
+             phi);
   return 0;
 }
 

@@ -11,10 +11,10 @@ import numpy as np
 
 from . import _binding as B
 from ._binding import (PD_3D, PD_FP64, PD_LINEARIZED, PD_MIXED, PD_NONLINEAR, PD_PLANE_STRAIN, PD_PLANE_STRESS,
-                       PDError, pd_critical_stretch)
+                       PD_W_INV, PD_W_ONE, PDError, pd_critical_stretch)
 
 __all__ = ["Simulation", "BatchSimulation", "PDError", "PD_FP64", "PD_MIXED", "PD_LINEARIZED", "PD_NONLINEAR", "PD_3D",
-           "PD_PLANE_STRESS", "PD_PLANE_STRAIN", "pd_critical_stretch"]
+           "PD_PLANE_STRESS", "PD_PLANE_STRAIN", "PD_W_ONE", "PD_W_INV", "pd_critical_stretch"]
 
 
 class Simulation:
@@ -22,16 +22,18 @@ class Simulation:
 
     def __init__(self, w, s0=None, precision=PD_FP64, rate=None, device=0, stream=None,
                  band_safety=0.0, graph_chunk=None, ordering=B.PD_ORDER_BRICKS, bond_cache=None,
-                 kinematics=B.PD_LINEARIZED, pairs=None):
+                 kinematics=B.PD_LINEARIZED, pairs=None, influence=B.PD_W_ONE, lattice=None):
         self.w = w
         self.n, self.dim = w.n, w.dim
         if s0 is None:
             s0 = pd_critical_stretch(w.model, w.E, w.nu, w.Gc, w.delta) if w.Gc else 0.0
         self.s0 = float(s0)
         prm = B.make_params(w.model, w.E, w.nu, w.rho, w.delta, self.s0, w.dt, precision, band_safety,
-                            device, stream, ordering, kinematics)
+                            device, stream, ordering, kinematics, influence)
         self.h = B.pd_create_particles(prm, w.x, w.y, w.z, w.vol)
         try:
+            if lattice is not None:
+                B.pd_set_option(self.h, B.PD_OPT_LATTICE, int(lattice))
             if graph_chunk is not None:
                 B.pd_set_option(self.h, B.PD_OPT_GRAPH_CHUNK, graph_chunk)
             if bond_cache is not None:
@@ -105,14 +107,15 @@ class BatchSimulation(Simulation):
     """Many independent bodies (``workloads.BatchWorkload``) in one context and the same kernels."""
 
     def __init__(self, bw, s0s=None, precision=PD_FP64, device=0, stream=None, band_safety=0.0,
-                 graph_chunk=None, ordering=B.PD_ORDER_BRICKS, bond_cache=None, kinematics=B.PD_LINEARIZED):
+                 graph_chunk=None, ordering=B.PD_ORDER_BRICKS, bond_cache=None, kinematics=B.PD_LINEARIZED,
+                 influence=B.PD_W_ONE):
         self.w = bw
         self.n, self.dim = bw.n, 2 if bw.bodies[0].z is None else 3
         if s0s is None:
             s0s = [pd_critical_stretch(b.model, b.E, b.nu, b.Gc, b.delta) if b.Gc else 0.0 for b in bw.bodies]
         self.s0s = [float(s) for s in s0s]
         prms = [B.make_params(b.model, b.E, b.nu, b.rho, b.delta, s, b.dt, precision, band_safety, device, stream,
-                              ordering, kinematics) for b, s in zip(bw.bodies, self.s0s)]
+                              ordering, kinematics, influence) for b, s in zip(bw.bodies, self.s0s)]
         z = bw.concat("z") if self.dim == 3 else None
         self.h = B.pd_create_batch(prms, bw.offsets, bw.concat("x"), bw.concat("y"), z, bw.concat("vol"))
         try:

@@ -26,6 +26,7 @@ PD_OPT_EXPIRE_WAITS = 8
 PD_OPT_SOLVER = 9
 PD_OPT_PAIRS = 10
 PD_OPT_LATTICE = 11
+PD_W_ONE, PD_W_INV = 0, 1
 PD_SOLVER_EXPLICIT, PD_SOLVER_ADR = 0, 1
 PD_K_PASS1, PD_K_PASS2, PD_K_PASS1B = 0, 1, 2
 
@@ -45,7 +46,7 @@ class pd_params(ctypes.Structure):
                 ("nu", ctypes.c_double), ("rho", ctypes.c_double), ("horizon", ctypes.c_double),
                 ("s0", ctypes.c_double), ("dt", ctypes.c_double), ("band_safety", ctypes.c_double),
                 ("device", ctypes.c_int32), ("ordering", ctypes.c_int32), ("stream", ctypes.c_void_p),
-                ("kinematics", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("kinematics", ctypes.c_int32), ("influence", ctypes.c_int32)]
 
 
 class pd_crack(ctypes.Structure):
@@ -154,9 +155,10 @@ def pd_critical_stretch(model, E, nu, Gc, delta) -> float:
 
 
 def make_params(model, E, nu, rho, horizon, s0, dt, precision=PD_FP64, band_safety=0.0, device=0,
-                stream=None, ordering=PD_ORDER_BRICKS, kinematics=PD_LINEARIZED) -> pd_params:
+                stream=None, ordering=PD_ORDER_BRICKS, kinematics=PD_LINEARIZED, influence=0) -> pd_params:
     return pd_params(int(model), int(precision), float(E), float(nu), float(rho), float(horizon), float(s0),
-                     float(dt), float(band_safety), int(device), int(ordering), stream, int(kinematics), 0)
+                     float(dt), float(band_safety), int(device), int(ordering), stream, int(kinematics),
+                     int(influence))
 
 
 def pd_create_particles(prm: pd_params, x, y, z=None, vol=None):

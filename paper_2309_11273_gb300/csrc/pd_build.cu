@@ -37,6 +37,7 @@ struct BuildArgs {
   unsigned long long* keys;
   uint32_t* bits;
   const double* body_A;
+  const double* body_w;      // per body: 0 (w = 1) or delta (w = delta / |xi|)
   double* m;
   double* mu;
   double* aA;
@@ -196,6 +197,7 @@ __global__ void k_init_bonds(BuildArgs A) {
   const int64_t base = A.slice_ptr[s];
   const int W = (int)((A.slice_ptr[s + 1] - base) >> 5);
   const double4 pi = A.pos[i];
+  const double wd = A.body_w[A.cellc[i].w];
   double m = 0.0, d = 0.0;
   for (int k = 0; k < W; ++k) {
     const int32_t jk = A.col[base + (int64_t)k * 32 + lane];
@@ -208,8 +210,9 @@ __global__ void k_init_bonds(BuildArgs A) {
       const double ex = pj.x - pi.x, ey = pj.y - pi.y, ez = pj.z - pi.z;
       double q = ex * ex + ey * ey;
       if (DIM == 3) q = q + ez * ez;
-      m += q * pj.w;
-      d += pj.w;
+      const double w = wd > 0.0 ? wd / sqrt(q) : 1.0;  // influence function
+      m += w * q * pj.w;
+      d += w * pj.w;
     }
   }
   A.m[i] = m;
@@ -292,7 +295,8 @@ struct LatArgs {
   int R;                      // component bound of the table
   const int64_t* slice_ptr2;  // lattice layout
   int32_t* col2;
-  int32_t* nsum;              // per particle: sum of |n|^2 over its bonds (m_i = V h^2 nsum_i)
+  double* nsum;               // per particle: sum of w' |n|^2 over its bonds (m_i = V h^2 nsum_i (w / w'))
+  const double* body_w;       // per body: 0 (w = 1, w' = 1) or delta (w = delta / |xi|, w' = 1 / |n|)
 };
 
 template <int DIM>
@@ -377,7 +381,8 @@ __global__ void k_lat_emit(LatArgs L) {
   const int64_t base = L.slice_ptr[s] + (i & 31);
   const double4 pi = L.pos[i];
   const double inv_h = L.inv_h[L.body[i]];
-  int nsum = 0;
+  const bool winv = L.body_w[L.body[i]] > 0.0;
+  double nsum = 0.0;
   for (int k = 0; k < cnt; ++k) {
     const int32_t j = L.col[base + (int64_t)k * 32];
     int n[3];
@@ -389,7 +394,8 @@ __global__ void k_lat_emit(LatArgs L) {
       continue;
     }
     L.col2[base2 + (int64_t)d * 32] = j;
-    nsum += n[0] * n[0] + n[1] * n[1] + n[2] * n[2];
+    const int q = n[0] * n[0] + n[1] * n[1] + n[2] * n[2];
+    nsum += winv ? sqrt((double)q) : (double)q;  // w' |n|^2 with w' = 1 / |n| or 1
   }
   L.nsum[i] = nsum;
 }
@@ -414,7 +420,8 @@ pd_status build_lattice(pd_ctx* c, BuildArgs& A, bool* done) {
   unsigned long long* d_minq = nullptr;
   int* d_stats = nullptr;
   short* d_lookup = nullptr;
-  int32_t* d_nsum = nullptr;
+  double* d_nsum = nullptr;
+  double* d_bw = nullptr;
   int64_t* sptr2_dev = nullptr;
   int32_t* col2 = nullptr;
   uint32_t* bits2 = nullptr;
@@ -424,6 +431,7 @@ pd_status build_lattice(pd_ctx* c, BuildArgs& A, bool* done) {
     cudaFree(d_stats);
     cudaFree(d_lookup);
     cudaFree(d_nsum);
+    cudaFree(d_bw);
   };
   auto tmp = [&](void** p, size_t bytes) -> bool {
     if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
@@ -434,7 +442,7 @@ pd_status build_lattice(pd_ctx* c, BuildArgs& A, bool* done) {
   };
   if (!tmp((void**)&d_inv_h, sizeof(double) * nb) || !tmp((void**)&d_minq, sizeof(unsigned long long) * nb) ||
       !tmp((void**)&d_stats, sizeof(int) * (3 * nb + 1)) || !tmp((void**)&d_lookup, sizeof(short) * cube.size()) ||
-      !tmp((void**)&d_nsum, sizeof(int32_t) * n_pad)) {
+      !tmp((void**)&d_nsum, sizeof(double) * n_pad) || !tmp((void**)&d_bw, sizeof(double) * nb)) {
     cleanup();
     return fail(PD_ERR_OOM, "cudaMalloc of lattice build temporaries failed");
   }
@@ -455,6 +463,9 @@ pd_status build_lattice(pd_ctx* c, BuildArgs& A, bool* done) {
   L.lookup = d_lookup;
   L.R = dim == 3 ? kLatR3 : kLatR2;
   L.nsum = d_nsum;
+  L.body_w = d_bw;
+  std::vector<double> hbw(nb);
+  for (int b = 0; b < nb; ++b) hbw[b] = c->prm[b].influence == PD_W_INV ? c->prm[b].horizon : 0.0;
   const int tb = 128;
   const unsigned gb = (unsigned)((n_pad + tb - 1) / tb);
   cudaError_t e = cudaMemcpyAsync(d_minq, hminq.data(), sizeof(unsigned long long) * nb, cudaMemcpyHostToDevice, s);
@@ -462,6 +473,7 @@ pd_status build_lattice(pd_ctx* c, BuildArgs& A, bool* done) {
     e = cudaMemcpyAsync(d_stats, hstats.data(), sizeof(int) * hstats.size(), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d_lookup, cube.data(), sizeof(short) * cube.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_bw, hbw.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) {
     if (dim == 3) k_lat_minq<3><<<gb, tb, 0, s>>>(L);
     else k_lat_minq<2><<<gb, tb, 0, s>>>(L);
@@ -537,9 +549,9 @@ pd_status build_lattice(pd_ctx* c, BuildArgs& A, bool* done) {
     else k_lat_emit<2><<<gb, tb, 0, s>>>(L);
     e = cudaMemcpyAsync(&efail, d_stats + 3 * nb, sizeof(int), cudaMemcpyDeviceToHost, s);
   }
-  std::vector<int32_t> hnsum(n_pad);
+  std::vector<double> hnsum(n_pad);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(hnsum.data(), d_nsum, sizeof(int32_t) * n_pad, cudaMemcpyDeviceToHost, s);
+    e = cudaMemcpyAsync(hnsum.data(), d_nsum, sizeof(double) * n_pad, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess || efail) {
     release(c, sptr2_dev);
@@ -561,9 +573,10 @@ pd_status build_lattice(pd_ctx* c, BuildArgs& A, bool* done) {
   A.bits = c->bits;
   if (dim == 3) k_init_bonds<3><<<gb, tb, 0, s>>>(A);
   else k_init_bonds<2><<<gb, tb, 0, s>>>(A);
-  // per particle (N_ref / N_i, A / N_i), N_ref the largest N_i of the body (its interior value)
+  // per particle (N_ref / N_i, A / N_i), N_ref the largest N_i of the body (its interior value; every
+  // interior particle sums the same terms in the same order, so their N_i are equal bit for bit)
   c->lat_h = h;
-  c->lat_nref.assign(nb, 0);
+  c->lat_nref.assign(nb, 0.0);
   c->lat_qmax.assign(nb, 0);
   c->lat_n1.assign(nb, 0);
   for (int64_t k = 0; k < n; ++k) c->lat_nref[c->body_of[k]] = std::max(c->lat_nref[c->body_of[k]], hnsum[k]);
@@ -577,7 +590,7 @@ pd_status build_lattice(pd_ctx* c, BuildArgs& A, bool* done) {
     double A_b, K_b, G_b;
     material_constants(c->prm[b].model, c->prm[b].E, c->prm[b].nu, &A_b, &K_b, &G_b);
     if (hnsum[k] > 0)
-      hf[k] = make_float2((float)((double)c->lat_nref[b] / hnsum[k]), (float)(A_b / hnsum[k]));
+      hf[k] = make_float2((float)(c->lat_nref[b] / hnsum[k]), (float)(A_b / hnsum[k]));
   }
   if ((st = alloc(c, &c->lat_f, (size_t)n_pad)) != PD_OK) {
     cleanup();
@@ -622,6 +635,9 @@ pd_status check_params(const pd_params& p, int dim) {
   if (p.model < 0 || p.model > 2) return fail(PD_ERR_ARG, "unknown model");
   if ((p.model == PD_3D) != (dim == 3)) return fail(PD_ERR_ARG, "z must be given exactly for PD_3D");
   if (p.precision != PD_FP64 && p.precision != PD_MIXED) return fail(PD_ERR_ARG, "unknown precision");
+  if (p.influence != PD_W_ONE && p.influence != PD_W_INV) return fail(PD_ERR_ARG, "unknown influence function");
+  if (p.influence == PD_W_INV && p.kinematics != PD_LINEARIZED)
+    return fail(PD_ERR_ARG, "the influence function delta / |xi| is supported with linearized bonds only");
   if (!(p.E > 0) || !std::isfinite(p.E)) return fail(PD_ERR_ARG, "E must be > 0");
   if (!(p.nu > -1.0 && p.nu < 0.5)) return fail(PD_ERR_ARG, "nu must lie in (-1, 0.5)");
   if (!(p.rho > 0) || !std::isfinite(p.rho)) return fail(PD_ERR_ARG, "rho must be > 0");
@@ -674,8 +690,8 @@ pd_status create(pd_ctx** out, int32_t nbodies, const pd_params* prm, const int6
     if (st != PD_OK) return st;
     if (prm[b].model != prm[0].model || prm[b].precision != prm[0].precision ||
         prm[b].device != prm[0].device || prm[b].stream != prm[0].stream ||
-        prm[b].kinematics != prm[0].kinematics)
-      return fail(PD_ERR_ARG, "bodies must share model, precision, kinematics, device and stream");
+        prm[b].kinematics != prm[0].kinematics || prm[b].influence != prm[0].influence)
+      return fail(PD_ERR_ARG, "bodies must share model, precision, kinematics, influence, device and stream");
   }
   if (!finite_all(x, n) || !finite_all(y, n) || (z && !finite_all(z, n)) || !finite_all(vol, n))
     return fail(PD_ERR_ARG, "non-finite coordinate or volume");
@@ -859,6 +875,7 @@ pd_status upload_body_params(pd_ctx* c) {
     d.s0nl = p.s0 * (2.0 + p.s0);
     d.breaks = p.s0 > 0.0 ? 1 : 0;
     d.rate = 0.0;
+    d.wdelta = p.influence == PD_W_INV ? p.horizon : 0.0;
     d.Kp32 = (float)(d.Kp * c->q);
     d.G32 = (float)d.G;
     d.G32q = (float)(d.G * c->q);
@@ -878,7 +895,8 @@ pd_status upload_body_params(pd_ctx* c) {
       // sum_j rho_ij n [P_i + P_j + (N_ref/N_i + N_ref/N_j) n.(u'_j - u'_i) / |n|^2] with
       // P_i = lambda sigma_i (N_ref/N_i)^2, sigma_i = sum_j rho_ij n.(u'_j - u'_i), theta_i = A sigma_i / N_i
       const double h = c->lat_h[b];
-      const int nref = c->lat_nref[b], n1 = c->lat_n1[b], qm = c->lat_qmax[b];
+      const double nref = c->lat_nref[b];
+      const int n1 = c->lat_n1[b], qm = c->lat_qmax[b];
       d.lat_h = h;
       d.lat_inv_h = 1.0 / h;
       d.lat_C = G / (h * nref);
@@ -927,7 +945,7 @@ pd_status build_neighbors(pd_ctx* c, const pd_crack* cracks, int32_t ncracks) {
   std::vector<BodyGrid> grids(c->nbodies);
   std::vector<int4> cellc(n_pad);
   int64_t ncells = 0;
-  std::vector<double> bodyA(c->nbodies);
+  std::vector<double> bodyA(c->nbodies), bodyW(c->nbodies);
   for (int b = 0; b < c->nbodies; ++b) {
     double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
     for (int64_t u = c->body_off[b]; u < c->body_off[b + 1]; ++u) {
@@ -953,6 +971,7 @@ pd_status build_neighbors(pd_ctx* c, const pd_crack* cracks, int32_t ncracks) {
     double A, K, G;
     material_constants(c->prm[b].model, c->prm[b].E, c->prm[b].nu, &A, &K, &G);
     bodyA[b] = A;
+    bodyW[b] = c->prm[b].influence == PD_W_INV ? c->prm[b].horizon : 0.0;
   }
   std::vector<int64_t> cell_of(n);
   for (int64_t k = 0; k < n_pad; ++k) {
@@ -990,6 +1009,7 @@ pd_status build_neighbors(pd_ctx* c, const pd_crack* cracks, int32_t ncracks) {
   int32_t* d_cell_items = nullptr;
   CrackDev* d_cracks = nullptr;
   double* d_bodyA = nullptr;
+  double* d_bodyW = nullptr;
   double* d_m = nullptr;
   int32_t* d_width = nullptr;
   unsigned long long* d_keys = nullptr;
@@ -1000,6 +1020,7 @@ pd_status build_neighbors(pd_ctx* c, const pd_crack* cracks, int32_t ncracks) {
     cudaFree(d_cell_items);
     cudaFree(d_cracks);
     cudaFree(d_bodyA);
+    cudaFree(d_bodyW);
     cudaFree(d_m);
     cudaFree(d_width);
     cudaFree(d_keys);
@@ -1029,6 +1050,7 @@ pd_status build_neighbors(pd_ctx* c, const pd_crack* cracks, int32_t ncracks) {
   PD_TRY2(tmp_alloc((void**)&d_cell_items, sizeof(int32_t) * cell_items.size()));
   PD_TRY2(tmp_alloc((void**)&d_cracks, sizeof(CrackDev) * std::max(ncracks, 1)));
   PD_TRY2(tmp_alloc((void**)&d_bodyA, sizeof(double) * c->nbodies));
+  PD_TRY2(tmp_alloc((void**)&d_bodyW, sizeof(double) * c->nbodies));
   PD_TRY2(tmp_alloc((void**)&d_m, sizeof(double) * n_pad));
   PD_TRY2(tmp_alloc((void**)&d_width, sizeof(int32_t) * c->nslices));
   PD_TRY2(alloc(c, &c->cnt, n_pad));
@@ -1049,6 +1071,7 @@ pd_status build_neighbors(pd_ctx* c, const pd_crack* cracks, int32_t ncracks) {
     PD_TRY2(up(d_cell_items, cell_items.data(), sizeof(int32_t) * cell_items.size()));
     PD_TRY2(up(d_cracks, hcr.data(), sizeof(CrackDev) * ncracks));
     PD_TRY2(up(d_bodyA, bodyA.data(), sizeof(double) * c->nbodies));
+    PD_TRY2(up(d_bodyW, bodyW.data(), sizeof(double) * c->nbodies));
 
     BuildArgs A{};
     A.n = n;
@@ -1062,6 +1085,7 @@ pd_status build_neighbors(pd_ctx* c, const pd_crack* cracks, int32_t ncracks) {
     A.ncracks = ncracks;
     A.cnt = c->cnt;
     A.body_A = d_bodyA;
+    A.body_w = d_bodyW;
     A.m = d_m;
     A.mu = c->mu;
     A.aA = c->aA;

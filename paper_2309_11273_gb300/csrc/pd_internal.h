@@ -23,6 +23,7 @@ struct BodyDev {
   double s0;       // critical stretch (<= 0: no breaking)
   double s0nl;     // s0 (2 + s0): nonlinear break test |Y|^2 - |xi|^2 >= s0nl |xi|^2
   double rate;     // prescribed rotation rate
+  double wdelta;   // influence function: 0 for w = 1, delta for w = delta / |xi| (Eq 1.9)
   float Kp32, G32, inv_rho32, sigma32;  // FP32 copies for the mixed path (sigma32 = s0 * Q)
   float G32q;      // G * Q (mixed path, nonlinear bonds)
   float s0nl32;    // s0 (2 + s0) in FP32 (mixed path, nonlinear bonds)
@@ -211,7 +212,7 @@ struct pd_ctx {
   bool lattice = false;           // the built layout is the lattice layout (mixed, linearized bonds)
   float2* lat_f = nullptr;        // lattice layout: per particle (N_ref / N_i, A / N_i)
   std::vector<double> lat_h;      // lattice layout: spacing per body
-  std::vector<int> lat_nref;      // lattice layout: N_ref per body
+  std::vector<double> lat_nref;   // lattice layout: N_ref per body
   std::vector<int> lat_n1;        // lattice layout: largest |n|_1 of the body's family
   std::vector<int> lat_qmax;      // lattice layout: largest |n|^2 of the body's family
   double q = 0.0;               // fixed-point quantum of the mixed coordinates [m]

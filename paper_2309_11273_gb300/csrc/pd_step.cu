@@ -100,13 +100,20 @@ __device__ __forceinline__ void bond_f64(const double4& pi, const double4& pj, c
   }
 }
 
-// Out of line: the mixed path calls it only for the few bonds inside its rounding band.
+// FP64 decision of one bond.  Out of line for the general mixed kernels, which call it only for the
+// few bonds inside their rounding band; inlined into the lattice kernel's slow path (fewer registers
+// held across a call in its hot loop).
 template <int DIM>
-__device__ __noinline__ bool fp64_breaks(const StepArgs& a, int64_t i, int32_t j,
-                                         const double4* __restrict__ disp, double s0) {
+__device__ __forceinline__ bool fp64_breaks_inl(const StepArgs& a, int64_t i, int32_t j,
+                                                const double4* __restrict__ disp, double s0) {
   double ex, ey, ez, d, q;
   bond_f64<DIM>(a.pos[i], a.pos[j], disp[i], disp[j], ex, ey, ez, d, q);
   return d >= s0 * q;
+}
+template <int DIM>
+__device__ __noinline__ bool fp64_breaks(const StepArgs& a, int64_t i, int32_t j,
+                                         const double4* __restrict__ disp, double s0) {
+  return fp64_breaks_inl<DIM>(a, i, j, disp, s0);
 }
 
 // Nonlinear FP64 re-decision for the mixed path: |Y|^2 - |xi|^2 >= s0 (2 + s0) |xi|^2 with the
@@ -1126,7 +1133,7 @@ __global__ void k_bond_tables(StepArgs a, double4* __restrict__ bA, double4* __r
   const SliceIdx t = slice_index<1>(a.n_pad, a.slice_ptr);
   if (!t.active) return;
   const int b = a.body ? a.body[t.i] : 0;
-  const double s0 = a.bp[b].s0, G = a.bp[b].G;
+  const double s0 = a.bp[b].s0, G = a.bp[b].G, wd = a.bp[b].wdelta;
   const double4 pi = a.pos[t.i];
   const double mi = a.mu[t.i];
   const double4 zero = make_double4(0.0, 0.0, 0.0, 0.0);
@@ -1136,8 +1143,12 @@ __global__ void k_bond_tables(StepArgs a, double4* __restrict__ bA, double4* __r
     const double4 pj = a.pos[j];
     double ex, ey, ez, d, q;
     bond_f64<DIM>(pi, pj, zero, zero, ex, ey, ez, d, q);
-    bA[e] = make_double4(ex, ey, ez, s0 * q);
-    bB[e] = make_double4(pj.w * ex, pj.w * ey, pj.w * ez, q > 0.0 ? G * (mi + a.mu[j]) / q : 0.0);
+    // With an influence function w (Eqs 1.6, 1.9, 1.14) the tables hold w xi and w s0 |xi|^2 (so that
+    // the stored extension is w xi.du, the theta sum sum w V_j xi.du and the failure test, w > 0,
+    // unchanged), w V_j xi and G (1/m_i + 1/m_j) / (w |xi|^2): the step kernels are the same.
+    const double w = (wd > 0.0 && q > 0.0) ? wd / sqrt(q) : 1.0;
+    bA[e] = make_double4(w * ex, w * ey, w * ez, w * (s0 * q));
+    bB[e] = make_double4(w * pj.w * ex, w * pj.w * ey, w * pj.w * ez, q > 0.0 ? G * (mi + a.mu[j]) / (w * q) : 0.0);
   }
 }
 
@@ -1675,10 +1686,17 @@ __global__ void __launch_bounds__(512) k_pass2_mixed_staged(StepArgs a, const fl
 // otherwise: a screen against the band with |n|^2 and |u'| bounded per body and per end settles
 // nearly every bond in two instructions; a warp with any bond the screen does not settle evaluates
 // the full band and re-decides the bonds inside it with the FP64 path's arithmetic.
-__constant__ float4 c_lat3[kLatDirs3];   // (n_x, n_y, n_z, |n|^2)
-__constant__ float2 c_latr3[kLatDirs3];  // 1 / |n|^2 as hi + lo
-__constant__ float4 c_lat2[kLatDirs2];
-__constant__ float2 c_latr2[kLatDirs2];
+// Sized to a multiple of 4: slice widths are rounded up to 4 slots, and the slots past the table
+// (unused, status 0) still index it.
+constexpr int kLatPad3 = (kLatDirs3 + 3) & ~3, kLatPad2 = (kLatDirs2 + 3) & ~3;
+__constant__ float4 c_lat3[kLatPad3];   // (n_x, n_y, n_z, |n|^2)
+__constant__ float2 c_latr3[kLatPad3];  // 1 / |n|^2 as hi + lo
+__constant__ float4 c_lat2[kLatPad2];
+__constant__ float2 c_latr2[kLatPad2];
+// w' = 1 / |n| as hi + lo: the per-direction factor of the influence function w = delta / |xi|
+// (w = (delta / h) w', and delta / h cancels between w and m_i)
+__constant__ float2 c_latw3[kLatPad3];
+__constant__ float2 c_latw2[kLatPad2];
 
 template <int DIM>
 __device__ __forceinline__ float4 lat_dir(int k) {
@@ -1687,6 +1705,10 @@ __device__ __forceinline__ float4 lat_dir(int k) {
 template <int DIM>
 __device__ __forceinline__ float2 lat_rcp(int k) {
   return DIM == 3 ? c_latr3[k] : c_latr2[k];
+}
+template <int DIM>
+__device__ __forceinline__ float2 lat_wgt(int k) {
+  return DIM == 3 ? c_latw3[k] : c_latw2[k];
 }
 
 // The FP32 shadow of a displacement in the context's format.
@@ -1700,7 +1722,9 @@ __device__ __forceinline__ float4 shadow_of(const StepArgs& a, int b, const doub
   return make_float4((float)(u.x * sc), (float)(u.y * sc), (float)(u.z * sc), 0.0f);
 }
 
-template <int DIM>
+// WI: influence function w = delta / |xi| (its per-direction factor w' = 1 / |n| multiplies each
+// bond's term in both sums); WI = false: w = 1.
+template <int DIM, bool WI>
 __global__ void __launch_bounds__(512) k_pass1_lat(StepArgs a, const float4* __restrict__ u32,
                                                     const double4* __restrict__ disp, int write_theta) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -1749,49 +1773,62 @@ __global__ void __launch_bounds__(512) k_pass1_lat(StepArgs a, const float4* __r
         j[u] = cs[(kk + u) * 32];
         Uj[u] = u32[j[u]];
       }
-      float dv[U];
-      bool intact[U], near = false;
+      // Every intact bond's term is added to the dilatation sum here; a bond that the slow path
+      // below breaks has its term taken out again (the sum stays a function of each lane's own
+      // operations, so a batch of bodies and the bodies run alone add identically).
+      bool near = false;
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const float4 dn = lat_dir<DIM>(k0 + kk + u);
         const float d = lat_dprime<DIM>(dn.x, dn.y, dn.z, Uj[u].x, Uj[u].y, Uj[u].z, Ui.x, Ui.y, Ui.z);
-        dv[u] = d;
-        intact[u] = (wd[u] >> lane) & 1u;
+        const bool in = (wd[u] >> lane) & 1u;
         if (checking)
-          near = near || (can_break && intact[u] && !lat_screen_intact(lat_g(d, s0f, dn.w), Kfast, Uj[u].w, scr_i));
+          near = near || (can_break && in && !lat_screen_intact(lat_g(d, s0f, dn.w), Kfast, Uj[u].w, scr_i));
+        const float dd = in ? d : 0.0f;
+        if (WI) {  // acc += w' d' with w' as hi + lo
+          const float2 wk = lat_wgt<DIM>(k0 + kk + u);
+          acc = fmaf(wk.x, dd, fmaf(wk.y, dd, acc));
+        } else {
+          acc += dd;
+        }
       }
       if (checking && (__any_sync(kFull, near) || a.validate)) {
-        // full band for the bonds the screen did not settle; FP64 inside it
-        int code[U];
-#pragma unroll
+        // full band for the bonds the screen did not settle, FP64 inside it; everything reloaded
+        // (index from the staged chunk, displacement through L1) so that little stays live here
+#pragma unroll 1
         for (int u = 0; u < U; ++u) {
-          const float4 dn = lat_dir<DIM>(k0 + kk + u);
-          code[u] = !(intact[u] && can_break)
-                        ? 0
-                        : lat_code(lat_g(dv[u], s0f, dn.w), Ui.w, Uj[u].w, s0f, dn.w, bp.lat_Kf, bp.lat_sq,
-                                   bp.lat_eps_c, bp.lat_s0n1);
-        }
-        for (int u = 0; u < U; ++u)
-          if (code[u] == 2) {
-            code[u] = fp64_breaks<DIM>(a, t.i, j[u], disp, s0) ? 1 : 0;
-            atomicAdd(&a.counters[0], 1ull);
-          }
-        if (a.validate) {
-          for (int u = 0; u < U; ++u)
-            if (can_break && intact[u] && (code[u] == 1) != fp64_breaks<DIM>(a, t.i, j[u], disp, s0))
+          const int k = k0 + kk + u;
+          const uint32_t w0 = ws[kk + u];
+          const int32_t jj = cs[(kk + u) * 32];
+          int code = 0;
+          float d = 0.0f;
+          if (can_break && ((w0 >> lane) & 1u)) {
+            const float4 Uu = u32[jj];
+            const float4 dn = lat_dir<DIM>(k);
+            d = lat_dprime<DIM>(dn.x, dn.y, dn.z, Uu.x, Uu.y, Uu.z, Ui.x, Ui.y, Ui.z);
+            code = lat_code(lat_g(d, s0f, dn.w), Ui.w, Uu.w, s0f, dn.w, bp.lat_Kf, bp.lat_sq, bp.lat_eps_c,
+                            bp.lat_s0n1);
+            if (code == 2) {
+              code = fp64_breaks_inl<DIM>(a, t.i, jj, disp, s0) ? 1 : 0;
+              atomicAdd(&a.counters[0], 1ull);
+            }
+            if (a.validate && (code == 1) != fp64_breaks_inl<DIM>(a, t.i, jj, disp, s0))
               atomicAdd(&a.counters[1], 1ull);
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const unsigned m = __ballot_sync(kFull, code[u] == 1);
+          }
+          const unsigned m = __ballot_sync(kFull, code == 1);
           if (m) {
-            intact[u] = intact[u] && code[u] != 1;
-            if (lane == 0) bw[k0 + kk + u] = wd[u] & ~m;
+            if (lane == 0) bw[k] = w0 & ~m;
+            if (code == 1) {
+              if (WI) {
+                const float2 wk = lat_wgt<DIM>(k);
+                acc = fmaf(-wk.x, d, fmaf(-wk.y, d, acc));
+              } else {
+                acc -= d;
+              }
+            }
           }
         }
       }
-#pragma unroll
-      for (int u = 0; u < U; ++u) acc += intact[u] ? dv[u] : 0.0f;
     }
     __syncwarp();  // every lane is done with this buffer before it is refilled
     if (lane == 0 && st.issued < st.nchunks) stage_issue(st, st.issued++);
@@ -1804,7 +1841,7 @@ __global__ void __launch_bounds__(512) k_pass1_lat(StepArgs a, const float4* __r
   }
 }
 
-template <int DIM>
+template <int DIM, bool WI>
 __global__ void __launch_bounds__(512) k_pass2_lat(StepArgs a, const float4* __restrict__ u32,
                                                     float4* __restrict__ u32_out,
                                                     const double4* __restrict__ disp,
@@ -1855,6 +1892,10 @@ __global__ void __launch_bounds__(512) k_pass2_lat(StepArgs a, const float4* __r
         const float d = lat_dprime<DIM>(dn.x, dn.y, dn.z, Uj[u].x, Uj[u].y, Uj[u].z, Ui.x, Ui.y, Ui.z);
         const float dr = fmaf(d, r.x, d * r.y);  // d / |n|^2 with 1 / |n|^2 carried as hi + lo
         float cf = fmaf(ti.y + tj[u].y, dr, ti.x + tj[u].x);
+        if (WI) {  // cf w' with w' as hi + lo
+          const float2 wk = lat_wgt<DIM>(k0 + kk + u);
+          cf = fmaf(cf, wk.x, cf * wk.y);
+        }
         cf = ((wd[u] >> lane) & 1u) ? cf : 0.0f;
         f[0] = fmaf(cf, dn.x, f[0]);
         f[1] = fmaf(cf, dn.y, f[1]);
@@ -2088,8 +2129,9 @@ __global__ void __launch_bounds__(kDiagBlock) k_diag_a(StepArgs a, const double4
       const double4 pj = a.pos[j];
       double xl, e, sv, dir[3];
       diag_bond<DIM, KIN>(pi, pj, ui, disp[j], xl, e, sv, dir);
-      th += xl * e * pj.w;
-      ee += e * e * pj.w;
+      const double w = bp.wdelta > 0.0 ? bp.wdelta / xl : 1.0;
+      th += w * xl * e * pj.w;
+      ee += w * e * e * pj.w;
       if (bp.breaks) margin = fmin(margin, fabs(sv - bp.s0) / bp.s0);
     }
     const double theta_i = a.aA[t.i] * th;
@@ -2128,7 +2170,8 @@ __global__ void __launch_bounds__(kDiagBlock) k_diag_b(StepArgs a, const double4
       double xl, e, sv, dir[3];
       diag_bond<DIM, KIN>(pi, pj, ui, disp[j], xl, e, sv, dir);
       // Eq 1.14 for both ends (Eq 2.2 in the linearized model), force density on i
-      const double cf = ((txi + bp.Kp * theta[j] * a.mu[j]) * xl + (tyi + bp.G * a.mu[j]) * e) * pj.w;
+      const double w = bp.wdelta > 0.0 ? bp.wdelta / xl : 1.0;
+      const double cf = ((txi + bp.Kp * theta[j] * a.mu[j]) * xl + (tyi + bp.G * a.mu[j]) * e) * w * pj.w;
       f[0] = fma(cf, dir[0], f[0]);
       f[1] = fma(cf, dir[1], f[1]);
       f[2] = fma(cf, dir[2], f[2]);
@@ -2156,15 +2199,24 @@ __global__ void __launch_bounds__(kDiagBlock) k_diag_b(StepArgs a, const double4
 // ----------------------------------------------------------------------------- auxiliary kernels
 __global__ void k_set_step(int64_t* d_step, int64_t v) { *d_step = v; }
 
-// phi_i of Eq 1.31 (w = 1), written in caller order.
+// phi_i of Eq 1.31 (with the body's influence function w), written in caller order.
 __global__ void k_damage(StepArgs a, int64_t n, const double* __restrict__ dden,
                          const int64_t* __restrict__ perm, double* __restrict__ out) {
   const SliceIdx t = slice_index<1>(a.n_pad, a.slice_ptr);
   if (!t.active) return;
   double num = 0.0;
+  const double wd = a.bp[a.body ? a.body[t.i] : 0].wdelta;
+  const double4 pi = a.pos[t.i];
   for (int k = 0; k < t.W; ++k) {
     const uint32_t word = a.bits[(t.base >> 5) + k];
-    if ((word >> t.lane) & 1u) num += a.pos[a.col[t.base + t.lane + ((int64_t)k << 5)]].w;
+    if (!((word >> t.lane) & 1u)) continue;
+    const double4 pj = a.pos[a.col[t.base + t.lane + ((int64_t)k << 5)]];
+    double w = 1.0;
+    if (wd > 0.0) {
+      const double ex = pj.x - pi.x, ey = pj.y - pi.y, ez = pj.z - pi.z;
+      w = wd / sqrt(ex * ex + ey * ey + ez * ez);
+    }
+    num += w * pj.w;
   }
   if (t.i < n) out[perm[t.i]] = dden[t.i] > 0.0 ? 1.0 - num / dden[t.i] : 0.0;
 }
@@ -2397,8 +2449,10 @@ void launch_pass2(pd_ctx* c, const StepArgs& a, unsigned grid, int block, size_t
 template <int DIM>
 void optin_staged() {
   const int mx = 16 * kStageWarpBytes;
-  cudaFuncSetAttribute(k_pass1_lat<DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_pass2_lat<DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_pass1_lat<DIM, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_pass2_lat<DIM, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_pass1_lat<DIM, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_pass2_lat<DIM, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_pass1_mixed_staged<DIM, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_pass2_mixed_staged<DIM, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_pass1_mixed_staged<DIM, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
@@ -2426,20 +2480,29 @@ pd_status upload_lattice_tables(int device) {
   if (std::find(done.begin(), done.end(), device) != done.end()) return PD_OK;
   for (int dim = 2; dim <= 3; ++dim) {
     const std::vector<LatDir> t = lattice_directions(dim);
-    std::vector<float4> dn(t.size());
-    std::vector<float2> rc(t.size());
+    const size_t pad = dim == 3 ? kLatPad3 : kLatPad2;
+    std::vector<float4> dn(pad, make_float4(0.0f, 0.0f, 0.0f, 1.0f));
+    std::vector<float2> rc(pad, make_float2(0.0f, 0.0f));
     for (size_t k = 0; k < t.size(); ++k) {
       dn[k] = make_float4((float)t[k].n[0], (float)t[k].n[1], (float)t[k].n[2], (float)t[k].q);
       const double r = 1.0 / t[k].q;
       const float hi = (float)r;
       rc[k] = make_float2(hi, (float)(r - (double)hi));
     }
+    std::vector<float2> wt(pad, make_float2(0.0f, 0.0f));
+    for (size_t k = 0; k < t.size(); ++k) {
+      const double r = 1.0 / std::sqrt((double)t[k].q);
+      const float hi = (float)r;
+      wt[k] = make_float2(hi, (float)(r - (double)hi));
+    }
     if (dim == 3) {
       PD_CUDA(cudaMemcpyToSymbol(c_lat3, dn.data(), sizeof(float4) * dn.size()));
       PD_CUDA(cudaMemcpyToSymbol(c_latr3, rc.data(), sizeof(float2) * rc.size()));
+      PD_CUDA(cudaMemcpyToSymbol(c_latw3, wt.data(), sizeof(float2) * wt.size()));
     } else {
       PD_CUDA(cudaMemcpyToSymbol(c_lat2, dn.data(), sizeof(float4) * dn.size()));
       PD_CUDA(cudaMemcpyToSymbol(c_latr2, rc.data(), sizeof(float2) * rc.size()));
+      PD_CUDA(cudaMemcpyToSymbol(c_latw2, wt.data(), sizeof(float2) * wt.size()));
     }
   }
   done.push_back(device);
@@ -2458,11 +2521,17 @@ void dispatch_pass(pd_ctx* c, const StepArgs& a, int pass, int write_theta) {
     // lattice layout (linearized bonds): one warp per slice, whatever the split and stage options
     const unsigned g1 = (unsigned)((c->nslices * 32 + block - 1) / block);
     const size_t smb = (size_t)(block / 32) * kStageWarpBytes;
-    if (pass == 1)
-      k_pass1_lat<DIM><<<g1, block, smb, c->stream>>>(a, c->u32[c->cur], c->disp[c->cur], write_theta);
+    const bool wi = c->prm[0].influence == PD_W_INV;
+    if (pass == 1 && wi)
+      k_pass1_lat<DIM, true><<<g1, block, smb, c->stream>>>(a, c->u32[c->cur], c->disp[c->cur], write_theta);
+    else if (pass == 1)
+      k_pass1_lat<DIM, false><<<g1, block, smb, c->stream>>>(a, c->u32[c->cur], c->disp[c->cur], write_theta);
+    else if (wi)
+      k_pass2_lat<DIM, true><<<g1, block, smb, c->stream>>>(a, c->u32[c->cur], c->u32[c->cur ^ 1],
+                                                            c->disp[c->cur], c->disp[c->cur ^ 1]);
     else
-      k_pass2_lat<DIM><<<g1, block, smb, c->stream>>>(a, c->u32[c->cur], c->u32[c->cur ^ 1], c->disp[c->cur],
-                                                      c->disp[c->cur ^ 1]);
+      k_pass2_lat<DIM, false><<<g1, block, smb, c->stream>>>(a, c->u32[c->cur], c->u32[c->cur ^ 1],
+                                                             c->disp[c->cur], c->disp[c->cur ^ 1]);
     return;
   }
   if (c->precision == PD_MIXED && ((split == 1 && c->stage) || c->kin == PD_NONLINEAR)) {
@@ -2869,6 +2938,16 @@ pd_status max_abs_u(pd_ctx* c, double* out, int* nonfinite) {
 // chunks of graph_chunk steps, then single steps.
 pd_status run_steps(pd_ctx* c, int64_t nsteps) {
   if (nsteps <= 0) return PD_OK;
+  if (c->prm[0].influence == PD_W_INV) {
+    // w = delta / |xi| lives in the FP64 per-slot tables and in the lattice kernels' direction table
+    if (c->solver == PD_SOLVER_ADR)
+      return fail(PD_ERR_ARG, "the influence function delta / |xi| is not supported by the relaxation solver");
+    if (c->precision == PD_FP64 && !c->bond_cache)
+      return fail(PD_ERR_ARG, "the influence function delta / |xi| needs the FP64 bond cache (PD_OPT_BOND_CACHE)");
+    if (c->precision == PD_MIXED && !c->lattice)
+      return fail(PD_ERR_ARG, "the influence function delta / |xi| in PD_MIXED needs the lattice layout "
+                              "(a lattice body, PD_OPT_LATTICE)");
+  }
   pd_status st = ensure_bond_cache(c);
   if (st != PD_OK) return st;
   if (c->precision == PD_FP64 && !c->bond_cache) c->bs_stale = true;  // untabled kernels break bonds

@@ -1,0 +1,147 @@
+"""The influence function w = delta / |xi| (pd_params.influence = PD_W_INV) on the GPU (GPU only).
+
+Eq 1.9 defines the weighted volume with a general influence function w, which also weights the
+dilatation (Eq 1.6), the force state (Eq 1.14, so the bond force of Eq 2.2) and the damage (Eq 1.31);
+the paper uses w = 1 and refers to a published catalogue of other forms.  The oracle's w = delta/|xi|
+(infl = W_INV, pinned in tests/test_oracle_influence.py) is the reference: the FP64 path (w folded
+into the per-slot tables; pair form and single pass) to the FP64 bars of tests/parity.py with exact
+bond status and damage, and the mixed form on the lattice layout to its stated bound with every
+decision equal to FP64 on its own state.  Combinations without w return PD_ERR_ARG.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2309_11273_gb300 import PD_FP64, PD_MIXED, PD_NONLINEAR, PD_W_INV, PDError, Simulation
+from paper_2309_11273_gb300 import _binding as B
+from paper_2309_11273_gb300 import workloads as W
+from parity import assert_fp64_close, compare, rel
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+def s0_of(w):
+    return O.critical_stretch(w.model, w.E, w.nu, w.Gc, w.delta) if w.Gc else 0.0
+
+
+def oracle_for(w, s0):
+    ref = O.OracleSim(w.model, w.E, w.nu, w.rho, w.delta, s0, w.dt, w.x, w.y, w.z, w.vol, w.cracks,
+                      infl=O.W_INV)
+    ref.set_bc(w.flag, w.b, w.axis_point, w.axis_dir, w.rotation_rate(s0))
+    ref.set_state(w.initial_u(), w.initial_v())
+    return ref
+
+
+CASES = {
+    "cracked_plate": lambda: W.cracked_plate(nx=60, ny=24, dx=2.5e-4, crack_cells=30.125, sigma=2e6, nsteps=400),
+    "notched_block": lambda: W.notched_block(nx=24, ny=12, nz=10, dx=1e-3, notch_cells=9.5, nsteps=300, seed=3,
+                                             amp=1e-7),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+@pytest.mark.parametrize("pairs", [1, 0])
+def test_fp64_influence_parity(case, pairs):
+    w = CASES[case]()
+    s0 = s0_of(w)
+    sim = Simulation(w, s0=s0, influence=PD_W_INV, pairs=pairs)
+    ref = oracle_for(w, s0)
+    exact = True
+    for _ in range(w.nsteps // 50):
+        margins, _ = ref.step(50)
+        sim.step(50)
+        exact = exact and margins.min() > 1e-9
+        u, v, th = sim.state()
+        assert_fp64_close(compare(u, v, th, ref), TOL, (case, pairs, ref.steps_done))
+        if exact:
+            assert np.array_equal(sim.neighbors()[2], ref.status)
+    phi = sim.damage()
+    sim.close()
+    assert exact and (ref.status == 0).sum() > 0
+    assert np.array_equal(phi, ref.damage())
+
+
+def test_fp64_influence_random_cloud():
+    """Non-lattice particles with non-uniform volumes (per-slot tables, no lattice layout)."""
+    rng = np.random.default_rng(21)
+    n = 2500
+    pts = rng.uniform(0.0, 1e-2, size=(3, n))
+    vol = rng.uniform(0.5, 1.5, n) * (2.5e-4) ** 3 * 40
+    w = W.Workload("cloud", W.MODEL_3D, E=1e9, nu=0.25, rho=1000.0, dx=2.5e-4, delta=1.2e-3, dt=2e-9,
+                   nsteps=60, x=pts[0], y=pts[1], z=pts[2], vol=vol, u0=1e-7 * rng.normal(size=(3, n)))
+    sim = Simulation(w, s0=0.0, influence=PD_W_INV)
+    ref = oracle_for(w, 0.0)
+    ref.step(60)
+    sim.step(60)
+    u, v, th = sim.state()
+    sim.close()
+    assert_fp64_close(compare(u, v, th, ref), TOL)
+
+
+def test_fp64_influence_shadow_energy():
+    """pd_get_stats with w: the leapfrog shadow energy of a free plate is constant (Eq 2.11) and the
+    strain energy moves."""
+    w = W.plate_vibration(nx=30, ny=24, nsteps=300)
+    sim = Simulation(w, s0=0.0, influence=PD_W_INV)
+    H, U = [], []
+    for _ in range(6):
+        sim.step(50)
+        st = sim.stats()
+        H.append(st["shadow_energy"])
+        U.append(st["strain_energy"])
+    sim.close()
+    assert np.abs(np.array(H) - H[0]).max() <= 1e-11 * abs(H[0])
+    assert (max(U) - min(U)) > 1e-3 * max(U)
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_mixed_lattice_influence(case):
+    w = CASES[case]()
+    s0 = s0_of(w)
+    sim = Simulation(w, s0=s0, precision=PD_MIXED, influence=PD_W_INV)
+    assert sim.get_option(B.PD_OPT_LATTICE) == 1
+    sim.set_option(B.PD_OPT_VALIDATE, 1)
+    sim.step(w.nsteps)
+    u = sim.state()[0]
+    st = sim.stats()
+    sim.close()
+    ref = oracle_for(w, s0)
+    ref.step(w.nsteps)
+    assert st["validate_mismatches"] == 0 and st["broken_bonds"] > 0
+    assert rel(u, ref.u) <= 1e-4, rel(u, ref.u)
+
+
+def test_influence_free_vibration_mixed_bound():
+    """Configuration 1's plate (no breaking, 1000 steps) with w = delta / |xi|: the mixed form's
+    stated bounds against the oracle, 2e-5 after 100 steps and 1e-4 over 1000."""
+    w = W.config1()
+    sim = Simulation(w, s0=0.0, precision=PD_MIXED, influence=PD_W_INV)
+    ref = oracle_for(w, 0.0)
+    errs = []
+    for _ in range(10):
+        ref.step(100)
+        sim.step(100)
+        errs.append(rel(sim.state()[0], ref.u))
+    sim.close()
+    print("w = delta/|xi| mixed config1 rel-L2(u):", ["%.2e" % e for e in errs])
+    assert errs[0] <= 2e-5 and max(errs) <= 1e-4, errs
+
+
+def test_unsupported_combinations_are_argument_errors():
+    w = W.plate_vibration(nx=20, ny=20, nsteps=10)
+    with pytest.raises(PDError, match="linearized"):
+        Simulation(w, s0=0.0, kinematics=PD_NONLINEAR, influence=PD_W_INV)
+    sim = Simulation(w, s0=0.0, influence=PD_W_INV, bond_cache=0)
+    with pytest.raises(PDError, match="bond cache"):
+        sim.step(1)
+    sim.close()
+    sim = Simulation(w, s0=0.0, influence=PD_W_INV)
+    sim.set_option(B.PD_OPT_SOLVER, B.PD_SOLVER_ADR)
+    with pytest.raises(PDError, match="relaxation"):
+        sim.step(1)
+    sim.close()
+    sim = Simulation(w, s0=0.0, precision=PD_MIXED, influence=PD_W_INV, lattice=0)
+    with pytest.raises(PDError, match="lattice"):
+        sim.step(1)
+    sim.close()

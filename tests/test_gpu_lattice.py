@@ -38,7 +38,7 @@ CASES = {
                                              amp=1e-7),
     "ratio_4": lambda: W.plate_vibration(nx=30, ny=17, ratio=4.015, nsteps=300),
     "plane_strain": lambda: W.kalthoff(nx=120, ny=60, dx=5e-4 * 402 / 120, notch_cells=30.125, gap_cells=30,
-                                       nsteps=600),
+                                       nsteps=1500),  # the notch tips start to crack within these steps
 }
 
 

@@ -1,13 +1,22 @@
-"""Error of the FP32-bond / FP64-integration form per configuration, at each configuration's full
-length (GPU only; takes a few minutes).
+"""Error of the FP32-bond / FP64-integration form per configuration (GPU only; a few minutes).
 
 Reported per configuration: rel-L2(u) against an FP64 reference and the number of directed bonds
 whose status differs from it.  The reference is the oracle for configurations 1 and 2, and the FP64
 GPU path -- itself held to 1e-12 of the oracle by test_gpu_parity / test_gpu_scale -- for the 3D and
 batched configurations, whose full runs (thousands of steps over 1e8-1e9 bonds) are beyond the
-oracle's reach.  Status differences are expected once bonds break: a different FP32 force history
-moves the crack front by whole bonds; the decisions themselves are certified separately (zero
-differences from FP64 on the mixed run's own state, test_mixed_decisions_equal_fp64_on_own_state).
+oracle's reach.
+
+On the torsion blocks (configurations 3 and 5) bonds break by the million.  Eq 1.30 decides each
+bond by a threshold, so two evaluations whose rounding differs at all -- even two FP64 runs that sum
+in a different order -- eventually break different bonds, and the crack patterns then separate.  To
+tell that fracture sensitivity from the FP32 force error, each block also runs a second FP64
+trajectory with a different summation order (the particles in Morton order instead of bricks: other
+slices, other slot order, the same physics), and its distance from the reference -- the FP64 floor
+-- is reported beside the mixed one at every checkpoint.  Bound: the mixed error stays within
+max(1e-3, 10 x the FP64 floor) at every checkpoint (before fracture the floor is ~1e-13 and the
+first bound applies; once the FP64 runs themselves separate, the mixed divergence is the fracture's).
+Every mixed decision is separately certified equal to FP64 on the run's own state (validation mode,
+tests/test_gpu_lattice.py).
 """
 import json
 
@@ -16,20 +25,47 @@ import pytest
 
 import oracle as O
 from paper_2309_11273_gb300 import PD_FP64, PD_MIXED, BatchSimulation, Simulation
+from paper_2309_11273_gb300 import _binding as B
 from paper_2309_11273_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-# stated bounds on rel-L2(u) at the end of the full run (configurations 1, 2, 4) and at the first
-# tenth of the run (configurations 3, 5, whose torsion fractures millions of bonds; once the FP32 and
-# FP64 runs break different bonds the two crack patterns diverge and the end-of-run difference is a
-# property of the fracture, reported but not bounded).  Configuration 5 has already broken ~4e6
-# bonds at its first tenth (step 100), so its bound there is looser than configuration 3's.
-BOUNDS = {"config1": 1e-4, "config2": 1e-5, "config4": 1e-3, "config3": 1e-3, "config5": 1e-2}
+# stated bounds on rel-L2(u) at the end of the full run (configurations 1, 2, 4)
+BOUNDS = {"config1": 1e-4, "config2": 1e-5, "config4": 1e-3}
+BLOCK_BOUND, FLOOR_FACTOR = 1e-3, 10.0
 
 
 def _rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _block_trajectories(w, nsteps, nchk, with_status=True):
+    """Reference FP64 (bricks), FP64 in Morton order, and mixed, all from the same state; at nchk
+    checkpoints rel-L2(u) and status mismatches of the latter two against the reference.  Two
+    contexts at a time (the reference is deterministic: its second run is bitwise its first)."""
+    k = nsteps // nchk
+    out = {"fp64_order": [], "mixed": []}
+    for tag, kw in (("fp64_order", dict(precision=PD_FP64, ordering=B.PD_ORDER_MORTON)),
+                    ("mixed", dict(precision=PD_MIXED))):
+        ref = Simulation(w, precision=PD_FP64)
+        sim = Simulation(w, **kw)
+        for _ in range(nchk):
+            ref.step(k)
+            sim.step(k)
+            u64, u = ref.state()[0], sim.state()[0]
+            row = {"step": ref.stats()["steps"], "rel_l2_u": _rel(u, u64)}
+            if with_status:
+                s64, s = ref.neighbors()[2], sim.neighbors()[2]
+                row.update(status_mismatch=int((s != s64).sum()), broken_reference=int((s64 == 0).sum()))
+            else:
+                row.update(broken_reference=int(ref.stats()["broken_bonds"]), broken=int(sim.stats()["broken_bonds"]))
+            out[tag].append(row)
+        if tag == "mixed":
+            out["band_rechecks"] = sim.stats()["band_rechecks"]
+            out["lattice"] = sim.get_option(B.PD_OPT_LATTICE)
+        ref.close()
+        sim.close()
+    return out
 
 
 def test_mixed_error_per_configuration(capsys):
@@ -49,21 +85,11 @@ def test_mixed_error_per_configuration(capsys):
         out[name] = {"steps": w.nsteps, "reference": "oracle", "rel_l2_u": _rel(u, ref.u),
                      "status_mismatch": int((st != ref.status).sum()),
                      "broken_reference": int((ref.status == 0).sum()), "band_rechecks": stats["band_rechecks"]}
-    for name, w in (("config3", W.config3()), ("config5", W.config5())):
-        ref = Simulation(w, precision=PD_FP64)
-        sim = Simulation(w, precision=PD_MIXED)
-        traj = []
-        for _ in range(10):
-            ref.step(w.nsteps // 10)
-            sim.step(w.nsteps // 10)
-            u64, st64 = ref.state()[0], ref.neighbors()[2]
-            u32, st32 = sim.state()[0], sim.neighbors()[2]
-            traj.append({"step": ref.stats()["steps"], "rel_l2_u": _rel(u32, u64),
-                         "status_mismatch": int((st32 != st64).sum()), "broken_reference": int((st64 == 0).sum())})
-        out[name] = dict(traj[-1], reference="FP64 GPU path", band_rechecks=sim.stats()["band_rechecks"],
-                         first_tenth=traj[0], trajectory=traj)
-        ref.close()
-        sim.close()
+    out["config3"] = dict(_block_trajectories(W.config3(), 2000, 10), steps=2000, reference="FP64 GPU path")
+    # configuration 5 (8M particles, ~9.6e8 bonds): its first 200 steps (millions of bonds break by
+    # step 100), broken counts instead of per-bond mismatches (a full status read-back takes ~30 s)
+    out["config5"] = dict(_block_trajectories(W.config5(), 200, 2, with_status=False), steps=200,
+                          reference="FP64 GPU path")
     bw = W.config4()
     res = {}
     for prec in (PD_FP64, PD_MIXED):
@@ -78,6 +104,8 @@ def test_mixed_error_per_configuration(capsys):
                       "band_rechecks": res[PD_MIXED][2]["band_rechecks"]}
     with capsys.disabled():
         print("\nMIXED_ACCURACY " + json.dumps(out))
-    for name, r in out.items():
-        val = r["first_tenth"]["rel_l2_u"] if "first_tenth" in r else r["rel_l2_u"]
-        assert val <= BOUNDS[name], (name, r)
+    for name in ("config1", "config2", "config4"):
+        assert out[name]["rel_l2_u"] <= BOUNDS[name], (name, out[name])
+    for name in ("config3", "config5"):
+        for fl, mx in zip(out[name]["fp64_order"], out[name]["mixed"]):
+            assert mx["rel_l2_u"] <= max(BLOCK_BOUND, FLOOR_FACTOR * fl["rel_l2_u"]), (name, fl, mx)
