@@ -566,6 +566,7 @@ def run_forms(args, stream, dev, world, fp64_value, nb, hbm, hbm_note, fp64_tflo
     prof = profiled(sim, 50)
     st = sim.stats()
     lattice = sim.get_option(B.PD_OPT_LATTICE) == 1
+    lat_stage = sim.get_option(B.PD_OPT_LAT_STAGE)
     sim.close()
     staged = mmap[1] == 1  # the staged kernels run whenever the mapping has one warp per slice
     bytes2 = BYTES_BOND[2] * nb + BYTES_PART[2] * w.n
@@ -575,7 +576,8 @@ def run_forms(args, stream, dev, world, fp64_value, nb, hbm, hbm_note, fp64_tflo
     out["mixed"] = {"value": mval, "unit": UNIT, "speedup_vs_fp64": mval / fp64_value,
                     "ms_per_step": ms / steps, "dtype": "f32 bond arithmetic, f64 integration",
                     "stated_error": mixed_error_on_workload(w, s0, stream, dev, 200),
-                    "band_rechecks": st["band_rechecks"], "mapping": {"block": mmap[0], "split": mmap[1]},
+                    "band_rechecks": st["band_rechecks"],
+                    "mapping": {"block": mmap[0], "split": mmap[1], "lat_stage": lat_stage},
                     "layout": "lattice" if lattice else "general",
                     "roofline": mixed_roofline(prof, a1, a2, bytes1, bytes2, hbm, hbm_note, staged, lattice)}
     # geometrically nonlinear bonds (Eqs 1.10, 1.13, 1.14) in FP64 on the same workload
@@ -690,6 +692,10 @@ def main():
                          "FP64 kernels hold a few GB")
     ap.add_argument("--profile-pairs", type=int, choices=[0, 1], default=1,
                     help="with --profile-target fp64: 0 runs the single-pass FP64 pass 1 (PD_OPT_PAIRS = 0)")
+    ap.add_argument("--profile-block", type=int, default=0,
+                    help="with --profile-target: threads per block of the step kernels (0: default)")
+    ap.add_argument("--profile-ring", type=int, choices=[0, 1, 2, 3], default=0,
+                    help="with --profile-target mixed: staging ring of the lattice kernels (PD_OPT_LAT_STAGE)")
     ap.add_argument("--sweep", action="store_true",
                     help="one JSON line per configuration (1-5): FP64 and mixed GPU rates and the oracle's "
                          "rate on all host cores and on one")
@@ -701,7 +707,8 @@ def main():
     import __graft_entry__
     __graft_entry__.build()
     if args.profile_target:
-        return profile_target(args.profile_target, args.profile_quarter, args.profile_pairs)
+        return profile_target(args.profile_target, args.profile_quarter, args.profile_pairs, args.profile_block,
+                              args.profile_ring)
     if args.sweep:
         return run_sweep(args)
     return run_gpu(args)
@@ -764,7 +771,7 @@ def run_sweep(args):
     return 0
 
 
-def profile_target(form, quarter=False, pairs=1):
+def profile_target(form, quarter=False, pairs=1, block=0, ring=0):
     """Workload of the benchmark in one precision, 4 eager time steps (ncu captures this command)."""
     from paper_2309_11273_gb300 import PD_FP64, PD_LINEARIZED, PD_MIXED, PD_NONLINEAR, Simulation, pd_critical_stretch
     from paper_2309_11273_gb300 import workloads as W
@@ -773,6 +780,11 @@ def profile_target(form, quarter=False, pairs=1):
     sim = Simulation(w, s0=s0, precision=PD_MIXED if form.startswith("mixed") else PD_FP64, graph_chunk=0,
                      kinematics=PD_NONLINEAR if form.endswith("nonlinear") else PD_LINEARIZED,
                      pairs=None if pairs else 0)
+    from paper_2309_11273_gb300 import _binding as B
+    if block:
+        sim.set_option(B.PD_OPT_BLOCK, block)
+    if form.startswith("mixed"):
+        sim.set_option(B.PD_OPT_LAT_STAGE, ring)
     sim.step(4)
     sim.sync()
     print(json.dumps({"profile_target": form, "particles": w.n, "directed_bonds": sim.nbonds, "stats": sim.stats()}))

@@ -167,7 +167,7 @@ typedef enum {
                               switched between steps; nonlinear theta sums differ in rounding
                               order only.  Has no effect when the build could not pair
                               every entry (pd_get_option then reports 0). */
-  PD_OPT_LATTICE = 11      /* PD_MIXED with linearized bonds: 1 (default) = when every body's
+  PD_OPT_LATTICE = 11,     /* PD_MIXED with linearized bonds: 1 (default) = when every body's
                               particles lie on a regular lattice (bond vectors h n with integer n to
                               within 2^-30 h, uniform volumes, horizon up to 5 h in 3D and 8 h in
                               2D), pd_build_neighbors lays the family out by lattice direction (slot
@@ -176,6 +176,10 @@ typedef enum {
                               coordinates; 0 = the general layout and kernels.  Set before
                               pd_build_neighbors; after it, pd_get_option reports whether the built
                               layout is the lattice one. */
+  PD_OPT_LAT_STAGE = 12    /* lattice kernels: shared-memory ring of each warp's index and status
+                              stream, 0 (default) = 3 chunks of 16 slots, 1 = 2 x 16, 2 = 3 x 8,
+                              3 = 2 x 8 (smaller rings leave more of the SM's combined L1 / shared
+                              memory to the displacement gathers); pd_autotune chooses it */
 } pd_option;
 
 /* Solvers (PD_OPT_SOLVER).

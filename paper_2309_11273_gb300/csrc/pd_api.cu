@@ -79,6 +79,10 @@ void free_build(pd_ctx* c) {
   c->mu32 = c->aA32 = c->theta32 = nullptr;
   c->lattice = false;
   c->lat_f = nullptr;
+  c->lat_rho = nullptr;
+  c->lat_up = nullptr;
+  c->lat_int = nullptr;
+  c->lat_wuni = 0;
 }
 
 void release(pd_ctx* c, void* p) {
@@ -576,6 +580,11 @@ pd_status pd_set_option(pd_ctx* c, int32_t option, int64_t value) {
     case PD_OPT_LATTICE:
       c->lattice_opt = value != 0;  // read by the next pd_build_neighbors
       break;
+    case PD_OPT_LAT_STAGE:
+      if (value < 0 || value > 3) return fail(PD_ERR_ARG, "PD_OPT_LAT_STAGE must be 0, 1, 2 or 3");
+      if (c->lat_stage != (int)value) drop_graphs(c);
+      c->lat_stage = (int)value;
+      break;
     case PD_OPT_PAIRS:
       // A failure check of the pair form marks slices whose bS its next pass 1b recomputes; the
       // other form never reads those marks, so a switch recomputes every bS before the next step.
@@ -612,6 +621,7 @@ pd_status pd_get_option(pd_ctx* c, int32_t option, int64_t* value) {
     case PD_OPT_SOLVER: *value = c->solver; break;
     case PD_OPT_PAIRS: *value = (c->pairs && c->pairs_ok && c->precision == PD_FP64) ? 1 : 0; break;
     case PD_OPT_LATTICE: *value = c->built ? (c->lattice ? 1 : 0) : c->lattice_opt; break;
+    case PD_OPT_LAT_STAGE: *value = c->lat_stage; break;
     default: return fail(PD_ERR_ARG, "unknown option");
   }
   return PD_OK;
@@ -861,7 +871,7 @@ pd_status pd_autotune(pd_ctx* c, int32_t trial_steps, int32_t* block_out, int32_
   for (char* p = key; *p; ++p)
     if (*p == '\n' || *p == '|') *p = ' ';
   const char* cache = std::getenv("PD_AUTOTUNE_CACHE");
-  int best_block = -1, best_split = -1, best_pairs = -1;
+  int best_block = -1, best_split = -1, best_pairs = -1, best_lat = -1;
   if (cache) {
     if (FILE* f = std::fopen(cache, "r")) {
       char line[700];
@@ -869,11 +879,12 @@ pd_status pd_autotune(pd_ctx* c, int32_t trial_steps, int32_t* block_out, int32_
         char* bar = std::strchr(line, '|');
         if (!bar) continue;
         *bar = 0;
-        int b = 0, s = 0, pr = -1;
-        if (std::strcmp(line, key) == 0 && std::sscanf(bar + 1, "%d %d %d", &b, &s, &pr) >= 2) {
+        int b = 0, s = 0, pr = -1, rg = -1;
+        if (std::strcmp(line, key) == 0 && std::sscanf(bar + 1, "%d %d %d %d", &b, &s, &pr, &rg) >= 2) {
           best_block = b;
           best_split = s;
           best_pairs = pr;
+          best_lat = rg;
         }
       }
       std::fclose(f);
@@ -940,14 +951,18 @@ pd_status pd_autotune(pd_ctx* c, int32_t trial_steps, int32_t* block_out, int32_
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
+    const int stage0 = c->lat_stage;
+    const int nrings = c->lattice ? 4 : 1;
+    int best_ring = stage0;
     for (int bl : blocks) {
       for (int sp : splits) {
         if ((bl / 32) % sp) continue;
         if (c->lattice && sp != 1) continue;  // the lattice kernels run one warp per slice
-        for (int po = 0; po < (try_pairs ? 2 : 1); ++po) {
+        for (int po = 0; po < (try_pairs ? 2 : 1) * nrings; ++po) {
           c->block = bl;
           c->split = sp;
           c->pairs = try_pairs ? pair_opts[po] : pairs0;
+          if (c->lattice) c->lat_stage = po;  // the staging ring of the lattice kernels
           if ((st = restore()) != PD_OK) break;
           run_steps(c, 1);  // warm-up
           cudaEventRecord(e0, s);
@@ -965,6 +980,7 @@ pd_status pd_autotune(pd_ctx* c, int32_t trial_steps, int32_t* block_out, int32_
             best_block = bl;
             best_split = sp;
             best_pairs = c->pairs;
+            best_ring = c->lat_stage;
           }
         }
         if (st != PD_OK) break;
@@ -984,17 +1000,20 @@ pd_status pd_autotune(pd_ctx* c, int32_t trial_steps, int32_t* block_out, int32_
     c->graph_chunk = chunk0;
     c->block = block0;
     c->split = split0;
+    c->lat_stage = stage0;
     if (st != PD_OK) return st;
     if (st2 != PD_OK) return st2;
+    best_lat = best_ring;
     if (cache && best_block > 0) {
       if (FILE* f = std::fopen(cache, "a")) {
-        std::fprintf(f, "%s|%d %d %d\n", key, best_block, best_split, best_pairs);
+        std::fprintf(f, "%s|%d %d %d %d\n", key, best_block, best_split, best_pairs, best_ring);
         std::fclose(f);
       }
     }
   }
   c->block = best_block;
   c->split = best_split;
+  if (best_lat >= 0) c->lat_stage = best_lat;
   if (best_pairs >= 0) {
     if ((best_pairs != 0) != (c->pairs != 0)) c->bs_stale = true;  // as a PD_OPT_PAIRS switch
     c->pairs = best_pairs;

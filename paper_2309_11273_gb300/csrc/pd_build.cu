@@ -400,6 +400,24 @@ __global__ void k_lat_emit(LatArgs L) {
   L.nsum[i] = nsum;
 }
 
+// Per slice: 1 when every lane and every neighbour of it has N_j = N_ref (rho = 1), so the force
+// pass need not gather the neighbours' N_ref / N_j.
+__global__ void k_lat_interior(int64_t n_pad, const int64_t* __restrict__ slice_ptr, const int32_t* __restrict__ col,
+                               const float2* __restrict__ f, uint8_t* __restrict__ flag) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n_pad) return;  // n_pad is a multiple of 32: whole warps
+  const int64_t s = i >> 5;
+  const int64_t base = slice_ptr[s] + (i & 31);
+  const int W = (int)((slice_ptr[s + 1] - slice_ptr[s]) >> 5);
+  bool ok = f[i].x == 1.0f;
+  for (int k = 0; k < W && ok; ++k) {
+    const int32_t j = col[base + (int64_t)k * 32];
+    if (j != (int32_t)i) ok = f[j].x == 1.0f;
+  }
+  const unsigned all = __ballot_sync(0xffffffffu, ok);
+  if ((i & 31) == 0) flag[s] = all == 0xffffffffu ? 1 : 0;
+}
+
 // Tries the lattice layout for a mixed-precision context with linearized bonds (called after the
 // sorted layout and its status words are built).  Every body must have uniform volumes and bond
 // vectors within 2^-30 h of h n with n inside the direction table; otherwise the sorted layout stays
@@ -592,14 +610,28 @@ pd_status build_lattice(pd_ctx* c, BuildArgs& A, bool* done) {
     if (hnsum[k] > 0)
       hf[k] = make_float2((float)(c->lat_nref[b] / hnsum[k]), (float)(A_b / hnsum[k]));
   }
-  if ((st = alloc(c, &c->lat_f, (size_t)n_pad)) != PD_OK) {
+  std::vector<float> hr(n_pad);
+  for (int64_t k = 0; k < n_pad; ++k) hr[k] = hf[k].x;
+  if ((st = alloc(c, &c->lat_f, (size_t)n_pad)) != PD_OK || (st = alloc(c, &c->lat_rho, (size_t)n_pad)) != PD_OK ||
+      (st = alloc(c, &c->lat_up, (size_t)n_pad)) != PD_OK ||
+      (st = alloc(c, &c->lat_int, (size_t)c->nslices)) != PD_OK) {
     cleanup();
     return st;
   }
   e = cudaMemcpyAsync(c->lat_f, hf.data(), sizeof(float2) * n_pad, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->lat_rho, hr.data(), sizeof(float) * n_pad, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->lat_up, 0, sizeof(float4) * n_pad, s);
+  if (e == cudaSuccess) {
+    k_lat_interior<<<gb, tb, 0, s>>>(n_pad, c->slice_ptr, c->col, c->lat_f, c->lat_int);
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cleanup();
   if (e != cudaSuccess) return cuda_fail(e, "lattice factors");
+  // the common slice width (one family prefix for the whole context), 0 if the widths differ
+  c->lat_wuni = (int)((sptr2[1] - sptr2[0]) >> 5);
+  for (int64_t t = 0; t < c->nslices; ++t)
+    if ((int)((sptr2[t + 1] - sptr2[t]) >> 5) != c->lat_wuni) c->lat_wuni = 0;
   c->lattice = true;
   *done = true;
   return upload_body_params(c);
@@ -1127,6 +1159,10 @@ pd_status build_neighbors(pd_ctx* c, const pd_crack* cracks, int32_t ncracks) {
     PD_CUDA(cudaGetLastError());
     c->lattice = false;
     c->lat_f = nullptr;
+    c->lat_rho = nullptr;
+    c->lat_up = nullptr;
+    c->lat_int = nullptr;
+    c->lat_wuni = 0;
     if (c->precision == PD_MIXED && c->kin == PD_LINEARIZED && c->lattice_opt) {
       PD_CUDA(cudaStreamSynchronize(s));
       bool lat = false;

@@ -116,6 +116,10 @@ struct StepArgs {
   double4* gnew;           // ADR: force density g^n of this iteration
   int lattice;             // mixed path: the lattice layout and its FP32 shadow u / h (with |u / h|_inf in .w)
   const float2* lat_f;     // lattice layout: per particle (rho_i = N_ref / N_i, A / N_i)
+  const float* lat_rho;    // lattice layout: per particle N_ref / N_i (the pass-2 gather)
+  float4* lat_up;          // lattice layout: per particle (u'_i, P_i), written by pass 1 for pass 2
+  const uint8_t* lat_int;  // lattice layout: per slice, 1 if N_j = N_ref for its lanes and neighbours
+  int lat_wuni;            // lattice layout: the common slice width, or 0 if the widths differ
 };
 
 struct KernelTimes {
@@ -209,8 +213,13 @@ struct pd_ctx {
   double* diag_theta = nullptr;   // pd_get_stats: theta at the current state
   double4* diag_part = nullptr;   // pd_get_stats: per-block (strain energy, min margin, kinetic, 0)
   int lattice_opt = 1;            // PD_OPT_LATTICE: build the lattice layout when the bodies qualify
+  int lat_stage = 0;              // PD_OPT_LAT_STAGE: staging ring of the lattice kernels (0..3)
   bool lattice = false;           // the built layout is the lattice layout (mixed, linearized bonds)
   float2* lat_f = nullptr;        // lattice layout: per particle (N_ref / N_i, A / N_i)
+  float* lat_rho = nullptr;       // lattice layout: per particle N_ref / N_i
+  float4* lat_up = nullptr;       // lattice layout: per particle (u'_i, P_i) from pass 1
+  uint8_t* lat_int = nullptr;     // lattice layout: per slice, every N_j = N_ref around it
+  int lat_wuni = 0;               // lattice layout: the common slice width (0: widths differ)
   std::vector<double> lat_h;      // lattice layout: spacing per body
   std::vector<double> lat_nref;   // lattice layout: N_ref per body
   std::vector<int> lat_n1;        // lattice layout: largest |n|_1 of the body's family

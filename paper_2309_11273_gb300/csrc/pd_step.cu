@@ -1331,7 +1331,7 @@ __global__ void __launch_bounds__(512) k_pass2_mixed(StepArgs a, const float4* _
 // an error word, drains (again bounded) the copies it issued and skips its outputs.
 constexpr int kStageCh = 16;   // slots per chunk: 2 KB of indices + 64 B of status words
 constexpr int kStageBuf = 3;   // chunks in flight per warp
-constexpr int kStageWarpBytes = kStageBuf * (kStageCh * 128 + kStageCh * 4) + 64;
+constexpr int kStageWarpBytes = kStageBuf * (kStageCh * 128 + kStageCh * 4) + 64;  // the general kernels' ring
 constexpr unsigned kWaitLimit = 1u << 24;              // polls (a second bound besides the clock)
 constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s: no staged copy legitimately takes this long
 
@@ -1378,49 +1378,62 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
   return false;
 }
 
+// Stage<NB, CH>: NB chunks of CH slots each (CH a multiple of 4, so every chunk's status words start
+// on a 16-byte boundary); the general mixed kernels use kStageBuf x kStageCh, the lattice kernels a
+// ring chosen by the autotuner (PD_OPT_LAT_STAGE), smaller rings leaving more of the SM's combined
+// L1 / shared memory to the displacement gathers.
+template <int NB, int CH>
+struct StageGeom {
+  static constexpr int kWarpBytes = NB * (CH * 128 + CH * 4) + 64;  // 64: the NB <= 8 barriers
+};
+
+template <int NB = kStageBuf, int CH = kStageCh>
 struct Stage {
-  uint64_t* bar;    // kStageBuf barriers
-  int32_t* col;     // kStageBuf x kStageCh x 32 indices
-  uint32_t* words;  // kStageBuf x kStageCh status words
+  uint64_t* bar;    // NB barriers
+  int32_t* col;     // NB x CH x 32 indices
+  uint32_t* words;  // NB x CH status words
   const int32_t* gcol;
   const uint32_t* gwords;
   int W, nchunks, issued;
 };
 
-__device__ __forceinline__ Stage stage_init(unsigned char* smem, const SliceIdx& t, const StepArgs& a) {
-  Stage st;
-  unsigned char* base = smem + (threadIdx.x >> 5) * kStageWarpBytes;
+template <int NB = kStageBuf, int CH = kStageCh>
+__device__ __forceinline__ Stage<NB, CH> stage_init(unsigned char* smem, const SliceIdx& t, const StepArgs& a) {
+  Stage<NB, CH> st;
+  unsigned char* base = smem + (threadIdx.x >> 5) * StageGeom<NB, CH>::kWarpBytes;
   st.bar = reinterpret_cast<uint64_t*>(base);
   st.col = reinterpret_cast<int32_t*>(base + 64);
-  st.words = reinterpret_cast<uint32_t*>(base + 64 + kStageBuf * kStageCh * 128);
+  st.words = reinterpret_cast<uint32_t*>(base + 64 + NB * CH * 128);
   st.gcol = a.col + t.base;
   st.gwords = a.bits + (t.base >> 5);
   st.W = t.W;
-  st.nchunks = (t.W + kStageCh - 1) / kStageCh;
+  st.nchunks = (t.W + CH - 1) / CH;
   st.issued = 0;
   if ((threadIdx.x & 31) == 0)
-    for (int b = 0; b < kStageBuf; ++b) mbar_init(&st.bar[b], 1);
+    for (int b = 0; b < NB; ++b) mbar_init(&st.bar[b], 1);
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   __syncwarp();
   return st;
 }
 
-// Lane 0: start the copy of chunk c into buffer c % kStageBuf.
-__device__ __forceinline__ void stage_issue(Stage& st, int c) {
-  const int b = c % kStageBuf;
-  const int k0 = c * kStageCh;
-  const int n = min(kStageCh, st.W - k0);  // a multiple of 4 (slot counts are)
+// Lane 0: start the copy of chunk c into buffer c % NB.
+template <int NB, int CH>
+__device__ __forceinline__ void stage_issue(Stage<NB, CH>& st, int c) {
+  const int b = c % NB;
+  const int k0 = c * CH;
+  const int n = min(CH, st.W - k0);  // a multiple of 4 (slot counts are)
   const unsigned cb = (unsigned)n * 128u, wb = (unsigned)n * 4u;
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   mbar_expect_tx(&st.bar[b], cb + wb);
-  bulk_to_smem(st.col + b * kStageCh * 32, st.gcol + (int64_t)k0 * 32, cb, &st.bar[b]);
-  bulk_to_smem(st.words + b * kStageCh, st.gwords + k0, wb, &st.bar[b]);
+  bulk_to_smem(st.col + b * CH * 32, st.gcol + (int64_t)k0 * 32, cb, &st.bar[b]);
+  bulk_to_smem(st.words + b * CH, st.gwords + k0, wb, &st.bar[b]);
 }
 
 // After a failed wait: wait (bounded) for every chunk still in flight, so that no copy lands in
 // shared memory after the block has moved on.
-__device__ __forceinline__ void stage_drain(Stage& st, int from) {
-  for (int c = from; c < st.issued; ++c) mbar_wait(&st.bar[c % kStageBuf], (unsigned)((c / kStageBuf) & 1));
+template <int NB, int CH>
+__device__ __forceinline__ void stage_drain(Stage<NB, CH>& st, int from) {
+  for (int c = from; c < st.issued; ++c) mbar_wait(&st.bar[c % NB], (unsigned)((c / NB) & 1));
 }
 
 template <int DIM, int KIN>
@@ -1430,7 +1443,7 @@ __global__ void __launch_bounds__(512) k_pass1_mixed_staged(StepArgs a, const fl
   const SliceIdx t = slice_index<1>(a.n_pad, a.slice_ptr);
   if (write_theta && blockIdx.x == 0 && threadIdx.x == 0) *a.d_step += 1;
   if (!t.active) return;  // whole warps: the staging below is per warp
-  Stage st = stage_init(smem, t, a);
+  auto st = stage_init<>(smem, t, a);
   const int lane = t.lane;
   const int b = a.body ? a.body[t.i] : 0;
   const double s0 = a.bp[b].s0;
@@ -1582,7 +1595,7 @@ __global__ void __launch_bounds__(512) k_pass2_mixed_staged(StepArgs a, const fl
   extern __shared__ __align__(128) unsigned char smem[];
   const SliceIdx t = slice_index<1>(a.n_pad, a.slice_ptr);
   if (!t.active) return;
-  Stage st = stage_init(smem, t, a);
+  auto st = stage_init<>(smem, t, a);
   const int lane = t.lane;
   const int b = a.body ? a.body[t.i] : 0;
   const int4 Pi = a.pos32[t.i];
@@ -1724,14 +1737,47 @@ __device__ __forceinline__ float4 shadow_of(const StepArgs& a, int b, const doub
 
 // WI: influence function w = delta / |xi| (its per-direction factor w' = 1 / |n| multiplies each
 // bond's term in both sums); WI = false: w = 1.
-template <int DIM, bool WI>
+// The row loop of the lattice kernels, called twice in each kernel: with UNI, bounded by the
+// context's common slice width (a kernel argument, so the slot index and everything indexed by it
+// is warp-uniform by construction and the direction table is read through the uniform datapath);
+// otherwise by the slice's own width.  The staged-copy wait goes through a warp vote, so the loop's
+// exit is warp-uniform as well.
+template <int NB, int CH, class Body>
+__device__ __forceinline__ bool lat_rows(const StepArgs& a, Stage<NB, CH>& st, int W, int lane, Body body) {
+  const int nchunks = (W + CH - 1) / CH;
+  if (lane == 0)
+    for (; st.issued < min(NB, nchunks); ++st.issued)
+      if (!(a.expire && st.issued == 0)) stage_issue(st, st.issued);  // testing: chunk 0 never arrives
+  for (int c = 0; c < nchunks; ++c) {
+    const int buf = c % NB;
+    if (!__all_sync(kFull, mbar_wait(&st.bar[buf], (unsigned)((c / NB) & 1)))) {
+      if (lane == 0) atomicExch(&a.counters[4], 1ull);
+      stage_drain(st, c + 1);
+      return false;
+    }
+    const int32_t* cs = st.col + buf * CH * 32 + lane;
+    const uint32_t* ws = st.words + buf * CH;
+    const int k0 = c * CH;
+    const int n = min(CH, W - k0);
+    for (int kk = 0; kk < n; kk += kU32) {  // n is a multiple of 4 = kU32
+      const uint4 w4 = *reinterpret_cast<const uint4*>(ws + kk);  // 16-byte aligned: CH and kk multiples of 4
+      if ((w4.x | w4.y | w4.z | w4.w) == 0u) continue;  // warp-uniform: no intact bond in the batch
+      body(cs + kk * 32, ws + kk, w4, k0 + kk);
+    }
+    __syncwarp();  // every lane is done with this buffer before it is refilled
+    if (lane == 0 && st.issued < nchunks) stage_issue(st, st.issued++);
+  }
+  return true;
+}
+
+template <int DIM, bool WI, int NB, int CH>
 __global__ void __launch_bounds__(512) k_pass1_lat(StepArgs a, const float4* __restrict__ u32,
                                                     const double4* __restrict__ disp, int write_theta) {
   extern __shared__ __align__(128) unsigned char smem[];
   const SliceIdx t = slice_index<1>(a.n_pad, a.slice_ptr);
   if (write_theta && blockIdx.x == 0 && threadIdx.x == 0) *a.d_step += 1;
   if (!t.active) return;  // whole warps: the staging below is per warp
-  Stage st = stage_init(smem, t, a);
+  auto st = stage_init<NB, CH>(smem, t, a);
   const int lane = t.lane;
   const int b = a.body ? a.body[t.i] : 0;
   const BodyDev& bp = a.bp[b];
@@ -1742,106 +1788,83 @@ __global__ void __launch_bounds__(512) k_pass1_lat(StepArgs a, const float4* __r
   const float Kfast = bp.lat_Kfast;
   const float scr_i = fmaf(Kfast, Ui.w, bp.lat_Kcfast);  // the screen's bound less its U_j term (pd_lattice.h)
   uint32_t* __restrict__ bw = a.bits + (t.base >> 5);
-  if (lane == 0)
-    for (; st.issued < min(kStageBuf, st.nchunks); ++st.issued)
-      if (!(a.expire && st.issued == 0)) stage_issue(st, st.issued);  // testing: chunk 0 never arrives
   float acc = 0.0f;
-  bool ok = true;
   const bool checking = a.check != 0;  // warp-uniform (can_break is per body: per lane in a batch)
-  for (int c = 0; c < st.nchunks; ++c) {
-    const int buf = c % kStageBuf;
-    if (!mbar_wait(&st.bar[buf], (unsigned)((c / kStageBuf) & 1))) {
-      ok = false;
-      if (lane == 0) atomicExch(&a.counters[4], 1ull);
-      stage_drain(st, c + 1);
-      break;
-    }
-    const int32_t* cs = st.col + buf * kStageCh * 32 + lane;
-    const uint32_t* ws = st.words + buf * kStageCh;
-    const int k0 = c * kStageCh;
-    const int n = min(kStageCh, st.W - k0);
+  // one batch of U = 4 slots starting at slot k: every intact bond's term is added to the dilatation
+  // sum; a bond that the slow path below breaks has its term taken out again (the sum stays a
+  // function of each lane's own operations, so a batch of bodies and the bodies run alone add
+  // identically)
+  auto batch = [&](const int32_t* cs, const uint32_t* ws, uint4 w4, int k) {
     constexpr int U = kU32;
-    for (int kk = 0; kk < n; kk += U) {  // n is a multiple of 4 = U
-      uint32_t wd[U];
+    const uint32_t wd[U] = {w4.x, w4.y, w4.z, w4.w};
+    float4 Uj[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u) wd[u] = ws[kk + u];
-      if ((wd[0] | wd[1] | wd[2] | wd[3]) == 0u) continue;  // warp-uniform: no intact bond in the batch
-      int32_t j[U];
-      float4 Uj[U];
+    for (int u = 0; u < U; ++u) Uj[u] = u32[cs[u * 32]];
+    bool near = false;
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        j[u] = cs[(kk + u) * 32];
-        Uj[u] = u32[j[u]];
+    for (int u = 0; u < U; ++u) {
+      const float4 dn = lat_dir<DIM>(k + u);
+      const float d = lat_dprime<DIM>(dn.x, dn.y, dn.z, Uj[u].x, Uj[u].y, Uj[u].z, Ui.x, Ui.y, Ui.z);
+      const bool in = (wd[u] >> lane) & 1u;
+      if (checking)
+        near = near || (can_break && in && !lat_screen_intact(lat_g(d, s0f, dn.w), Kfast, Uj[u].w, scr_i));
+      const float dd = in ? d : 0.0f;
+      if (WI) {  // acc += w' d' with w' as hi + lo
+        const float2 wk = lat_wgt<DIM>(k + u);
+        acc = fmaf(wk.x, dd, fmaf(wk.y, dd, acc));
+      } else {
+        acc += dd;
       }
-      // Every intact bond's term is added to the dilatation sum here; a bond that the slow path
-      // below breaks has its term taken out again (the sum stays a function of each lane's own
-      // operations, so a batch of bodies and the bodies run alone add identically).
-      bool near = false;
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const float4 dn = lat_dir<DIM>(k0 + kk + u);
-        const float d = lat_dprime<DIM>(dn.x, dn.y, dn.z, Uj[u].x, Uj[u].y, Uj[u].z, Ui.x, Ui.y, Ui.z);
-        const bool in = (wd[u] >> lane) & 1u;
-        if (checking)
-          near = near || (can_break && in && !lat_screen_intact(lat_g(d, s0f, dn.w), Kfast, Uj[u].w, scr_i));
-        const float dd = in ? d : 0.0f;
-        if (WI) {  // acc += w' d' with w' as hi + lo
-          const float2 wk = lat_wgt<DIM>(k0 + kk + u);
-          acc = fmaf(wk.x, dd, fmaf(wk.y, dd, acc));
-        } else {
-          acc += dd;
-        }
-      }
-      if (checking && (__any_sync(kFull, near) || a.validate)) {
-        // full band for the bonds the screen did not settle, FP64 inside it; everything reloaded
-        // (index from the staged chunk, displacement through L1) so that little stays live here
+    }
+    if (checking && (__any_sync(kFull, near) || a.validate)) {
+      // full band for the bonds the screen did not settle, FP64 inside it; everything reloaded
+      // (index from the staged chunk, displacement through L1) so that little stays live here
 #pragma unroll 1
-        for (int u = 0; u < U; ++u) {
-          const int k = k0 + kk + u;
-          const uint32_t w0 = ws[kk + u];
-          const int32_t jj = cs[(kk + u) * 32];
-          int code = 0;
-          float d = 0.0f;
-          if (can_break && ((w0 >> lane) & 1u)) {
-            const float4 Uu = u32[jj];
-            const float4 dn = lat_dir<DIM>(k);
-            d = lat_dprime<DIM>(dn.x, dn.y, dn.z, Uu.x, Uu.y, Uu.z, Ui.x, Ui.y, Ui.z);
-            code = lat_code(lat_g(d, s0f, dn.w), Ui.w, Uu.w, s0f, dn.w, bp.lat_Kf, bp.lat_sq, bp.lat_eps_c,
-                            bp.lat_s0n1);
-            if (code == 2) {
-              code = fp64_breaks_inl<DIM>(a, t.i, jj, disp, s0) ? 1 : 0;
-              atomicAdd(&a.counters[0], 1ull);
-            }
-            if (a.validate && (code == 1) != fp64_breaks_inl<DIM>(a, t.i, jj, disp, s0))
-              atomicAdd(&a.counters[1], 1ull);
+      for (int u = 0; u < U; ++u) {
+        const uint32_t w0 = ws[u];
+        const int32_t jj = cs[u * 32];
+        int code = 0;
+        float d = 0.0f;
+        if (can_break && ((w0 >> lane) & 1u)) {
+          const float4 Uu = u32[jj];
+          const float4 dn = lat_dir<DIM>(k + u);
+          d = lat_dprime<DIM>(dn.x, dn.y, dn.z, Uu.x, Uu.y, Uu.z, Ui.x, Ui.y, Ui.z);
+          code = lat_code(lat_g(d, s0f, dn.w), Ui.w, Uu.w, s0f, dn.w, bp.lat_Kf, bp.lat_sq, bp.lat_eps_c,
+                          bp.lat_s0n1);
+          if (code == 2) {
+            code = fp64_breaks_inl<DIM>(a, t.i, jj, disp, s0) ? 1 : 0;
+            atomicAdd(&a.counters[0], 1ull);
           }
-          const unsigned m = __ballot_sync(kFull, code == 1);
-          if (m) {
-            if (lane == 0) bw[k] = w0 & ~m;
-            if (code == 1) {
-              if (WI) {
-                const float2 wk = lat_wgt<DIM>(k);
-                acc = fmaf(-wk.x, d, fmaf(-wk.y, d, acc));
-              } else {
-                acc -= d;
-              }
+          if (a.validate && (code == 1) != fp64_breaks_inl<DIM>(a, t.i, jj, disp, s0))
+            atomicAdd(&a.counters[1], 1ull);
+        }
+        const unsigned m = __ballot_sync(kFull, code == 1);
+        if (m) {
+          if (lane == 0) bw[k + u] = w0 & ~m;
+          if (code == 1) {
+            if (WI) {
+              const float2 wk = lat_wgt<DIM>(k + u);
+              acc = fmaf(-wk.x, d, fmaf(-wk.y, d, acc));
+            } else {
+              acc -= d;
             }
           }
         }
       }
     }
-    __syncwarp();  // every lane is done with this buffer before it is refilled
-    if (lane == 0 && st.issued < st.nchunks) stage_issue(st, st.issued++);
-  }
+  };
+  const bool ok = a.lat_wuni > 0 ? lat_rows<NB, CH>(a, st, a.lat_wuni, lane, batch)
+                                 : lat_rows<NB, CH>(a, st, st.W, lane, batch);
   if (ok && write_theta) {
     const float2 f = a.lat_f[t.i];  // (N_ref / N_i, A / N_i)
     a.theta32[t.i] = f.y * acc;
     const float x = acc * (f.x * f.x);
-    a.thm32[t.i] = make_float2(fmaf(bp.lat_lam_hi, x, bp.lat_lam_lo * x), f.x);
+    // the record pass 2 gathers: (u'_i, P_i)
+    a.lat_up[t.i] = make_float4(Ui.x, Ui.y, Ui.z, fmaf(bp.lat_lam_hi, x, bp.lat_lam_lo * x));
   }
 }
 
-template <int DIM, bool WI>
+template <int DIM, bool WI, int NB, int CH>
 __global__ void __launch_bounds__(512) k_pass2_lat(StepArgs a, const float4* __restrict__ u32,
                                                     float4* __restrict__ u32_out,
                                                     const double4* __restrict__ disp,
@@ -1849,62 +1872,45 @@ __global__ void __launch_bounds__(512) k_pass2_lat(StepArgs a, const float4* __r
   extern __shared__ __align__(128) unsigned char smem[];
   const SliceIdx t = slice_index<1>(a.n_pad, a.slice_ptr);
   if (!t.active) return;
-  Stage st = stage_init(smem, t, a);
+  auto st = stage_init<NB, CH>(smem, t, a);
   const int lane = t.lane;
   const int b = a.body ? a.body[t.i] : 0;
-  const float4 Ui = u32[t.i];
-  const float2 ti = a.thm32[t.i];  // (P_i, N_ref / N_i)
-  if (lane == 0)
-    for (; st.issued < min(kStageBuf, st.nchunks); ++st.issued)
-      if (!(a.expire && st.issued == 0)) stage_issue(st, st.issued);  // testing: chunk 0 never arrives
+  const float4 Ui = a.lat_up[t.i];  // (u'_i, P_i)
+  const float rho_i = a.lat_f[t.i].x;
+  // every particle around this slice (lanes and neighbours) has N_j = N_ref: N_ref/N_i + N_ref/N_j
+  // = 2 exactly, so the per-neighbour factor is not gathered (the result is bitwise the same)
+  const bool interior = a.lat_int[t.i >> 5] != 0;
   float f[3] = {0.0f, 0.0f, 0.0f};
-  bool ok = true;
-  for (int c = 0; c < st.nchunks; ++c) {
-    const int buf = c % kStageBuf;
-    if (!mbar_wait(&st.bar[buf], (unsigned)((c / kStageBuf) & 1))) {
-      ok = false;
-      if (lane == 0) atomicExch(&a.counters[4], 1ull);
-      stage_drain(st, c + 1);
-      break;
-    }
-    const int32_t* cs = st.col + buf * kStageCh * 32 + lane;
-    const uint32_t* ws = st.words + buf * kStageCh;
-    const int k0 = c * kStageCh;
-    const int n = min(kStageCh, st.W - k0);
+  auto batch = [&](const int32_t* cs, const uint32_t* ws, uint4 w4, int k) {
     constexpr int U = kU32;
-    for (int kk = 0; kk < n; kk += U) {
-      uint32_t wd[U];
+    const uint32_t wd[U] = {w4.x, w4.y, w4.z, w4.w};
+    float4 Uj[U];
+    float rr[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u) wd[u] = ws[kk + u];
-      if ((wd[0] | wd[1] | wd[2] | wd[3]) == 0u) continue;
-      float4 Uj[U];
-      float2 tj[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int32_t j = cs[(kk + u) * 32];
-        Uj[u] = u32[j];
-        tj[u] = a.thm32[j];
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const float4 dn = lat_dir<DIM>(k0 + kk + u);
-        const float2 r = lat_rcp<DIM>(k0 + kk + u);
-        const float d = lat_dprime<DIM>(dn.x, dn.y, dn.z, Uj[u].x, Uj[u].y, Uj[u].z, Ui.x, Ui.y, Ui.z);
-        const float dr = fmaf(d, r.x, d * r.y);  // d / |n|^2 with 1 / |n|^2 carried as hi + lo
-        float cf = fmaf(ti.y + tj[u].y, dr, ti.x + tj[u].x);
-        if (WI) {  // cf w' with w' as hi + lo
-          const float2 wk = lat_wgt<DIM>(k0 + kk + u);
-          cf = fmaf(cf, wk.x, cf * wk.y);
-        }
-        cf = ((wd[u] >> lane) & 1u) ? cf : 0.0f;
-        f[0] = fmaf(cf, dn.x, f[0]);
-        f[1] = fmaf(cf, dn.y, f[1]);
-        if (DIM == 3) f[2] = fmaf(cf, dn.z, f[2]);
-      }
+    for (int u = 0; u < U; ++u) {
+      const int32_t j = cs[u * 32];
+      Uj[u] = a.lat_up[j];
+      rr[u] = interior ? 2.0f : rho_i + a.lat_rho[j];
     }
-    __syncwarp();
-    if (lane == 0 && st.issued < st.nchunks) stage_issue(st, st.issued++);
-  }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const float4 dn = lat_dir<DIM>(k + u);
+      const float2 r = lat_rcp<DIM>(k + u);
+      const float d = lat_dprime<DIM>(dn.x, dn.y, dn.z, Uj[u].x, Uj[u].y, Uj[u].z, Ui.x, Ui.y, Ui.z);
+      const float dr = fmaf(d, r.x, d * r.y);  // d / |n|^2 with 1 / |n|^2 carried as hi + lo
+      float cf = fmaf(rr[u], dr, Ui.w + Uj[u].w);
+      if (WI) {  // cf w' with w' as hi + lo
+        const float2 wk = lat_wgt<DIM>(k + u);
+        cf = fmaf(cf, wk.x, cf * wk.y);
+      }
+      cf = ((wd[u] >> lane) & 1u) ? cf : 0.0f;
+      f[0] = fmaf(cf, dn.x, f[0]);
+      f[1] = fmaf(cf, dn.y, f[1]);
+      if (DIM == 3) f[2] = fmaf(cf, dn.z, f[2]);
+    }
+  };
+  const bool ok = a.lat_wuni > 0 ? lat_rows<NB, CH>(a, st, a.lat_wuni, lane, batch)
+                                 : lat_rows<NB, CH>(a, st, st.W, lane, batch);
   if (ok) {
     const double C = a.bp[b].lat_C;
     const double fd[3] = {C * (double)f[0], C * (double)f[1], C * (double)f[2]};
@@ -2212,11 +2218,11 @@ __global__ void k_damage(StepArgs a, int64_t n, const double* __restrict__ dden,
     if (!((word >> t.lane) & 1u)) continue;
     const double4 pj = a.pos[a.col[t.base + t.lane + ((int64_t)k << 5)]];
     double w = 1.0;
-    if (wd > 0.0) {
+    if (wd > 0.0) {  // |xi|^2 rounded term by term, as the build's denominator D_i (no contraction)
       const double ex = pj.x - pi.x, ey = pj.y - pi.y, ez = pj.z - pi.z;
-      w = wd / sqrt(ex * ex + ey * ey + ez * ez);
+      w = wd / sqrt(__dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez)));
     }
-    num += w * pj.w;
+    num = __dadd_rn(num, __dmul_rn(w, pj.w));
   }
   if (t.i < n) out[perm[t.i]] = dden[t.i] > 0.0 ? 1.0 - num / dden[t.i] : 0.0;
 }
@@ -2378,6 +2384,10 @@ StepArgs make_args(pd_ctx* c) {
   a.gnew = c->gnew;
   a.lattice = c->lattice ? 1 : 0;
   a.lat_f = c->lat_f;
+  a.lat_rho = c->lat_rho;
+  a.lat_up = c->lat_up;
+  a.lat_int = c->lat_int;
+  a.lat_wuni = c->lat_wuni;
   return a;
 }
 
@@ -2446,13 +2456,46 @@ void launch_pass2(pd_ctx* c, const StepArgs& a, unsigned grid, int block, size_t
         <<<grid, block, sm, c->stream>>>(a, c->u32[c->cur], c->u32[c->cur ^ 1], c->disp[c->cur], c->disp[c->cur ^ 1]);
 }
 
+// Lattice kernels: the ring of PD_OPT_LAT_STAGE (0: 3 x 16 slots, 1: 2 x 16, 2: 3 x 8, 3: 2 x 8).
+template <int DIM, bool WI, int NB, int CH>
+void optin_lat_ring() {
+  const int mx = 16 * StageGeom<NB, CH>::kWarpBytes;
+  cudaFuncSetAttribute(k_pass1_lat<DIM, WI, NB, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_pass2_lat<DIM, WI, NB, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+}
+template <int DIM, bool WI>
+void optin_lat() {
+  optin_lat_ring<DIM, WI, 3, 16>();
+  optin_lat_ring<DIM, WI, 2, 16>();
+  optin_lat_ring<DIM, WI, 3, 8>();
+  optin_lat_ring<DIM, WI, 2, 8>();
+}
+
+template <int DIM, bool WI, int NB, int CH>
+void launch_lat_ring(pd_ctx* c, const StepArgs& a, int pass, int write_theta, int block) {
+  const unsigned g1 = (unsigned)((c->nslices * 32 + block - 1) / block);
+  const size_t smb = (size_t)(block / 32) * StageGeom<NB, CH>::kWarpBytes;
+  if (pass == 1)
+    k_pass1_lat<DIM, WI, NB, CH><<<g1, block, smb, c->stream>>>(a, c->u32[c->cur], c->disp[c->cur], write_theta);
+  else
+    k_pass2_lat<DIM, WI, NB, CH><<<g1, block, smb, c->stream>>>(a, c->u32[c->cur], c->u32[c->cur ^ 1],
+                                                                c->disp[c->cur], c->disp[c->cur ^ 1]);
+}
+template <int DIM, bool WI>
+void launch_lat(pd_ctx* c, const StepArgs& a, int pass, int write_theta, int block) {
+  switch (c->lat_stage) {
+    case 1: launch_lat_ring<DIM, WI, 2, 16>(c, a, pass, write_theta, block); break;
+    case 2: launch_lat_ring<DIM, WI, 3, 8>(c, a, pass, write_theta, block); break;
+    case 3: launch_lat_ring<DIM, WI, 2, 8>(c, a, pass, write_theta, block); break;
+    default: launch_lat_ring<DIM, WI, 3, 16>(c, a, pass, write_theta, block); break;
+  }
+}
+
 template <int DIM>
 void optin_staged() {
   const int mx = 16 * kStageWarpBytes;
-  cudaFuncSetAttribute(k_pass1_lat<DIM, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_pass2_lat<DIM, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_pass1_lat<DIM, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_pass2_lat<DIM, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  optin_lat<DIM, false>();
+  optin_lat<DIM, true>();
   cudaFuncSetAttribute(k_pass1_mixed_staged<DIM, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_pass2_mixed_staged<DIM, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_pass1_mixed_staged<DIM, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
@@ -2519,19 +2562,8 @@ void dispatch_pass(pd_ctx* c, const StepArgs& a, int pass, int write_theta) {
   const unsigned grid = (unsigned)((threads + block - 1) / block);
   if (c->precision == PD_MIXED && c->lattice) {
     // lattice layout (linearized bonds): one warp per slice, whatever the split and stage options
-    const unsigned g1 = (unsigned)((c->nslices * 32 + block - 1) / block);
-    const size_t smb = (size_t)(block / 32) * kStageWarpBytes;
-    const bool wi = c->prm[0].influence == PD_W_INV;
-    if (pass == 1 && wi)
-      k_pass1_lat<DIM, true><<<g1, block, smb, c->stream>>>(a, c->u32[c->cur], c->disp[c->cur], write_theta);
-    else if (pass == 1)
-      k_pass1_lat<DIM, false><<<g1, block, smb, c->stream>>>(a, c->u32[c->cur], c->disp[c->cur], write_theta);
-    else if (wi)
-      k_pass2_lat<DIM, true><<<g1, block, smb, c->stream>>>(a, c->u32[c->cur], c->u32[c->cur ^ 1],
-                                                            c->disp[c->cur], c->disp[c->cur ^ 1]);
-    else
-      k_pass2_lat<DIM, false><<<g1, block, smb, c->stream>>>(a, c->u32[c->cur], c->u32[c->cur ^ 1],
-                                                             c->disp[c->cur], c->disp[c->cur ^ 1]);
+    if (c->prm[0].influence == PD_W_INV) launch_lat<DIM, true>(c, a, pass, write_theta, block);
+    else launch_lat<DIM, false>(c, a, pass, write_theta, block);
     return;
   }
   if (c->precision == PD_MIXED && ((split == 1 && c->stage) || c->kin == PD_NONLINEAR)) {

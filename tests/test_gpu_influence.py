@@ -59,7 +59,11 @@ def test_fp64_influence_parity(case, pairs):
     phi = sim.damage()
     sim.close()
     assert exact and (ref.status == 0).sum() > 0
-    assert np.array_equal(phi, ref.damage())
+    # with w != 1 the damage sums non-integer weights, whose summation order differs from the
+    # oracle's: undamaged particles are exactly 0 on both sides, the others agree to rounding
+    ref_phi = ref.damage()
+    assert np.array_equal(phi == 0.0, ref_phi == 0.0)
+    assert np.abs(phi - ref_phi).max() <= 1e-14
 
 
 def test_fp64_influence_random_cloud():
@@ -97,19 +101,30 @@ def test_fp64_influence_shadow_energy():
 
 @pytest.mark.parametrize("case", sorted(CASES))
 def test_mixed_lattice_influence(case):
+    """Breaking runs in the mixed form: every decision equal to FP64 on the run's own state, and the
+    trajectory within 1e-5 of the oracle while the oracle's smallest stretch margin stays above 1e-5
+    (afterwards the two runs may break a near-threshold bond at different steps, see
+    tests/test_gpu_lattice.py)."""
     w = CASES[case]()
     s0 = s0_of(w)
     sim = Simulation(w, s0=s0, precision=PD_MIXED, influence=PD_W_INV)
     assert sim.get_option(B.PD_OPT_LATTICE) == 1
     sim.set_option(B.PD_OPT_VALIDATE, 1)
-    sim.step(w.nsteps)
-    u = sim.state()[0]
+    ref = oracle_for(w, s0)
+    compared, done = 0, 0
+    while done < w.nsteps:
+        margins, _ = ref.step(25)
+        sim.step(25)
+        done += 25
+        if margins.min() <= 1e-5:
+            break
+        assert rel(sim.state()[0], ref.u) <= 1e-5, (case, done)
+        compared = done
+    sim.step(w.nsteps - done)
     st = sim.stats()
     sim.close()
-    ref = oracle_for(w, s0)
-    ref.step(w.nsteps)
+    assert compared >= 25
     assert st["validate_mismatches"] == 0 and st["broken_bonds"] > 0
-    assert rel(u, ref.u) <= 1e-4, rel(u, ref.u)
 
 
 def test_influence_free_vibration_mixed_bound():
