@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <cmath>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "pd_internal.h"
@@ -1761,7 +1762,7 @@ __device__ __forceinline__ bool lat_rows(const StepArgs& a, Stage<NB, CH>& st, i
     const int n = min(CH, W - k0);
     for (int kk = 0; kk < n; kk += kU32) {  // n is a multiple of 4 = kU32
       const uint4 w4 = *reinterpret_cast<const uint4*>(ws + kk);  // 16-byte aligned: CH and kk multiples of 4
-      if ((w4.x | w4.y | w4.z | w4.w) == 0u) continue;  // warp-uniform: no intact bond in the batch
+      if ((w4.x | w4.y | w4.z | w4.w) == 0u) continue;  // no intact bond in the batch (the same words in every lane)
       body(cs + kk * 32, ws + kk, w4, k0 + kk);
     }
     __syncwarp();  // every lane is done with this buffer before it is refilled
@@ -1790,47 +1791,40 @@ __global__ void __launch_bounds__(512) k_pass1_lat(StepArgs a, const float4* __r
   uint32_t* __restrict__ bw = a.bits + (t.base >> 5);
   float acc = 0.0f;
   const bool checking = a.check != 0;  // warp-uniform (can_break is per body: per lane in a batch)
-  // one batch of U = 4 slots starting at slot k: every intact bond's term is added to the dilatation
-  // sum; a bond that the slow path below breaks has its term taken out again (the sum stays a
-  // function of each lane's own operations, so a batch of bodies and the bodies run alone add
-  // identically)
+  const uint32_t lmask = 1u << lane;
+  // one batch of U = 4 slots starting at slot k: the extensions and the intact mask first, the
+  // failure decisions next (the rare slow path clears the mask bits of the bonds it breaks), then
+  // the dilatation terms of the bonds still intact in slot order, so that the sum does not depend on
+  // whether a bond broke here or in an earlier check (a state read between steps)
   auto batch = [&](const int32_t* cs, const uint32_t* ws, uint4 w4, int k) {
     constexpr int U = kU32;
     const uint32_t wd[U] = {w4.x, w4.y, w4.z, w4.w};
     float4 Uj[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) Uj[u] = u32[cs[u * 32]];
+    float dv[U];
+    unsigned mask = 0u;
     bool near = false;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const float4 dn = lat_dir<DIM>(k + u);
-      const float d = lat_dprime<DIM>(dn.x, dn.y, dn.z, Uj[u].x, Uj[u].y, Uj[u].z, Ui.x, Ui.y, Ui.z);
-      const bool in = (wd[u] >> lane) & 1u;
-      if (checking)
-        near = near || (can_break && in && !lat_screen_intact(lat_g(d, s0f, dn.w), Kfast, Uj[u].w, scr_i));
-      const float dd = in ? d : 0.0f;
-      if (WI) {  // acc += w' d' with w' as hi + lo
-        const float2 wk = lat_wgt<DIM>(k + u);
-        acc = fmaf(wk.x, dd, fmaf(wk.y, dd, acc));
-      } else {
-        acc += dd;
-      }
+      dv[u] = lat_dprime<DIM>(dn.x, dn.y, dn.z, Uj[u].x, Uj[u].y, Uj[u].z, Ui.x, Ui.y, Ui.z);
+      const bool in = (wd[u] & lmask) != 0u;
+      mask |= in ? (1u << u) : 0u;
+      if (checking) near |= can_break & in & !lat_screen_intact(lat_g(dv[u], s0f, dn.w), Kfast, Uj[u].w, scr_i);
     }
-    if (checking && (__any_sync(kFull, near) || a.validate)) {
-      // full band for the bonds the screen did not settle, FP64 inside it; everything reloaded
-      // (index from the staged chunk, displacement through L1) so that little stays live here
+    if (checking && (__any_sync(kFull, near) | (a.validate != 0))) {
+      // full band for the bonds the screen did not settle, FP64 inside it; the neighbour index and
+      // its |u'| are reloaded (staged chunk, L1) so that little stays live across this block
 #pragma unroll 1
       for (int u = 0; u < U; ++u) {
-        const uint32_t w0 = ws[u];
-        const int32_t jj = cs[u * 32];
         int code = 0;
-        float d = 0.0f;
-        if (can_break && ((w0 >> lane) & 1u)) {
-          const float4 Uu = u32[jj];
-          const float4 dn = lat_dir<DIM>(k + u);
-          d = lat_dprime<DIM>(dn.x, dn.y, dn.z, Uu.x, Uu.y, Uu.z, Ui.x, Ui.y, Ui.z);
-          code = lat_code(lat_g(d, s0f, dn.w), Ui.w, Uu.w, s0f, dn.w, bp.lat_Kf, bp.lat_sq, bp.lat_eps_c,
-                          bp.lat_s0n1);
+        if (can_break && ((mask >> u) & 1u)) {
+          const int32_t jj = cs[u * 32];
+          const float Ujw = u32[jj].w;
+          const float q = lat_dir<DIM>(k + u).w;
+          const float du = u == 0 ? dv[0] : (u == 1 ? dv[1] : (u == 2 ? dv[2] : dv[3]));  // no indexed array
+          code = lat_code(lat_g(du, s0f, q), Ui.w, Ujw, s0f, q, bp.lat_Kf, bp.lat_sq, bp.lat_eps_c, bp.lat_s0n1);
           if (code == 2) {
             code = fp64_breaks_inl<DIM>(a, t.i, jj, disp, s0) ? 1 : 0;
             atomicAdd(&a.counters[0], 1ull);
@@ -1840,16 +1834,19 @@ __global__ void __launch_bounds__(512) k_pass1_lat(StepArgs a, const float4* __r
         }
         const unsigned m = __ballot_sync(kFull, code == 1);
         if (m) {
-          if (lane == 0) bw[k + u] = w0 & ~m;
-          if (code == 1) {
-            if (WI) {
-              const float2 wk = lat_wgt<DIM>(k + u);
-              acc = fmaf(-wk.x, d, fmaf(-wk.y, d, acc));
-            } else {
-              acc -= d;
-            }
-          }
+          if (lane == 0) bw[k + u] = ws[u] & ~m;
+          if (code == 1) mask &= ~(1u << u);
         }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const float dd = ((mask >> u) & 1u) ? dv[u] : 0.0f;
+      if (WI) {  // acc += w' d' with w' as hi + lo
+        const float2 wk = lat_wgt<DIM>(k + u);
+        acc = fmaf(wk.x, dd, fmaf(wk.y, dd, acc));
+      } else {
+        acc += dd;
       }
     }
   };
@@ -1878,10 +1875,13 @@ __global__ void __launch_bounds__(512) k_pass2_lat(StepArgs a, const float4* __r
   const float4 Ui = a.lat_up[t.i];  // (u'_i, P_i)
   const float rho_i = a.lat_f[t.i].x;
   // every particle around this slice (lanes and neighbours) has N_j = N_ref: N_ref/N_i + N_ref/N_j
-  // = 2 exactly, so the per-neighbour factor is not gathered (the result is bitwise the same)
-  const bool interior = a.lat_int[t.i >> 5] != 0;
+  // = 2 exactly, so the per-neighbour factor is not gathered (the result is bitwise the same); the
+  // vote makes the per-slice flag warp-uniform for the compiler
+  const bool interior = __all_sync(kFull, a.lat_int[t.i >> 5] != 0);
+  const uint32_t lmask = 1u << lane;
   float f[3] = {0.0f, 0.0f, 0.0f};
-  auto batch = [&](const int32_t* cs, const uint32_t* ws, uint4 w4, int k) {
+  auto batch_t = [&](auto intr, const int32_t* cs, uint4 w4, int k) {
+    constexpr bool INTR = decltype(intr)::value;
     constexpr int U = kU32;
     const uint32_t wd[U] = {w4.x, w4.y, w4.z, w4.w};
     float4 Uj[U];
@@ -1890,7 +1890,7 @@ __global__ void __launch_bounds__(512) k_pass2_lat(StepArgs a, const float4* __r
     for (int u = 0; u < U; ++u) {
       const int32_t j = cs[u * 32];
       Uj[u] = a.lat_up[j];
-      rr[u] = interior ? 2.0f : rho_i + a.lat_rho[j];
+      rr[u] = INTR ? 2.0f : rho_i + a.lat_rho[j];
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -1903,11 +1903,15 @@ __global__ void __launch_bounds__(512) k_pass2_lat(StepArgs a, const float4* __r
         const float2 wk = lat_wgt<DIM>(k + u);
         cf = fmaf(cf, wk.x, cf * wk.y);
       }
-      cf = ((wd[u] >> lane) & 1u) ? cf : 0.0f;
+      cf = (wd[u] & lmask) ? cf : 0.0f;
       f[0] = fmaf(cf, dn.x, f[0]);
       f[1] = fmaf(cf, dn.y, f[1]);
       if (DIM == 3) f[2] = fmaf(cf, dn.z, f[2]);
     }
+  };
+  auto batch = [&](const int32_t* cs, const uint32_t*, uint4 w4, int k) {
+    if (interior) batch_t(std::true_type{}, cs, w4, k);
+    else batch_t(std::false_type{}, cs, w4, k);
   };
   const bool ok = a.lat_wuni > 0 ? lat_rows<NB, CH>(a, st, a.lat_wuni, lane, batch)
                                  : lat_rows<NB, CH>(a, st, st.W, lane, batch);
