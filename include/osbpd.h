@@ -176,10 +176,17 @@ typedef enum {
                               coordinates; 0 = the general layout and kernels.  Set before
                               pd_build_neighbors; after it, pd_get_option reports whether the built
                               layout is the lattice one. */
-  PD_OPT_LAT_STAGE = 12    /* lattice kernels: shared-memory ring of each warp's index and status
+  PD_OPT_LAT_STAGE = 12,   /* lattice kernels: shared-memory ring of each warp's index and status
                               stream, 0 (default) = 3 chunks of 16 slots, 1 = 2 x 16, 2 = 3 x 8,
                               3 = 2 x 8 (smaller rings leave more of the SM's combined L1 / shared
                               memory to the displacement gathers); pd_autotune chooses it */
+  PD_OPT_LAT_FIXED = 13    /* lattice layout with w = 1 and every body's horizon 3 h <= delta <
+                              sqrt(10) h (family |n|^2 <= 9: 122 directions in 3D, 28 in 2D):
+                              1 (default) = step kernels compiled for that family, each slot's
+                              direction a constant of the code; 0 = the kernels that read it from
+                              a table.  Results are bitwise the same (finite states).  After
+                              pd_build_neighbors, pd_get_option reports whether the compiled
+                              family's kernels run. */
 } pd_option;
 
 /* Solvers (PD_OPT_SOLVER).

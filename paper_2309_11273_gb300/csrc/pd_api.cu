@@ -585,6 +585,10 @@ pd_status pd_set_option(pd_ctx* c, int32_t option, int64_t value) {
       if (c->lat_stage != (int)value) drop_graphs(c);
       c->lat_stage = (int)value;
       break;
+    case PD_OPT_LAT_FIXED:
+      if ((c->lat_fixed_opt != 0) != (value != 0)) drop_graphs(c);
+      c->lat_fixed_opt = value != 0;
+      break;
     case PD_OPT_PAIRS:
       // A failure check of the pair form marks slices whose bS its next pass 1b recomputes; the
       // other form never reads those marks, so a switch recomputes every bS before the next step.
@@ -622,6 +626,7 @@ pd_status pd_get_option(pd_ctx* c, int32_t option, int64_t* value) {
     case PD_OPT_PAIRS: *value = (c->pairs && c->pairs_ok && c->precision == PD_FP64) ? 1 : 0; break;
     case PD_OPT_LATTICE: *value = c->built ? (c->lattice ? 1 : 0) : c->lattice_opt; break;
     case PD_OPT_LAT_STAGE: *value = c->lat_stage; break;
+    case PD_OPT_LAT_FIXED: *value = c->built ? (lattice_fixed_active(c) ? 1 : 0) : c->lat_fixed_opt; break;
     default: return fail(PD_ERR_ARG, "unknown option");
   }
   return PD_OK;

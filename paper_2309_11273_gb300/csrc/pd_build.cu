@@ -632,6 +632,9 @@ pd_status build_lattice(pd_ctx* c, BuildArgs& A, bool* done) {
   c->lat_wuni = (int)((sptr2[1] - sptr2[0]) >> 5);
   for (int64_t t = 0; t < c->nslices; ++t)
     if ((int)((sptr2[t + 1] - sptr2[t]) >> 5) != c->lat_wuni) c->lat_wuni = 0;
+  c->lat_q = c->lat_qmax[0];
+  for (int b = 1; b < nb; ++b)
+    if (c->lat_qmax[b] != c->lat_q) c->lat_q = 0;
   c->lattice = true;
   *done = true;
   return upload_body_params(c);
@@ -1163,6 +1166,7 @@ pd_status build_neighbors(pd_ctx* c, const pd_crack* cracks, int32_t ncracks) {
     c->lat_up = nullptr;
     c->lat_int = nullptr;
     c->lat_wuni = 0;
+    c->lat_q = 0;
     if (c->precision == PD_MIXED && c->kin == PD_LINEARIZED && c->lattice_opt) {
       PD_CUDA(cudaStreamSynchronize(s));
       bool lat = false;

@@ -214,6 +214,8 @@ struct pd_ctx {
   double4* diag_part = nullptr;   // pd_get_stats: per-block (strain energy, min margin, kinetic, 0)
   int lattice_opt = 1;            // PD_OPT_LATTICE: build the lattice layout when the bodies qualify
   int lat_stage = 0;              // PD_OPT_LAT_STAGE: staging ring of the lattice kernels (0..3)
+  int lat_fixed_opt = 1;          // PD_OPT_LAT_FIXED: kernels compiled for the family |n|^2 <= 9
+  int lat_q = 0;                  // lattice layout: every body's largest |n|^2 if they agree, else 0
   bool lattice = false;           // the built layout is the lattice layout (mixed, linearized bonds)
   float2* lat_f = nullptr;        // lattice layout: per particle (N_ref / N_i, A / N_i)
   float* lat_rho = nullptr;       // lattice layout: per particle N_ref / N_i
@@ -277,7 +279,8 @@ pd_status ensure_bond_cache(pd_ctx* c);
 pd_status ensure_adr(pd_ctx* c);      // ADR arrays and lambda (once per build)
 pd_status diagnostics(pd_ctx* c, double* min_margin, double* strain, double* kinetic);
 pd_status prepare_staged_kernels(pd_ctx* c);  // shared-memory opt-in of the staged kernels
-pd_status upload_lattice_tables(int device);   // direction tables of the lattice kernels (once per device)
+pd_status upload_lattice_tables(int device);  // direction tables of the lattice kernels (once per device)
+bool lattice_fixed_active(const pd_ctx* c);   // the lattice kernels compiled for the context's family run
 pd_status upload_field(pd_ctx* c, const double* host_soa, double4* dst, int comps);
 pd_status gather_field(pd_ctx* c, const double* dev_soa, double4* dst, int comps);
 pd_status launch_nonfinite(const double* a, int64_t n, unsigned long long* flag, cudaStream_t s);

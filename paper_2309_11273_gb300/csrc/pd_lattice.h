@@ -38,29 +38,66 @@ struct LatDir {
   int q;  // |n|^2
 };
 
-inline std::vector<LatDir> lattice_directions(int dim) {
-  const int qmax = dim == 3 ? kLatQmax3 : kLatQmax2;
-  const int R = dim == 3 ? kLatR3 : kLatR2;
-  std::vector<LatDir> pos;
-  for (int z = (dim == 3 ? -R : 0); z <= (dim == 3 ? R : 0); ++z)
+// The table as a compile-time constant (so that kernels specialized for one family take each slot's
+// direction as an immediate).  Insertion sort of the positive representatives by (|n|^2, z, y, x),
+// then each followed by its opposite.
+template <int DIM>
+struct LatTable {
+  static constexpr int kCount = DIM == 3 ? kLatDirs3 : kLatDirs2;
+  LatDir d[kCount];
+};
+
+template <int DIM>
+constexpr LatTable<DIM> lattice_table() {
+  constexpr int qmax = DIM == 3 ? kLatQmax3 : kLatQmax2;
+  constexpr int R = DIM == 3 ? kLatR3 : kLatR2;
+  LatTable<DIM> t{};
+  LatDir pos[LatTable<DIM>::kCount / 2] = {};
+  int np = 0;
+  for (int z = (DIM == 3 ? -R : 0); z <= (DIM == 3 ? R : 0); ++z)
     for (int y = -R; y <= R; ++y)
       for (int x = -R; x <= R; ++x) {
         const int q = x * x + y * y + z * z;
         if (q == 0 || q > qmax) continue;
         const bool positive = z > 0 || (z == 0 && (y > 0 || (y == 0 && x > 0)));
-        if (positive) pos.push_back(LatDir{{x, y, z}, q});
+        if (!positive) continue;
+        LatDir e{{x, y, z}, q};
+        int k = np++;
+        while (k > 0) {
+          const LatDir& p = pos[k - 1];
+          const bool after = p.q != e.q ? p.q > e.q
+                                        : (p.n[2] != e.n[2] ? p.n[2] > e.n[2]
+                                                            : (p.n[1] != e.n[1] ? p.n[1] > e.n[1] : p.n[0] > e.n[0]));
+          if (!after) break;
+          pos[k] = pos[k - 1];
+          --k;
+        }
+        pos[k] = e;
       }
-  std::sort(pos.begin(), pos.end(), [](const LatDir& a, const LatDir& b) {
-    if (a.q != b.q) return a.q < b.q;
-    if (a.n[2] != b.n[2]) return a.n[2] < b.n[2];
-    if (a.n[1] != b.n[1]) return a.n[1] < b.n[1];
-    return a.n[0] < b.n[0];
-  });
+  for (int k = 0; k < np; ++k) {
+    t.d[2 * k] = pos[k];
+    t.d[2 * k + 1] = LatDir{{-pos[k].n[0], -pos[k].n[1], -pos[k].n[2]}, pos[k].q};
+  }
+  return t;
+}
+
+// Number of directions with |n|^2 <= q (a family), at compile time.
+template <int DIM>
+constexpr int lattice_prefix_c(int q) {
+  const LatTable<DIM> t = lattice_table<DIM>();
+  int k = 0;
+  while (k < LatTable<DIM>::kCount && t.d[k].q <= q) ++k;
+  return k;
+}
+
+inline std::vector<LatDir> lattice_directions(int dim) {
   std::vector<LatDir> out;
-  out.reserve(2 * pos.size());
-  for (const LatDir& d : pos) {
-    out.push_back(d);
-    out.push_back(LatDir{{-d.n[0], -d.n[1], -d.n[2]}, d.q});
+  if (dim == 3) {
+    constexpr LatTable<3> t = lattice_table<3>();
+    out.assign(t.d, t.d + LatTable<3>::kCount);
+  } else {
+    constexpr LatTable<2> t = lattice_table<2>();
+    out.assign(t.d, t.d + LatTable<2>::kCount);
   }
   return out;
 }

@@ -7,7 +7,9 @@ bodies that are not lattices keep the general layout; the lattice kernels follow
 the mixed form's stated bounds and decide every bond as FP64 does on their own state (validation
 mode, Eq 1.30), on 2D and 3D bodies with breaking, on a batch of uneven plates, and on the
 benchmark's 1M-particle block through its first 400 steps; graph chunks equal eager launches and a
-batch equals its bodies run one by one, bit for bit.
+batch equals its bodies run one by one, bit for bit; the kernels compiled for the family
+|n|^2 <= 9 (PD_OPT_LAT_FIXED, each slot's direction a constant of the code) equal the table-driven
+kernels bit for bit.
 """
 import numpy as np
 import pytest
@@ -193,3 +195,50 @@ def test_lattice_benchmark_block_validation_first_400_steps():
     print("config3 mixed, 400 steps with validation:", {k: st[k] for k in ("broken_bonds", "band_rechecks",
                                                                             "validate_mismatches")})
     assert st["broken_bonds"] > 0 and st["validate_mismatches"] == 0
+
+
+@pytest.mark.parametrize("case,rings", [("cracked_plate", (0,)), ("plane_strain", (0,)),
+                                        ("notched_block", (0, 1, 2, 3))])
+def test_fixed_family_kernels_equal_the_table_kernels(case, rings):
+    """Breaking runs in validation mode with the kernels compiled for the family (every staging
+    ring for the 3D block) and with the table-driven ones: displacements, velocities, dilatations,
+    bond status and every counter bitwise equal.  The operations the compiled kernels leave out are
+    exact (products by 0 and +-1, additions of zero), so nothing else may differ."""
+    w = CASES[case]()
+    s0 = s0_of(w)
+
+    def run(fixed, ring):
+        sim = Simulation(w, s0=s0, precision=PD_MIXED)
+        sim.set_option(B.PD_OPT_LAT_FIXED, fixed)
+        sim.set_option(B.PD_OPT_LAT_STAGE, ring)
+        assert sim.get_option(B.PD_OPT_LAT_FIXED) == fixed
+        sim.set_option(B.PD_OPT_VALIDATE, 1)
+        sim.step(w.nsteps)
+        u, v, th = sim.state()
+        st = sim.stats()
+        intact = sim.neighbors()[2]
+        sim.close()
+        return u, v, th, intact, {k: st[k] for k in ("broken_bonds", "band_rechecks", "validate_mismatches")}
+
+    ref = run(0, 0)
+    assert ref[4]["broken_bonds"] > 0 and ref[4]["validate_mismatches"] == 0
+    for ring in rings:
+        got = run(1, ring)
+        for a, b, name in zip(got[:4], ref[:4], ("u", "v", "theta", "status")):
+            assert np.array_equal(a, b), (case, ring, name)
+        assert got[4] == ref[4], (case, ring)
+
+
+def test_fixed_family_kernels_only_for_their_family():
+    """Other horizons, w = delta / |xi| and the general layout keep the table-driven kernels."""
+    for w, kw, expect in ((CASES["ratio_4"](), {}, 0), (CASES["notched_block"](), {}, 1),
+                          (CASES["notched_block"](), {"influence": B.PD_W_INV}, 0)):
+        sim = Simulation(w, s0=0.0, precision=PD_MIXED, **kw)
+        assert sim.get_option(B.PD_OPT_LATTICE) == 1
+        assert sim.get_option(B.PD_OPT_LAT_FIXED) == expect
+        sim.step(5)
+        sim.close()
+    w = CASES["cracked_plate"]()
+    sim = Simulation(w, s0=0.0, precision=PD_MIXED, lattice=0)
+    assert sim.get_option(B.PD_OPT_LAT_FIXED) == 0
+    sim.close()

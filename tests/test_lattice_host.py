@@ -39,6 +39,14 @@ extern "C" int table(int dim, int* out, int cap) {
   return (int)t.size();
 }
 extern "C" int prefix(int dim, int q) { return lattice_prefix(dim, q); }
+// the compile-time table and prefix (the specialized kernels' directions)
+extern "C" int table_c(int dim, int k, int c) {
+  constexpr LatTable<3> t3 = lattice_table<3>();
+  constexpr LatTable<2> t2 = lattice_table<2>();
+  const LatDir& e = dim == 3 ? t3.d[k] : t2.d[k];
+  return c < 3 ? e.n[c] : e.q;
+}
+extern "C" int prefix_c(int dim, int q) { return dim == 3 ? lattice_prefix_c<3>(q) : lattice_prefix_c<2>(q); }
 // per bond: xi (3, FP64 positions' difference), n (3), ui (3), uj (3) in metres, h, s0;
 // band_safety, n1, qmax; out: screen (1 = settled intact), code (0, 1, 2)
 extern "C" void decide(long m, const double* xi, const int* n, const double* ui, const double* uj, const double* h,
@@ -77,6 +85,8 @@ def so():
     L = ctypes.CDLL(lib)
     L.table.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_int]
     L.prefix.argtypes = [ctypes.c_int, ctypes.c_int]
+    L.prefix_c.argtypes = [ctypes.c_int, ctypes.c_int]
+    L.table_c.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
     L.decide.argtypes = [ctypes.c_long] + [ctypes.c_void_p] * 6 + [ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                                                     ctypes.c_void_p, ctypes.c_void_p]
     yield L
@@ -111,6 +121,17 @@ def test_family_prefixes(so):
     for dim, q in ((2, 9), (2, 16), (3, 9), (3, 16)):
         t = get_table(so, dim)
         assert so.prefix(dim, q) == int((t[:, 3] <= q).sum())
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_compile_time_table_is_the_runtime_table(so, dim):
+    """The kernels compiled for one family take their directions from the compile-time table: it is
+    the table the layout is built with, entry by entry, and so are its prefixes."""
+    t = get_table(so, dim)
+    for k in range(len(t)):
+        assert [so.table_c(dim, k, c) for c in range(4)] == list(t[k]), k
+    for q in range(1, 26 if dim == 3 else 65):
+        assert so.prefix_c(dim, q) == so.prefix(dim, q), q
 
 
 def near_threshold(rng, m, h, umag, s0_lo, s0_hi, dirs, rel=None):
