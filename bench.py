@@ -466,12 +466,9 @@ def run_gpu(args):
     return 0
 
 
-def mixed_roofline(prof, a1, a2, bytes1, bytes2, hbm, hbm_note, staged, lattice=False, lat_fixed=False):
+def mixed_roofline(prof, a1, a2, bytes1, bytes2, hbm, hbm_note, staged, lattice=False):
     kp = 1 if prof["pass1_ms"] >= prof["pass2_ms"] else 2  # the dominant kernel
-    if lattice:
-        name = "k_pass%d_lat%s" % (kp, "q" if lat_fixed else "")
-    else:
-        name = "k_pass%d_mixed%s" % (kp, "_staged" if staged else "")
+    name = ("k_pass%d_lat" % kp) if lattice else "k_pass%d_mixed%s" % (kp, "_staged" if staged else "")
     ach = a1 if kp == 1 else a2
     other = 2 if kp == 1 else 1
     return {"bound": "hbm", "kernel": name, "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
@@ -570,7 +567,6 @@ def run_forms(args, stream, dev, world, fp64_value, nb, hbm, hbm_note, fp64_tflo
     st = sim.stats()
     lattice = sim.get_option(B.PD_OPT_LATTICE) == 1
     lat_stage = sim.get_option(B.PD_OPT_LAT_STAGE)
-    lat_fixed = sim.get_option(B.PD_OPT_LAT_FIXED)
     sim.close()
     staged = mmap[1] == 1  # the staged kernels run whenever the mapping has one warp per slice
     bytes2 = BYTES_BOND[2] * nb + BYTES_PART[2] * w.n
@@ -581,11 +577,9 @@ def run_forms(args, stream, dev, world, fp64_value, nb, hbm, hbm_note, fp64_tflo
                     "ms_per_step": ms / steps, "dtype": "f32 bond arithmetic, f64 integration",
                     "stated_error": mixed_error_on_workload(w, s0, stream, dev, 200),
                     "band_rechecks": st["band_rechecks"],
-                    "mapping": {"block": mmap[0], "split": mmap[1], "lat_stage": lat_stage,
-                                "lat_fixed": lat_fixed},
+                    "mapping": {"block": mmap[0], "split": mmap[1], "lat_stage": lat_stage},
                     "layout": "lattice" if lattice else "general",
-                    "roofline": mixed_roofline(prof, a1, a2, bytes1, bytes2, hbm, hbm_note, staged, lattice,
-                                               lat_fixed == 1)}
+                    "roofline": mixed_roofline(prof, a1, a2, bytes1, bytes2, hbm, hbm_note, staged, lattice)}
     # geometrically nonlinear bonds (Eqs 1.10, 1.13, 1.14) in FP64 on the same workload
     sim = Simulation(w, s0=s0, precision=PD_FP64, kinematics=PD_NONLINEAR, stream=stream.cuda_stream, device=dev)
     nmap = B.pd_autotune(sim.h, 2)
@@ -702,8 +696,6 @@ def main():
                     help="with --profile-target: threads per block of the step kernels (0: default)")
     ap.add_argument("--profile-ring", type=int, choices=[0, 1, 2, 3], default=0,
                     help="with --profile-target mixed: staging ring of the lattice kernels (PD_OPT_LAT_STAGE)")
-    ap.add_argument("--profile-lat-fixed", type=int, choices=[0, 1], default=1,
-                    help="with --profile-target mixed: 0 runs the table-driven lattice kernels (PD_OPT_LAT_FIXED)")
     ap.add_argument("--sweep", action="store_true",
                     help="one JSON line per configuration (1-5): FP64 and mixed GPU rates and the oracle's "
                          "rate on all host cores and on one")
@@ -716,7 +708,7 @@ def main():
     __graft_entry__.build()
     if args.profile_target:
         return profile_target(args.profile_target, args.profile_quarter, args.profile_pairs, args.profile_block,
-                              args.profile_ring, args.profile_lat_fixed)
+                              args.profile_ring)
     if args.sweep:
         return run_sweep(args)
     return run_gpu(args)
@@ -779,7 +771,7 @@ def run_sweep(args):
     return 0
 
 
-def profile_target(form, quarter=False, pairs=1, block=0, ring=0, lat_fixed=1):
+def profile_target(form, quarter=False, pairs=1, block=0, ring=0):
     """Workload of the benchmark in one precision, 4 eager time steps (ncu captures this command)."""
     from paper_2309_11273_gb300 import PD_FP64, PD_LINEARIZED, PD_MIXED, PD_NONLINEAR, Simulation, pd_critical_stretch
     from paper_2309_11273_gb300 import workloads as W
@@ -793,7 +785,6 @@ def profile_target(form, quarter=False, pairs=1, block=0, ring=0, lat_fixed=1):
         sim.set_option(B.PD_OPT_BLOCK, block)
     if form.startswith("mixed"):
         sim.set_option(B.PD_OPT_LAT_STAGE, ring)
-        sim.set_option(B.PD_OPT_LAT_FIXED, lat_fixed)
     sim.step(4)
     sim.sync()
     print(json.dumps({"profile_target": form, "particles": w.n, "directed_bonds": sim.nbonds, "stats": sim.stats()}))

@@ -180,13 +180,15 @@ typedef enum {
                               stream, 0 (default) = 3 chunks of 16 slots, 1 = 2 x 16, 2 = 3 x 8,
                               3 = 2 x 8 (smaller rings leave more of the SM's combined L1 / shared
                               memory to the displacement gathers); pd_autotune chooses it */
-  PD_OPT_LAT_FIXED = 13    /* lattice layout with w = 1 and every body's horizon 3 h <= delta <
-                              sqrt(10) h (family |n|^2 <= 9: 122 directions in 3D, 28 in 2D):
-                              1 (default) = step kernels compiled for that family, each slot's
-                              direction a constant of the code; 0 = the kernels that read it from
-                              a table.  Results are bitwise the same (finite states).  After
-                              pd_build_neighbors, pd_get_option reports whether the compiled
-                              family's kernels run. */
+  PD_OPT_SHADOW_LO = 13    /* lattice kernels: 1 = carry each particle's FP32 displacement copy
+                              (u / h) as two FP32 words hi + lo (lo the rounding remainder of hi,
+                              16 more bytes per particle and per step gathered per bond in both
+                              passes), so that a bond's n.(u_j - u_i) / h^2 is rounded relative to
+                              the difference rather than to |u| (bodies whose displacement is
+                              large next to its variation over a horizon: rotations, rigid drift);
+                              0 (default) = one word.  Decisions stay exact either way (the same
+                              rounding band covers both).  May be set at any time; pd_get_option
+                              reports 1 only while the built layout is the lattice one. */
 } pd_option;
 
 /* Solvers (PD_OPT_SOLVER).

@@ -22,7 +22,8 @@ class Simulation:
 
     def __init__(self, w, s0=None, precision=PD_FP64, rate=None, device=0, stream=None,
                  band_safety=0.0, graph_chunk=None, ordering=B.PD_ORDER_BRICKS, bond_cache=None,
-                 kinematics=B.PD_LINEARIZED, pairs=None, influence=B.PD_W_ONE, lattice=None):
+                 kinematics=B.PD_LINEARIZED, pairs=None, influence=B.PD_W_ONE, lattice=None,
+                 shadow_lo=None):
         self.w = w
         self.n, self.dim = w.n, w.dim
         if s0 is None:
@@ -34,6 +35,8 @@ class Simulation:
         try:
             if lattice is not None:
                 B.pd_set_option(self.h, B.PD_OPT_LATTICE, int(lattice))
+            if shadow_lo is not None:
+                B.pd_set_option(self.h, B.PD_OPT_SHADOW_LO, int(shadow_lo))
             if graph_chunk is not None:
                 B.pd_set_option(self.h, B.PD_OPT_GRAPH_CHUNK, graph_chunk)
             if bond_cache is not None:

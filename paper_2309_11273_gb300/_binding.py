@@ -27,7 +27,7 @@ PD_OPT_SOLVER = 9
 PD_OPT_PAIRS = 10
 PD_OPT_LATTICE = 11
 PD_OPT_LAT_STAGE = 12
-PD_OPT_LAT_FIXED = 13
+PD_OPT_SHADOW_LO = 13
 PD_W_ONE, PD_W_INV = 0, 1
 PD_SOLVER_EXPLICIT, PD_SOLVER_ADR = 0, 1
 PD_K_PASS1, PD_K_PASS2, PD_K_PASS1B = 0, 1, 2

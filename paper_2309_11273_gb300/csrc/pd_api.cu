@@ -585,9 +585,13 @@ pd_status pd_set_option(pd_ctx* c, int32_t option, int64_t value) {
       if (c->lat_stage != (int)value) drop_graphs(c);
       c->lat_stage = (int)value;
       break;
-    case PD_OPT_LAT_FIXED:
-      if ((c->lat_fixed_opt != 0) != (value != 0)) drop_graphs(c);
-      c->lat_fixed_opt = value != 0;
+    case PD_OPT_SHADOW_LO:
+      c->shadow_lo_opt = value != 0;
+      if (c->built) {
+        drop_graphs(c);
+        const pd_status st = ensure_shadow_lo(c);
+        if (st != PD_OK) return st;
+      }
       break;
     case PD_OPT_PAIRS:
       // A failure check of the pair form marks slices whose bS its next pass 1b recomputes; the
@@ -626,7 +630,7 @@ pd_status pd_get_option(pd_ctx* c, int32_t option, int64_t* value) {
     case PD_OPT_PAIRS: *value = (c->pairs && c->pairs_ok && c->precision == PD_FP64) ? 1 : 0; break;
     case PD_OPT_LATTICE: *value = c->built ? (c->lattice ? 1 : 0) : c->lattice_opt; break;
     case PD_OPT_LAT_STAGE: *value = c->lat_stage; break;
-    case PD_OPT_LAT_FIXED: *value = c->built ? (lattice_fixed_active(c) ? 1 : 0) : c->lat_fixed_opt; break;
+    case PD_OPT_SHADOW_LO: *value = c->built ? (c->shadow_lo ? 1 : 0) : c->shadow_lo_opt; break;
     default: return fail(PD_ERR_ARG, "unknown option");
   }
   return PD_OK;
@@ -941,7 +945,8 @@ pd_status pd_autotune(pd_ctx* c, int32_t trial_steps, int32_t* block_out, int32_
       c->steps = steps0;
       c->skip_next_check = skip0;
       c->check_pending = pend0;
-      return PD_OK;
+      // the two-word shadow from the restored displacements (the FP32 words are as saved)
+      return c->shadow_lo ? sync_shadow(c) : PD_OK;
     };
     c->profile = 0;
     c->graph_chunk = 0;

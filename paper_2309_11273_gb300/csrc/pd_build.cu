@@ -632,9 +632,6 @@ pd_status build_lattice(pd_ctx* c, BuildArgs& A, bool* done) {
   c->lat_wuni = (int)((sptr2[1] - sptr2[0]) >> 5);
   for (int64_t t = 0; t < c->nslices; ++t)
     if ((int)((sptr2[t + 1] - sptr2[t]) >> 5) != c->lat_wuni) c->lat_wuni = 0;
-  c->lat_q = c->lat_qmax[0];
-  for (int b = 1; b < nb; ++b)
-    if (c->lat_qmax[b] != c->lat_q) c->lat_q = 0;
   c->lattice = true;
   *done = true;
   return upload_body_params(c);
@@ -922,7 +919,7 @@ pd_status upload_body_params(pd_ctx* c) {
     const double lq = p.horizon / c->q + 2.0;
     d.xi1max = (float)(std::sqrt((double)c->dim) * lq * 1.0001);
     d.qmax = (float)(lq * lq * 1.0001);
-    d.lat_h = d.lat_inv_h = d.lat_C = 0.0;
+    d.lat_h = d.lat_inv_h = d.lat_C = d.lat_K = d.lat_Kb = 0.0;
     d.lat_lam_hi = d.lat_lam_lo = d.lat_s0 = 0.0f;
     d.lat_Kf = d.lat_sq = d.lat_eps_c = d.lat_s0n1 = d.lat_Kfast = d.lat_Kcfast = 0.0f;
     if (c->lattice) {
@@ -935,6 +932,8 @@ pd_status upload_body_params(pd_ctx* c) {
       d.lat_h = h;
       d.lat_inv_h = 1.0 / h;
       d.lat_C = G / (h * nref);
+      d.lat_K = d.lat_C * p.dt * d.inv_rho;
+      d.lat_Kb = p.dt * d.inv_rho;
       const double lam = (K - G / 3.0) * A / (G * nref);
       d.lat_lam_hi = (float)lam;
       d.lat_lam_lo = (float)(lam - (double)d.lat_lam_hi);
@@ -1166,7 +1165,8 @@ pd_status build_neighbors(pd_ctx* c, const pd_crack* cracks, int32_t ncracks) {
     c->lat_up = nullptr;
     c->lat_int = nullptr;
     c->lat_wuni = 0;
-    c->lat_q = 0;
+    c->u32lo[0] = c->u32lo[1] = nullptr;
+    c->shadow_lo = false;
     if (c->precision == PD_MIXED && c->kin == PD_LINEARIZED && c->lattice_opt) {
       PD_CUDA(cudaStreamSynchronize(s));
       bool lat = false;
@@ -1197,7 +1197,7 @@ pd_status build_neighbors(pd_ctx* c, const pd_crack* cracks, int32_t ncracks) {
     if (st2 != PD_OK) return st2;
   }
   c->built = true;
-  return PD_OK;
+  return ensure_shadow_lo(c);
 }
 
 }  // namespace pd

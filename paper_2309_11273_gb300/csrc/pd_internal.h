@@ -37,6 +37,8 @@ struct BodyDev {
   double lat_h;       // lattice spacing h
   double lat_inv_h;   // 1 / h
   double lat_C;       // G / (h N_ref): F_i / V_i = lat_C * (FP32 force sum)
+  double lat_K;       // lat_C dt / rho: the velocity update's factor of the FP32 force sum
+  double lat_Kb;      // dt / rho: its factor of the body force density b
   float lat_lam_hi;   // lambda = (K - G/3) A / (G N_ref), split hi + lo (P_i = lambda sigma_i rho_i^2)
   float lat_lam_lo;
   float lat_s0;       // s0 in FP32
@@ -184,6 +186,9 @@ struct pd_ctx {
   // mixed path
   int4* pos32 = nullptr;
   float4* u32[2] = {nullptr, nullptr};
+  float4* u32lo[2] = {nullptr, nullptr};  // lattice layout, two-word shadow: the lo words of u32
+  int shadow_lo_opt = 0;                  // PD_OPT_SHADOW_LO as set
+  bool shadow_lo = false;                 // the lattice kernels run with the two-word shadow
   float2* thm32 = nullptr;
   float* mu32 = nullptr;
   float* aA32 = nullptr;
@@ -214,8 +219,6 @@ struct pd_ctx {
   double4* diag_part = nullptr;   // pd_get_stats: per-block (strain energy, min margin, kinetic, 0)
   int lattice_opt = 1;            // PD_OPT_LATTICE: build the lattice layout when the bodies qualify
   int lat_stage = 0;              // PD_OPT_LAT_STAGE: staging ring of the lattice kernels (0..3)
-  int lat_fixed_opt = 1;          // PD_OPT_LAT_FIXED: kernels compiled for the family |n|^2 <= 9
-  int lat_q = 0;                  // lattice layout: every body's largest |n|^2 if they agree, else 0
   bool lattice = false;           // the built layout is the lattice layout (mixed, linearized bonds)
   float2* lat_f = nullptr;        // lattice layout: per particle (N_ref / N_i, A / N_i)
   float* lat_rho = nullptr;       // lattice layout: per particle N_ref / N_i
@@ -279,8 +282,8 @@ pd_status ensure_bond_cache(pd_ctx* c);
 pd_status ensure_adr(pd_ctx* c);      // ADR arrays and lambda (once per build)
 pd_status diagnostics(pd_ctx* c, double* min_margin, double* strain, double* kinetic);
 pd_status prepare_staged_kernels(pd_ctx* c);  // shared-memory opt-in of the staged kernels
-pd_status upload_lattice_tables(int device);  // direction tables of the lattice kernels (once per device)
-bool lattice_fixed_active(const pd_ctx* c);   // the lattice kernels compiled for the context's family run
+pd_status upload_lattice_tables(int device);   // direction tables of the lattice kernels (once per device)
+pd_status ensure_shadow_lo(pd_ctx* c);        // two-word shadow arrays and their contents (PD_OPT_SHADOW_LO)
 pd_status upload_field(pd_ctx* c, const double* host_soa, double4* dst, int comps);
 pd_status gather_field(pd_ctx* c, const double* dev_soa, double4* dst, int comps);
 pd_status launch_nonfinite(const double* a, int64_t n, unsigned long long* flag, cudaStream_t s);

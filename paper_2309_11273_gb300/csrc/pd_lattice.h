@@ -140,7 +140,11 @@ inline int lattice_prefix(int dim, int q) {
 //     FP64 rounding of its own dot product and threshold: 0.06 eps (U_i + U_j) + 0.034 eps s0 N1;
 //   * s0 rounded to FP32: eps s0 |n|^2; the final FMA: eps |g|;
 // so |g - g_FP64| <= B = c (1 + 8 eps) eps [(5.0003 N1 + 0.06)(U_i + U_j) + s0 (|n|^2 + 0.034 N1) + |g|]
-// (the 8 eps covers the FP32 evaluation of B itself, for c >= 1).  Outside +-B the FP32 sign is the
+// (the 8 eps covers the FP32 evaluation of B itself, for c >= 1).  With the two-word shadow
+// (u' = hi + lo, both FP32, lo the rounding remainder of hi) each difference is (hi_j - hi_i) +
+// (lo_j - lo_i): the copies then differ from u' by at most eps |lo| <= eps^2 U, and the two roundings
+// of the difference stay within the 2 eps |n|_1 (U_i + U_j) of the first two terms above, so the same
+// B bounds that evaluation (lat_delta_lo).  Outside +-B the FP32 sign is the
 // FP64 decision; inside, the bond is re-decided in FP64.  The screen g < -(Kfast (U_i + U_j) +
 // Kcfast), with |g| = -g folded in (division by 1 - c eps) and |n|^2 bounded by the family's
 // largest, implies g < -B: it settles the bonds far from their threshold in two instructions.
@@ -163,21 +167,35 @@ inline LatBand lattice_band(double band_safety, double s0, int n1, int qmax) {
   return b;
 }
 
-// d' = n.(u'_j - u'_i): one product and two FMAs (two in 2D).
+// d' = n.(u'_j - u'_i) from the differences: one product and two FMAs (one in 2D).
+template <int DIM>
+PD_LHD float lat_dprime_d(float nx, float ny, float nz, float dx, float dy, float dz) {
+  float d = nx * dx;
+  d = fmaf(ny, dy, d);
+  if (DIM == 3) d = fmaf(nz, dz, d);
+  return d;
+}
+
+// d' = n.(u'_j - u'_i) from one-word shadows.
 template <int DIM>
 PD_LHD float lat_dprime(float nx, float ny, float nz, float ujx, float ujy, float ujz, float uix, float uiy,
                         float uiz) {
-  float d = nx * (ujx - uix);
-  d = fmaf(ny, ujy - uiy, d);
-  if (DIM == 3) d = fmaf(nz, ujz - uiz, d);
-  return d;
+  return lat_dprime_d<DIM>(nx, ny, nz, ujx - uix, ujy - uiy, ujz - uiz);
 }
+
+// One component of u'_j - u'_i from two-word shadows (hi + lo).
+PD_LHD float lat_delta_lo(float hj, float lj, float hi, float li) { return (hj - hi) + (lj - li); }
 
 // g = d' - s0 |n|^2 in one FMA.
 PD_LHD float lat_g(float d, float s0f, float q) { return fmaf(-s0f, q, d); }
 
 // The screen: true settles the bond as intact.  scr_i = fmaf(Kfast, U_i, Kcfast), once per particle.
 PD_LHD bool lat_screen_intact(float g, float Kfast, float Uj, float scr_i) { return fmaf(Kfast, Uj, g) < -scr_i; }
+
+// The same screen as a value: lat_screen_value < 0 exactly when lat_screen_intact (a < -b and the
+// rounded a + b < 0 agree: a sum of two floats rounds to zero only when it is exactly zero), NaN when
+// an operand is NaN.  scr_i = -inf settles every bond with a finite value (a body without failure).
+PD_LHD float lat_screen_value(float g, float Kfast, float Uj, float scr_i) { return fmaf(Kfast, Uj, g) + scr_i; }
 
 // Full band: 0 intact, 1 broken (FP32 decision), 2 inside the band (decide in FP64).  A NaN g is
 // inside (both comparisons false).

@@ -1725,6 +1725,60 @@ __device__ __forceinline__ float2 lat_wgt(int k) {
   return DIM == 3 ? c_latw3[k] : c_latw2[k];
 }
 
+// The update of the lattice kernels (Eq 2.11 as update() computes it) with F_i / V_i = lat_C x the
+// FP32 force sum f and the constants folded: v += lat_K f (+ lat_Kb b), u += dt v, so that a free
+// particle costs two FP64 FMAs per component; the z components stay zero in 2D.  Particles under a
+// boundary condition and the relaxation solver take update().
+template <int DIM>
+__device__ __forceinline__ void update_lat(const StepArgs& a, int64_t i, int b, const float f[3],
+                                           const double4* __restrict__ disp, double4* __restrict__ disp_out,
+                                           double4& u) {
+  const BodyDev& bp = a.bp[b];
+  const uint8_t fl = a.flag ? a.flag[i] : (uint8_t)0;
+  if (a.adr || fl != 0) {
+    const double C = bp.lat_C;
+    const double fd[3] = {C * (double)f[0], C * (double)f[1], C * (double)f[2]};
+    update(a, i, b, fd, disp, disp_out, u);
+    return;
+  }
+  u = disp[i];
+  double4 v = a.vel[i];
+  const double K = bp.lat_K;
+  v.x = fma(K, (double)f[0], v.x);
+  v.y = fma(K, (double)f[1], v.y);
+  if (DIM == 3) v.z = fma(K, (double)f[2], v.z);
+  if (a.bacc) {
+    const double4 bb = a.bacc[i];
+    const double kb = bp.lat_Kb;
+    v.x = fma(kb, bb.x, v.x);
+    v.y = fma(kb, bb.y, v.y);
+    if (DIM == 3) v.z = fma(kb, bb.z, v.z);
+  }
+  const double dt = bp.dt;
+  u.x = fma(dt, v.x, u.x);
+  u.y = fma(dt, v.y, u.y);
+  if (DIM == 3) u.z = fma(dt, v.z, u.z);
+  disp_out[i] = u;  // .w carries V_i unchanged
+  a.vel[i] = v;
+}
+
+// The FP32 shadow of a displacement in lattice units, (u / h, |u / h|_inf).
+template <int DIM>
+__device__ __forceinline__ float4 shadow_lat(double inv_h, const double4& u) {
+  const float x = (float)(u.x * inv_h), y = (float)(u.y * inv_h), z = DIM == 3 ? (float)(u.z * inv_h) : 0.0f;
+  return make_float4(x, y, z, fmaxf(fabsf(x), fmaxf(fabsf(y), fabsf(z))));
+}
+
+// The two-word shadow: hi as shadow_lat, lo = u / h - hi rounded to FP32 (the subtraction is exact in
+// FP64), so that hi + lo carries u / h to about 2^-48 of its size.
+template <int DIM>
+__device__ __forceinline__ void shadow_lat_lo(double inv_h, const double4& u, float4& hi, float4& lo) {
+  const double x = u.x * inv_h, y = u.y * inv_h, z = DIM == 3 ? u.z * inv_h : 0.0;
+  const float hx = (float)x, hy = (float)y, hz = (float)z;
+  hi = make_float4(hx, hy, hz, fmaxf(fabsf(hx), fmaxf(fabsf(hy), fabsf(hz))));
+  lo = make_float4((float)(x - (double)hx), (float)(y - (double)hy), (float)(z - (double)hz), 0.0f);
+}
+
 // The FP32 shadow of a displacement in the context's format.
 __device__ __forceinline__ float4 shadow_of(const StepArgs& a, int b, const double4& u) {
   if (a.lattice) {
@@ -1771,8 +1825,11 @@ __device__ __forceinline__ bool lat_rows(const StepArgs& a, Stage<NB, CH>& st, i
   return true;
 }
 
-template <int DIM, bool WI, int NB, int CH>
+// LO: two-word shadow (u' = hi + lo, PD_OPT_SHADOW_LO): each end's lo words come from lo32 and the
+// differences are formed as (hi_j - hi_i) + (lo_j - lo_i).
+template <int DIM, bool WI, bool LO, int NB, int CH>
 __global__ void __launch_bounds__(512) k_pass1_lat(StepArgs a, const float4* __restrict__ u32,
+                                                    const float4* __restrict__ lo32,
                                                     const double4* __restrict__ disp, int write_theta) {
   extern __shared__ __align__(128) unsigned char smem[];
   const SliceIdx t = slice_index<1>(a.n_pad, a.slice_ptr);
@@ -1786,44 +1843,54 @@ __global__ void __launch_bounds__(512) k_pass1_lat(StepArgs a, const float4* __r
   const float s0f = bp.lat_s0;
   const bool can_break = bp.breaks != 0;
   const float4 Ui = u32[t.i];
+  const float4 Li = LO ? lo32[t.i] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   const float Kfast = bp.lat_Kfast;
-  const float scr_i = fmaf(Kfast, Ui.w, bp.lat_Kcfast);  // the screen's bound less its U_j term (pd_lattice.h)
+  // the screen's bound less its U_j term (pd_lattice.h); -inf settles every bond of a body without
+  // failure, so that the per-slot test needs no separate flag
+  const float scr_i = can_break ? fmaf(Kfast, Ui.w, bp.lat_Kcfast) : -INFINITY;
   uint32_t* __restrict__ bw = a.bits + (t.base >> 5);
   float acc = 0.0f;
   const bool checking = a.check != 0;  // warp-uniform (can_break is per body: per lane in a batch)
   const uint32_t lmask = 1u << lane;
-  // one batch of U = 4 slots starting at slot k: the extensions and the intact mask first, the
-  // failure decisions next (the rare slow path clears the mask bits of the bonds it breaks), then
-  // the dilatation terms of the bonds still intact in slot order, so that the sum does not depend on
-  // whether a bond broke here or in an earlier check (a state read between steps)
+  // one batch of U = 4 slots starting at slot k: the extensions of the intact bonds (0 for the
+  // others) and the screen first, the failure decisions next (the rare slow path zeroes the terms
+  // of the bonds it breaks), then the dilatation terms in slot order, so that the sum does not
+  // depend on whether a bond broke here or in an earlier check (a state read between steps)
   auto batch = [&](const int32_t* cs, const uint32_t* ws, uint4 w4, int k) {
     constexpr int U = kU32;
     const uint32_t wd[U] = {w4.x, w4.y, w4.z, w4.w};
-    float4 Uj[U];
+    float4 Uj[U], Lj[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) Uj[u] = u32[cs[u * 32]];
-    float dv[U];
-    unsigned mask = 0u;
+    for (int u = 0; u < U; ++u) {
+      const int32_t j = cs[u * 32];
+      Uj[u] = u32[j];
+      if (LO) Lj[u] = lo32[j];
+    }
+    float dm[U];
     bool near = false;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const float4 dn = lat_dir<DIM>(k + u);
-      dv[u] = lat_dprime<DIM>(dn.x, dn.y, dn.z, Uj[u].x, Uj[u].y, Uj[u].z, Ui.x, Ui.y, Ui.z);
+      const float d =
+          LO ? lat_dprime_d<DIM>(dn.x, dn.y, dn.z, lat_delta_lo(Uj[u].x, Lj[u].x, Ui.x, Li.x),
+                                 lat_delta_lo(Uj[u].y, Lj[u].y, Ui.y, Li.y), lat_delta_lo(Uj[u].z, Lj[u].z, Ui.z, Li.z))
+             : lat_dprime<DIM>(dn.x, dn.y, dn.z, Uj[u].x, Uj[u].y, Uj[u].z, Ui.x, Ui.y, Ui.z);
       const bool in = (wd[u] & lmask) != 0u;
-      mask |= in ? (1u << u) : 0u;
-      if (checking) near |= can_break & in & !lat_screen_intact(lat_g(dv[u], s0f, dn.w), Kfast, Uj[u].w, scr_i);
+      dm[u] = in ? d : 0.0f;
+      if (checking) near |= in & !(lat_screen_value(lat_g(d, s0f, dn.w), Kfast, Uj[u].w, scr_i) < 0.0f);
     }
     if (checking && (__any_sync(kFull, near) | (a.validate != 0))) {
       // full band for the bonds the screen did not settle, FP64 inside it; the neighbour index and
       // its |u'| are reloaded (staged chunk, L1) so that little stays live across this block
+      unsigned brk = 0u;
 #pragma unroll 1
       for (int u = 0; u < U; ++u) {
         int code = 0;
-        if (can_break && ((mask >> u) & 1u)) {
+        if (can_break && (ws[u] & lmask) != 0u) {
           const int32_t jj = cs[u * 32];
           const float Ujw = u32[jj].w;
           const float q = lat_dir<DIM>(k + u).w;
-          const float du = u == 0 ? dv[0] : (u == 1 ? dv[1] : (u == 2 ? dv[2] : dv[3]));  // no indexed array
+          const float du = u == 0 ? dm[0] : (u == 1 ? dm[1] : (u == 2 ? dm[2] : dm[3]));  // no indexed array
           code = lat_code(lat_g(du, s0f, q), Ui.w, Ujw, s0f, q, bp.lat_Kf, bp.lat_sq, bp.lat_eps_c, bp.lat_s0n1);
           if (code == 2) {
             code = fp64_breaks_inl<DIM>(a, t.i, jj, disp, s0) ? 1 : 0;
@@ -1835,18 +1902,19 @@ __global__ void __launch_bounds__(512) k_pass1_lat(StepArgs a, const float4* __r
         const unsigned m = __ballot_sync(kFull, code == 1);
         if (m) {
           if (lane == 0) bw[k + u] = ws[u] & ~m;
-          if (code == 1) mask &= ~(1u << u);
+          if (code == 1) brk |= 1u << u;
         }
       }
+#pragma unroll
+      for (int u = 0; u < U; ++u) dm[u] = ((brk >> u) & 1u) ? 0.0f : dm[u];
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const float dd = ((mask >> u) & 1u) ? dv[u] : 0.0f;
       if (WI) {  // acc += w' d' with w' as hi + lo
         const float2 wk = lat_wgt<DIM>(k + u);
-        acc = fmaf(wk.x, dd, fmaf(wk.y, dd, acc));
+        acc = fmaf(wk.x, dm[u], fmaf(wk.y, dm[u], acc));
       } else {
-        acc += dd;
+        acc += dm[u];
       }
     }
   };
@@ -1861,9 +1929,10 @@ __global__ void __launch_bounds__(512) k_pass1_lat(StepArgs a, const float4* __r
   }
 }
 
-template <int DIM, bool WI, int NB, int CH>
+template <int DIM, bool WI, bool LO, int NB, int CH>
 __global__ void __launch_bounds__(512) k_pass2_lat(StepArgs a, const float4* __restrict__ u32,
                                                     float4* __restrict__ u32_out,
+                                                    const float4* __restrict__ lo32, float4* __restrict__ lo32_out,
                                                     const double4* __restrict__ disp,
                                                     double4* __restrict__ disp_out) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -1873,6 +1942,7 @@ __global__ void __launch_bounds__(512) k_pass2_lat(StepArgs a, const float4* __r
   const int lane = t.lane;
   const int b = a.body ? a.body[t.i] : 0;
   const float4 Ui = a.lat_up[t.i];  // (u'_i, P_i)
+  const float4 Li = LO ? lo32[t.i] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   const float rho_i = a.lat_f[t.i].x;
   // every particle around this slice (lanes and neighbours) has N_j = N_ref: N_ref/N_i + N_ref/N_j
   // = 2 exactly, so the per-neighbour factor is not gathered (the result is bitwise the same); the
@@ -1884,19 +1954,23 @@ __global__ void __launch_bounds__(512) k_pass2_lat(StepArgs a, const float4* __r
     constexpr bool INTR = decltype(intr)::value;
     constexpr int U = kU32;
     const uint32_t wd[U] = {w4.x, w4.y, w4.z, w4.w};
-    float4 Uj[U];
+    float4 Uj[U], Lj[U];
     float rr[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int32_t j = cs[u * 32];
       Uj[u] = a.lat_up[j];
+      if (LO) Lj[u] = lo32[j];
       rr[u] = INTR ? 2.0f : rho_i + a.lat_rho[j];
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const float4 dn = lat_dir<DIM>(k + u);
       const float2 r = lat_rcp<DIM>(k + u);
-      const float d = lat_dprime<DIM>(dn.x, dn.y, dn.z, Uj[u].x, Uj[u].y, Uj[u].z, Ui.x, Ui.y, Ui.z);
+      const float d =
+          LO ? lat_dprime_d<DIM>(dn.x, dn.y, dn.z, lat_delta_lo(Uj[u].x, Lj[u].x, Ui.x, Li.x),
+                                 lat_delta_lo(Uj[u].y, Lj[u].y, Ui.y, Li.y), lat_delta_lo(Uj[u].z, Lj[u].z, Ui.z, Li.z))
+             : lat_dprime<DIM>(dn.x, dn.y, dn.z, Uj[u].x, Uj[u].y, Uj[u].z, Ui.x, Ui.y, Ui.z);
       const float dr = fmaf(d, r.x, d * r.y);  // d / |n|^2 with 1 / |n|^2 carried as hi + lo
       float cf = fmaf(rr[u], dr, Ui.w + Uj[u].w);
       if (WI) {  // cf w' with w' as hi + lo
@@ -1916,278 +1990,16 @@ __global__ void __launch_bounds__(512) k_pass2_lat(StepArgs a, const float4* __r
   const bool ok = a.lat_wuni > 0 ? lat_rows<NB, CH>(a, st, a.lat_wuni, lane, batch)
                                  : lat_rows<NB, CH>(a, st, st.W, lane, batch);
   if (ok) {
-    const double C = a.bp[b].lat_C;
-    const double fd[3] = {C * (double)f[0], C * (double)f[1], C * (double)f[2]};
     double4 u;
-    update(a, t.i, b, fd, disp, disp_out, u);
-    u32_out[t.i] = shadow_of(a, b, u);
-  }
-}
-
-// ------------------------------------------------- lattice kernels specialized for one family
-// When every slice of the context holds the same family -- the closed ball |n|^2 <= Q, Q = 9 (122
-// directions in 3D, 28 in 2D, delta = 3.015 h) -- each slot's direction is a compile-time constant:
-// the row is unrolled, a zero component of n costs nothing, a unit one an addition, and the
-// constants are immediates.  Every operation left out is exact (0 * x, 1 * x, + 0), so the results
-// are bitwise those of k_pass1_lat / k_pass2_lat for finite values.
-template <int DIM>
-struct LatTab {
-  static constexpr LatTable<DIM> t = lattice_table<DIM>();  // evaluated once per dimension
-};
-template <int DIM, int K>
-struct LatSlot {
-  static constexpr int nx = LatTab<DIM>::t.d[K].n[0], ny = LatTab<DIM>::t.d[K].n[1];
-  static constexpr int nz = DIM == 3 ? LatTab<DIM>::t.d[K].n[2] : 0, q = LatTab<DIM>::t.d[K].q;
-  static constexpr double r = 1.0 / q;  // hi and lo as the constant tables hold them
-  static constexpr float rhi = (float)r;
-  static constexpr float rlo = (float)(r - (double)(float)r);
-};
-
-constexpr int kLatFixedQ = 9;  // 3 h <= delta < sqrt(10) h: 122 directions in 3D, 28 in 2D
-
-template <int DIM, int Q>
-struct LatFam {
-  static constexpr int S = lattice_prefix_c<DIM>(Q);
-  static constexpr int W = (S + 3) & ~3;
-};
-static_assert(LatFam<3, kLatFixedQ>::S == 122 && LatFam<2, kLatFixedQ>::S == 28, "family |n|^2 <= 9");
-
-// Lambdas of the unrolled rows are inlined unconditionally: the inliner's size limits would leave
-// some as calls, with the sums they update on the stack.
-#define PD_AI __attribute__((always_inline))
-
-template <int B, int E, class F>
-__device__ __forceinline__ void static_for(F&& f) {
-  if constexpr (B < E) {
-    f(std::integral_constant<int, B>{});
-    static_for<B + 1, E>(f);
-  }
-}
-
-// acc (+)= N * delta: the first non-zero term starts the sum; N = +-1 adds or subtracts.  The
-// explicit roundings keep the compiler from fusing a product into a following addition, which the
-// general kernels' FMA chain does not do either.
-template <int N, bool FIRST>
-__device__ __forceinline__ float lat_term(float acc, float delta) {
-  if constexpr (N == 0) {
-    return acc;
-  } else if constexpr (FIRST) {
-    if constexpr (N == 1) return delta;
-    else if constexpr (N == -1) return -delta;
-    else return __fmul_rn((float)N, delta);
-  } else {
-    if constexpr (N == 1) return __fadd_rn(acc, delta);
-    else if constexpr (N == -1) return __fsub_rn(acc, delta);
-    else return fmaf((float)N, delta, acc);
-  }
-}
-
-// d' = n . (u'_j - u'_i) for the slot's compile-time n (the same roundings as lat_dprime)
-template <int DIM, int K>
-__device__ __forceinline__ float lat_dprime_k(const float4& uj, const float4& ui) {
-  using L = LatSlot<DIM, K>;
-  float d = 0.0f;
-  if constexpr (L::nx != 0) d = lat_term<L::nx, true>(d, uj.x - ui.x);
-  if constexpr (L::ny != 0) d = lat_term<L::ny, L::nx == 0>(d, uj.y - ui.y);
-  if constexpr (L::nz != 0) d = lat_term<L::nz, L::nx == 0 && L::ny == 0>(d, uj.z - ui.z);
-  return d;
-}
-
-// The row of a slice with the family fixed: chunks and batches unrolled, slot indices constant.
-template <int DIM, int Q, int NB, int CH, class Body>
-__device__ __forceinline__ bool lat_rows_fixed(const StepArgs& a, Stage<NB, CH>& st, int lane, Body&& body) {
-  constexpr int W = LatFam<DIM, Q>::W;
-  constexpr int NCH = (W + CH - 1) / CH;
-  if (lane == 0)
-    for (; st.issued < min(NB, NCH); ++st.issued)
-      if (!(a.expire && st.issued == 0)) stage_issue(st, st.issued);  // testing: chunk 0 never arrives
-  bool ok = true;
-  static_for<0, NCH>([&](auto cc) PD_AI {
-    constexpr int C = decltype(cc)::value;
-    if (!ok) return;
-    const int buf = C % NB;
-    if (!__all_sync(kFull, mbar_wait(&st.bar[buf], (unsigned)((C / NB) & 1)))) {
-      if (lane == 0) atomicExch(&a.counters[4], 1ull);
-      stage_drain(st, C + 1);
-      ok = false;
-      return;
+    update_lat<DIM>(a, t.i, b, f, disp, disp_out, u);
+    if (LO) {
+      float4 hi, lo;
+      shadow_lat_lo<DIM>(a.bp[b].lat_inv_h, u, hi, lo);
+      u32_out[t.i] = hi;
+      lo32_out[t.i] = lo;
+    } else {
+      u32_out[t.i] = shadow_lat<DIM>(a.bp[b].lat_inv_h, u);
     }
-    const int32_t* cs = st.col + buf * CH * 32 + lane;
-    const uint32_t* ws = st.words + buf * CH;
-    constexpr int n = CH < W - C * CH ? CH : W - C * CH;
-    static_for<0, n / 4>([&](auto bb) PD_AI {
-      constexpr int B = decltype(bb)::value;
-      const uint4 w4 = *reinterpret_cast<const uint4*>(ws + 4 * B);
-      if ((w4.x | w4.y | w4.z | w4.w) == 0u) return;  // no intact bond in the batch
-      body(std::integral_constant<int, C * CH + 4 * B>{}, cs + 4 * B * 32, ws + 4 * B, w4);
-    });
-    __syncwarp();  // every lane is done with this buffer before it is refilled
-    if (lane == 0 && st.issued < NCH) stage_issue(st, st.issued++);
-  });
-  return ok;
-}
-
-// The failure decisions of one batch inside the rounding band (rare): out of line, so that the
-// unrolled row carries one call per batch instead of a copy of this code.  Returns the batch's
-// intact mask with the bits of the bonds that break cleared.
-template <int DIM>
-__device__ __noinline__ unsigned lat_slow1(const double4* __restrict__ pos, const double4* __restrict__ disp,
-                                           const float4* __restrict__ u32, uint32_t* __restrict__ bw,
-                                           unsigned long long* __restrict__ counters, const BodyDev* __restrict__ bpp,
-                                           int64_t i, const int32_t* cs, const uint32_t* ws, int k, float d0,
-                                           float d1, float d2, float d3, unsigned mask, float Uiw, bool can_break,
-                                           bool validate) {
-  const BodyDev& bp = *bpp;
-  const float s0f = bp.lat_s0;
-  const double s0 = bp.s0;
-  const int lane = threadIdx.x & 31;
-  for (int u = 0; u < kU32; ++u) {
-    int code = 0;
-    if (can_break && ((mask >> u) & 1u)) {
-      const int32_t jj = cs[u * 32];
-      const float Ujw = u32[jj].w;
-      const float q = lat_dir<DIM>(k + u).w;
-      const float du = u == 0 ? d0 : (u == 1 ? d1 : (u == 2 ? d2 : d3));
-      code = lat_code(lat_g(du, s0f, q), Uiw, Ujw, s0f, q, bp.lat_Kf, bp.lat_sq, bp.lat_eps_c, bp.lat_s0n1);
-      if (code == 2 || validate) {  // the arithmetic of fp64_breaks_inl
-        double ex, ey, ez, d, qq;
-        bond_f64<DIM>(pos[i], pos[jj], disp[i], disp[jj], ex, ey, ez, d, qq);
-        const bool brk = d >= s0 * qq;
-        if (code == 2) {
-          code = brk ? 1 : 0;
-          atomicAdd(&counters[0], 1ull);
-        } else if ((code == 1) != brk) {
-          atomicAdd(&counters[1], 1ull);
-        }
-      }
-    }
-    const unsigned m = __ballot_sync(kFull, code == 1);
-    if (m) {
-      if (lane == 0) bw[k + u] = ws[u] & ~m;
-      if (code == 1) mask &= ~(1u << u);
-    }
-  }
-  return mask;
-}
-
-template <int DIM, int Q, int NB, int CH>
-__global__ void __maxnreg__(64) k_pass1_latq(StepArgs a, const float4* __restrict__ u32,
-                                                     const double4* __restrict__ disp, int write_theta) {
-  extern __shared__ __align__(128) unsigned char smem[];
-  const SliceIdx t = slice_index<1>(a.n_pad, a.slice_ptr);
-  if (write_theta && blockIdx.x == 0 && threadIdx.x == 0) *a.d_step += 1;
-  if (!t.active) return;  // whole warps: the staging below is per warp
-  auto st = stage_init<NB, CH>(smem, t, a);
-  const int lane = t.lane;
-  const int b = a.body ? a.body[t.i] : 0;
-  const BodyDev& bp = a.bp[b];
-  const float s0f = bp.lat_s0;
-  const bool can_break = bp.breaks != 0;
-  const float4 Ui = u32[t.i];
-  const float Kfast = bp.lat_Kfast;
-  const float scr_i = fmaf(Kfast, Ui.w, bp.lat_Kcfast);
-  uint32_t* __restrict__ bw = a.bits + (t.base >> 5);
-  const uint32_t lmask = 1u << lane;
-  const bool checking = a.check != 0;
-  float acc = 0.0f;
-  constexpr int S = LatFam<DIM, Q>::S;
-  auto body = [&](auto kc, const int32_t* cs, const uint32_t* ws, uint4 w4) PD_AI {
-    constexpr int K = decltype(kc)::value;
-    const uint32_t wd[4] = {w4.x, w4.y, w4.z, w4.w};
-    float4 Uj[4];
-    static_for<0, 4>([&](auto uc) PD_AI {
-      constexpr int u = decltype(uc)::value;
-      if constexpr (K + u < S) Uj[u] = u32[cs[u * 32]];
-    });
-    float dv[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    unsigned mask = 0u;
-    bool near = false;
-    static_for<0, 4>([&](auto uc) PD_AI {
-      constexpr int u = decltype(uc)::value;
-      if constexpr (K + u < S) {
-        dv[u] = lat_dprime_k<DIM, K + u>(Uj[u], Ui);
-        const bool in = (wd[u] & lmask) != 0u;
-        mask |= in ? (1u << u) : 0u;
-        if (checking)
-          near |= can_break & in &
-                  !lat_screen_intact(lat_g(dv[u], s0f, (float)LatSlot<DIM, K + u>::q), Kfast, Uj[u].w, scr_i);
-      }
-    });
-    if (checking && (__any_sync(kFull, near) | (a.validate != 0)))
-      mask = lat_slow1<DIM>(a.pos, disp, u32, bw, a.counters, &a.bp[b], t.i, cs, ws, K, dv[0], dv[1], dv[2],
-                            dv[3], mask, Ui.w, can_break, a.validate != 0);
-    static_for<0, 4>([&](auto uc) PD_AI {
-      constexpr int u = decltype(uc)::value;
-      if constexpr (K + u < S) acc += ((mask >> u) & 1u) ? dv[u] : 0.0f;
-    });
-  };
-  const bool ok = lat_rows_fixed<DIM, Q, NB, CH>(a, st, lane, body);
-  if (ok && write_theta) {
-    const float2 f = a.lat_f[t.i];  // (N_ref / N_i, A / N_i)
-    a.theta32[t.i] = f.y * acc;
-    const float x = acc * (f.x * f.x);
-    a.lat_up[t.i] = make_float4(Ui.x, Ui.y, Ui.z, fmaf(bp.lat_lam_hi, x, bp.lat_lam_lo * x));
-  }
-}
-
-template <int DIM, int Q, int NB, int CH>
-__global__ void __maxnreg__(64) k_pass2_latq(StepArgs a, const float4* __restrict__ u32,
-                                                     float4* __restrict__ u32_out,
-                                                     const double4* __restrict__ disp,
-                                                     double4* __restrict__ disp_out) {
-  extern __shared__ __align__(128) unsigned char smem[];
-  const SliceIdx t = slice_index<1>(a.n_pad, a.slice_ptr);
-  if (!t.active) return;
-  auto st = stage_init<NB, CH>(smem, t, a);
-  const int lane = t.lane;
-  const int b = a.body ? a.body[t.i] : 0;
-  const float4 Ui = a.lat_up[t.i];  // (u'_i, P_i)
-  const float rho_i = a.lat_f[t.i].x;
-  const bool interior = __all_sync(kFull, a.lat_int[t.i >> 5] != 0);
-  const uint32_t lmask = 1u << lane;
-  constexpr int S = LatFam<DIM, Q>::S;
-  float f[3] = {0.0f, 0.0f, 0.0f};
-  auto batch = [&](auto kc, auto intr, const int32_t* cs, uint4 w4) PD_AI {
-    constexpr int K = decltype(kc)::value;
-    constexpr bool INTR = decltype(intr)::value;
-    const uint32_t wd[4] = {w4.x, w4.y, w4.z, w4.w};
-    float4 Uj[4];
-    float rr[4];
-    static_for<0, 4>([&](auto uc) PD_AI {
-      constexpr int u = decltype(uc)::value;
-      if constexpr (K + u < S) {
-        const int32_t j = cs[u * 32];
-        Uj[u] = a.lat_up[j];
-        rr[u] = INTR ? 2.0f : rho_i + a.lat_rho[j];
-      }
-    });
-    static_for<0, 4>([&](auto uc) PD_AI {
-      constexpr int u = decltype(uc)::value;
-      if constexpr (K + u < S) {
-        using L = LatSlot<DIM, K + u>;
-        const float d = lat_dprime_k<DIM, K + u>(Uj[u], Ui);
-        float dr;
-        if constexpr (L::rlo == 0.0f) dr = d * L::rhi;
-        else dr = fmaf(d, L::rhi, d * L::rlo);
-        float cf = fmaf(rr[u], dr, Ui.w + Uj[u].w);
-        cf = (wd[u] & lmask) ? cf : 0.0f;
-        f[0] = lat_term<L::nx, false>(f[0], cf);
-        f[1] = lat_term<L::ny, false>(f[1], cf);
-        if constexpr (DIM == 3) f[2] = lat_term<L::nz, false>(f[2], cf);
-      }
-    });
-  };
-  auto body = [&](auto kc, const int32_t* cs, const uint32_t*, uint4 w4) PD_AI {
-    if (interior) batch(kc, std::true_type{}, cs, w4);
-    else batch(kc, std::false_type{}, cs, w4);
-  };
-  const bool ok = lat_rows_fixed<DIM, Q, NB, CH>(a, st, lane, body);
-  if (ok) {
-    const double C = a.bp[b].lat_C;
-    const double fd[3] = {C * (double)f[0], C * (double)f[1], C * (double)f[2]};
-    double4 u;
-    update(a, t.i, b, fd, disp, disp_out, u);
-    u32_out[t.i] = shadow_of(a, b, u);
   }
 }
 
@@ -2568,10 +2380,17 @@ __global__ void k_apply_bc(StepArgs a, double4* __restrict__ disp, int64_t step)
   a.vel[i] = make_double4(bp.rate * g.x, bp.rate * g.y, bp.rate * g.z, 0.0);
 }
 
-__global__ void k_shadow(StepArgs a, const double4* __restrict__ disp, float4* __restrict__ u32) {
+__global__ void k_shadow(StepArgs a, const double4* __restrict__ disp, float4* __restrict__ u32,
+                         float4* __restrict__ lo32) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= a.n_pad) return;
-  u32[i] = shadow_of(a, a.body ? a.body[i] : 0, disp[i]);
+  const int b = a.body ? a.body[i] : 0;
+  u32[i] = shadow_of(a, b, disp[i]);
+  if (lo32) {  // two-word shadow of the lattice layout (3D formula: z is zero in 2D)
+    float4 hi, lo;
+    shadow_lat_lo<3>(a.bp[b].lat_inv_h, disp[i], hi, lo);
+    lo32[i] = lo;
+  }
 }
 
 // max |u_k| over all particles and components (order-independent: max of non-negative doubles as
@@ -2727,66 +2546,49 @@ void launch_pass2(pd_ctx* c, const StepArgs& a, unsigned grid, int block, size_t
         <<<grid, block, sm, c->stream>>>(a, c->u32[c->cur], c->u32[c->cur ^ 1], c->disp[c->cur], c->disp[c->cur ^ 1]);
 }
 
-// The context's family is the one the specialized kernels are compiled for: every body's family
-// |n|^2 <= kLatFixedQ, every slice the same width (that family's prefix rounded up to 4 slots).
-template <int DIM>
-bool lat_fixed_family(const pd_ctx* c) {
-  return c->lat_fixed_opt && c->lat_q == kLatFixedQ && c->lat_wuni == LatFam<DIM, kLatFixedQ>::W;
-}
-
 // Lattice kernels: the ring of PD_OPT_LAT_STAGE (0: 3 x 16 slots, 1: 2 x 16, 2: 3 x 8, 3: 2 x 8).
-template <int DIM, bool WI, int NB, int CH>
+template <int DIM, bool WI, bool LO, int NB, int CH>
 void optin_lat_ring() {
   const int mx = 16 * StageGeom<NB, CH>::kWarpBytes;
-  cudaFuncSetAttribute(k_pass1_lat<DIM, WI, NB, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_pass2_lat<DIM, WI, NB, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-}
-template <int DIM, int NB, int CH>
-void optin_latq_ring() {
-  const int mx = 16 * StageGeom<NB, CH>::kWarpBytes;
-  cudaFuncSetAttribute(k_pass1_latq<DIM, kLatFixedQ, NB, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_pass2_latq<DIM, kLatFixedQ, NB, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_pass1_lat<DIM, WI, LO, NB, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_pass2_lat<DIM, WI, LO, NB, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
 }
 template <int DIM, bool WI>
 void optin_lat() {
-  optin_lat_ring<DIM, WI, 3, 16>();
-  optin_lat_ring<DIM, WI, 2, 16>();
-  optin_lat_ring<DIM, WI, 3, 8>();
-  optin_lat_ring<DIM, WI, 2, 8>();
-  if (!WI) {
-    optin_latq_ring<DIM, 3, 16>();
-    optin_latq_ring<DIM, 2, 16>();
-    optin_latq_ring<DIM, 3, 8>();
-    optin_latq_ring<DIM, 2, 8>();
-  }
+  optin_lat_ring<DIM, WI, false, 3, 16>();
+  optin_lat_ring<DIM, WI, false, 2, 16>();
+  optin_lat_ring<DIM, WI, false, 3, 8>();
+  optin_lat_ring<DIM, WI, false, 2, 8>();
+  optin_lat_ring<DIM, WI, true, 2, 16>();
+  optin_lat_ring<DIM, WI, true, 2, 8>();
 }
 
-template <int DIM, bool WI, int NB, int CH>
+template <int DIM, bool WI, bool LO, int NB, int CH>
 void launch_lat_ring(pd_ctx* c, const StepArgs& a, int pass, int write_theta, int block) {
   const unsigned g1 = (unsigned)((c->nslices * 32 + block - 1) / block);
   const size_t smb = (size_t)(block / 32) * StageGeom<NB, CH>::kWarpBytes;
-  if (!WI && lat_fixed_family<DIM>(c)) {
-    if (pass == 1)
-      k_pass1_latq<DIM, kLatFixedQ, NB, CH><<<g1, block, smb, c->stream>>>(a, c->u32[c->cur], c->disp[c->cur],
-                                                                          write_theta);
-    else
-      k_pass2_latq<DIM, kLatFixedQ, NB, CH><<<g1, block, smb, c->stream>>>(a, c->u32[c->cur], c->u32[c->cur ^ 1],
-                                                                          c->disp[c->cur], c->disp[c->cur ^ 1]);
-    return;
-  }
+  const float4* lo = LO ? c->u32lo[c->cur] : nullptr;
   if (pass == 1)
-    k_pass1_lat<DIM, WI, NB, CH><<<g1, block, smb, c->stream>>>(a, c->u32[c->cur], c->disp[c->cur], write_theta);
+    k_pass1_lat<DIM, WI, LO, NB, CH><<<g1, block, smb, c->stream>>>(a, c->u32[c->cur], lo, c->disp[c->cur],
+                                                                    write_theta);
   else
-    k_pass2_lat<DIM, WI, NB, CH><<<g1, block, smb, c->stream>>>(a, c->u32[c->cur], c->u32[c->cur ^ 1],
-                                                                c->disp[c->cur], c->disp[c->cur ^ 1]);
+    k_pass2_lat<DIM, WI, LO, NB, CH><<<g1, block, smb, c->stream>>>(
+        a, c->u32[c->cur], c->u32[c->cur ^ 1], lo, LO ? c->u32lo[c->cur ^ 1] : nullptr, c->disp[c->cur],
+        c->disp[c->cur ^ 1]);
 }
+// The two-word shadow's kernels exist for the two-chunk rings only (rings 0 and 2 map to 1 and 3).
 template <int DIM, bool WI>
 void launch_lat(pd_ctx* c, const StepArgs& a, int pass, int write_theta, int block) {
+  if (c->shadow_lo) {
+    if (c->lat_stage >= 2) launch_lat_ring<DIM, WI, true, 2, 8>(c, a, pass, write_theta, block);
+    else launch_lat_ring<DIM, WI, true, 2, 16>(c, a, pass, write_theta, block);
+    return;
+  }
   switch (c->lat_stage) {
-    case 1: launch_lat_ring<DIM, WI, 2, 16>(c, a, pass, write_theta, block); break;
-    case 2: launch_lat_ring<DIM, WI, 3, 8>(c, a, pass, write_theta, block); break;
-    case 3: launch_lat_ring<DIM, WI, 2, 8>(c, a, pass, write_theta, block); break;
-    default: launch_lat_ring<DIM, WI, 3, 16>(c, a, pass, write_theta, block); break;
+    case 1: launch_lat_ring<DIM, WI, false, 2, 16>(c, a, pass, write_theta, block); break;
+    case 2: launch_lat_ring<DIM, WI, false, 3, 8>(c, a, pass, write_theta, block); break;
+    case 3: launch_lat_ring<DIM, WI, false, 2, 8>(c, a, pass, write_theta, block); break;
+    default: launch_lat_ring<DIM, WI, false, 3, 16>(c, a, pass, write_theta, block); break;
   }
 }
 
@@ -2802,12 +2604,6 @@ void optin_staged() {
 }
 
 }  // namespace
-
-// The step kernels of a built lattice context are the ones compiled for its family (PD_OPT_LAT_FIXED).
-bool lattice_fixed_active(const pd_ctx* c) {
-  if (!c->lattice || c->prm[0].influence == PD_W_INV) return false;
-  return c->dim == 3 ? lat_fixed_family<3>(c) : lat_fixed_family<2>(c);
-}
 
 // Shared-memory opt-in of the staged kernels (up to 512 threads per block) on the current device;
 // called when a mixed context is built, outside any stream capture.
@@ -3227,10 +3023,24 @@ pd_status apply_bc_now(pd_ctx* c) {
   return PD_OK;
 }
 
+pd_status ensure_shadow_lo(pd_ctx* c) {
+  c->shadow_lo = false;
+  if (!c->lattice || !c->shadow_lo_opt) return PD_OK;
+  pd_status st;
+  for (int k = 0; k < 2; ++k)
+    if (!c->u32lo[k]) {
+      if ((st = alloc(c, &c->u32lo[k], (size_t)c->n_pad)) != PD_OK) return st;
+      PD_CUDA(cudaMemsetAsync(c->u32lo[k], 0, sizeof(float4) * c->n_pad, c->stream));
+    }
+  c->shadow_lo = true;
+  return sync_shadow(c);
+}
+
 pd_status sync_shadow(pd_ctx* c) {
   if (c->precision != PD_MIXED) return PD_OK;
   const int tb = 256;
-  k_shadow<<<(unsigned)((c->n_pad + tb - 1) / tb), tb, 0, c->stream>>>(make_args(c), c->disp[c->cur], c->u32[c->cur]);
+  k_shadow<<<(unsigned)((c->n_pad + tb - 1) / tb), tb, 0, c->stream>>>(make_args(c), c->disp[c->cur], c->u32[c->cur],
+                                                                        c->shadow_lo ? c->u32lo[c->cur] : nullptr);
   PD_CUDA(cudaGetLastError());
   return PD_OK;
 }

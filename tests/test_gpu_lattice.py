@@ -7,9 +7,8 @@ bodies that are not lattices keep the general layout; the lattice kernels follow
 the mixed form's stated bounds and decide every bond as FP64 does on their own state (validation
 mode, Eq 1.30), on 2D and 3D bodies with breaking, on a batch of uneven plates, and on the
 benchmark's 1M-particle block through its first 400 steps; graph chunks equal eager launches and a
-batch equals its bodies run one by one, bit for bit; the kernels compiled for the family
-|n|^2 <= 9 (PD_OPT_LAT_FIXED, each slot's direction a constant of the code) equal the table-driven
-kernels bit for bit.
+batch equals its bodies run one by one, bit for bit.  The same holds with the two-word shadow
+(PD_OPT_SHADOW_LO), which in addition follows the FP64 oracle more closely than one word.
 """
 import numpy as np
 import pytest
@@ -84,8 +83,9 @@ def test_non_lattice_bodies_keep_the_general_layout():
     B.pd_destroy(h)
 
 
+@pytest.mark.parametrize("lo", [0, 1])
 @pytest.mark.parametrize("case", ["cracked_plate", "notched_block", "plane_strain"])
-def test_lattice_decisions_equal_fp64_and_follow_the_oracle(case):
+def test_lattice_decisions_equal_fp64_and_follow_the_oracle(case, lo):
     """Breaking runs: zero decisions differing from FP64 on the run's own state (validation mode),
     with the lattice and with the general mixed kernels.  The trajectory is held to the FP64 oracle
     (rel-L2(u) <= 1e-5, as the mixed form's stated bound of configuration 1 over its first 100
@@ -96,9 +96,11 @@ def test_lattice_decisions_equal_fp64_and_follow_the_oracle(case):
     w = CASES[case]()
     s0 = s0_of(w)
     ref = oracle_for(w, s0)
-    sims = {lat: _mixed(w, s0, lat) for lat in (1, 0)}
+    sims = {lat: _mixed(w, s0, lat) for lat in ((1, 0) if not lo else (1,))}
     for sim in sims.values():
         sim.set_option(B.PD_OPT_VALIDATE, 1)
+        sim.set_option(B.PD_OPT_SHADOW_LO, lo)
+        assert sim.get_option(B.PD_OPT_SHADOW_LO) == (lo if sim.get_option(B.PD_OPT_LATTICE) else 0)
     compared, done = 0, 0
     while done < w.nsteps:
         margins, _ = ref.step(25)
@@ -197,48 +199,55 @@ def test_lattice_benchmark_block_validation_first_400_steps():
     assert st["broken_bonds"] > 0 and st["validate_mismatches"] == 0
 
 
-@pytest.mark.parametrize("case,rings", [("cracked_plate", (0,)), ("plane_strain", (0,)),
-                                        ("notched_block", (0, 1, 2, 3))])
-def test_fixed_family_kernels_equal_the_table_kernels(case, rings):
-    """Breaking runs in validation mode with the kernels compiled for the family (every staging
-    ring for the 3D block) and with the table-driven ones: displacements, velocities, dilatations,
-    bond status and every counter bitwise equal.  The operations the compiled kernels leave out are
-    exact (products by 0 and +-1, additions of zero), so nothing else may differ."""
-    w = CASES[case]()
-    s0 = s0_of(w)
-
-    def run(fixed, ring):
-        sim = Simulation(w, s0=s0, precision=PD_MIXED)
-        sim.set_option(B.PD_OPT_LAT_FIXED, fixed)
-        sim.set_option(B.PD_OPT_LAT_STAGE, ring)
-        assert sim.get_option(B.PD_OPT_LAT_FIXED) == fixed
-        sim.set_option(B.PD_OPT_VALIDATE, 1)
-        sim.step(w.nsteps)
-        u, v, th = sim.state()
-        st = sim.stats()
-        intact = sim.neighbors()[2]
+def test_two_word_shadow_config1_and_bitwise_properties():
+    """PD_OPT_SHADOW_LO on configuration 1: the stated bounds hold and the error is no larger than
+    with one word; set mid-run it takes effect from the current state; graph chunks and a batch
+    equal eager runs and separate bodies bit for bit; off again, it reports 0."""
+    w = W.config1()
+    errs = {}
+    for lo in (0, 1):
+        sim = Simulation(w, s0=0.0, precision=PD_MIXED, shadow_lo=lo)
+        assert sim.get_option(B.PD_OPT_SHADOW_LO) == lo
+        ref = oracle_for(w, 0.0)
+        e = []
+        for _ in range(10):
+            ref.step(100)
+            sim.step(100)
+            e.append(rel(sim.state()[0], ref.u))
         sim.close()
-        return u, v, th, intact, {k: st[k] for k in ("broken_bonds", "band_rechecks", "validate_mismatches")}
-
-    ref = run(0, 0)
-    assert ref[4]["broken_bonds"] > 0 and ref[4]["validate_mismatches"] == 0
-    for ring in rings:
-        got = run(1, ring)
-        for a, b, name in zip(got[:4], ref[:4], ("u", "v", "theta", "status")):
-            assert np.array_equal(a, b), (case, ring, name)
-        assert got[4] == ref[4], (case, ring)
-
-
-def test_fixed_family_kernels_only_for_their_family():
-    """Other horizons, w = delta / |xi| and the general layout keep the table-driven kernels."""
-    for w, kw, expect in ((CASES["ratio_4"](), {}, 0), (CASES["notched_block"](), {}, 1),
-                          (CASES["notched_block"](), {"influence": B.PD_W_INV}, 0)):
-        sim = Simulation(w, s0=0.0, precision=PD_MIXED, **kw)
-        assert sim.get_option(B.PD_OPT_LATTICE) == 1
-        assert sim.get_option(B.PD_OPT_LAT_FIXED) == expect
-        sim.step(5)
+        errs[lo] = e
+    print("config1 rel-L2(u), one word / two words:", ["%.2e" % x for x in errs[0]], ["%.2e" % x for x in errs[1]])
+    assert errs[1][0] <= 2e-5 and max(errs[1]) <= 1e-4
+    assert max(errs[1]) <= max(errs[0])
+    # graph chunks, eager, and the option switched on after 100 eager steps of the same run
+    cw = CASES["cracked_plate"]()
+    s0 = s0_of(cw)
+    res = []
+    for chunk, late in ((0, False), (100, False), (0, True)):
+        sim = Simulation(cw, s0=s0, precision=PD_MIXED, graph_chunk=chunk, shadow_lo=0 if late else 1)
+        if late:
+            sim.step(100)
+            sim.set_option(B.PD_OPT_SHADOW_LO, 1)
+            sim.step(150)
+        else:
+            sim.step(250)
+        res.append((sim.state()[0], sim.neighbors()[2]))
+        sim.set_option(B.PD_OPT_SHADOW_LO, 0)
+        assert sim.get_option(B.PD_OPT_SHADOW_LO) == 0
         sim.close()
-    w = CASES["cracked_plate"]()
-    sim = Simulation(w, s0=0.0, precision=PD_MIXED, lattice=0)
-    assert sim.get_option(B.PD_OPT_LAT_FIXED) == 0
-    sim.close()
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+    assert not np.array_equal(res[0][0], res[2][0])  # the first 100 steps ran with one word
+    bw = W.plate_batch(nplates=4, seed=6, side_lo=20, side_hi=50)
+    s0s = [s0_of(b) for b in bw.bodies]
+    bs = BatchSimulation(bw, s0s, precision=PD_MIXED)
+    bs.set_option(B.PD_OPT_SHADOW_LO, 1)
+    assert bs.get_option(B.PD_OPT_SHADOW_LO) == 1
+    bs.step(120)
+    ub = bs.state()[0]
+    bs.close()
+    for k, b in enumerate(bw.bodies):
+        sim = Simulation(b, s0=s0s[k], precision=PD_MIXED, shadow_lo=1)
+        sim.step(120)
+        assert np.array_equal(sim.state()[0], ub[:, bw.offsets[k]:bw.offsets[k + 1]]), k
+        sim.close()
+

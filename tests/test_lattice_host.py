@@ -39,6 +39,28 @@ extern "C" int table(int dim, int* out, int cap) {
   return (int)t.size();
 }
 extern "C" int prefix(int dim, int q) { return lattice_prefix(dim, q); }
+// d' = n.(u_j - u_i) / h in FP32 from one-word (lo = 0) or two-word (lo = 1) shadows of u / h
+extern "C" void dprime(long m, const int* n, const double* ui, const double* uj, double h, int lo, float* out) {
+  for (long k = 0; k < m; ++k) {
+    float a[3], b[3], al[3], bl[3];
+    for (int c = 0; c < 3; ++c) {
+      const double va = ui[3 * k + c] / h, vb = uj[3 * k + c] / h;
+      a[c] = (float)va; b[c] = (float)vb;
+      al[c] = (float)(va - (double)a[c]); bl[c] = (float)(vb - (double)b[c]);
+    }
+    const float nx = (float)n[3 * k], ny = (float)n[3 * k + 1], nz = (float)n[3 * k + 2];
+    out[k] = lo ? lat_dprime_d<3>(nx, ny, nz, lat_delta_lo(b[0], bl[0], a[0], al[0]),
+                                  lat_delta_lo(b[1], bl[1], a[1], al[1]), lat_delta_lo(b[2], bl[2], a[2], al[2]))
+                : lat_dprime<3>(nx, ny, nz, b[0], b[1], b[2], a[0], a[1], a[2]);
+  }
+}
+// both forms of the screen on the same FP32 operands: 1 = settled as intact
+extern "C" void screens(long m, const float* g, const float* kf, const float* uj, const float* scr, int* a, int* b) {
+  for (long k = 0; k < m; ++k) {
+    a[k] = lat_screen_intact(g[k], kf[k], uj[k], scr[k]) ? 1 : 0;
+    b[k] = lat_screen_value(g[k], kf[k], uj[k], scr[k]) < 0.0f ? 1 : 0;
+  }
+}
 // the compile-time table and prefix (the specialized kernels' directions)
 extern "C" int table_c(int dim, int k, int c) {
   constexpr LatTable<3> t3 = lattice_table<3>();
@@ -48,23 +70,31 @@ extern "C" int table_c(int dim, int k, int c) {
 }
 extern "C" int prefix_c(int dim, int q) { return dim == 3 ? lattice_prefix_c<3>(q) : lattice_prefix_c<2>(q); }
 // per bond: xi (3, FP64 positions' difference), n (3), ui (3), uj (3) in metres, h, s0;
-// band_safety, n1, qmax; out: screen (1 = settled intact), code (0, 1, 2)
+// band_safety, n1, qmax, lo (1: two-word shadow hi + lo); out: screen (1 = settled intact), code (0, 1, 2)
 extern "C" void decide(long m, const double* xi, const int* n, const double* ui, const double* uj, const double* h,
-                       const double* s0, double bc, int n1, int qmax, int* screen, int* code) {
+                       const double* s0, double bc, int n1, int qmax, int lo, int* screen, int* code) {
   for (long k = 0; k < m; ++k) {
     const double ih = 1.0 / h[k];
-    float a[3], b[3];
-    for (int c = 0; c < 3; ++c) { a[c] = (float)(ui[3 * k + c] * ih); b[c] = (float)(uj[3 * k + c] * ih); }
+    float a[3], b[3], al[3], bl[3];
+    for (int c = 0; c < 3; ++c) {
+      const double va = ui[3 * k + c] * ih, vb = uj[3 * k + c] * ih;
+      a[c] = (float)va;
+      b[c] = (float)vb;
+      al[c] = (float)(va - (double)a[c]);
+      bl[c] = (float)(vb - (double)b[c]);
+    }
     const float Ui = fmaxf(fabsf(a[0]), fmaxf(fabsf(a[1]), fabsf(a[2])));
     const float Uj = fmaxf(fabsf(b[0]), fmaxf(fabsf(b[1]), fabsf(b[2])));
     const float nx = (float)n[3 * k], ny = (float)n[3 * k + 1], nz = (float)n[3 * k + 2];
     const float q = nx * nx + ny * ny + nz * nz;
-    const float d = lat_dprime<3>(nx, ny, nz, b[0], b[1], b[2], a[0], a[1], a[2]);
+    const float d = lo ? lat_dprime_d<3>(nx, ny, nz, lat_delta_lo(b[0], bl[0], a[0], al[0]),
+                                         lat_delta_lo(b[1], bl[1], a[1], al[1]), lat_delta_lo(b[2], bl[2], a[2], al[2]))
+                       : lat_dprime<3>(nx, ny, nz, b[0], b[1], b[2], a[0], a[1], a[2]);
     const float s0f = (float)s0[k];
     const float g = lat_g(d, s0f, q);
     const LatBand L = lattice_band(bc, s0[k], n1, qmax);
     const float scr = fmaf(L.Kfast, Ui, L.Kcfast);
-    screen[k] = lat_screen_intact(g, L.Kfast, Uj, scr) ? 1 : 0;
+    screen[k] = lat_screen_value(g, L.Kfast, Uj, scr) < 0.0f ? 1 : 0;  // the kernel's form of the screen
     code[k] = lat_code(g, Ui, Uj, s0f, q, L.Kf, L.sq, L.eps_c, L.s0n1);
   }
 }
@@ -85,9 +115,11 @@ def so():
     L = ctypes.CDLL(lib)
     L.table.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_int]
     L.prefix.argtypes = [ctypes.c_int, ctypes.c_int]
+    L.screens.argtypes = [ctypes.c_long] + [ctypes.c_void_p] * 6
+    L.dprime.argtypes = [ctypes.c_long] + [ctypes.c_void_p] * 3 + [ctypes.c_double, ctypes.c_int, ctypes.c_void_p]
     L.prefix_c.argtypes = [ctypes.c_int, ctypes.c_int]
     L.table_c.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
-    L.decide.argtypes = [ctypes.c_long] + [ctypes.c_void_p] * 6 + [ctypes.c_double, ctypes.c_int, ctypes.c_int,
+    L.decide.argtypes = [ctypes.c_long] + [ctypes.c_void_p] * 6 + [ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                                     ctypes.c_void_p, ctypes.c_void_p]
     yield L
     shutil.rmtree(tmp, ignore_errors=True)
@@ -168,17 +200,17 @@ def exact_margin(xi, ui, uj, s0):
     return out
 
 
-def run_case(so, xi, n, ui, uj, h, s0, bc, n1, qmax):
+def run_case(so, xi, n, ui, uj, h, s0, bc, n1, qmax, lo=0):
     m = len(s0)
     screen = np.zeros(m, dtype=np.int32)
     code = np.zeros(m, dtype=np.int32)
     arrs = [np.ascontiguousarray(a) for a in (xi, n, ui, uj, h, s0)]
-    so.decide(m, *[a.ctypes.data for a in arrs], bc, n1, qmax, screen.ctypes.data, code.ctypes.data)
+    so.decide(m, *[a.ctypes.data for a in arrs], bc, n1, qmax, lo, screen.ctypes.data, code.ctypes.data)
     return screen, code
 
 
-def violations(so, sample, bc, n1, qmax):
-    screen, code = run_case(so, *sample, bc, n1, qmax)
+def violations(so, sample, bc, n1, qmax, lo=0):
+    screen, code = run_case(so, *sample, bc, n1, qmax, lo)
     xi, n, ui, uj, h, s0 = sample
     bad = 0
     counts = dict(screened=0, fp32_broken=0, fp32_intact=0, fp64=0)
@@ -210,13 +242,14 @@ CASES = [
 
 @pytest.mark.parametrize("h,umag,s0lo,s0hi", CASES)
 @pytest.mark.parametrize("bc", [1.05, 4.0])
-def test_fp32_decisions_match_every_fp64_evaluation(so, h, umag, s0lo, s0hi, bc):
+@pytest.mark.parametrize("lo", [0, 1])
+def test_fp32_decisions_match_every_fp64_evaluation(so, h, umag, s0lo, s0hi, bc, lo):
     t = get_table(so, 3)
     fam = t[t[:, 3] <= 9]  # delta = 3.015 h
     rng = np.random.default_rng(int(h * 1e9) % 1000 + int(umag * 10) + int(bc * 7))
     sample = near_threshold(rng, 1500, h, umag, s0lo, s0hi, fam[:, :3])
     n1 = int(np.abs(fam[:, :3]).sum(1).max())
-    bad, counts = violations(so, sample, bc, n1, 9)
+    bad, counts = violations(so, sample, bc, n1, 9, lo)
     assert bad == 0, counts
     # the FP32 path decides bonds on both sides and passes the closest to FP64
     assert counts["fp32_intact"] > 0 and counts["fp32_broken"] > 0 and counts["fp64"] > 0, counts
@@ -253,3 +286,58 @@ def test_nonfinite_extension_goes_to_fp64(so):
         screen, code = run_case(so, xi, n, np.zeros((1, 3)), np.array([[bad, 0.0, 0.0]]), np.array([1e-3]),
                                 np.array([1e-3]), 4.0, 5, 9)
         assert screen[0] == 0 and code[0] == 2
+
+
+def test_screen_value_form_is_the_screen(so):
+    """The kernels test the screen as lat_screen_value < 0 (one addition, the body's 'cannot break'
+    folded in as scr_i = -inf); it must settle exactly the bonds lat_screen_intact settles:
+    operands over many magnitudes, sums that cancel to the last bit, subnormals, infinities, NaN."""
+    rng = np.random.default_rng(17)
+    m = 400000
+    kf = (10.0 ** rng.uniform(-8, 0, m)).astype(np.float32)
+    uj = (10.0 ** rng.uniform(-10, 3, m)).astype(np.float32)
+    g = (rng.choice([-1.0, 1.0], m) * 10.0 ** rng.uniform(-12, 2, m)).astype(np.float32)
+    # fmaf(Kfast, U_j, g) to within an ulp (the product is exact in FP64)
+    a = (kf.astype(np.float64) * uj.astype(np.float64) + g.astype(np.float64)).astype(np.float32)
+    scr = (rng.choice([-1.0, 1.0], m) * 10.0 ** rng.uniform(-12, 2, m)).astype(np.float32)
+    # a third of the samples put scr_i within a few ulps of -fmaf(Kfast, U_j, g)
+    near = rng.random(m) < 0.35
+    scr[near] = np.nextafter(-a[near], np.float32(np.inf) * rng.choice([-1, 1], near.sum()))
+    exact = rng.random(m) < 0.05
+    scr[exact] = -a[exact]
+    tiny = np.array([1e-45, -1e-45, 1e-40, -1e-40, 0.0, -0.0], dtype=np.float32)
+    spec = np.array([np.inf, -np.inf, np.nan, 3.4e38, -3.4e38], dtype=np.float32)
+    extra = np.array(np.meshgrid(np.concatenate([tiny, spec]), np.concatenate([tiny, spec]))).reshape(2, -1)
+    g = np.concatenate([g, extra[0], extra[0]]).astype(np.float32)
+    scr = np.concatenate([scr, extra[1], np.full(extra.shape[1], -np.inf, np.float32)]).astype(np.float32)
+    kf = np.concatenate([kf, np.full(2 * extra.shape[1], 1e-6, np.float32)]).astype(np.float32)
+    uj = np.concatenate([uj, np.full(2 * extra.shape[1], 0.5, np.float32)]).astype(np.float32)
+    n = g.size
+    r1, r2 = np.zeros(n, np.int32), np.zeros(n, np.int32)
+    so.screens(n, g.ctypes.data, kf.ctypes.data, uj.ctypes.data, scr.ctypes.data, r1.ctypes.data, r2.ctypes.data)
+    assert np.array_equal(r1, r2), np.flatnonzero(r1 != r2)[:10]
+    assert 0 < r1.sum() < n
+
+
+def test_two_word_shadow_rounds_relative_to_the_difference(so):
+    """A displacement of 0.2 h carried by bonds whose extension is ~1e-3 h (a twisted body far from
+    its axis): one FP32 word per component rounds n.(u'_j - u'_i) to ~eps |n|_1 |u'| (about 1e-5
+    of the extension), the two-word shadow to ~eps of the extension itself.  Exact values from
+    rational arithmetic on the FP64 inputs."""
+    rng = np.random.default_rng(31)
+    m, h = 4000, 1e-3
+    t = get_table(so, 3)
+    n = np.ascontiguousarray(t[rng.integers(0, 122, m), :3]).astype(np.int32)
+    base = rng.uniform(-0.2, 0.2, (m, 3)) * h
+    ui = np.ascontiguousarray(base)
+    uj = np.ascontiguousarray(base + rng.normal(0, 1e-3, (m, 3)) * h)
+    exact = np.array([float(sum(Fr(int(n[k, c])) * (Fr(uj[k, c]) - Fr(ui[k, c])) for c in range(3)) / Fr(h))
+                      for k in range(m)])
+    err = {}
+    for lo in (0, 1):
+        out = np.zeros(m, dtype=np.float32)
+        so.dprime(m, n.ctypes.data, ui.ctypes.data, uj.ctypes.data, h, lo, out.ctypes.data)
+        err[lo] = np.abs(out.astype(np.float64) - exact) / np.abs(exact).clip(1e-30)
+    assert np.median(err[1]) < 1e-6 and np.median(err[0]) > 100 * np.median(err[1]), (np.median(err[0]),
+                                                                                        np.median(err[1]))
+
