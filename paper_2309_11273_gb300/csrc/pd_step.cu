@@ -1769,6 +1769,13 @@ __device__ __forceinline__ float4 shadow_lat(double inv_h, const double4& u) {
   return make_float4(x, y, z, fmaxf(fabsf(x), fmaxf(fabsf(y), fabsf(z))));
 }
 
+// lat_dprime with the x and y differences as one packed FP32 pair addition (the same roundings).
+template <int DIM>
+__device__ __forceinline__ float lat_dprime_pair(const float4& dn, const float4& uj, const float4& nui) {
+  const float2 dxy = __fadd2_rn(make_float2(uj.x, uj.y), make_float2(nui.x, nui.y));
+  return lat_dprime_d<DIM>(dn.x, dn.y, dn.z, dxy.x, dxy.y, uj.z + nui.z);
+}
+
 // The two-word shadow: hi as shadow_lat, lo = u / h - hi rounded to FP32 (the subtraction is exact in
 // FP64), so that hi + lo carries u / h to about 2^-48 of its size.
 template <int DIM>
@@ -1844,13 +1851,16 @@ __global__ void __launch_bounds__(512) k_pass1_lat(StepArgs a, const float4* __r
   const bool can_break = bp.breaks != 0;
   const float4 Ui = u32[t.i];
   const float4 Li = LO ? lo32[t.i] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  const float4 nUi = make_float4(-Ui.x, -Ui.y, -Ui.z, 0.0f);  // u'_j - u'_i as u'_j + (-u'_i), exactly
   const float Kfast = bp.lat_Kfast;
-  // the screen's bound less its U_j term (pd_lattice.h); -inf settles every bond of a body without
-  // failure, so that the per-slot test needs no separate flag
-  const float scr_i = can_break ? fmaf(Kfast, Ui.w, bp.lat_Kcfast) : -INFINITY;
+  const bool checking = a.check != 0;  // warp-uniform (can_break is per body: per lane in a batch)
+  // the screen's bound less its U_j term (pd_lattice.h); -inf settles every bond with a finite
+  // extension, for a body without failure and in a pass that checks nothing, so that the per-slot
+  // test needs no flag (a NaN still reaches the slow path, which decides nothing unless checking)
+  const float scr_i = (can_break && checking) ? fmaf(Kfast, Ui.w, bp.lat_Kcfast) : -INFINITY;
+  const bool every = checking && a.validate != 0;  // validation: every batch takes the slow path
   uint32_t* __restrict__ bw = a.bits + (t.base >> 5);
   float acc = 0.0f;
-  const bool checking = a.check != 0;  // warp-uniform (can_break is per body: per lane in a batch)
   const uint32_t lmask = 1u << lane;
   // one batch of U = 4 slots starting at slot k: the extensions of the intact bonds (0 for the
   // others) and the screen first, the failure decisions next (the rare slow path zeroes the terms
@@ -1874,19 +1884,19 @@ __global__ void __launch_bounds__(512) k_pass1_lat(StepArgs a, const float4* __r
       const float d =
           LO ? lat_dprime_d<DIM>(dn.x, dn.y, dn.z, lat_delta_lo(Uj[u].x, Lj[u].x, Ui.x, Li.x),
                                  lat_delta_lo(Uj[u].y, Lj[u].y, Ui.y, Li.y), lat_delta_lo(Uj[u].z, Lj[u].z, Ui.z, Li.z))
-             : lat_dprime<DIM>(dn.x, dn.y, dn.z, Uj[u].x, Uj[u].y, Uj[u].z, Ui.x, Ui.y, Ui.z);
+             : lat_dprime_pair<DIM>(dn, Uj[u], nUi);
       const bool in = (wd[u] & lmask) != 0u;
       dm[u] = in ? d : 0.0f;
-      if (checking) near |= in & !(lat_screen_value(lat_g(d, s0f, dn.w), Kfast, Uj[u].w, scr_i) < 0.0f);
+      near |= in & !(lat_screen_value(lat_g(d, s0f, dn.w), Kfast, Uj[u].w, scr_i) < 0.0f);
     }
-    if (checking && (__any_sync(kFull, near) | (a.validate != 0))) {
+    if (__any_sync(kFull, near) | every) {
       // full band for the bonds the screen did not settle, FP64 inside it; the neighbour index and
       // its |u'| are reloaded (staged chunk, L1) so that little stays live across this block
       unsigned brk = 0u;
 #pragma unroll 1
       for (int u = 0; u < U; ++u) {
         int code = 0;
-        if (can_break && (ws[u] & lmask) != 0u) {
+        if (checking && can_break && (ws[u] & lmask) != 0u) {
           const int32_t jj = cs[u * 32];
           const float Ujw = u32[jj].w;
           const float q = lat_dir<DIM>(k + u).w;
@@ -1943,6 +1953,7 @@ __global__ void __launch_bounds__(512) k_pass2_lat(StepArgs a, const float4* __r
   const int b = a.body ? a.body[t.i] : 0;
   const float4 Ui = a.lat_up[t.i];  // (u'_i, P_i)
   const float4 Li = LO ? lo32[t.i] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  const float4 nUi = make_float4(-Ui.x, -Ui.y, -Ui.z, 0.0f);  // u'_j - u'_i as u'_j + (-u'_i), exactly
   const float rho_i = a.lat_f[t.i].x;
   // every particle around this slice (lanes and neighbours) has N_j = N_ref: N_ref/N_i + N_ref/N_j
   // = 2 exactly, so the per-neighbour factor is not gathered (the result is bitwise the same); the
