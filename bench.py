@@ -481,7 +481,7 @@ def mixed_roofline(prof, a1, a2, bytes1, bytes2, hbm, hbm_note, staged, lattice=
             "step_frac": (bytes1 + bytes2) / ((prof["pass1_ms"] + prof["pass2_ms"]) * 1e-3) / 1e9 / hbm}
 
 
-def mixed_error_on_workload(w, s0, stream, dev, nsteps):
+def mixed_error_on_workload(w, s0, stream, dev, nsteps, shadow_lo=0):
     """The mixed form against the plain FP64 GPU path on the benchmark's own workload: both run
     nsteps from the same initial state (the FP64 path is held to 1e-12 of the oracle by the parity
     tests); rel-L2(u), the largest per-particle error, and the directed bonds whose status differs,
@@ -491,7 +491,8 @@ def mixed_error_on_workload(w, s0, stream, dev, nsteps):
     from paper_2309_11273_gb300 import _binding as B
     res = {}
     for prec in (PD_FP64, PD_MIXED):
-        sim = Simulation(w, s0=s0, precision=prec, stream=stream.cuda_stream, device=dev)
+        sim = Simulation(w, s0=s0, precision=prec, stream=stream.cuda_stream, device=dev,
+                         shadow_lo=shadow_lo if prec == PD_MIXED else None)
         if prec == PD_MIXED:
             sim.set_option(B.PD_OPT_VALIDATE, 1)
         sim.step(nsteps)
@@ -580,6 +581,24 @@ def run_forms(args, stream, dev, world, fp64_value, nb, hbm, hbm_note, fp64_tflo
                     "mapping": {"block": mmap[0], "split": mmap[1], "lat_stage": lat_stage},
                     "layout": "lattice" if lattice else "general",
                     "roofline": mixed_roofline(prof, a1, a2, bytes1, bytes2, hbm, hbm_note, staged, lattice)}
+    # the same with the two-word FP32 shadow (PD_OPT_SHADOW_LO): each bond's relative displacement
+    # rounded relative to itself rather than to |u|
+    sim = Simulation(w, s0=s0, precision=PD_MIXED, stream=stream.cuda_stream, device=dev, shadow_lo=1)
+    lmap = B.pd_autotune(sim.h, 5)
+    sim.step(args.warmup)
+    ms = max_over_ranks(timed(sim, stream, steps, world), world)
+    lval = world * nb * steps / (ms * 1e-3)
+    prof = profiled(sim, 50)
+    lo_on = sim.get_option(B.PD_OPT_SHADOW_LO) == 1
+    sim.close()
+    out["mixed"]["shadow_lo"] = {
+        "value": lval, "unit": UNIT, "speedup_vs_fp64": lval / fp64_value, "ms_per_step": ms / steps,
+        "active": lo_on, "mapping": {"block": lmap[0], "split": lmap[1]},
+        "pass1_ms": prof["pass1_ms"], "pass2_ms": prof["pass2_ms"],
+        "step_frac": (bytes1 + bytes2 + 48 * w.n) / ((prof["pass1_ms"] + prof["pass2_ms"]) * 1e-3) / 1e9 / hbm,
+        "algorithmic": "the one-word step's bytes + 48 B per particle (the lo words read by both passes and "
+                       "written by pass 2)",
+        "stated_error": mixed_error_on_workload(w, s0, stream, dev, 600, shadow_lo=1)}
     # geometrically nonlinear bonds (Eqs 1.10, 1.13, 1.14) in FP64 on the same workload
     sim = Simulation(w, s0=s0, precision=PD_FP64, kinematics=PD_NONLINEAR, stream=stream.cuda_stream, device=dev)
     nmap = B.pd_autotune(sim.h, 2)
