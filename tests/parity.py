@@ -90,3 +90,33 @@ def assert_fp64_close(errs, tol=1e-12, what=""):
     """Every measure in ``errs`` (from ``compare``) within tol."""
     bad = {k: v for k, v in errs.items() if k in ("ru", "rv", "eu", "ev", "et", "rt") and not (v <= tol)}
     assert not bad, (what, bad)
+
+
+def rigid_split(err, P):
+    """Split an error field into its best-fit rigid motion and the rest.
+
+    err, P: (dim, n) arrays (displacement error, reference positions).  Least squares over the
+    translations and infinitesimal rotations about the centroid (3 fields in 2D, 6 in 3D).  Returns
+    (rigid, deformation): the L2 norms of the fitted rigid field and of the residual.  An internal
+    force field whose bond forces are exactly antisymmetric and parallel to the bond moves no rigid
+    mode; FP32 accumulation of those forces does (each particle's sum is rounded on its own), so on a
+    free body the mixed form's error splits into a rigid drift that grows with time and a deformation
+    error that measures the force arithmetic."""
+    err = np.asarray(err, dtype=np.float64)
+    P = np.asarray(P, dtype=np.float64)
+    dim, n = err.shape
+    X = P - P.mean(axis=1, keepdims=True)
+    cols = []
+    for a in range(dim):  # translations
+        c = np.zeros((dim, n))
+        c[a] = 1.0
+        cols.append(c)
+    for a, b in ((0, 1),) if dim == 2 else ((0, 1), (1, 2), (2, 0)):  # rotations in the (a, b) plane
+        c = np.zeros((dim, n))
+        c[a] = -X[b]
+        c[b] = X[a]
+        cols.append(c)
+    M = np.stack([c.reshape(-1) for c in cols], axis=1)
+    coef, *_ = np.linalg.lstsq(M, err.reshape(-1), rcond=None)
+    fit = M @ coef
+    return float(np.linalg.norm(fit)), float(np.linalg.norm(err.reshape(-1) - fit))
