@@ -82,6 +82,7 @@ void free_build(pd_ctx* c) {
   c->lat_rho = nullptr;
   c->lat_up = nullptr;
   c->lat_int = nullptr;
+  c->lat_umax = nullptr;
   c->lat_wuni = 0;
 }
 
@@ -946,7 +947,7 @@ pd_status pd_autotune(pd_ctx* c, int32_t trial_steps, int32_t* block_out, int32_
       c->skip_next_check = skip0;
       c->check_pending = pend0;
       // the two-word shadow from the restored displacements (the FP32 words are as saved)
-      return c->shadow_lo ? sync_shadow(c) : PD_OK;
+      return (c->shadow_lo || c->lattice) ? sync_shadow(c) : PD_OK;  // lattice: the shadow's bound too
     };
     c->profile = 0;
     c->graph_chunk = 0;

@@ -614,13 +614,16 @@ pd_status build_lattice(pd_ctx* c, BuildArgs& A, bool* done) {
   for (int64_t k = 0; k < n_pad; ++k) hr[k] = hf[k].x;
   if ((st = alloc(c, &c->lat_f, (size_t)n_pad)) != PD_OK || (st = alloc(c, &c->lat_rho, (size_t)n_pad)) != PD_OK ||
       (st = alloc(c, &c->lat_up, (size_t)n_pad)) != PD_OK ||
-      (st = alloc(c, &c->lat_int, (size_t)c->nslices)) != PD_OK) {
+      (st = alloc(c, &c->lat_int, (size_t)c->nslices)) != PD_OK ||
+      (st = alloc(c, &c->lat_umax, (size_t)2 * nb)) != PD_OK) {
     cleanup();
     return st;
   }
   e = cudaMemcpyAsync(c->lat_f, hf.data(), sizeof(float2) * n_pad, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->lat_rho, hr.data(), sizeof(float) * n_pad, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->lat_up, 0, sizeof(float4) * n_pad, s);
+  // 0x7f7f7f7f = 3.4e38: a bound above any shadow until the first shadow write replaces it
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->lat_umax, 0x7f, sizeof(unsigned) * 2 * nb, s);
   if (e == cudaSuccess) {
     k_lat_interior<<<gb, tb, 0, s>>>(n_pad, c->slice_ptr, c->col, c->lat_f, c->lat_int);
     e = cudaGetLastError();
@@ -1164,6 +1167,7 @@ pd_status build_neighbors(pd_ctx* c, const pd_crack* cracks, int32_t ncracks) {
     c->lat_rho = nullptr;
     c->lat_up = nullptr;
     c->lat_int = nullptr;
+    c->lat_umax = nullptr;
     c->lat_wuni = 0;
     c->u32lo[0] = c->u32lo[1] = nullptr;
     c->shadow_lo = false;

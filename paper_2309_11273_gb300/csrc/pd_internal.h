@@ -122,6 +122,12 @@ struct StepArgs {
   float4* lat_up;          // lattice layout: per particle (u'_i, P_i), written by pass 1 for pass 2
   const uint8_t* lat_int;  // lattice layout: per slice, 1 if N_j = N_ref for its lanes and neighbours
   int lat_wuni;            // lattice layout: the common slice width, or 0 if the widths differ
+  // lattice layout: per body, an upper bound of |u'|_inf over the current shadow (float bits; the
+  // failure screen's neighbour term), and the same for the shadow the step writes (reset by pass 1,
+  // raised by every kernel that writes that shadow)
+  const unsigned* lat_umax;
+  unsigned* lat_umax_next;
+  int nbody;
 };
 
 struct KernelTimes {
@@ -187,6 +193,7 @@ struct pd_ctx {
   int4* pos32 = nullptr;
   float4* u32[2] = {nullptr, nullptr};
   float4* u32lo[2] = {nullptr, nullptr};  // lattice layout, two-word shadow: the lo words of u32
+  unsigned* lat_umax = nullptr;           // lattice layout: [2][nbodies] bounds of |u'|_inf per shadow buffer
   int shadow_lo_opt = 0;                  // PD_OPT_SHADOW_LO as set
   bool shadow_lo = false;                 // the lattice kernels run with the two-word shadow
   float2* thm32 = nullptr;

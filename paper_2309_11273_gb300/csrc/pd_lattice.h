@@ -197,6 +197,25 @@ PD_LHD bool lat_screen_intact(float g, float Kfast, float Uj, float scr_i) { ret
 // an operand is NaN.  scr_i = -inf settles every bond with a finite value (a body without failure).
 PD_LHD float lat_screen_value(float g, float Kfast, float Uj, float scr_i) { return fmaf(Kfast, Uj, g) + scr_i; }
 
+// The per-body screen of the kernels: the neighbour's |u'_j|_inf replaced by an upper bound U_max of
+// |u'|_inf over the particle's body (the largest the shadow holds), so that the screen's per-particle
+// part scr_c = fmaf(Kfast, U_i + U_max', Kcfast) is formed once and a batch of slots is settled as
+// intact when (max over its slots of g) + scr_c < 0.  U_max' = U_max (1 + 2^-20): with U_i <= U_max
+// it keeps the rounded U_i + U_max' above U_i + U_j for every neighbour j, with a margin far above
+// the roundings of the sum and of the FMA, so the screen stays at least as wide as the
+// per-neighbour one.  The max propagates NaN (a batch with a NaN extension is not settled).
+PD_LHD float lat_umax_bound(float umax) { return umax * (1.0f + 0x1p-20f); }
+PD_LHD float lat_screen_part(float Kfast, float Ui, float umax_b, float Kcfast) { return fmaf(Kfast, Ui + umax_b, Kcfast); }
+PD_LHD float lat_max_nan(float a, float b) {
+#if defined(__CUDA_ARCH__)
+  float r;
+  asm("max.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+  return r;
+#else
+  return (a != a || b != b) ? NAN : (a > b ? a : b);
+#endif
+}
+
 // Full band: 0 intact, 1 broken (FP32 decision), 2 inside the band (decide in FP64).  A NaN g is
 // inside (both comparisons false).
 PD_LHD int lat_code(float g, float Ui, float Uj, float s0f, float q, float Kf, float sq, float eps_c,

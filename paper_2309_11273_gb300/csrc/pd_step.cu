@@ -1697,9 +1697,10 @@ __global__ void __launch_bounds__(512) k_pass2_mixed_staged(StepArgs a, const fl
 // of the body (such a shared rounding would shift every vibration frequency by the same amount and
 // grow as a phase error).  The failure check (Eq 1.30, d' >= s0 |n|^2) is decided in FP32 where its
 // rounding band (see BodyDev) cannot reach the threshold, and in FP64 from the master state
-// otherwise: a screen against the band with |n|^2 and |u'| bounded per body and per end settles
-// nearly every bond in two instructions; a warp with any bond the screen does not settle evaluates
-// the full band and re-decides the bonds inside it with the FP64 path's arithmetic.
+// otherwise: a screen against the band with |n|^2 bounded per body, |u'_i| per particle and |u'_j| by
+// the body's largest |u'| (raised by every kernel that writes the shadow) settles nearly every bond
+// with one FMA and one max per slot; a warp with any bond the screen does not settle evaluates the
+// full band and re-decides the bonds inside it with the FP64 path's arithmetic.
 // Sized to a multiple of 4: slice widths are rounded up to 4 slots, and the slots past the table
 // (unused, status 0) still index it.
 constexpr int kLatPad3 = (kLatDirs3 + 3) & ~3, kLatPad2 = (kLatDirs2 + 3) & ~3;
@@ -1723,6 +1724,13 @@ __device__ __forceinline__ float2 lat_rcp(int k) {
 template <int DIM>
 __device__ __forceinline__ float2 lat_wgt(int k) {
   return DIM == 3 ? c_latw3[k] : c_latw2[k];
+}
+// Entry k ^ 1 of the table is -entry k exactly (integer components), with the same |n|^2, 1 / |n|^2
+// and w', and a batch starts at a multiple of 4 slots: its four directions are two loaded entries
+// and their negations, the sign folded into the arithmetic that uses them (bitwise the same values
+// as loading all four).
+__device__ __forceinline__ float4 lat_twin(const float4& d, bool odd) {
+  return odd ? make_float4(-d.x, -d.y, -d.z, d.w) : d;
 }
 
 // The update of the lattice kernels (Eq 2.11 as update() computes it) with F_i / V_i = lat_C x the
@@ -1797,6 +1805,20 @@ __device__ __forceinline__ float4 shadow_of(const StepArgs& a, int b, const doub
   return make_float4((float)(u.x * sc), (float)(u.y * sc), (float)(u.z * sc), 0.0f);
 }
 
+// Raises the body's bound umax[b] to at least U (|u'|_inf of a shadow just written; non-negative
+// floats order as their bits): one atomic per warp when its particles share a body, else one per
+// lane.  All 32 lanes call it.  A NaN U raises the bound to NaN, which settles nothing.
+__device__ __forceinline__ void lat_raise_umax(unsigned* umax, int b, float U) {
+  const unsigned bits = __float_as_uint(U);
+  const int b0 = __shfl_sync(kFull, b, 0);
+  if (__all_sync(kFull, b == b0)) {
+    const unsigned m = __reduce_max_sync(kFull, bits);
+    if ((threadIdx.x & 31) == 0) atomicMax(umax + b0, m);
+  } else {
+    atomicMax(umax + b, bits);
+  }
+}
+
 // WI: influence function w = delta / |xi| (its per-direction factor w' = 1 / |n| multiplies each
 // bond's term in both sums); WI = false: w = 1.
 // The row loop of the lattice kernels, called twice in each kernel: with UNI, bounded by the
@@ -1841,6 +1863,8 @@ __global__ void __launch_bounds__(512) k_pass1_lat(StepArgs a, const float4* __r
   extern __shared__ __align__(128) unsigned char smem[];
   const SliceIdx t = slice_index<1>(a.n_pad, a.slice_ptr);
   if (write_theta && blockIdx.x == 0 && threadIdx.x == 0) *a.d_step += 1;
+  if (blockIdx.x == 0)  // the bound of the shadow that pass 2 writes next starts from zero
+    for (int k = threadIdx.x; k < a.nbody; k += blockDim.x) a.lat_umax_next[k] = 0u;
   if (!t.active) return;  // whole warps: the staging below is per warp
   auto st = stage_init<NB, CH>(smem, t, a);
   const int lane = t.lane;
@@ -1854,10 +1878,12 @@ __global__ void __launch_bounds__(512) k_pass1_lat(StepArgs a, const float4* __r
   const float4 nUi = make_float4(-Ui.x, -Ui.y, -Ui.z, 0.0f);  // u'_j - u'_i as u'_j + (-u'_i), exactly
   const float Kfast = bp.lat_Kfast;
   const bool checking = a.check != 0;  // warp-uniform (can_break is per body: per lane in a batch)
-  // the screen's bound less its U_j term (pd_lattice.h); -inf settles every bond with a finite
-  // extension, for a body without failure and in a pass that checks nothing, so that the per-slot
-  // test needs no flag (a NaN still reaches the slow path, which decides nothing unless checking)
-  const float scr_i = (can_break && checking) ? fmaf(Kfast, Ui.w, bp.lat_Kcfast) : -INFINITY;
+  // the screen's per-particle part with the body's bound of |u'_j| (pd_lattice.h); -inf settles
+  // every bond with a finite extension, for a body without failure and in a pass that checks
+  // nothing, so that the per-batch test needs no flag (a NaN still reaches the slow path, which
+  // decides nothing unless checking)
+  const float umax_b = lat_umax_bound(__uint_as_float(a.lat_umax[b]));
+  const float scr_i = (can_break && checking) ? lat_screen_part(Kfast, Ui.w, umax_b, bp.lat_Kcfast) : -INFINITY;
   const bool every = checking && a.validate != 0;  // validation: every batch takes the slow path
   uint32_t* __restrict__ bw = a.bits + (t.base >> 5);
   float acc = 0.0f;
@@ -1877,18 +1903,19 @@ __global__ void __launch_bounds__(512) k_pass1_lat(StepArgs a, const float4* __r
       if (LO) Lj[u] = lo32[j];
     }
     float dm[U];
-    bool near = false;
+    float gmax = -INFINITY;  // the largest g = d' - s0 |n|^2 of the batch's intact bonds (0 - s0 |n|^2 for the others)
+    const float4 dA = lat_dir<DIM>(k), dB = lat_dir<DIM>(k + 2);  // k is a multiple of 4
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const float4 dn = lat_dir<DIM>(k + u);
+      const float4 dn = lat_twin(u < 2 ? dA : dB, u & 1);
       const float d =
           LO ? lat_dprime_d<DIM>(dn.x, dn.y, dn.z, lat_delta_lo(Uj[u].x, Lj[u].x, Ui.x, Li.x),
                                  lat_delta_lo(Uj[u].y, Lj[u].y, Ui.y, Li.y), lat_delta_lo(Uj[u].z, Lj[u].z, Ui.z, Li.z))
              : lat_dprime_pair<DIM>(dn, Uj[u], nUi);
-      const bool in = (wd[u] & lmask) != 0u;
-      dm[u] = in ? d : 0.0f;
-      near |= in & !(lat_screen_value(lat_g(d, s0f, dn.w), Kfast, Uj[u].w, scr_i) < 0.0f);
+      dm[u] = (wd[u] & lmask) ? d : 0.0f;
+      gmax = lat_max_nan(gmax, lat_g(dm[u], s0f, dn.w));
     }
+    const bool near = !(gmax + scr_i < 0.0f);
     if (__any_sync(kFull, near) | every) {
       // full band for the bonds the screen did not settle, FP64 inside it; the neighbour index and
       // its |u'| are reloaded (staged chunk, L1) so that little stays live across this block
@@ -1918,10 +1945,15 @@ __global__ void __launch_bounds__(512) k_pass1_lat(StepArgs a, const float4* __r
 #pragma unroll
       for (int u = 0; u < U; ++u) dm[u] = ((brk >> u) & 1u) ? 0.0f : dm[u];
     }
+    float2 wA = make_float2(1.0f, 0.0f), wB = wA;
+    if (WI) {
+      wA = lat_wgt<DIM>(k);
+      wB = lat_wgt<DIM>(k + 2);
+    }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       if (WI) {  // acc += w' d' with w' as hi + lo
-        const float2 wk = lat_wgt<DIM>(k + u);
+        const float2 wk = u < 2 ? wA : wB;
         acc = fmaf(wk.x, dm[u], fmaf(wk.y, dm[u], acc));
       } else {
         acc += dm[u];
@@ -1974,10 +2006,17 @@ __global__ void __launch_bounds__(512) k_pass2_lat(StepArgs a, const float4* __r
       if (LO) Lj[u] = lo32[j];
       rr[u] = INTR ? 2.0f : rho_i + a.lat_rho[j];
     }
+    const float4 dA = lat_dir<DIM>(k), dB = lat_dir<DIM>(k + 2);  // k is a multiple of 4
+    const float2 rA = lat_rcp<DIM>(k), rB = lat_rcp<DIM>(k + 2);
+    float2 wA = make_float2(1.0f, 0.0f), wB = wA;
+    if (WI) {
+      wA = lat_wgt<DIM>(k);
+      wB = lat_wgt<DIM>(k + 2);
+    }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const float4 dn = lat_dir<DIM>(k + u);
-      const float2 r = lat_rcp<DIM>(k + u);
+      const float4 dn = lat_twin(u < 2 ? dA : dB, u & 1);
+      const float2 r = u < 2 ? rA : rB;
       const float d =
           LO ? lat_dprime_d<DIM>(dn.x, dn.y, dn.z, lat_delta_lo(Uj[u].x, Lj[u].x, Ui.x, Li.x),
                                  lat_delta_lo(Uj[u].y, Lj[u].y, Ui.y, Li.y), lat_delta_lo(Uj[u].z, Lj[u].z, Ui.z, Li.z))
@@ -1985,7 +2024,7 @@ __global__ void __launch_bounds__(512) k_pass2_lat(StepArgs a, const float4* __r
       const float dr = fmaf(d, r.x, d * r.y);  // d / |n|^2 with 1 / |n|^2 carried as hi + lo
       float cf = fmaf(rr[u], dr, Ui.w + Uj[u].w);
       if (WI) {  // cf w' with w' as hi + lo
-        const float2 wk = lat_wgt<DIM>(k + u);
+        const float2 wk = u < 2 ? wA : wB;
         cf = fmaf(cf, wk.x, cf * wk.y);
       }
       cf = (wd[u] & lmask) ? cf : 0.0f;
@@ -2000,17 +2039,19 @@ __global__ void __launch_bounds__(512) k_pass2_lat(StepArgs a, const float4* __r
   };
   const bool ok = a.lat_wuni > 0 ? lat_rows<NB, CH>(a, st, a.lat_wuni, lane, batch)
                                  : lat_rows<NB, CH>(a, st, st.W, lane, batch);
-  if (ok) {
+  if (ok) {  // warp-uniform
     double4 u;
     update_lat<DIM>(a, t.i, b, f, disp, disp_out, u);
+    float4 hi;
     if (LO) {
-      float4 hi, lo;
+      float4 lo;
       shadow_lat_lo<DIM>(a.bp[b].lat_inv_h, u, hi, lo);
-      u32_out[t.i] = hi;
       lo32_out[t.i] = lo;
     } else {
-      u32_out[t.i] = shadow_lat<DIM>(a.bp[b].lat_inv_h, u);
+      hi = shadow_lat<DIM>(a.bp[b].lat_inv_h, u);
     }
+    u32_out[t.i] = hi;
+    lat_raise_umax(a.lat_umax_next, b, hi.w);
   }
 }
 
@@ -2137,7 +2178,7 @@ __global__ void __launch_bounds__(kAdrBlock) k_adr_update(StepArgs a, const doub
                                                            double4* __restrict__ gold,
                                                            const double* __restrict__ lam,
                                                            const double2* __restrict__ st,
-                                                           float4* __restrict__ u32_out) {
+                                                           float4* __restrict__ u32_out, unsigned* umax) {
   const int64_t i = blockIdx.x * (int64_t)kAdrBlock + threadIdx.x;
   if (i >= a.n_pad) return;
   const int b = a.body ? a.body[i] : 0;
@@ -2175,7 +2216,11 @@ __global__ void __launch_bounds__(kAdrBlock) k_adr_update(StepArgs a, const doub
   disp_out[i] = u;
   a.vel[i] = v;
   gold[i] = g;
-  if (u32_out) u32_out[i] = shadow_of(a, b, u);  // mixed form: the FP32 shadow of the new state
+  if (u32_out) {  // mixed form: the FP32 shadow of the new state (and, lattice layout, its bound)
+    const float4 sh = shadow_of(a, b, u);
+    u32_out[i] = sh;
+    if (umax) lat_raise_umax(umax, b, sh.w);  // whole warps: n_pad is a multiple of 32
+  }
 }
 
 
@@ -2392,11 +2437,13 @@ __global__ void k_apply_bc(StepArgs a, double4* __restrict__ disp, int64_t step)
 }
 
 __global__ void k_shadow(StepArgs a, const double4* __restrict__ disp, float4* __restrict__ u32,
-                         float4* __restrict__ lo32) {
+                         float4* __restrict__ lo32, unsigned* __restrict__ umax) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= a.n_pad) return;
+  if (i >= a.n_pad) return;  // whole warps: n_pad is a multiple of 32
   const int b = a.body ? a.body[i] : 0;
-  u32[i] = shadow_of(a, b, disp[i]);
+  const float4 sh = shadow_of(a, b, disp[i]);
+  u32[i] = sh;
+  if (umax) lat_raise_umax(umax, b, sh.w);  // lattice layout: the bound of this shadow (zeroed before)
   if (lo32) {  // two-word shadow of the lattice layout (3D formula: z is zero in 2D)
     float4 hi, lo;
     shadow_lat_lo<3>(a.bp[b].lat_inv_h, disp[i], hi, lo);
@@ -2489,6 +2536,9 @@ StepArgs make_args(pd_ctx* c) {
   a.lat_up = c->lat_up;
   a.lat_int = c->lat_int;
   a.lat_wuni = c->lat_wuni;
+  a.lat_umax = c->lat_umax ? c->lat_umax + (size_t)c->cur * c->nbodies : nullptr;
+  a.lat_umax_next = c->lat_umax ? c->lat_umax + (size_t)(c->cur ^ 1) * c->nbodies : nullptr;
+  a.nbody = c->nbodies;
   return a;
 }
 
@@ -2892,7 +2942,8 @@ pd_status launch_step(pd_ctx* c, bool check) {
     k_adr_coef<<<1, 1024, 0, c->stream>>>(c->adr_part, (int)nblk, c->adr_first, c->adr_st);
     k_adr_update<<<nblk, kAdrBlock, 0, c->stream>>>(a, c->disp[c->cur], c->disp[c->cur ^ 1], c->gold, c->lam,
                                                     c->adr_st,
-                                                    c->precision == PD_MIXED ? c->u32[c->cur ^ 1] : nullptr);
+                                                    c->precision == PD_MIXED ? c->u32[c->cur ^ 1] : nullptr,
+                                                    c->precision == PD_MIXED && c->lattice ? a.lat_umax_next : nullptr);
   }
   if (prof) {
     cudaEventRecord(e2, c->stream);
@@ -3050,8 +3101,10 @@ pd_status ensure_shadow_lo(pd_ctx* c) {
 pd_status sync_shadow(pd_ctx* c) {
   if (c->precision != PD_MIXED) return PD_OK;
   const int tb = 256;
+  unsigned* umax = c->lattice ? c->lat_umax + (size_t)c->cur * c->nbodies : nullptr;
+  if (umax) PD_CUDA(cudaMemsetAsync(umax, 0, sizeof(unsigned) * c->nbodies, c->stream));
   k_shadow<<<(unsigned)((c->n_pad + tb - 1) / tb), tb, 0, c->stream>>>(make_args(c), c->disp[c->cur], c->u32[c->cur],
-                                                                        c->shadow_lo ? c->u32lo[c->cur] : nullptr);
+                                                                        c->shadow_lo ? c->u32lo[c->cur] : nullptr, umax);
   PD_CUDA(cudaGetLastError());
   return PD_OK;
 }

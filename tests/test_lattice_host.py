@@ -5,7 +5,8 @@
    prefix, with entry k ^ 1 = -entry k (the two directed entries of one bond); the family sizes of
    the workloads' horizons (28 and 48 in 2D for delta = 3.015 h and 4.015 h, 122 in 3D) are prefixes.
 2. The FP32 break decision of the lattice kernels (Eq 1.30 as n.(u'_j - u'_i) >= s0 |n|^2 in lattice
-   units): its FP32 operations (lat_dprime, lat_g, the screen and the full band) are run by the
+   units): its FP32 operations (lat_dprime, lat_g, both forms of the screen -- per neighbour, and
+   per body with the body's largest |u'| at its tightest, max(U_i, U_j) -- and the full band) are run by the
    header's own code on bonds placed within 1e-9 .. 0.5 of their threshold, with lattice positions
    rounded in FP64, displacements from 1e-6 to 1e3 lattice spacings and rigid rotations on top.  Every
    bond the screen or the band decides in FP32 must be decided the same way by any FP64 evaluation:
@@ -72,7 +73,8 @@ extern "C" int prefix_c(int dim, int q) { return dim == 3 ? lattice_prefix_c<3>(
 // per bond: xi (3, FP64 positions' difference), n (3), ui (3), uj (3) in metres, h, s0;
 // band_safety, n1, qmax, lo (1: two-word shadow hi + lo); out: screen (1 = settled intact), code (0, 1, 2)
 extern "C" void decide(long m, const double* xi, const int* n, const double* ui, const double* uj, const double* h,
-                       const double* s0, double bc, int n1, int qmax, int lo, int* screen, int* code) {
+                       const double* s0, double bc, int n1, int qmax, int lo, int* screen, int* code,
+                       int* screen_c) {
   for (long k = 0; k < m; ++k) {
     const double ih = 1.0 / h[k];
     float a[3], b[3], al[3], bl[3];
@@ -94,7 +96,10 @@ extern "C" void decide(long m, const double* xi, const int* n, const double* ui,
     const float g = lat_g(d, s0f, q);
     const LatBand L = lattice_band(bc, s0[k], n1, qmax);
     const float scr = fmaf(L.Kfast, Ui, L.Kcfast);
-    screen[k] = lat_screen_value(g, L.Kfast, Uj, scr) < 0.0f ? 1 : 0;  // the kernel's form of the screen
+    screen[k] = lat_screen_value(g, L.Kfast, Uj, scr) < 0.0f ? 1 : 0;  // the per-neighbour screen
+    // the kernels' per-body screen at its tightest: the body's largest |u'| is max(U_i, U_j)
+    const float scr_c = lat_screen_part(L.Kfast, Ui, lat_umax_bound(fmaxf(Ui, Uj)), L.Kcfast);
+    screen_c[k] = lat_max_nan(-INFINITY, g) + scr_c < 0.0f ? 1 : 0;
     code[k] = lat_code(g, Ui, Uj, s0f, q, L.Kf, L.sq, L.eps_c, L.s0n1);
   }
 }
@@ -120,7 +125,7 @@ def so():
     L.prefix_c.argtypes = [ctypes.c_int, ctypes.c_int]
     L.table_c.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
     L.decide.argtypes = [ctypes.c_long] + [ctypes.c_void_p] * 6 + [ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                                                    ctypes.c_void_p, ctypes.c_void_p]
+                                                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     yield L
     shutil.rmtree(tmp, ignore_errors=True)
 
@@ -200,21 +205,29 @@ def exact_margin(xi, ui, uj, s0):
     return out
 
 
-def run_case(so, xi, n, ui, uj, h, s0, bc, n1, qmax, lo=0):
+def run_case(so, xi, n, ui, uj, h, s0, bc, n1, qmax, lo=0, with_body_screen=False):
     m = len(s0)
     screen = np.zeros(m, dtype=np.int32)
     code = np.zeros(m, dtype=np.int32)
+    screen_c = np.zeros(m, dtype=np.int32)
     arrs = [np.ascontiguousarray(a) for a in (xi, n, ui, uj, h, s0)]
-    so.decide(m, *[a.ctypes.data for a in arrs], bc, n1, qmax, lo, screen.ctypes.data, code.ctypes.data)
+    so.decide(m, *[a.ctypes.data for a in arrs], bc, n1, qmax, lo, screen.ctypes.data, code.ctypes.data,
+              screen_c.ctypes.data)
+    if with_body_screen:
+        return screen, code, screen_c
     return screen, code
 
 
 def violations(so, sample, bc, n1, qmax, lo=0):
-    screen, code = run_case(so, *sample, bc, n1, qmax, lo)
+    screen, code, screen_c = run_case(so, *sample, bc, n1, qmax, lo, with_body_screen=True)
     xi, n, ui, uj, h, s0 = sample
     bad = 0
-    counts = dict(screened=0, fp32_broken=0, fp32_intact=0, fp64=0)
+    counts = dict(screened=0, body_screened=0, fp32_broken=0, fp32_intact=0, fp64=0)
     for k, (G, M) in enumerate(exact_margin(xi, ui, uj, s0)):
+        if screen_c[k]:
+            counts["body_screened"] += 1
+            bad += not (G < -M)
+            bad += code[k] != 0  # the per-body screen implies the band's intact decision
         if screen[k]:
             counts["screened"] += 1
             bad += not (G < -M)
@@ -261,8 +274,8 @@ def test_screen_settles_bonds_clear_of_the_threshold(so):
     fam = t[t[:, 3] <= 9]
     rng = np.random.default_rng(5)
     xi, n, ui, uj, h, s0 = near_threshold(rng, 500, 1e-3, 0.9, 6.7e-4, 6.8e-4, fam[:, :3], rel=-0.5)
-    screen, code = run_case(so, xi, n, ui, uj, h, s0, 4.0, 5, 9)
-    assert screen.all() and (code == 0).all()
+    screen, code, screen_c = run_case(so, xi, n, ui, uj, h, s0, 4.0, 5, 9, with_body_screen=True)
+    assert screen.all() and screen_c.all() and (code == 0).all()
 
 
 def test_an_undersized_band_is_caught(so):
@@ -277,15 +290,20 @@ def test_an_undersized_band_is_caught(so):
                             rel=None)
     bad, counts = violations(so, sample, 0.02, 5, 9)
     assert bad > 0, counts
+    # the per-body screen alone, too
+    screen, code, screen_c = run_case(so, *sample, 0.02, 5, 9, with_body_screen=True)
+    xi, n, ui, uj, h, s0 = sample
+    margins = exact_margin(xi, ui, uj, s0)
+    assert sum(1 for k in np.flatnonzero(screen_c) if not (margins[k][0] < -margins[k][1])) > 0
 
 
 def test_nonfinite_extension_goes_to_fp64(so):
     xi = np.array([[1e-3, 0.0, 0.0]])
     n = np.array([[1, 0, 0]], dtype=np.int32)
     for bad in (np.nan, np.inf, -np.inf):
-        screen, code = run_case(so, xi, n, np.zeros((1, 3)), np.array([[bad, 0.0, 0.0]]), np.array([1e-3]),
-                                np.array([1e-3]), 4.0, 5, 9)
-        assert screen[0] == 0 and code[0] == 2
+        screen, code, screen_c = run_case(so, xi, n, np.zeros((1, 3)), np.array([[bad, 0.0, 0.0]]), np.array([1e-3]),
+                                          np.array([1e-3]), 4.0, 5, 9, with_body_screen=True)
+        assert screen[0] == 0 and screen_c[0] == 0 and code[0] == 2
 
 
 def test_screen_value_form_is_the_screen(so):
