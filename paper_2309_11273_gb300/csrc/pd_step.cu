@@ -1972,7 +1972,7 @@ __global__ void __launch_bounds__(512) k_pass1_lat(StepArgs a, const float4* __r
 }
 
 template <int DIM, bool WI, bool LO, int NB, int CH>
-__global__ void __launch_bounds__(512) k_pass2_lat(StepArgs a, const float4* __restrict__ u32,
+__global__ void __maxnreg__(56) k_pass2_lat(StepArgs a, const float4* __restrict__ u32,
                                                     float4* __restrict__ u32_out,
                                                     const float4* __restrict__ lo32, float4* __restrict__ lo32_out,
                                                     const double4* __restrict__ disp,
@@ -1993,8 +1993,9 @@ __global__ void __launch_bounds__(512) k_pass2_lat(StepArgs a, const float4* __r
   const bool interior = __all_sync(kFull, a.lat_int[t.i >> 5] != 0);
   const uint32_t lmask = 1u << lane;
   float f[3] = {0.0f, 0.0f, 0.0f};
-  auto batch_t = [&](auto intr, const int32_t* cs, uint4 w4, int k) {
+  auto batch_t = [&](auto intr, auto full, const int32_t* cs, uint4 w4, int k) {
     constexpr bool INTR = decltype(intr)::value;
+    constexpr bool FULL = decltype(full)::value;  // every bond of the batch intact for every lane
     constexpr int U = kU32;
     const uint32_t wd[U] = {w4.x, w4.y, w4.z, w4.w};
     float4 Uj[U], Lj[U];
@@ -2027,15 +2028,19 @@ __global__ void __launch_bounds__(512) k_pass2_lat(StepArgs a, const float4* __r
         const float2 wk = u < 2 ? wA : wB;
         cf = fmaf(cf, wk.x, cf * wk.y);
       }
-      cf = (wd[u] & lmask) ? cf : 0.0f;
+      if (!FULL) cf = (wd[u] & lmask) ? cf : 0.0f;
       f[0] = fmaf(cf, dn.x, f[0]);
       f[1] = fmaf(cf, dn.y, f[1]);
       if (DIM == 3) f[2] = fmaf(cf, dn.z, f[2]);
     }
   };
   auto batch = [&](const int32_t* cs, const uint32_t*, uint4 w4, int k) {
-    if (interior) batch_t(std::true_type{}, cs, w4, k);
-    else batch_t(std::false_type{}, cs, w4, k);
+    if (interior) {
+      if ((w4.x & w4.y & w4.z & w4.w) == 0xffffffffu) batch_t(std::true_type{}, std::true_type{}, cs, w4, k);
+      else batch_t(std::true_type{}, std::false_type{}, cs, w4, k);
+    } else {
+      batch_t(std::false_type{}, std::false_type{}, cs, w4, k);
+    }
   };
   const bool ok = a.lat_wuni > 0 ? lat_rows<NB, CH>(a, st, a.lat_wuni, lane, batch)
                                  : lat_rows<NB, CH>(a, st, st.W, lane, batch);
