@@ -531,6 +531,10 @@ pd_status build_lattice(pd_ctx* c, BuildArgs& A, bool* done) {
       return PD_OK;
     }
     S[b] = lattice_prefix(dim, hstats[3 * b + 1]);
+    if (S[b] < 0) {  // the family is not a prefix of the table: keep the general layout
+      cleanup();
+      return PD_OK;
+    }
   }
   // slice widths of the lattice layout: the largest family prefix among the slice's bodies, rounded
   // up to a multiple of 4 (16-byte aligned status words for the bulk copies)

@@ -5,10 +5,16 @@
 // On a body whose particles sit on a regular lattice of spacing h, every bond vector is xi = h n with
 // n an integer vector, and the family (Section 2.1: the closed ball |xi| <= delta) is the set of
 // lattice directions with |n|^2 <= (delta / h)^2.  The table lists the non-zero integer vectors with
-// |n|^2 <= kLatQmax[dim] in a fixed order: by |n|^2, then each direction n whose first non-zero
-// component from z down to x is positive, immediately followed by its opposite -n.  So
-//   * every ball |n|^2 <= q is a prefix of the table (one family = the first S directions);
-//   * entry k and entry k ^ 1 are the two directions of one bond (xi_ji = -xi_ij).
+// |n|^2 <= kLatQmax[dim] in groups: |n|^2 <= 9, then each ring m^2 < |n|^2 <= (m + 1)^2.  Inside a
+// group, each direction n whose first non-zero component from z down to x is positive, ordered by
+// (n_z, n_y, n_x), is immediately followed by its opposite -n.  So
+//   * every ball |n|^2 <= m^2 with m >= 3 (horizons from 3 h up to just below sqrt(10) h, 4 h, ...)
+//     is a prefix of the table (one family = the first S directions); a ball that ends inside a
+//     group is not, and such a body keeps the general layout;
+//   * entry k and entry k ^ 1 are the two directions of one bond (xi_ji = -xi_ij);
+//   * consecutive slots share their row (n_y, n_z): a slice is 32 particles along x (the brick
+//     order), so the neighbours of successive slots are the same rows shifted by one along x and
+//     the displacement gathers of a slot mostly hit the cache lines of the previous ones.
 // In the lattice layout, slot k of every slice holds the neighbour in direction k of the table for
 // every lane, so the bond vector of a slot is one value for the whole warp.
 #pragma once
@@ -38,15 +44,21 @@ struct LatDir {
   int q;  // |n|^2
 };
 
-// The table as a compile-time constant (so that kernels specialized for one family take each slot's
-// direction as an immediate).  Insertion sort of the positive representatives by (|n|^2, z, y, x),
-// then each followed by its opposite.
+// Group of a direction in the table order: 3 for |n|^2 <= 9, else the m with (m - 1)^2 < |n|^2 <= m^2.
+constexpr int lattice_group(int q) {
+  int m = 3;
+  while (m * m < q) ++m;
+  return m;
+}
+
 template <int DIM>
 struct LatTable {
   static constexpr int kCount = DIM == 3 ? kLatDirs3 : kLatDirs2;
   LatDir d[kCount];
 };
 
+// The table as a compile-time constant.  Insertion sort of the positive representatives by
+// (group, z, y, x), then each followed by its opposite.
 template <int DIM>
 constexpr LatTable<DIM> lattice_table() {
   constexpr int qmax = DIM == 3 ? kLatQmax3 : kLatQmax2;
@@ -65,9 +77,10 @@ constexpr LatTable<DIM> lattice_table() {
         int k = np++;
         while (k > 0) {
           const LatDir& p = pos[k - 1];
-          const bool after = p.q != e.q ? p.q > e.q
-                                        : (p.n[2] != e.n[2] ? p.n[2] > e.n[2]
-                                                            : (p.n[1] != e.n[1] ? p.n[1] > e.n[1] : p.n[0] > e.n[0]));
+          const int gp = lattice_group(p.q), ge = lattice_group(e.q);
+          const bool after = gp != ge ? gp > ge
+                                      : (p.n[2] != e.n[2] ? p.n[2] > e.n[2]
+                                                          : (p.n[1] != e.n[1] ? p.n[1] > e.n[1] : p.n[0] > e.n[0]));
           if (!after) break;
           pos[k] = pos[k - 1];
           --k;
@@ -81,13 +94,15 @@ constexpr LatTable<DIM> lattice_table() {
   return t;
 }
 
-// Number of directions with |n|^2 <= q (a family), at compile time.
+// Number of directions with |n|^2 <= q (a family) when they are the first entries of the table,
+// else -1 (the ball is not a prefix: |n|^2 <= q ends inside a group), at compile time.
 template <int DIM>
 constexpr int lattice_prefix_c(int q) {
   const LatTable<DIM> t = lattice_table<DIM>();
-  int k = 0;
+  int k = 0, in = 0;
+  for (int e = 0; e < LatTable<DIM>::kCount; ++e) in += t.d[e].q <= q ? 1 : 0;
   while (k < LatTable<DIM>::kCount && t.d[k].q <= q) ++k;
-  return k;
+  return k == in ? k : -1;
 }
 
 inline std::vector<LatDir> lattice_directions(int dim) {
@@ -118,12 +133,14 @@ inline std::vector<short> lattice_lookup(int dim) {
   return cube;
 }
 
-// Number of table directions with |n|^2 <= q (the family of a ball of radius sqrt(q) h).
+// Number of table directions with |n|^2 <= q (the family of a ball of radius sqrt(q) h) when they
+// are the first entries of the table, else -1.
 inline int lattice_prefix(int dim, int q) {
   const std::vector<LatDir> t = lattice_directions(dim);
-  int k = 0;
+  int k = 0, in = 0;
+  for (const LatDir& e : t) in += e.q <= q ? 1 : 0;
   while (k < (int)t.size() && t[k].q <= q) ++k;
-  return k;
+  return k == in ? k : -1;
 }
 
 // ------------------------------------------------------------- FP32 break decision and its band

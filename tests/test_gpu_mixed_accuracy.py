@@ -28,8 +28,13 @@ rounded per particle, so the body's momentum takes a random walk), and the defor
 error less its best-fit rigid motion, is held to 2e-5 beside the total.
 Bounds: configurations 1, 2, 4 as BOUNDS (both shadows); the blocks at their first checkpoint
 (FIRST_BOUND, one word); with two words configuration 3 within 1e-8 and no status difference through
-step 600, configuration 5 within 1e-3 over its 200 steps.  Every mixed decision is separately
-certified equal to FP64 on the run's own state (validation mode, tests/test_gpu_lattice.py).
+step 600.  Configuration 5 with two words is reported, not bounded: it follows FP64 until a bond
+closer to its threshold than the two-word rounding (~1e-9 of the state) is decided on the other side,
+and when that happens depends on the rounding pattern: with the slots ordered by |n|^2 it was
+2.3e-9 after 100 steps with the same broken bonds; with the slots ordered by row, 3.3e-3 with 3,444
+more (both with every decision equal to FP64's on the run's own state).  Configuration 5's mixed
+runs take every decision in validation mode here, and the test requires zero mismatches; the other
+configurations' decisions are certified in tests/test_gpu_lattice.py.
 """
 import json
 
@@ -67,7 +72,7 @@ def _round_state(sim):
     sim.set_state(_f32(u), _f32(v))
 
 
-def _block_trajectories(w, nsteps, nchk, with_status=True):
+def _block_trajectories(w, nsteps, nchk, with_status=True, validate=False):
     """Reference FP64 and, from the same state, FP64 with another summation order, FP64 rounded to
     FP32 once at step ROUND_AT, and mixed; at nchk checkpoints rel-L2(u) and status mismatches of the
     latter three against the reference.  Two contexts at a time (the reference is deterministic:
@@ -80,6 +85,8 @@ def _block_trajectories(w, nsteps, nchk, with_status=True):
         sim = Simulation(w, **kw)
         if tag == "fp64_order":
             sim.set_option(B.PD_OPT_SPLIT, 2)  # another summation order
+        if validate and tag.startswith("mixed"):
+            sim.set_option(B.PD_OPT_VALIDATE, 1)  # every decision also taken in FP64 and compared
         for c in range(nchk):
             if c == 0 and tag == "fp64_rounded":
                 ref.step(ROUND_AT)
@@ -100,6 +107,8 @@ def _block_trajectories(w, nsteps, nchk, with_status=True):
             out[tag].append(row)
         if tag.startswith("mixed"):
             out["band_rechecks" + tag[5:]] = sim.stats()["band_rechecks"]
+            if validate:
+                out["validate_mismatches" + tag[5:]] = sim.stats()["validate_mismatches"]
             out["lattice"] = sim.get_option(B.PD_OPT_LATTICE)
         ref.close()
         sim.close()
@@ -129,7 +138,7 @@ def test_mixed_error_per_configuration(capsys):
     out["config3"] = dict(_block_trajectories(W.config3(), 2000, 10), steps=2000, reference="FP64 GPU path")
     # configuration 5 (8M particles, ~9.6e8 bonds): its first 200 steps (millions of bonds break by
     # step 100), broken counts instead of per-bond mismatches (a full status read-back takes ~30 s)
-    out["config5"] = dict(_block_trajectories(W.config5(), 200, 2, with_status=False), steps=200,
+    out["config5"] = dict(_block_trajectories(W.config5(), 200, 2, with_status=False, validate=True), steps=200,
                           reference="FP64 GPU path")
     bw = W.config4()
     res = {}
@@ -177,5 +186,5 @@ def test_mixed_error_per_configuration(capsys):
     for row in out["config3"]["mixed_lo"]:
         if row["step"] <= 600:
             assert row["rel_l2_u"] <= 1e-8 and row["status_mismatch"] == 0, row
-    for row in out["config5"]["mixed_lo"]:
-        assert row["rel_l2_u"] <= 1e-3, row
+    # configuration 5 (reported): both forms decide every bond as FP64 does on their own state
+    assert out["config5"]["validate_mismatches"] == 0 and out["config5"]["validate_mismatches_lo"] == 0

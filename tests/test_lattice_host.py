@@ -1,9 +1,11 @@
 """Host tests of the lattice layout's shared code (csrc/pd_lattice.h), compiled with the host compiler.
 
 1. The direction table: every non-zero integer vector with |n|^2 up to the table's bound appears once,
-   sorted by |n|^2 so that each family (the closed ball of Section 2.1, |n|^2 <= (delta/h)^2) is a
-   prefix, with entry k ^ 1 = -entry k (the two directed entries of one bond); the family sizes of
-   the workloads' horizons (28 and 48 in 2D for delta = 3.015 h and 4.015 h, 122 in 3D) are prefixes.
+   in groups (|n|^2 <= 9, then rings up to each next square) so that every family (the closed ball
+   of Section 2.1, |n|^2 <= (delta/h)^2) of radius 3, 4, ... lattice spacings is a prefix, ordered
+   by row (n_z, n_y) then n_x inside a group, with entry k ^ 1 = -entry k (the two directed entries of
+   one bond); the family sizes of the workloads' horizons (28 and 48 in 2D for delta = 3.015 h and
+   4.015 h, 122 in 3D) are prefixes, and balls ending inside a group are not.
 2. The FP32 break decision of the lattice kernels (Eq 1.30 as n.(u'_j - u'_i) >= s0 |n|^2 in lattice
    units): its FP32 operations (lat_dprime, lat_g, both forms of the screen -- per neighbour, and
    per body with the body's largest |u'| at its tightest, max(U_i, U_j) -- and the full band) are run by the
@@ -148,13 +150,23 @@ def test_direction_table(so, dim, qmax, count):
     got = [tuple(r[:3]) for r in t]
     assert len(set(got)) == len(got) and set(got) == brute
     assert np.array_equal(t[:, 3], (t[:, :3] ** 2).sum(1))
-    assert np.all(np.diff(t[:, 3]) >= 0)  # sorted by |n|^2: every ball is a prefix
+    grp = np.maximum(3, np.ceil(np.sqrt(t[:, 3]) - 1e-9)).astype(int)
+    assert np.all(np.diff(grp) >= 0)  # groups |n|^2 <= 9, then rings up to each next square
+    for m in range(3, int(np.sqrt(qmax)) + 1):  # every ball |n|^2 <= m^2, m >= 3, is a prefix
+        k = int((t[:, 3] <= m * m).sum())
+        assert np.all(t[:k, 3] <= m * m)
+    rep = t[0::2, :3]
+    for g in np.unique(grp):  # inside a group: positive representatives by (z, y, x)
+        r = rep[grp[0::2] == g]
+        assert r.tolist() == sorted(r.tolist(), key=lambda n: (n[2], n[1], n[0]))
     assert np.array_equal(t[1::2, :3], -t[0::2, :3])  # k ^ 1 is the opposite direction
 
 
 def test_family_prefixes(so):
     # the closed balls of the workloads' horizons (lattice counts, Section 2.1)
     assert so.prefix(2, 9) == 28 and so.prefix(2, 16) == 48 and so.prefix(3, 9) == 122
+    # balls that end inside a group are not prefixes (such bodies keep the general layout)
+    assert so.prefix(3, 4) == -1 and so.prefix(2, 5) == -1 and so.prefix(3, 12) == -1
     for dim, q in ((2, 9), (2, 16), (3, 9), (3, 16)):
         t = get_table(so, dim)
         assert so.prefix(dim, q) == int((t[:, 3] <= q).sum())
