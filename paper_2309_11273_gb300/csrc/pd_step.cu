@@ -1999,7 +1999,7 @@ __global__ void __maxnreg__(56) k_pass2_lat(StepArgs a, const float4* __restrict
     constexpr int U = kU32;
     const uint32_t wd[U] = {w4.x, w4.y, w4.z, w4.w};
     float4 Uj[U], Lj[U];
-    float rr[U];
+    float rr[U], cfm[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int32_t j = cs[u * 32];
@@ -2028,10 +2028,15 @@ __global__ void __maxnreg__(56) k_pass2_lat(StepArgs a, const float4* __restrict
         const float2 wk = u < 2 ? wA : wB;
         cf = fmaf(cf, wk.x, cf * wk.y);
       }
-      if (!FULL) cf = (wd[u] & lmask) ? cf : 0.0f;
-      f[0] = fmaf(cf, dn.x, f[0]);
-      f[1] = fmaf(cf, dn.y, f[1]);
-      if (DIM == 3) f[2] = fmaf(cf, dn.z, f[2]);
+      cfm[u] = FULL ? cf : ((wd[u] & lmask) ? cf : 0.0f);
+    }
+#pragma unroll
+    for (int p = 0; p < U / 2; ++p) {  // twin slots 2p, 2p + 1: cf_a n + cf_b (-n) = (cf_a - cf_b) n
+      const float dd = cfm[2 * p] - cfm[2 * p + 1];
+      const float4& dn = p == 0 ? dA : dB;
+      f[0] = fmaf(dd, dn.x, f[0]);
+      f[1] = fmaf(dd, dn.y, f[1]);
+      if (DIM == 3) f[2] = fmaf(dd, dn.z, f[2]);
     }
   };
   auto batch = [&](const int32_t* cs, const uint32_t*, uint4 w4, int k) {
