@@ -760,6 +760,13 @@ pd_status create(pd_ctx** out, int32_t nbodies, const pd_params* prm, const int6
   c->hy.assign(y, y + n);
   if (z) c->hz.assign(z, z + n);
   c->hvol.assign(vol, vol + n);
+  c->vol_uniform = true;
+  for (int b = 0; b < nbodies && c->vol_uniform; ++b)
+    for (int64_t u = offsets[b]; u < offsets[b + 1]; ++u)
+      if (vol[u] != vol[offsets[b]]) {
+        c->vol_uniform = false;
+        break;
+      }
   if (prm[0].stream) {
     c->stream = (cudaStream_t)prm[0].stream;
   } else {

@@ -158,6 +158,7 @@ struct pd_ctx {
   std::vector<pd_params> prm;
   std::vector<int64_t> body_off;  // caller-order offsets of the bodies (nbodies + 1)
   std::vector<double> hx, hy, hz, hvol;   // caller order, host copies
+  bool vol_uniform = false;               // every body has one particle volume (V_j = V_i on every bond)
   std::vector<int64_t> perm;              // internal k -> caller index (k < n)
   std::vector<int32_t> body_of;           // internal k -> body
   // device storage

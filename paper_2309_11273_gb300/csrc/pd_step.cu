@@ -904,7 +904,10 @@ __global__ void __launch_bounds__(512) k_pass1a_f64p(StepArgs a, const double4* 
   }
 }
 
-template <int DIM, int SPLIT>
+// UV: every body has one particle volume, so V_j = V_i for every bond (same body) and the sum takes
+// the lane's own V_i: the same FMAs on the same values, without the neighbour index stream and the
+// gather of V_j.
+template <int DIM, int SPLIT, bool UV>
 __global__ void __launch_bounds__(512) k_pass1b_f64p(StepArgs a, const double4* __restrict__ disp, int write_theta) {
   const SliceIdx t = slice_index<SPLIT>(a.n_pad, a.slice_ptr);
   if (write_theta && blockIdx.x == 0 && threadIdx.x == 0) *a.d_step += 1;
@@ -915,10 +918,19 @@ __global__ void __launch_bounds__(512) k_pass1b_f64p(StepArgs a, const double4* 
     const uint32_t* __restrict__ bw = a.bits + (t.base >> 5);
     const int32_t* __restrict__ cl = a.col + t.base + t.lane;
     const double* __restrict__ td = a.bd + t.base + t.lane;
+    const double vi = UV ? disp[t.i].w : 0.0;
     constexpr int U = 4;
     int32_t jn[U];
     uint32_t wn[U];
-    load_slots<U, SPLIT>(t, cl, bw, t.sub, jn, wn);
+    if (UV) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int k = t.sub + u * SPLIT;
+        wn[u] = k < t.W ? bw[k] : 0u;
+      }
+    } else {
+      load_slots<U, SPLIT>(t, cl, bw, t.sub, jn, wn);
+    }
     double dn[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) dn[u] = td[(int64_t)min(t.sub + u * SPLIT, t.W - 1) << 5];
@@ -929,9 +941,17 @@ __global__ void __launch_bounds__(512) k_pass1b_f64p(StepArgs a, const double4* 
       for (int u = 0; u < U; ++u) {
         wd[u] = wn[u];
         d[u] = dn[u];
-        v[u] = disp[jn[u]].w;
+        v[u] = UV ? vi : disp[jn[u]].w;
       }
-      load_slots<U, SPLIT>(t, cl, bw, k0 + U * SPLIT, jn, wn);
+      if (UV) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int k = k0 + (U + u) * SPLIT;
+          wn[u] = k < t.W ? bw[k] : 0u;
+        }
+      } else {
+        load_slots<U, SPLIT>(t, cl, bw, k0 + U * SPLIT, jn, wn);
+      }
 #pragma unroll
       for (int u = 0; u < U; ++u) dn[u] = td[(int64_t)min(k0 + (U + u) * SPLIT, t.W - 1) << 5];
 #pragma unroll
@@ -2587,7 +2607,10 @@ void launch_pass1(pd_ctx* c, const StepArgs& a, int write_theta, unsigned grid, 
       c->times.mid = take_event(c);
       cudaEventRecord(c->times.mid, c->stream);
     }
-    k_pass1b_f64p<DIM, SPLIT><<<grid, block, sm, c->stream>>>(a, c->disp[c->cur], write_theta);
+    if (c->vol_uniform)
+      k_pass1b_f64p<DIM, SPLIT, true><<<grid, block, sm, c->stream>>>(a, c->disp[c->cur], write_theta);
+    else
+      k_pass1b_f64p<DIM, SPLIT, false><<<grid, block, sm, c->stream>>>(a, c->disp[c->cur], write_theta);
   } else if (c->precision == PD_FP64 && a.bA) {
     if (write_theta)
       k_pass1_f64t<DIM, SPLIT, true><<<grid, block, sm, c->stream>>>(a, c->disp[c->cur], write_theta);
