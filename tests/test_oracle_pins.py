@@ -6,6 +6,7 @@ a classical elasticity formula, or an exact rational computation.
 """
 import itertools
 import math
+import os
 from fractions import Fraction
 
 import numpy as np
@@ -29,12 +30,22 @@ def lattice_offsets(dim, ratio):
 
 
 # --------------------------------------------------------------------------- family / Section 3.3
+def _golden(name):
+    """Rows of a fixture under tests/golden/ (comments and blank lines skipped)."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)
+    with open(path) as f:
+        return [ln.split() for ln in f if ln.strip() and not ln.lstrip().startswith("#")]
+
+
 def test_paper_bond_count_10x10():
-    """Section 3.3: a 10 x 10 grid with m-ratio 3 has 1058 PD bonds (undirected)."""
-    x, y = W.grid_2d(10, 10, 1.0)
+    """Section 3: a 10 x 10 grid with m-ratio 3 has 1058 PD bonds (undirected); the printed value
+    is the fixture tests/golden/paper_bond_count.txt."""
+    rows = {r[0]: r[1:] for r in _golden("paper_bond_count.txt")}
+    nx, ny, ratio, bonds = rows["bonds_10x10_m3"]
+    x, y = W.grid_2d(int(nx), int(ny), 1.0)
     for method in ("bruteforce", "binned"):
-        rp, col = O.family(x, y, None, 3.015, method=method)
-        assert col.size == 2 * 1058
+        rp, col = O.family(x, y, None, float(ratio), method=method)
+        assert col.size == 2 * int(bonds)
 
 
 @pytest.mark.parametrize("dim,ratio,expected", [(2, 3.015, 28), (3, 3.015, 122), (2, 4.015, 48)])
