@@ -241,4 +241,69 @@ PD_LHD int lat_code(float g, float Ui, float Uj, float s0f, float q, float Kf, f
   return g > B ? 1 : (g < -B ? 0 : 2);
 }
 
+// ------------------------------------------------ nonlinear bonds: FP32 break decision and its band
+// With the nonlinear extension (Eq 1.10) the failure criterion of Eq 1.30, e / |xi| >= s0, reads
+// |Y|^2 - |xi|^2 >= c |xi|^2 with c = s0 (2 + s0), and in lattice units (eta' = u'_j - u'_i, Y' = n +
+// eta') g = eta'.(2 n + eta') - c |n|^2 >= 0 (no cancellation between |Y'|^2 and |n|^2).  The kernels
+// evaluate it in FP32 as lat_g_nl does: eta'_c one rounding, a_c = 2 n_c + eta'_c one FMA, the dot
+// product eta'.a one product and two FMAs, g = fmaf(-c32, |n|^2, p).  With eps = 2^-24, S = U_i + U_j
+// (|u'|_inf of the two ends), D = |eta'|_1 (FP32), N1 / Ninf = the family's largest |n|_1 / |n_c|:
+//   * the FP32 copies of u move each eta'_c by at most eps S, and p by at most 2 eps S sum |Y'_c| <=
+//     2 eps S (N1 + D) (dp / d eta'_c = 2 Y'_c);
+//   * the rounding of eta'_c moves p by 2 |Y'_c| eps |eta'_c|, that of a_c by eps |eta'_c a_c|, the dot
+//     product's three roundings by 3 eps sum |eta'_c a_c|: together at most eps (10 Ninf D + 6 D^2);
+//   * c rounded to FP32: eps c |n|^2; the final FMA: eps |g|;
+//   * the FP64 side: bond vectors within 2^-30 h of h n (checked when the layout is built) move its
+//     value by 2^-29 (D + c N1) = eps (D + c N1) / 32, and its own roundings stay far below eps;
+// so |g - g_FP64| <= B = k (1 + 8 eps) eps [2 S N1 + c (qmax + N1 / 32) + D (10 Ninf + 2 S + 1/32)
+// + 6 D^2 + |g|] (the 8 eps covers the FP32 evaluation of B; k = pd_params.band_safety).  The
+// screen replaces U_j by the body's bound U_max (as for linearized bonds) and folds |g| = -g in.
+struct LatBandNL {
+  float A0, A0s, A1, A1s, A2, Ag;  // B = A0 + A0s S + D (A1 + A1s S) + A2 D^2 + Ag |g|
+  float F0, F0s, F1, F1s, F2;      // the screen's B for g < 0, |g| folded in (divided by 1 - Ag)
+};
+
+inline LatBandNL lattice_band_nl(double band_safety, double s0, int n1, int ninf, int qmax) {
+  const double k = band_safety > 0 ? band_safety : 4.0;
+  const double eps = 5.9604644775390625e-8, infl = 1.0 + 8.0 * eps;
+  const double c = s0 * (2.0 + s0);
+  const double m = k * eps * infl;
+  LatBandNL b;
+  b.A0 = (float)(m * c * (qmax + n1 / 32.0));
+  b.A0s = (float)(m * 2.0 * n1);
+  b.A1 = (float)(m * (10.0 * ninf + 1.0 / 32.0));
+  b.A1s = (float)(m * 2.0);
+  b.A2 = (float)(m * 6.0);
+  b.Ag = (float)(m);
+  const double fast = infl / (1.0 - m);
+  b.F0 = (float)(m * c * (qmax + n1 / 32.0) * fast);
+  b.F0s = (float)(m * 2.0 * n1 * fast);
+  b.F1 = (float)(m * (10.0 * ninf + 1.0 / 32.0) * fast);
+  b.F1s = (float)(m * 2.0 * fast);
+  b.F2 = (float)(m * 6.0 * fast);
+  return b;
+}
+
+// The FP32 criterion of a nonlinear bond from eta' = u'_j - u'_i (formed by the caller, one rounding
+// per component): p = eta'.(2 n + eta') and g = p - c32 |n|^2; D = |eta'|_1.
+template <int DIM>
+PD_LHD float lat_p_nl(float nx, float ny, float nz, float ex, float ey, float ez) {
+  float p = ex * fmaf(2.0f, nx, ex);
+  p = fmaf(ey, fmaf(2.0f, ny, ey), p);
+  if (DIM == 3) p = fmaf(ez, fmaf(2.0f, nz, ez), p);
+  return p;
+}
+PD_LHD float lat_g_nl(float p, float c32, float q) { return fmaf(-c32, q, p); }
+
+// The screen's half-width for a slot: S = U_i + U_max' (the lane's part of it precomputed as the
+// polynomial's coefficients f0 = F0 + F0s S, f1 = F1 + F1s S); the bond is settled as intact when
+// g + lat_screen_nl(...) < 0.
+PD_LHD float lat_screen_nl(float D, float f0, float f1, float F2) { return fmaf(D, fmaf(F2, D, f1), f0); }
+
+// Full band: 0 intact, 1 broken (FP32 decision), 2 inside the band (decide in FP64); NaN is inside.
+PD_LHD int lat_code_nl(float g, float D, float S, const LatBandNL& b) {
+  const float B = fmaf(b.Ag, fabsf(g), fmaf(D, fmaf(b.A2, D, fmaf(b.A1s, S, b.A1)), fmaf(b.A0s, S, b.A0)));
+  return g > B ? 1 : (g < -B ? 0 : 2);
+}
+
 }  // namespace pd
