@@ -960,6 +960,19 @@ pd_status upload_body_params(pd_ctx* c) {
       d.lat_s0n1 = lb.s0n1;
       d.lat_Kfast = lb.Kfast;
       d.lat_Kcfast = lb.Kcfast;
+      // nonlinear bonds: |n_c| <= sqrt(qmax) for every direction of the family
+      const LatBandNL nb = lattice_band_nl(p.band_safety, p.s0, n1, (int)std::floor(std::sqrt((double)qm)), qm);
+      d.nl_A0 = nb.A0;
+      d.nl_A0s = nb.A0s;
+      d.nl_A1 = nb.A1;
+      d.nl_A1s = nb.A1s;
+      d.nl_A2 = nb.A2;
+      d.nl_Ag = nb.Ag;
+      d.nl_F0 = nb.F0;
+      d.nl_F0s = nb.F0s;
+      d.nl_F1 = nb.F1;
+      d.nl_F1s = nb.F1s;
+      d.nl_F2 = nb.F2;
     }
   }
   for (int b = 0; b < c->nbodies; ++b) h[b].rate = c->rate;
@@ -1182,7 +1195,7 @@ pd_status build_neighbors(pd_ctx* c, const pd_crack* cracks, int32_t ncracks) {
     c->lat_wuni = 0;
     c->u32lo[0] = c->u32lo[1] = nullptr;
     c->shadow_lo = false;
-    if (c->precision == PD_MIXED && c->kin == PD_LINEARIZED && c->lattice_opt) {
+    if (c->precision == PD_MIXED && c->lattice_opt) {
       PD_CUDA(cudaStreamSynchronize(s));
       bool lat = false;
       PD_TRY2(build_lattice(c, A, &lat));

@@ -51,6 +51,8 @@ struct BodyDev {
   // ... and the screen that settles most bonds: g < -(Kfast (U_i + U_j) + Kcfast) implies intact.
   float lat_Kfast;
   float lat_Kcfast;
+  // lattice layout, nonlinear bonds: the FP32 break decision's band (pd_lattice.h, LatBandNL)
+  float nl_A0, nl_A0s, nl_A1, nl_A1s, nl_A2, nl_Ag, nl_F0, nl_F0s, nl_F1, nl_F1s, nl_F2;
 };
 
 // Per-body neighbour-search grid (cells of edge >= delta).

@@ -1732,6 +1732,9 @@ __constant__ float2 c_latr2[kLatPad2];
 // (w = (delta / h) w', and delta / h cancels between w and m_i)
 __constant__ float2 c_latw3[kLatPad3];
 __constant__ float2 c_latw2[kLatPad2];
+// |n| rounded to FP32 (nonlinear bonds: e' = (|Y'|^2 - |n|^2) / (|Y'| + |n|) and the dilatation term |n| e')
+__constant__ float c_latn3[kLatPad3];
+__constant__ float c_latn2[kLatPad2];
 
 template <int DIM>
 __device__ __forceinline__ float4 lat_dir(int k) {
@@ -1744,6 +1747,10 @@ __device__ __forceinline__ float2 lat_rcp(int k) {
 template <int DIM>
 __device__ __forceinline__ float2 lat_wgt(int k) {
   return DIM == 3 ? c_latw3[k] : c_latw2[k];
+}
+template <int DIM>
+__device__ __forceinline__ float lat_len(int k) {
+  return DIM == 3 ? c_latn3[k] : c_latn2[k];
 }
 // Entry k ^ 1 of the table is -entry k exactly (integer components), with the same |n|^2, 1 / |n|^2
 // and w', and a batch starts at a multiple of 4 slots: its four directions are two loaded entries
@@ -2080,6 +2087,186 @@ __global__ void __maxnreg__(56) k_pass2_lat(StepArgs a, const float4* __restrict
     } else {
       hi = shadow_lat<DIM>(a.bp[b].lat_inv_h, u);
     }
+    u32_out[t.i] = hi;
+    lat_raise_umax(a.lat_umax_next, b, hi.w);
+  }
+}
+
+// ------------------------------------------------- lattice layout, mixed form, nonlinear bonds
+// Geometrically nonlinear bonds (Eqs 1.10, 1.13, 1.14) on the lattice layout, in lattice units:
+// eta' = u'_j - u'_i, Y' = n + eta', p = |Y'|^2 - |n|^2 = eta'.(2 n + eta') (no cancellation),
+// e' = e / h = p / (|Y'| + |n|), M = Y' / |Y'|;
+//   pass 1: theta_i = (A / N_i) sum_j |n| e'_ij (Eq 1.6 with m_i = V h^2 N_i, w = 1);
+//   pass 2: F_i / V_i = G / (h N_ref) sum_j M [(P_i + P_j) |n| + (N_ref/N_i + N_ref/N_j) e'_ij] with
+//           P_i = (K - G/3) / G theta_i N_ref / N_i (Eq 1.14 with the nonlinear e and M),
+// which for small eta' is the linearized kernels' sum term by term.  The failure check (Eq 1.30 as
+// p >= s0 (2 + s0) |n|^2) is decided in FP32 outside the band of pd_lattice.h (LatBandNL) and in FP64
+// from the master state otherwise (fp64_breaks_nl, the FP64 nonlinear kernels' arithmetic); the
+// screen uses the body's bound of |u'_j| as the linearized kernels do.  One-word shadow only.
+template <int DIM, int NB, int CH>
+__global__ void __maxnreg__(72) k_pass1_latnl(StepArgs a, const float4* __restrict__ u32,
+                                                      const double4* __restrict__ disp, int write_theta) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const SliceIdx t = slice_index<1>(a.n_pad, a.slice_ptr);
+  if (write_theta && blockIdx.x == 0 && threadIdx.x == 0) *a.d_step += 1;
+  if (blockIdx.x == 0)  // the bound of the shadow that pass 2 writes next starts from zero
+    for (int k = threadIdx.x; k < a.nbody; k += blockDim.x) a.lat_umax_next[k] = 0u;
+  if (!t.active) return;  // whole warps: the staging below is per warp
+  auto st = stage_init<NB, CH>(smem, t, a);
+  const int lane = t.lane;
+  const int b = a.body ? a.body[t.i] : 0;
+  const BodyDev& bp = a.bp[b];
+  const bool can_break = bp.breaks != 0;
+  const bool checking = a.check != 0;
+  const bool screening = can_break && checking;
+  const bool every = checking && a.validate != 0;
+  const float4 Ui = u32[t.i];
+  const float4 nUi = make_float4(-Ui.x, -Ui.y, -Ui.z, 0.0f);
+  const float c32 = bp.s0nl32;
+  // the screen's per-lane coefficients with S = U_i + the body's bound of |u'_j|
+  const float Smax = Ui.w + lat_umax_bound(__uint_as_float(a.lat_umax[b]));
+  const float f0 = fmaf(bp.nl_F0s, Smax, bp.nl_F0), f1 = fmaf(bp.nl_F1s, Smax, bp.nl_F1), F2 = bp.nl_F2;
+  uint32_t* __restrict__ bw = a.bits + (t.base >> 5);
+  float acc = 0.0f;
+  const uint32_t lmask = 1u << lane;
+  // per batch of 4 slots: p and |Y'|^2 of each bond, the screen, the decisions (the rare slow path
+  // marks the bonds it breaks), then the dilatation terms in slot order (as the linearized kernel)
+  auto batch = [&](const int32_t* cs, const uint32_t* ws, uint4 w4, int k) {
+    constexpr int U = kU32;
+    const uint32_t wd[U] = {w4.x, w4.y, w4.z, w4.w};
+    float4 Uj[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) Uj[u] = u32[cs[u * 32]];
+    float ev[U];  // e' of the intact bonds (0 for the others)
+    float smax = -INFINITY;
+    const float4 dA = lat_dir<DIM>(k), dB = lat_dir<DIM>(k + 2);  // k is a multiple of 4
+    const float lA = lat_len<DIM>(k), lB = lat_len<DIM>(k + 2);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const float4 dn = lat_twin(u < 2 ? dA : dB, u & 1);
+      const float nl = u < 2 ? lA : lB;
+      const float2 exy = __fadd2_rn(make_float2(Uj[u].x, Uj[u].y), make_float2(nUi.x, nUi.y));
+      const float ez = DIM == 3 ? Uj[u].z + nUi.z : 0.0f;
+      const bool in = (wd[u] & lmask) != 0u;
+      const float p = lat_p_nl<DIM>(dn.x, dn.y, dn.z, exy.x, exy.y, ez);
+      const float yx = dn.x + exy.x, yy = dn.y + exy.y, yz = dn.z + ez;
+      float q2 = fmaf(yx, yx, yy * yy);
+      if (DIM == 3) q2 = fmaf(yz, yz, q2);
+      const float pm = in ? p : 0.0f;
+      ev[u] = in ? __fdividef(p, fmaf(q2, rsqrtf(q2), nl)) : 0.0f;
+      if (screening) {
+        const float D = in ? fabsf(exy.x) + fabsf(exy.y) + fabsf(ez) : 0.0f;
+        smax = lat_max_nan(smax, lat_g_nl(pm, c32, dn.w) + lat_screen_nl(D, f0, f1, F2));
+      }
+    }
+    const bool near = screening && !(smax < 0.0f);
+    unsigned brk = 0u;
+    if (__any_sync(kFull, near) | every) {
+      // full band for every intact bond of the batch, FP64 inside it (neighbour index and record
+      // reloaded from the staged chunk and L1)
+#pragma unroll 1
+      for (int u = 0; u < U; ++u) {
+        int code = 0;
+        if (checking && can_break && (ws[u] & lmask) != 0u) {
+          const int32_t jj = cs[u * 32];
+          const float4 uj = u32[jj];
+          const float4 dn = lat_dir<DIM>(k + u);
+          const float ex = uj.x - Ui.x, ey = uj.y - Ui.y, ez = DIM == 3 ? uj.z - Ui.z : 0.0f;
+          const float g = lat_g_nl(lat_p_nl<DIM>(dn.x, dn.y, dn.z, ex, ey, ez), c32, dn.w);
+          LatBandNL band;
+          band.A0 = bp.nl_A0;
+          band.A0s = bp.nl_A0s;
+          band.A1 = bp.nl_A1;
+          band.A1s = bp.nl_A1s;
+          band.A2 = bp.nl_A2;
+          band.Ag = bp.nl_Ag;
+          code = lat_code_nl(g, fabsf(ex) + fabsf(ey) + fabsf(ez), Ui.w + uj.w, band);
+          if (code == 2) {
+            code = fp64_breaks_nl<DIM>(a, t.i, jj, disp) ? 1 : 0;
+            atomicAdd(&a.counters[0], 1ull);
+          }
+          if (a.validate && (code == 1) != fp64_breaks_nl<DIM>(a, t.i, jj, disp)) atomicAdd(&a.counters[1], 1ull);
+        }
+        const unsigned m = __ballot_sync(kFull, code == 1);
+        if (m) {
+          if (lane == 0) bw[k + u] = ws[u] & ~m;
+          if (code == 1) brk |= 1u << u;
+        }
+      }
+    }
+    // dilatation terms |n| e' of the bonds intact after the decisions, in slot order
+#pragma unroll
+    for (int u = 0; u < U; ++u) acc = fmaf(u < 2 ? lA : lB, ((brk >> u) & 1u) ? 0.0f : ev[u], acc);
+  };
+  const bool ok = a.lat_wuni > 0 ? lat_rows<NB, CH>(a, st, a.lat_wuni, lane, batch)
+                                 : lat_rows<NB, CH>(a, st, st.W, lane, batch);
+  if (ok && write_theta) {
+    const float2 f = a.lat_f[t.i];  // (N_ref / N_i, A / N_i)
+    a.theta32[t.i] = f.y * acc;
+    const float x = acc * (f.x * f.x);
+    a.lat_up[t.i] = make_float4(Ui.x, Ui.y, Ui.z, fmaf(bp.lat_lam_hi, x, bp.lat_lam_lo * x));
+  }
+}
+
+template <int DIM, int NB, int CH>
+__global__ void __maxnreg__(64) k_pass2_latnl(StepArgs a, const float4* __restrict__ u32, float4* __restrict__ u32_out,
+                                               const double4* __restrict__ disp, double4* __restrict__ disp_out) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const SliceIdx t = slice_index<1>(a.n_pad, a.slice_ptr);
+  if (!t.active) return;
+  auto st = stage_init<NB, CH>(smem, t, a);
+  const int lane = t.lane;
+  const int b = a.body ? a.body[t.i] : 0;
+  const float4 Ui = a.lat_up[t.i];  // (u'_i, P_i)
+  const float4 nUi = make_float4(-Ui.x, -Ui.y, -Ui.z, 0.0f);
+  const float rho_i = a.lat_f[t.i].x;
+  const bool interior = __all_sync(kFull, a.lat_int[t.i >> 5] != 0);
+  const uint32_t lmask = 1u << lane;
+  float f[3] = {0.0f, 0.0f, 0.0f};
+  auto batch_t = [&](auto intr, const int32_t* cs, uint4 w4, int k) {
+    constexpr bool INTR = decltype(intr)::value;
+    constexpr int U = kU32;
+    const uint32_t wd[U] = {w4.x, w4.y, w4.z, w4.w};
+    float4 Uj[U];
+    float rr[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int32_t j = cs[u * 32];
+      Uj[u] = a.lat_up[j];
+      rr[u] = INTR ? 2.0f : rho_i + a.lat_rho[j];
+    }
+    const float4 dA = lat_dir<DIM>(k), dB = lat_dir<DIM>(k + 2);  // k is a multiple of 4
+    const float lA = lat_len<DIM>(k), lB = lat_len<DIM>(k + 2);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const float4 dn = lat_twin(u < 2 ? dA : dB, u & 1);
+      const float nl = u < 2 ? lA : lB;
+      const float2 exy = __fadd2_rn(make_float2(Uj[u].x, Uj[u].y), make_float2(nUi.x, nUi.y));
+      const float ez = DIM == 3 ? Uj[u].z + nUi.z : 0.0f;
+      const float p = lat_p_nl<DIM>(dn.x, dn.y, dn.z, exy.x, exy.y, ez);
+      const float yx = dn.x + exy.x, yy = dn.y + exy.y, yz = dn.z + ez;
+      float q2 = fmaf(yx, yx, yy * yy);
+      if (DIM == 3) q2 = fmaf(yz, yz, q2);
+      const float ry = rsqrtf(q2);
+      const float e = __fdividef(p, fmaf(q2, ry, nl));
+      // coefficient along M = Y' / |Y'|: (P_i + P_j) |n| + (rho_i + rho_j) e'
+      float cf = fmaf(rr[u], e, (Ui.w + Uj[u].w) * nl) * ry;
+      cf = (wd[u] & lmask) ? cf : 0.0f;
+      f[0] = fmaf(cf, yx, f[0]);
+      f[1] = fmaf(cf, yy, f[1]);
+      if (DIM == 3) f[2] = fmaf(cf, yz, f[2]);
+    }
+  };
+  auto batch = [&](const int32_t* cs, const uint32_t*, uint4 w4, int k) {
+    if (interior) batch_t(std::true_type{}, cs, w4, k);
+    else batch_t(std::false_type{}, cs, w4, k);
+  };
+  const bool ok = a.lat_wuni > 0 ? lat_rows<NB, CH>(a, st, a.lat_wuni, lane, batch)
+                                 : lat_rows<NB, CH>(a, st, st.W, lane, batch);
+  if (ok) {  // warp-uniform
+    double4 u;
+    update_lat<DIM>(a, t.i, b, f, disp, disp_out, u);
+    const float4 hi = shadow_lat<DIM>(a.bp[b].lat_inv_h, u);
     u32_out[t.i] = hi;
     lat_raise_umax(a.lat_umax_next, b, hi.w);
   }
@@ -2647,6 +2834,12 @@ void optin_lat_ring() {
   cudaFuncSetAttribute(k_pass1_lat<DIM, WI, LO, NB, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_pass2_lat<DIM, WI, LO, NB, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
 }
+template <int DIM, int NB, int CH>
+void optin_latnl_ring() {
+  const int mx = 16 * StageGeom<NB, CH>::kWarpBytes;
+  cudaFuncSetAttribute(k_pass1_latnl<DIM, NB, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_pass2_latnl<DIM, NB, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+}
 template <int DIM, bool WI>
 void optin_lat() {
   optin_lat_ring<DIM, WI, false, 3, 16>();
@@ -2686,11 +2879,30 @@ void launch_lat(pd_ctx* c, const StepArgs& a, int pass, int write_theta, int blo
   }
 }
 
+// Nonlinear bonds on the lattice layout: rings 0 and 1 run 2 x 16 slots, rings 2 and 3 run 2 x 8.
+template <int DIM, int NB, int CH>
+void launch_latnl_ring(pd_ctx* c, const StepArgs& a, int pass, int write_theta, int block) {
+  const unsigned g1 = (unsigned)((c->nslices * 32 + block - 1) / block);
+  const size_t smb = (size_t)(block / 32) * StageGeom<NB, CH>::kWarpBytes;
+  if (pass == 1)
+    k_pass1_latnl<DIM, NB, CH><<<g1, block, smb, c->stream>>>(a, c->u32[c->cur], c->disp[c->cur], write_theta);
+  else
+    k_pass2_latnl<DIM, NB, CH><<<g1, block, smb, c->stream>>>(a, c->u32[c->cur], c->u32[c->cur ^ 1], c->disp[c->cur],
+                                                               c->disp[c->cur ^ 1]);
+}
+template <int DIM>
+void launch_latnl(pd_ctx* c, const StepArgs& a, int pass, int write_theta, int block) {
+  if (c->lat_stage >= 2) launch_latnl_ring<DIM, 2, 8>(c, a, pass, write_theta, block);
+  else launch_latnl_ring<DIM, 2, 16>(c, a, pass, write_theta, block);
+}
+
 template <int DIM>
 void optin_staged() {
   const int mx = 16 * kStageWarpBytes;
   optin_lat<DIM, false>();
   optin_lat<DIM, true>();
+  optin_latnl_ring<DIM, 2, 16>();
+  optin_latnl_ring<DIM, 2, 8>();
   cudaFuncSetAttribute(k_pass1_mixed_staged<DIM, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_pass2_mixed_staged<DIM, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_pass1_mixed_staged<DIM, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
@@ -2727,6 +2939,8 @@ pd_status upload_lattice_tables(int device) {
       const float hi = (float)r;
       rc[k] = make_float2(hi, (float)(r - (double)hi));
     }
+    std::vector<float> ln(pad, 1.0f);
+    for (size_t k = 0; k < t.size(); ++k) ln[k] = (float)std::sqrt((double)t[k].q);
     std::vector<float2> wt(pad, make_float2(0.0f, 0.0f));
     for (size_t k = 0; k < t.size(); ++k) {
       const double r = 1.0 / std::sqrt((double)t[k].q);
@@ -2737,10 +2951,12 @@ pd_status upload_lattice_tables(int device) {
       PD_CUDA(cudaMemcpyToSymbol(c_lat3, dn.data(), sizeof(float4) * dn.size()));
       PD_CUDA(cudaMemcpyToSymbol(c_latr3, rc.data(), sizeof(float2) * rc.size()));
       PD_CUDA(cudaMemcpyToSymbol(c_latw3, wt.data(), sizeof(float2) * wt.size()));
+      PD_CUDA(cudaMemcpyToSymbol(c_latn3, ln.data(), sizeof(float) * ln.size()));
     } else {
       PD_CUDA(cudaMemcpyToSymbol(c_lat2, dn.data(), sizeof(float4) * dn.size()));
       PD_CUDA(cudaMemcpyToSymbol(c_latr2, rc.data(), sizeof(float2) * rc.size()));
       PD_CUDA(cudaMemcpyToSymbol(c_latw2, wt.data(), sizeof(float2) * wt.size()));
+      PD_CUDA(cudaMemcpyToSymbol(c_latn2, ln.data(), sizeof(float) * ln.size()));
     }
   }
   done.push_back(device);
@@ -2756,8 +2972,9 @@ void dispatch_pass(pd_ctx* c, const StepArgs& a, int pass, int write_theta) {
   const int64_t threads = c->nslices * 32 * (int64_t)split;
   const unsigned grid = (unsigned)((threads + block - 1) / block);
   if (c->precision == PD_MIXED && c->lattice) {
-    // lattice layout (linearized bonds): one warp per slice, whatever the split and stage options
-    if (c->prm[0].influence == PD_W_INV) launch_lat<DIM, true>(c, a, pass, write_theta, block);
+    // lattice layout: one warp per slice, whatever the split and stage options
+    if (c->kin == PD_NONLINEAR) launch_latnl<DIM>(c, a, pass, write_theta, block);
+    else if (c->prm[0].influence == PD_W_INV) launch_lat<DIM, true>(c, a, pass, write_theta, block);
     else launch_lat<DIM, false>(c, a, pass, write_theta, block);
     return;
   }
@@ -3120,7 +3337,8 @@ pd_status apply_bc_now(pd_ctx* c) {
 
 pd_status ensure_shadow_lo(pd_ctx* c) {
   c->shadow_lo = false;
-  if (!c->lattice || !c->shadow_lo_opt) return PD_OK;
+  // the two-word shadow exists for linearized bonds (the nonlinear lattice kernels read one word)
+  if (!c->lattice || !c->shadow_lo_opt || c->kin != PD_LINEARIZED) return PD_OK;
   pd_status st;
   for (int k = 0; k < 2; ++k)
     if (!c->u32lo[k]) {

@@ -186,12 +186,15 @@ def _oracle_nl(w, s0, rate=0.0):
     return ref
 
 
-def test_mixed_nonlinear_error_bound():
+@pytest.mark.parametrize("lattice", [1, 0])
+def test_mixed_nonlinear_error_bound(lattice):
     """FP32 nonlinear bonds with FP64 integration on the vibrating plate (configuration 1's
     geometry): rel-L2(u) against the oracle's FP64 nonlinear run <= 2e-5 after 100 steps and <= 1e-4
-    over 1000 (the bounds of the linearized mixed form)."""
+    over 1000 (the bounds of the linearized mixed form), on the lattice layout (default for lattice
+    bodies) and on the general layout."""
     w = W.config1()
-    sim = Simulation(w, s0=0.0, precision=PD_MIXED, kinematics=PD_NONLINEAR)
+    sim = Simulation(w, s0=0.0, precision=PD_MIXED, kinematics=PD_NONLINEAR, lattice=lattice)
+    assert sim.get_option(B.PD_OPT_LATTICE) == lattice
     ref = _oracle_nl(w, 0.0)
     errs = []
     for _ in range(10):
@@ -202,11 +205,15 @@ def test_mixed_nonlinear_error_bound():
     assert errs[0] <= 2e-5 and max(errs) <= 1e-4, errs
 
 
-def test_mixed_nonlinear_decisions_equal_fp64_on_own_state():
+@pytest.mark.parametrize("lattice", [1, 0])
+def test_mixed_nonlinear_decisions_equal_fp64_on_own_state(lattice):
     """Zero spurious breaks for nonlinear bonds: with validation on, every decision of the FP32 +
-    band path equals the FP64 nonlinear decision on the mixed run's own state; bonds do break."""
+    band path equals the FP64 nonlinear decision on the mixed run's own state; bonds do break.  Both
+    layouts (the lattice kernels' band is LatBandNL of pd_lattice.h, the general kernels' the
+    fixed-point one)."""
     w = W.cracked_plate(nx=60, ny=24, dx=2.5e-4, crack_cells=30.125, sigma=2e6, nsteps=400)
-    sim = Simulation(w, s0=s0_of(w), precision=PD_MIXED, kinematics=PD_NONLINEAR)
+    sim = Simulation(w, s0=s0_of(w), precision=PD_MIXED, kinematics=PD_NONLINEAR, lattice=lattice)
+    assert sim.get_option(B.PD_OPT_LATTICE) == lattice
     sim.set_option(B.PD_OPT_VALIDATE, 1)
     sim.step(400)
     st = sim.stats()
