@@ -646,9 +646,15 @@ def run_forms(args, stream, dev, world, fp64_value, nb, hbm, hbm_note, fp64_tflo
     warm(sim, args.warmup)
     km = max(args.steps, 100)
     msm = max_over_ranks(timed(sim, stream, km, world), world)
+    nlat = sim.get_option(B.PD_OPT_LATTICE) == 1
     sim.close()
+    nbytes = (BYTES_BOND[1] + BYTES_BOND[2]) * nb + (BYTES_PART[1] + BYTES_PART[2]) * w.n
     nmixed = {"value": world * nb * km / (msm * 1e-3), "ms_per_step": msm / km, "steps": km,
-              "dtype": "f32 bond arithmetic, f64 integration", "speedup_vs_fp64_nonlinear": (nb * km / (msm * 1e-3)) / nval}
+              "dtype": "f32 bond arithmetic, f64 integration", "speedup_vs_fp64_nonlinear": (nb * km / (msm * 1e-3)) / nval,
+              "layout": "lattice" if nlat else "general",
+              "step_frac_hbm": nbytes / (msm / km * 1e-3) / 1e9 / hbm,
+              "step_frac_note": "the linearized step's algorithmic bytes (the same streams and state) over the "
+                                "timed step, against the measured HBM copy rate"}
     out["nonlinear"] = {"value": nval, "unit": UNIT, "ms_per_step": ms / k, "steps": k, "dtype": "f64",
                         "mixed": nmixed,
                         "kinematics": "e = |Y| - |xi|, force along Y/|Y| (Eqs 1.10, 1.13, 1.14)",
