@@ -81,6 +81,17 @@ def test_non_lattice_bodies_keep_the_general_layout():
     B.pd_build_neighbors(h, [])
     assert B.pd_get_option(h, B.PD_OPT_LATTICE) == 0
     B.pd_destroy(h)
+    # a lattice whose family is not a prefix of the direction table (horizon below 3 spacings:
+    # |n|^2 <= 4 ends inside the table's first group) keeps the general layout and still follows
+    # the oracle (the mixed form's stated bound after 100 steps)
+    w4 = W.plate_vibration(nx=20, ny=20, nsteps=100, ratio=2.015, dt=1e-7)  # well inside the stable step
+    sim = Simulation(w4, s0=0.0, precision=PD_MIXED)
+    assert sim.get_option(B.PD_OPT_LATTICE) == 0
+    ref = oracle_for(w4, 0.0)
+    sim.step(100)
+    ref.step(100)
+    assert float(np.linalg.norm(sim.state()[0] - ref.u) / np.linalg.norm(ref.u)) <= 2e-5
+    sim.close()
 
 
 @pytest.mark.parametrize("lo", [0, 1])
