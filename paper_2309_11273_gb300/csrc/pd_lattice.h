@@ -164,7 +164,8 @@ inline int lattice_prefix(int dim, int q) {
 // B bounds that evaluation (lat_delta_lo).  Outside +-B the FP32 sign is the
 // FP64 decision; inside, the bond is re-decided in FP64.  The screen g < -(Kfast (U_i + U_j) +
 // Kcfast), with |g| = -g folded in (division by 1 - c eps) and |n|^2 bounded by the family's
-// largest, implies g < -B: it settles the bonds far from their threshold in two instructions.
+// largest, implies g < -B: it settles the bonds far from their threshold in a few instructions
+// (with U_j replaced by the body's bound, below: one FMA and one max per slot).
 struct LatBand {
   float Kf, sq, eps_c, s0n1, Kfast, Kcfast;
 };
