@@ -2149,9 +2149,7 @@ __global__ void __maxnreg__(72) k_pass1_latnl(StepArgs a, const float4* __restri
       const float ez = DIM == 3 ? Uj[u].z + nUi.z : 0.0f;
       const bool in = (wd[u] & lmask) != 0u;
       const float p = lat_p_nl<DIM>(dn.x, dn.y, dn.z, exy.x, exy.y, ez);
-      const float yx = dn.x + exy.x, yy = dn.y + exy.y, yz = dn.z + ez;
-      float q2 = fmaf(yx, yx, yy * yy);
-      if (DIM == 3) q2 = fmaf(yz, yz, q2);
+      const float q2 = dn.w + p;  // |Y'|^2 = |n|^2 + p
       const float pm = in ? p : 0.0f;
       ev[u] = in ? __fdividef(p, fmaf(q2, rsqrtf(q2), nl)) : 0.0f;
       if (screening) {
@@ -2245,8 +2243,7 @@ __global__ void __maxnreg__(64) k_pass2_latnl(StepArgs a, const float4* __restri
       const float ez = DIM == 3 ? Uj[u].z + nUi.z : 0.0f;
       const float p = lat_p_nl<DIM>(dn.x, dn.y, dn.z, exy.x, exy.y, ez);
       const float yx = dn.x + exy.x, yy = dn.y + exy.y, yz = dn.z + ez;
-      float q2 = fmaf(yx, yx, yy * yy);
-      if (DIM == 3) q2 = fmaf(yz, yz, q2);
+      const float q2 = dn.w + p;  // |Y'|^2 = |n|^2 + p
       const float ry = rsqrtf(q2);
       const float e = __fdividef(p, fmaf(q2, ry, nl));
       // coefficient along M = Y' / |Y'|: (P_i + P_j) |n| + (rho_i + rho_j) e'
