@@ -194,20 +194,22 @@ def test_lattice_graph_chunks_and_batch_are_bitwise():
     assert broken >= 0
 
 
-def test_lattice_benchmark_block_validation_first_400_steps():
+@pytest.mark.parametrize("kin", ["linearized", "nonlinear"])
+def test_lattice_benchmark_block_validation_whole_run(kin):
     """The benchmark's block (configuration 3, 1M particles, ~1.17e8 bonds) in the mixed form with
-    every bond decision also taken in FP64 on the run's own state, through its first 400 steps
-    (bonds break from about step 23 on): no decision differs (Eq 1.30, zero spurious breaks)."""
+    every bond decision also taken in FP64 on the run's own state, through all 2000 steps of the
+    configuration (bonds break from about step 23 on; millions by the end): no decision differs
+    (Eq 1.30, zero spurious breaks), for linearized and for nonlinear bonds."""
     w = W.config3()
-    sim = Simulation(w, precision=PD_MIXED)
+    sim = Simulation(w, precision=PD_MIXED, kinematics=B.PD_NONLINEAR if kin == "nonlinear" else B.PD_LINEARIZED)
     assert sim.get_option(B.PD_OPT_LATTICE) == 1
     sim.set_option(B.PD_OPT_VALIDATE, 1)
-    sim.step(400)
+    sim.step(w.nsteps)
     st = sim.stats()
     sim.close()
-    print("config3 mixed, 400 steps with validation:", {k: st[k] for k in ("broken_bonds", "band_rechecks",
-                                                                            "validate_mismatches")})
-    assert st["broken_bonds"] > 0 and st["validate_mismatches"] == 0
+    print("config3 mixed (%s), %d steps with validation:" % (kin, w.nsteps),
+          {k: st[k] for k in ("broken_bonds", "band_rechecks", "validate_mismatches")})
+    assert st["broken_bonds"] > 1000000 and st["validate_mismatches"] == 0
 
 
 def test_two_word_shadow_config1_and_bitwise_properties():
