@@ -264,3 +264,26 @@ def test_two_word_shadow_config1_and_bitwise_properties():
         assert np.array_equal(sim.state()[0], ub[:, bw.offsets[k]:bw.offsets[k + 1]]), k
         sim.close()
 
+
+
+def test_autotune_mid_run_restores_the_lattice_state_bitwise():
+    """pd_autotune in the middle of a breaking mixed run (its trial steps advance the state, break
+    bonds and raise the shadow's per-body bound, then restore) leaves the run bitwise the one
+    without it: the lattice kernels' arithmetic does not depend on the mapping, and the restore
+    brings back u, v, the status bits, the FP32 shadow and its bound."""
+    w = W.cracked_plate(nx=60, ny=24, dx=2.5e-4, crack_cells=30.125, sigma=2e6, nsteps=300)
+    s0 = s0_of(w)
+    out = []
+    for tune in (False, True):
+        sim = Simulation(w, s0=s0, precision=PD_MIXED)
+        assert sim.get_option(B.PD_OPT_LATTICE) == 1
+        sim.step(150)
+        if tune:
+            B.pd_autotune(sim.h, 20)
+        sim.step(150)
+        u, v, _ = sim.state()
+        out.append((u, v, sim.neighbors()[2], sim.stats()["broken_bonds"]))
+        sim.close()
+    assert out[0][3] > 0
+    for a, b in zip(out[0][:3], out[1][:3]):
+        assert np.array_equal(a, b)
