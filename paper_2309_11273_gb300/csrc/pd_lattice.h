@@ -256,9 +256,14 @@ PD_LHD int lat_code(float g, float Ui, float Uj, float s0f, float q, float Kf, f
 //   * c rounded to FP32: eps c |n|^2; the final FMA: eps |g|;
 //   * the FP64 side: bond vectors within 2^-30 h of h n (checked when the layout is built) move its
 //     value by 2^-29 (D + c N1) = eps (D + c N1) / 32, and its own roundings stay far below eps;
-// so |g - g_FP64| <= B = k (1 + 8 eps) eps [2 S N1 + c (qmax + N1 / 32) + D (10 Ninf + 2 S + 1/32)
-// + 6 D^2 + |g|] (the 8 eps covers the FP32 evaluation of B; k = pd_params.band_safety).  The
-// screen replaces U_j by the body's bound U_max (as for linearized bonds) and folds |g| = -g in.
+// so |g - g_FP64| <= k (1 + 8 eps) eps [2 S N1 + c (qmax + N1 / 32) + D (10 Ninf + 2 S + 1/32) +
+// 6 D^2 + |g|] (the 8 eps covers the FP32 evaluation of B; k = pd_params.band_safety).  With the
+// two-word shadow (u' = hi + lo) eta'_c = (hi_j - hi_i) + (lo_j - lo_i): the copies then differ from
+// u' by at most eps |lo| <= eps^2 U (far below the 2 eps S (N1 + D) allotted to them) and eta'_c takes
+// two roundings instead of one, 2 eps |eta'_c| (1 + O(eps)), which adds at most eps (2 Ninf D + 2 D^2)
+// to the arithmetic term; the band B below carries 12 Ninf and 8 instead of 10 and 6, so one B
+// bounds both forms.  The screen replaces U_j by the body's bound U_max (as for linearized bonds) and
+// folds |g| = -g in.
 struct LatBandNL {
   float A0, A0s, A1, A1s, A2, Ag;  // B = A0 + A0s S + D (A1 + A1s S) + A2 D^2 + Ag |g|
   float F0, F0s, F1, F1s, F2;      // the screen's B for g < 0, |g| folded in (divided by 1 - Ag)
@@ -272,16 +277,16 @@ inline LatBandNL lattice_band_nl(double band_safety, double s0, int n1, int ninf
   LatBandNL b;
   b.A0 = (float)(m * c * (qmax + n1 / 32.0));
   b.A0s = (float)(m * 2.0 * n1);
-  b.A1 = (float)(m * (10.0 * ninf + 1.0 / 32.0));
+  b.A1 = (float)(m * (12.0 * ninf + 1.0 / 32.0));
   b.A1s = (float)(m * 2.0);
-  b.A2 = (float)(m * 6.0);
+  b.A2 = (float)(m * 8.0);
   b.Ag = (float)(m);
   const double fast = infl / (1.0 - m);
   b.F0 = (float)(m * c * (qmax + n1 / 32.0) * fast);
   b.F0s = (float)(m * 2.0 * n1 * fast);
-  b.F1 = (float)(m * (10.0 * ninf + 1.0 / 32.0) * fast);
+  b.F1 = (float)(m * (12.0 * ninf + 1.0 / 32.0) * fast);
   b.F1s = (float)(m * 2.0 * fast);
-  b.F2 = (float)(m * 6.0 * fast);
+  b.F2 = (float)(m * 8.0 * fast);
   return b;
 }
 

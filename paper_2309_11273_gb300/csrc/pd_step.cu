@@ -2102,9 +2102,11 @@ __global__ void __maxnreg__(56) k_pass2_lat(StepArgs a, const float4* __restrict
 // which for small eta' is the linearized kernels' sum term by term.  The failure check (Eq 1.30 as
 // p >= s0 (2 + s0) |n|^2) is decided in FP32 outside the band of pd_lattice.h (LatBandNL) and in FP64
 // from the master state otherwise (fp64_breaks_nl, the FP64 nonlinear kernels' arithmetic); the
-// screen uses the body's bound of |u'_j| as the linearized kernels do.  One-word shadow only.
-template <int DIM, int NB, int CH>
+// screen uses the body's bound of |u'_j| as the linearized kernels do.  LO: the two-word shadow (eta'
+// formed as (hi_j - hi_i) + (lo_j - lo_i); the band of pd_lattice.h covers both forms).
+template <int DIM, bool LO, int NB, int CH>
 __global__ void __maxnreg__(72) k_pass1_latnl(StepArgs a, const float4* __restrict__ u32,
+                                               const float4* __restrict__ lo32,
                                                       const double4* __restrict__ disp, int write_theta) {
   extern __shared__ __align__(128) unsigned char smem[];
   const SliceIdx t = slice_index<1>(a.n_pad, a.slice_ptr);
@@ -2121,6 +2123,7 @@ __global__ void __maxnreg__(72) k_pass1_latnl(StepArgs a, const float4* __restri
   const bool screening = can_break && checking;
   const bool every = checking && a.validate != 0;
   const float4 Ui = u32[t.i];
+  const float4 Li = LO ? lo32[t.i] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   const float4 nUi = make_float4(-Ui.x, -Ui.y, -Ui.z, 0.0f);
   const float c32 = bp.s0nl32;
   // the screen's per-lane coefficients with S = U_i + the body's bound of |u'_j|
@@ -2134,9 +2137,13 @@ __global__ void __maxnreg__(72) k_pass1_latnl(StepArgs a, const float4* __restri
   auto batch = [&](const int32_t* cs, const uint32_t* ws, uint4 w4, int k) {
     constexpr int U = kU32;
     const uint32_t wd[U] = {w4.x, w4.y, w4.z, w4.w};
-    float4 Uj[U];
+    float4 Uj[U], Lj[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) Uj[u] = u32[cs[u * 32]];
+    for (int u = 0; u < U; ++u) {
+      const int32_t j = cs[u * 32];
+      Uj[u] = u32[j];
+      if (LO) Lj[u] = lo32[j];
+    }
     float ev[U];  // e' of the intact bonds (0 for the others)
     float smax = -INFINITY;
     const float4 dA = lat_dir<DIM>(k), dB = lat_dir<DIM>(k + 2);  // k is a multiple of 4
@@ -2145,8 +2152,9 @@ __global__ void __maxnreg__(72) k_pass1_latnl(StepArgs a, const float4* __restri
     for (int u = 0; u < U; ++u) {
       const float4 dn = lat_twin(u < 2 ? dA : dB, u & 1);
       const float nl = u < 2 ? lA : lB;
-      const float2 exy = __fadd2_rn(make_float2(Uj[u].x, Uj[u].y), make_float2(nUi.x, nUi.y));
-      const float ez = DIM == 3 ? Uj[u].z + nUi.z : 0.0f;
+      const float2 exy = LO ? make_float2(lat_delta_lo(Uj[u].x, Lj[u].x, Ui.x, Li.x), lat_delta_lo(Uj[u].y, Lj[u].y, Ui.y, Li.y))
+                            : __fadd2_rn(make_float2(Uj[u].x, Uj[u].y), make_float2(nUi.x, nUi.y));
+      const float ez = DIM == 3 ? (LO ? lat_delta_lo(Uj[u].z, Lj[u].z, Ui.z, Li.z) : Uj[u].z + nUi.z) : 0.0f;
       const bool in = (wd[u] & lmask) != 0u;
       const float p = lat_p_nl<DIM>(dn.x, dn.y, dn.z, exy.x, exy.y, ez);
       const float q2 = dn.w + p;  // |Y'|^2 = |n|^2 + p
@@ -2168,8 +2176,11 @@ __global__ void __maxnreg__(72) k_pass1_latnl(StepArgs a, const float4* __restri
         if (checking && can_break && (ws[u] & lmask) != 0u) {
           const int32_t jj = cs[u * 32];
           const float4 uj = u32[jj];
+          const float4 lj = LO ? lo32[jj] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
           const float4 dn = lat_dir<DIM>(k + u);
-          const float ex = uj.x - Ui.x, ey = uj.y - Ui.y, ez = DIM == 3 ? uj.z - Ui.z : 0.0f;
+          const float ex = LO ? lat_delta_lo(uj.x, lj.x, Ui.x, Li.x) : uj.x - Ui.x;
+          const float ey = LO ? lat_delta_lo(uj.y, lj.y, Ui.y, Li.y) : uj.y - Ui.y;
+          const float ez = DIM == 3 ? (LO ? lat_delta_lo(uj.z, lj.z, Ui.z, Li.z) : uj.z - Ui.z) : 0.0f;
           const float g = lat_g_nl(lat_p_nl<DIM>(dn.x, dn.y, dn.z, ex, ey, ez), c32, dn.w);
           LatBandNL band;
           band.A0 = bp.nl_A0;
@@ -2206,8 +2217,9 @@ __global__ void __maxnreg__(72) k_pass1_latnl(StepArgs a, const float4* __restri
   }
 }
 
-template <int DIM, int NB, int CH>
+template <int DIM, bool LO, int NB, int CH>
 __global__ void __maxnreg__(64) k_pass2_latnl(StepArgs a, const float4* __restrict__ u32, float4* __restrict__ u32_out,
+                                               const float4* __restrict__ lo32, float4* __restrict__ lo32_out,
                                                const double4* __restrict__ disp, double4* __restrict__ disp_out) {
   extern __shared__ __align__(128) unsigned char smem[];
   const SliceIdx t = slice_index<1>(a.n_pad, a.slice_ptr);
@@ -2216,6 +2228,7 @@ __global__ void __maxnreg__(64) k_pass2_latnl(StepArgs a, const float4* __restri
   const int lane = t.lane;
   const int b = a.body ? a.body[t.i] : 0;
   const float4 Ui = a.lat_up[t.i];  // (u'_i, P_i)
+  const float4 Li = LO ? lo32[t.i] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   const float4 nUi = make_float4(-Ui.x, -Ui.y, -Ui.z, 0.0f);
   const float rho_i = a.lat_f[t.i].x;
   const bool interior = __all_sync(kFull, a.lat_int[t.i >> 5] != 0);
@@ -2225,12 +2238,13 @@ __global__ void __maxnreg__(64) k_pass2_latnl(StepArgs a, const float4* __restri
     constexpr bool INTR = decltype(intr)::value;
     constexpr int U = kU32;
     const uint32_t wd[U] = {w4.x, w4.y, w4.z, w4.w};
-    float4 Uj[U];
+    float4 Uj[U], Lj[U];
     float rr[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int32_t j = cs[u * 32];
       Uj[u] = a.lat_up[j];
+      if (LO) Lj[u] = lo32[j];
       rr[u] = INTR ? 2.0f : rho_i + a.lat_rho[j];
     }
     const float4 dA = lat_dir<DIM>(k), dB = lat_dir<DIM>(k + 2);  // k is a multiple of 4
@@ -2239,8 +2253,9 @@ __global__ void __maxnreg__(64) k_pass2_latnl(StepArgs a, const float4* __restri
     for (int u = 0; u < U; ++u) {
       const float4 dn = lat_twin(u < 2 ? dA : dB, u & 1);
       const float nl = u < 2 ? lA : lB;
-      const float2 exy = __fadd2_rn(make_float2(Uj[u].x, Uj[u].y), make_float2(nUi.x, nUi.y));
-      const float ez = DIM == 3 ? Uj[u].z + nUi.z : 0.0f;
+      const float2 exy = LO ? make_float2(lat_delta_lo(Uj[u].x, Lj[u].x, Ui.x, Li.x), lat_delta_lo(Uj[u].y, Lj[u].y, Ui.y, Li.y))
+                            : __fadd2_rn(make_float2(Uj[u].x, Uj[u].y), make_float2(nUi.x, nUi.y));
+      const float ez = DIM == 3 ? (LO ? lat_delta_lo(Uj[u].z, Lj[u].z, Ui.z, Li.z) : Uj[u].z + nUi.z) : 0.0f;
       const float p = lat_p_nl<DIM>(dn.x, dn.y, dn.z, exy.x, exy.y, ez);
       const float yx = dn.x + exy.x, yy = dn.y + exy.y, yz = dn.z + ez;
       const float q2 = dn.w + p;  // |Y'|^2 = |n|^2 + p
@@ -2263,7 +2278,14 @@ __global__ void __maxnreg__(64) k_pass2_latnl(StepArgs a, const float4* __restri
   if (ok) {  // warp-uniform
     double4 u;
     update_lat<DIM>(a, t.i, b, f, disp, disp_out, u);
-    const float4 hi = shadow_lat<DIM>(a.bp[b].lat_inv_h, u);
+    float4 hi;
+    if (LO) {
+      float4 lo;
+      shadow_lat_lo<DIM>(a.bp[b].lat_inv_h, u, hi, lo);
+      lo32_out[t.i] = lo;
+    } else {
+      hi = shadow_lat<DIM>(a.bp[b].lat_inv_h, u);
+    }
     u32_out[t.i] = hi;
     lat_raise_umax(a.lat_umax_next, b, hi.w);
   }
@@ -2831,11 +2853,11 @@ void optin_lat_ring() {
   cudaFuncSetAttribute(k_pass1_lat<DIM, WI, LO, NB, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_pass2_lat<DIM, WI, LO, NB, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
 }
-template <int DIM, int NB, int CH>
+template <int DIM, bool LO, int NB, int CH>
 void optin_latnl_ring() {
   const int mx = 16 * StageGeom<NB, CH>::kWarpBytes;
-  cudaFuncSetAttribute(k_pass1_latnl<DIM, NB, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_pass2_latnl<DIM, NB, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_pass1_latnl<DIM, LO, NB, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_pass2_latnl<DIM, LO, NB, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
 }
 template <int DIM, bool WI>
 void optin_lat() {
@@ -2877,20 +2899,28 @@ void launch_lat(pd_ctx* c, const StepArgs& a, int pass, int write_theta, int blo
 }
 
 // Nonlinear bonds on the lattice layout: rings 0 and 1 run 2 x 16 slots, rings 2 and 3 run 2 x 8.
-template <int DIM, int NB, int CH>
+template <int DIM, bool LO, int NB, int CH>
 void launch_latnl_ring(pd_ctx* c, const StepArgs& a, int pass, int write_theta, int block) {
   const unsigned g1 = (unsigned)((c->nslices * 32 + block - 1) / block);
   const size_t smb = (size_t)(block / 32) * StageGeom<NB, CH>::kWarpBytes;
+  const float4* lo = LO ? c->u32lo[c->cur] : nullptr;
   if (pass == 1)
-    k_pass1_latnl<DIM, NB, CH><<<g1, block, smb, c->stream>>>(a, c->u32[c->cur], c->disp[c->cur], write_theta);
+    k_pass1_latnl<DIM, LO, NB, CH><<<g1, block, smb, c->stream>>>(a, c->u32[c->cur], lo, c->disp[c->cur], write_theta);
   else
-    k_pass2_latnl<DIM, NB, CH><<<g1, block, smb, c->stream>>>(a, c->u32[c->cur], c->u32[c->cur ^ 1], c->disp[c->cur],
-                                                               c->disp[c->cur ^ 1]);
+    k_pass2_latnl<DIM, LO, NB, CH><<<g1, block, smb, c->stream>>>(a, c->u32[c->cur], c->u32[c->cur ^ 1], lo,
+                                                                   LO ? c->u32lo[c->cur ^ 1] : nullptr,
+                                                                   c->disp[c->cur], c->disp[c->cur ^ 1]);
 }
 template <int DIM>
 void launch_latnl(pd_ctx* c, const StepArgs& a, int pass, int write_theta, int block) {
-  if (c->lat_stage >= 2) launch_latnl_ring<DIM, 2, 8>(c, a, pass, write_theta, block);
-  else launch_latnl_ring<DIM, 2, 16>(c, a, pass, write_theta, block);
+  const bool lo = c->shadow_lo;
+  if (c->lat_stage >= 2) {
+    if (lo) launch_latnl_ring<DIM, true, 2, 8>(c, a, pass, write_theta, block);
+    else launch_latnl_ring<DIM, false, 2, 8>(c, a, pass, write_theta, block);
+  } else {
+    if (lo) launch_latnl_ring<DIM, true, 2, 16>(c, a, pass, write_theta, block);
+    else launch_latnl_ring<DIM, false, 2, 16>(c, a, pass, write_theta, block);
+  }
 }
 
 template <int DIM>
@@ -2898,8 +2928,10 @@ void optin_staged() {
   const int mx = 16 * kStageWarpBytes;
   optin_lat<DIM, false>();
   optin_lat<DIM, true>();
-  optin_latnl_ring<DIM, 2, 16>();
-  optin_latnl_ring<DIM, 2, 8>();
+  optin_latnl_ring<DIM, false, 2, 16>();
+  optin_latnl_ring<DIM, false, 2, 8>();
+  optin_latnl_ring<DIM, true, 2, 16>();
+  optin_latnl_ring<DIM, true, 2, 8>();
   cudaFuncSetAttribute(k_pass1_mixed_staged<DIM, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_pass2_mixed_staged<DIM, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_pass1_mixed_staged<DIM, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
@@ -3334,8 +3366,7 @@ pd_status apply_bc_now(pd_ctx* c) {
 
 pd_status ensure_shadow_lo(pd_ctx* c) {
   c->shadow_lo = false;
-  // the two-word shadow exists for linearized bonds (the nonlinear lattice kernels read one word)
-  if (!c->lattice || !c->shadow_lo_opt || c->kin != PD_LINEARIZED) return PD_OK;
+  if (!c->lattice || !c->shadow_lo_opt) return PD_OK;
   pd_status st;
   for (int k = 0; k < 2; ++k)
     if (!c->u32lo[k]) {

@@ -267,3 +267,28 @@ def test_mixed_nonlinear_full_size_block():
     ref.close()
     sim.close()
     assert e <= 1e-3 and st["validate_mismatches"] == 0, (e, st)
+
+
+def test_mixed_nonlinear_two_word_shadow():
+    """PD_OPT_SHADOW_LO with nonlinear bonds on the lattice layout: configuration 1's plate stays
+    within the stated bounds and no worse than one word; on the breaking cracked plate every
+    decision equals the FP64 nonlinear decision on the run's own state (validation mode)."""
+    w = W.config1()
+    ref = _oracle_nl(w, 0.0)
+    ref.step(1000)
+    errs = {}
+    for lo in (0, 1):
+        sim = Simulation(w, s0=0.0, precision=PD_MIXED, kinematics=PD_NONLINEAR, shadow_lo=lo)
+        assert sim.get_option(B.PD_OPT_LATTICE) == 1 and sim.get_option(B.PD_OPT_SHADOW_LO) == lo
+        sim.step(1000)
+        errs[lo] = rel(sim.state()[0], ref.u)
+        sim.close()
+    print("nonlinear config1 rel-L2(u) one / two words:", errs)
+    assert errs[1] <= 1e-4 and errs[1] <= 1.5 * errs[0], errs
+    w = W.cracked_plate(nx=60, ny=24, dx=2.5e-4, crack_cells=30.125, sigma=2e6, nsteps=400)
+    sim = Simulation(w, s0=s0_of(w), precision=PD_MIXED, kinematics=PD_NONLINEAR, shadow_lo=1)
+    sim.set_option(B.PD_OPT_VALIDATE, 1)
+    sim.step(400)
+    st = sim.stats()
+    sim.close()
+    assert st["broken_bonds"] > 0 and st["validate_mismatches"] == 0, st

@@ -5,7 +5,8 @@ the host compiler.
 Eq 1.30 with the nonlinear extension (Eq 1.10) as |Y|^2 - |xi|^2 >= s0 (2 + s0) |xi|^2.  Bonds are
 placed within 1e-9 .. 0.5 of their threshold (relative), on lattice positions rounded in FP64, with
 displacements from 1e-6 to 1e3 lattice spacings, rigid offsets and a perpendicular part; the header's
-FP32 operations decide them from FP32 copies of u / h.  Every bond the screen (at its tightest
+FP32 operations decide them from FP32 copies of u / h, one word per component or two (hi + lo, the
+two-word shadow).  Every bond the screen (at its tightest
 per-body bound, max(U_i, U_j)) or the full band decides in FP32 must be decided the same way by any
 FP64 evaluation: its exact margin eta.(2 xi + eta) - c |xi|^2 (rational arithmetic on the FP64
 inputs) has that sign and exceeds 2^-50 times the sum of the magnitudes of its terms.  At a safety
@@ -31,19 +32,24 @@ using namespace pd;
 // per bond: n (3), ui (3), uj (3) in metres, h, s0; band safety k, the family's N1, Ninf, qmax
 // out: screen (1 = settled intact), code (0, 1, 2)
 extern "C" void decide_nl(long m, const int* n, const double* ui, const double* uj, const double* h,
-                          const double* s0, double k, int n1, int ninf, int qmax, int* screen, int* code) {
+                          const double* s0, double k, int n1, int ninf, int qmax, int lo, int* screen, int* code) {
   for (long e = 0; e < m; ++e) {
     const double ih = 1.0 / h[e];
-    float a[3], b[3];
+    float a[3], b[3], al[3], bl[3];
     for (int c = 0; c < 3; ++c) {
-      a[c] = (float)(ui[3 * e + c] * ih);
-      b[c] = (float)(uj[3 * e + c] * ih);
+      const double va = ui[3 * e + c] * ih, vb = uj[3 * e + c] * ih;
+      a[c] = (float)va;
+      b[c] = (float)vb;
+      al[c] = (float)(va - (double)a[c]);  // the two-word shadow's lo words
+      bl[c] = (float)(vb - (double)b[c]);
     }
     const float Ui = fmaxf(fabsf(a[0]), fmaxf(fabsf(a[1]), fabsf(a[2])));
     const float Uj = fmaxf(fabsf(b[0]), fmaxf(fabsf(b[1]), fabsf(b[2])));
     const float nx = (float)n[3 * e], ny = (float)n[3 * e + 1], nz = (float)n[3 * e + 2];
     const float q = nx * nx + ny * ny + nz * nz;
-    const float ex = b[0] - a[0], ey = b[1] - a[1], ez = b[2] - a[2];
+    const float ex = lo ? lat_delta_lo(b[0], bl[0], a[0], al[0]) : b[0] - a[0];
+    const float ey = lo ? lat_delta_lo(b[1], bl[1], a[1], al[1]) : b[1] - a[1];
+    const float ez = lo ? lat_delta_lo(b[2], bl[2], a[2], al[2]) : b[2] - a[2];
     const float p = lat_p_nl<3>(nx, ny, nz, ex, ey, ez);
     const double c = s0[e] * (2.0 + s0[e]);
     const float g = lat_g_nl(p, (float)c, q);
@@ -72,7 +78,8 @@ def so():
                    check=True)
     L = ctypes.CDLL(lib)
     L.decide_nl.argtypes = [ctypes.c_long] + [ctypes.c_void_p] * 5 + [ctypes.c_double, ctypes.c_int, ctypes.c_int,
-                                                                      ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+                                                                      ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                                                      ctypes.c_void_p]
     yield L
     shutil.rmtree(tmp, ignore_errors=True)
 
@@ -117,17 +124,17 @@ def exact_margin_nl(xi, ui, uj, s0):
     return out
 
 
-def run_nl(so, xi, n, ui, uj, h, s0, k, n1=5, ninf=3, qmax=9):
+def run_nl(so, xi, n, ui, uj, h, s0, k, n1=5, ninf=3, qmax=9, lo=0):
     m = len(s0)
     screen = np.zeros(m, dtype=np.int32)
     code = np.zeros(m, dtype=np.int32)
     arrs = [np.ascontiguousarray(a) for a in (n, ui, uj, h, s0)]
-    so.decide_nl(m, *[a.ctypes.data for a in arrs], k, n1, ninf, qmax, screen.ctypes.data, code.ctypes.data)
+    so.decide_nl(m, *[a.ctypes.data for a in arrs], k, n1, ninf, qmax, lo, screen.ctypes.data, code.ctypes.data)
     return screen, code
 
 
-def violations_nl(so, sample, k):
-    screen, code = run_nl(so, *sample, k)
+def violations_nl(so, sample, k, lo=0):
+    screen, code = run_nl(so, *sample, k, lo=lo)
     xi, n, ui, uj, h, s0 = sample
     bad = 0
     counts = dict(screened=0, fp32_broken=0, fp32_intact=0, fp64=0)
@@ -158,10 +165,11 @@ CASES = [
 
 @pytest.mark.parametrize("h,umag,s0lo,s0hi", CASES)
 @pytest.mark.parametrize("k", [1.05, 4.0])
-def test_fp32_nonlinear_decisions_match_every_fp64_evaluation(so, h, umag, s0lo, s0hi, k):
-    rng = np.random.default_rng(int(h * 1e9) % 1000 + int(umag * 10) + int(k * 7))
+@pytest.mark.parametrize("lo", [0, 1])
+def test_fp32_nonlinear_decisions_match_every_fp64_evaluation(so, h, umag, s0lo, s0hi, k, lo):
+    rng = np.random.default_rng(int(h * 1e9) % 1000 + int(umag * 10) + int(k * 7) + lo)
     sample = near_threshold_nl(rng, 1500, h, umag, s0lo, s0hi, family())
-    bad, counts = violations_nl(so, sample, k)
+    bad, counts = violations_nl(so, sample, k, lo)
     assert bad == 0, counts
     assert counts["fp32_intact"] > 0 and counts["fp32_broken"] > 0 and counts["fp64"] > 0, counts
 
@@ -179,8 +187,9 @@ def test_undersized_nonlinear_band_is_caught(so):
     contradicts (in the band and in the screen), so the test above has teeth."""
     rng = np.random.default_rng(9)
     sample = near_threshold_nl(rng, 3000, 1e-3, 1.0, 1e-4, 1e-2, family())
-    bad, counts = violations_nl(so, sample, 0.02)
-    assert bad > 0, counts
+    for lo in (0, 1):
+        bad, counts = violations_nl(so, sample, 0.02, lo)
+        assert bad > 0, (lo, counts)
 
 
 def test_nonfinite_nonlinear_extension_goes_to_fp64(so):
