@@ -167,13 +167,14 @@ typedef enum {
                               switched between steps; nonlinear theta sums differ in rounding
                               order only.  Has no effect when the build could not pair
                               every entry (pd_get_option then reports 0). */
-  PD_OPT_LATTICE = 11,     /* PD_MIXED with linearized bonds: 1 (default) = when every body's
-                              particles lie on a regular lattice (bond vectors h n with integer n to
-                              within 2^-30 h, uniform volumes, horizon up to 5 h in 3D and 8 h in
-                              2D), pd_build_neighbors lays the family out by lattice direction (slot
-                              k of every slice = direction k for every lane) and the step kernels
-                              take each slot's bond vector from a table instead of gathering
-                              coordinates; 0 = the general layout and kernels.  Set before
+  PD_OPT_LATTICE = 11,     /* PD_MIXED (linearized or nonlinear bonds): 1 (default) = when every
+                              body's particles lie on a regular lattice (bond vectors h n with
+                              integer n to within 2^-30 h, uniform volumes, a family |n|^2 <= m^2 for
+                              an integer m from 3 to 5 in 3D or 8 in 2D: horizons from 3 h up to just
+                              below sqrt(m^2 + 1) h), pd_build_neighbors lays the family out by
+                              lattice direction (slot k of every slice = direction k for every lane)
+                              and the step kernels take each slot's bond vector from a table instead
+                              of gathering coordinates; 0 = the general layout and kernels.  Set before
                               pd_build_neighbors; after it, pd_get_option reports whether the built
                               layout is the lattice one. */
   PD_OPT_LAT_STAGE = 12,   /* lattice kernels: shared-memory ring of each warp's index and status
@@ -183,7 +184,8 @@ typedef enum {
   PD_OPT_SHADOW_LO = 13    /* lattice kernels: 1 = carry each particle's FP32 displacement copy
                               (u / h) as two FP32 words hi + lo (lo the rounding remainder of hi,
                               16 more bytes per particle and per step gathered per bond in both
-                              passes), so that a bond's n.(u_j - u_i) / h^2 is rounded relative to
+                              passes; linearized and nonlinear bonds), so that a bond's
+                              u_j - u_i is rounded relative to
                               the difference rather than to |u| (bodies whose displacement is
                               large next to its variation over a horizon: rotations, rigid drift);
                               0 (default) = one word.  Decisions stay exact either way (the same
