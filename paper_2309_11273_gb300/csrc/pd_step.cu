@@ -567,7 +567,9 @@ __device__ __forceinline__ double flip_sign(double x) {
 // pass 1b sums theta, and pass 2 takes the bond's direction and extension from the table instead of
 // recomputing Y from the displacements.  The root and the divide, most of the FP64 work of the
 // single pass, run once per bond.
-template <int DIM, int SPLIT>
+// UV: every body has one particle volume, so both entries' dilatation terms (V_j |xi| e and V_i |xi| e)
+// are the same product, formed once (bitwise the same values).
+template <int DIM, int SPLIT, bool UV>
 __global__ void __launch_bounds__(512) k_pass1a_nlp(StepArgs a, const double4* __restrict__ disp) {
   const SliceIdx t = slice_index<SPLIT>(a.n_pad, a.slice_ptr);
   if (!t.active) return;  // whole warps; no block-wide barrier below
@@ -619,8 +621,9 @@ __global__ void __launch_bounds__(512) k_pass1a_nlp(StepArgs a, const double4* _
       const double mx = ry * yx, my = ry * yy, mz = ry * yz;  // M = Y / |Y| (Eq 1.13), -M at j
       a.bY[e] = make_double4(mx, my, mz, ev);
       a.bY[te] = make_double4(flip_sign(mx), flip_sign(my), flip_sign(mz), ev);
-      a.bt[e] = (vj * xl) * ev;       // Eq 1.6 term of entry (i, j): w |xi| e V_j
-      a.bt[te] = (ui.w * xl) * ev;    // and of entry (j, i): w |xi| e V_i
+      const double tij = (vj * xl) * ev;  // Eq 1.6 term of entry (i, j): w |xi| e V_j
+      a.bt[e] = tij;
+      a.bt[te] = UV ? tij : (ui.w * xl) * ev;  // and of entry (j, i): w |xi| e V_i
     }
   }
 }
@@ -2787,7 +2790,10 @@ cudaEvent_t take_event(pd_ctx* c) {
 template <int DIM, int SPLIT>
 void launch_pass1(pd_ctx* c, const StepArgs& a, int write_theta, unsigned grid, int block, size_t sm) {
   if (c->kin == PD_NONLINEAR && a.bA && a.own0) {
-    k_pass1a_nlp<DIM, SPLIT><<<grid, block, 0, c->stream>>>(a, c->disp[c->cur]);
+    if (c->vol_uniform)
+      k_pass1a_nlp<DIM, SPLIT, true><<<grid, block, 0, c->stream>>>(a, c->disp[c->cur]);
+    else
+      k_pass1a_nlp<DIM, SPLIT, false><<<grid, block, 0, c->stream>>>(a, c->disp[c->cur]);
     if (write_theta) {
       if (c->profile) {
         c->times.mid = take_event(c);
