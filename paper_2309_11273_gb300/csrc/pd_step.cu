@@ -1177,6 +1177,24 @@ __global__ void k_bond_tables(StepArgs a, double4* __restrict__ bA, double4* __r
 }
 
 // ----------------------------------------------------------------------------------- mixed path
+// The hardware approximations of 1 / sqrt(x) and 1 / x with a subnormal x read as zero (PTX
+// rsqrt.approx.ftz.f32, rcp.approx.ftz.f32), for the FP32 nonlinear kernels: without .ftz each call
+// carries a test and rescaling for subnormal inputs.  Their arguments are squared bond lengths and
+// sums of bond lengths: |Y|^2 and |Y| + |xi| in units of the coordinate quantum (|xi| >= 1), and
+// |Y'|^2 = |n|^2 + p and |Y'| + |n| >= 1 in lattice units, normal numbers for every bond not
+// compressed to within 2^-63 of its length, where the results equal those of rsqrtf and __fdividef
+// bit for bit.
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float rcp_ftz(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 // FP32 bond arithmetic on fixed-point coordinates (xi exact as an integer multiple of the quantum Q,
 // then rounded once to FP32) and an FP32 shadow copy of u.  The band half-width B bounds
 // |g32 - g| for g = xi.du - s0 |xi|^2 (in Q units) from the FP32 representation of u, the rounding
@@ -1565,8 +1583,8 @@ __global__ void __launch_bounds__(512) k_pass1_mixed_staged(StepArgs a, const fl
             q = fmaf(ez, ez, q);
             y2 = fmaf(yz, yz, y2);
           }
-          const float xl = q * rsqrtf(q);
-          dv[u] = xl * __fdividef(d, fmaf(y2, rsqrtf(y2), xl));
+          const float xl = q * rsqrt_ftz(q);
+          dv[u] = xl * (d * rcp_ftz(fmaf(y2, rsqrt_ftz(y2), xl)));
         }
       }
       if (a.check) {
@@ -1681,8 +1699,9 @@ __global__ void __launch_bounds__(512) k_pass2_mixed_staged(StepArgs a, const fl
             q = fmaf(ez, ez, q);
             y2 = fmaf(yz, yz, y2);
           }
+          // rsqrtf here: with rsqrt_ftz ptxas gives the 2D instance 40 registers and spills
           const float xl = q * rsqrtf(q), ry = rsqrtf(y2);
-          const float e = __fdividef(pp, fmaf(y2, ry, xl));
+          const float e = pp * rcp_ftz(fmaf(y2, ry, xl));
           float cf = fmaf(ti.x + tj[u].x, xl, (ti.y + tj[u].y) * e) * ry;
           cf = ((wd[u] >> lane) & 1u) ? cf * __int_as_float(Pj[u].w) : 0.0f;
           f[0] = fmaf(cf, yx, f[0]);
@@ -2162,7 +2181,7 @@ __global__ void __maxnreg__(72) k_pass1_latnl(StepArgs a, const float4* __restri
       const float p = lat_p_nl<DIM>(dn.x, dn.y, dn.z, exy.x, exy.y, ez);
       const float q2 = dn.w + p;  // |Y'|^2 = |n|^2 + p
       const float pm = in ? p : 0.0f;
-      ev[u] = in ? __fdividef(p, fmaf(q2, rsqrtf(q2), nl)) : 0.0f;
+      ev[u] = in ? p * rcp_ftz(fmaf(q2, rsqrt_ftz(q2), nl)) : 0.0f;
       if (screening) {
         const float D = in ? fabsf(exy.x) + fabsf(exy.y) + fabsf(ez) : 0.0f;
         smax = lat_max_nan(smax, lat_g_nl(pm, c32, dn.w) + lat_screen_nl(D, f0, f1, F2));
@@ -2262,8 +2281,8 @@ __global__ void __maxnreg__(64) k_pass2_latnl(StepArgs a, const float4* __restri
       const float p = lat_p_nl<DIM>(dn.x, dn.y, dn.z, exy.x, exy.y, ez);
       const float yx = dn.x + exy.x, yy = dn.y + exy.y, yz = dn.z + ez;
       const float q2 = dn.w + p;  // |Y'|^2 = |n|^2 + p
-      const float ry = rsqrtf(q2);
-      const float e = __fdividef(p, fmaf(q2, ry, nl));
+      const float ry = rsqrt_ftz(q2);
+      const float e = p * rcp_ftz(fmaf(q2, ry, nl));
       // coefficient along M = Y' / |Y'|: (P_i + P_j) |n| + (rho_i + rho_j) e'
       float cf = fmaf(rr[u], e, (Ui.w + Uj[u].w) * nl) * ry;
       cf = (wd[u] & lmask) ? cf : 0.0f;
