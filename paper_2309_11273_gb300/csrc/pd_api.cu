@@ -69,7 +69,8 @@ void free_build(pd_ctx* c) {
   c->bX = nullptr;
   c->lam = nullptr;
   c->gnew = c->gold = nullptr;
-  c->adr_part = c->adr_st = nullptr;
+  c->adr_part = nullptr;
+  c->adr_st = nullptr;
   c->adr_first = nullptr;
   c->adr_restart = true;
   c->diag_theta = nullptr;

@@ -219,11 +219,11 @@ struct pd_ctx {
   int expire_waits = 0;           // testing: make the staged kernels' first wait expire
   int solver = 0;                 // pd_solver
   bool adr_restart = true;        // next ADR iteration starts from rest
-  double* lam = nullptr;          // ADR fictitious density lambda_i
+  double2* lam = nullptr;         // ADR fictitious density (lambda_i, 1 / lambda_i)
   double4* gnew = nullptr;        // ADR g^n (force density incl. body force)
   double4* gold = nullptr;        // ADR g^{n-1}
   double2* adr_part = nullptr;    // ADR per-block partial sums (u.k.u, u.u)
-  double2* adr_st = nullptr;      // ADR (c^n, start flag) of the current iteration
+  double4* adr_st = nullptr;      // ADR (c^n, start flag, 1 / (2 + c^n)) of the current iteration
   int* adr_first = nullptr;       // ADR: 1 = the next iteration starts from rest
   double* diag_theta = nullptr;   // pd_get_stats: theta at the current state
   double4* diag_part = nullptr;   // pd_get_stats: per-block (strain energy, min margin, kinetic, 0)

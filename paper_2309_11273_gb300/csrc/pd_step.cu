@@ -2342,9 +2342,11 @@ __global__ void k_adr_alpha(StepArgs a, double* __restrict__ alpha) {
 
 // lambda_i = R_i / 4 with R_i = 2 G sum_j (1/m_i + 1/m_j) V_j |M_ij|_1
 //                              + 2 |K - G/3| sum_j |xi_ij| V_j (alpha_i / m_i + alpha_j / m_j),
-// an upper bound of the absolute row sums of the force-density stiffness (Gerschgorin).
+// an upper bound of the absolute row sums of the force-density stiffness (Gerschgorin); stored with
+// its reciprocal, which the update multiplies by (an FP64 division costs many times an FMA on the
+// FP64 pipe, and lambda is fixed for the run).
 template <int DIM>
-__global__ void k_adr_lambda(StepArgs a, const double* __restrict__ alpha, double* __restrict__ lam) {
+__global__ void k_adr_lambda(StepArgs a, const double* __restrict__ alpha, double2* __restrict__ lam) {
   const SliceIdx t = slice_index<1>(a.n_pad, a.slice_ptr);
   if (!t.active) return;
   const int b = a.body ? a.body[t.i] : 0;
@@ -2365,7 +2367,8 @@ __global__ void k_adr_lambda(StepArgs a, const double* __restrict__ alpha, doubl
     }
   }
   const double R = 2.0 * a.bp[b].G * rg + 2.0 * fabs(a.bp[b].Kp) * rt;
-  lam[t.i] = 0.25 * R;
+  const double l = 0.25 * R;
+  lam[t.i] = make_double2(l, l > 0.0 ? 1.0 / l : 0.0);
 }
 
 constexpr int kAdrBlock = 256;
@@ -2373,14 +2376,14 @@ constexpr int kAdrBlock = 256;
 // Per block: sum over its free particles' components of u (k u) and u u, k = -(g - g_prev) / (lambda v).
 __global__ void __launch_bounds__(kAdrBlock) k_adr_sums(StepArgs a, const double4* __restrict__ disp,
                                                          const double4* __restrict__ gold,
-                                                         const double* __restrict__ lam,
+                                                         const double2* __restrict__ lam,
                                                          double2* __restrict__ part) {
   __shared__ double sn[kAdrBlock], sd[kAdrBlock];
   const int64_t i = blockIdx.x * (int64_t)kAdrBlock + threadIdx.x;
   double num = 0.0, den = 0.0;
-  if (i < a.n_pad && (!a.flag || a.flag[i] == 0) && lam[i] > 0.0) {
+  if (i < a.n_pad && (!a.flag || a.flag[i] == 0) && lam[i].x > 0.0) {
     const double4 u = disp[i], v = a.vel[i], g = a.gnew[i], go = gold[i];
-    const double li = lam[i];
+    const double li = lam[i].x;
     const double uu[3] = {u.x, u.y, u.z}, vv[3] = {v.x, v.y, v.z}, gg[3] = {g.x, g.y, g.z},
                  gp[3] = {go.x, go.y, go.z};
 #pragma unroll
@@ -2403,9 +2406,10 @@ __global__ void __launch_bounds__(kAdrBlock) k_adr_sums(StepArgs a, const double
   if (threadIdx.x == 0) part[blockIdx.x] = make_double2(sn[0], sd[0]);
 }
 
-// One block: c = 2 sqrt(num / den) (0 unless both are positive), and the start flag of this iteration.
+// One block: c = 2 sqrt(num / den) (0 unless both are positive), the start flag of this iteration and
+// 1 / (2 + c).
 __global__ void __launch_bounds__(1024) k_adr_coef(const double2* __restrict__ part, int nblk, int* first,
-                                                   double2* st) {
+                                                   double4* st) {
   __shared__ double sn[1024], sd[1024];
   double num = 0.0, den = 0.0;
   for (int b = threadIdx.x; b < nblk; b += 1024) {
@@ -2424,18 +2428,19 @@ __global__ void __launch_bounds__(1024) k_adr_coef(const double2* __restrict__ p
   }
   if (threadIdx.x == 0) {
     const double c = (sd[0] > 0.0 && sn[0] > 0.0) ? 2.0 * sqrt(sn[0] / sd[0]) : 0.0;
-    *st = make_double2(c, (double)*first);
+    *st = make_double4(c, (double)*first, 1.0 / (2.0 + c), 0.0);
     *first = 0;
   }
 }
 
 // v^{n+1/2} = ((2 - c) v^{n-1/2} + 2 g / lambda) / (2 + c) (from rest on a start: g / (2 lambda)),
-// u^{n+1} = u^n + v^{n+1/2}; constrained particles take their boundary value at t_{n+1}.
+// u^{n+1} = u^n + v^{n+1/2}; constrained particles take their boundary value at t_{n+1}.  The two
+// divisions are multiplications by the stored reciprocals 1 / lambda and 1 / (2 + c).
 __global__ void __launch_bounds__(kAdrBlock) k_adr_update(StepArgs a, const double4* __restrict__ disp,
                                                            double4* __restrict__ disp_out,
                                                            double4* __restrict__ gold,
-                                                           const double* __restrict__ lam,
-                                                           const double2* __restrict__ st,
+                                                           const double2* __restrict__ lam,
+                                                           const double4* __restrict__ st,
                                                            float4* __restrict__ u32_out, unsigned* umax) {
   const int64_t i = blockIdx.x * (int64_t)kAdrBlock + threadIdx.x;
   if (i >= a.n_pad) return;
@@ -2445,15 +2450,17 @@ __global__ void __launch_bounds__(kAdrBlock) k_adr_update(StepArgs a, const doub
   double4 u = disp[i], v = a.vel[i];
   const double4 g = a.gnew[i];
   if (fl == 0) {
-    const double li = lam[i];
-    if (li > 0.0) {
-      const double c = st->x;
-      if (st->y != 0.0) {
-        v = make_double4(g.x / (2.0 * li), g.y / (2.0 * li), g.z / (2.0 * li), 0.0);
+    const double2 li = lam[i];  // (lambda, 1 / lambda)
+    if (li.x > 0.0) {
+      const double4 s = *st;
+      if (s.y != 0.0) {
+        const double h = 0.5 * li.y;
+        v = make_double4(g.x * h, g.y * h, g.z * h, 0.0);
       } else {
-        v.x = ((2.0 - c) * v.x + 2.0 * g.x / li) / (2.0 + c);
-        v.y = ((2.0 - c) * v.y + 2.0 * g.y / li) / (2.0 + c);
-        v.z = ((2.0 - c) * v.z + 2.0 * g.z / li) / (2.0 + c);
+        const double cm = 2.0 - s.x, r2 = 2.0 * li.y;
+        v.x = (cm * v.x + g.x * r2) * s.z;
+        v.y = (cm * v.y + g.y * r2) * s.z;
+        v.z = (cm * v.z + g.z * r2) * s.z;
       }
       u.x = u.x + v.x;
       u.y = u.y + v.y;
