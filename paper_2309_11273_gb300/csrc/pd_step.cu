@@ -978,6 +978,68 @@ __global__ void __launch_bounds__(512) k_pass1b_f64p(StepArgs a, const double4* 
   }
 }
 
+// The failure check alone in the nonlinear pair form, applied to the current state before its bond
+// status is read between steps: |Y|^2 - |xi|^2 >= s0 (2 + s0) |xi|^2 (Eq 1.30 with the extension of
+// Eq 1.10) once per intact bond at its owned entry, with pass 1a's arithmetic so that each decision
+// is the one pass 1a takes, but without its reciprocal square root, division and table stores: the
+// next step's pass 1a (which does not check again) forms M, e and the dilatation terms of the bonds
+// still intact.
+template <int DIM, int SPLIT>
+__global__ void __launch_bounds__(512) k_check_nlp(StepArgs a, const double4* __restrict__ disp) {
+  const SliceIdx t = slice_index<SPLIT>(a.n_pad, a.slice_ptr);
+  if (!t.active) return;  // whole warps; no block-wide barrier below
+  const int b = a.body ? a.body[t.i] : 0;
+  const double s0nl = a.bp[b].s0nl;
+  const bool can_break = a.bp[b].breaks != 0;
+  if (!__any_sync(kFull, can_break)) return;
+  const int own = a.own0[t.i], cnt = a.cnt[t.i];
+  const int k_lo = __reduce_min_sync(kFull, (unsigned)own);
+  const int k_hi = __reduce_max_sync(kFull, (unsigned)cnt);
+  const double4 ui = disp[t.i];
+  uint32_t* bw = a.bits + (t.base >> 5);
+  const int32_t* __restrict__ cl = a.col + t.base + t.lane;
+  const double4* __restrict__ ta = a.bA + t.base + t.lane;
+  // the next slot's index and table row are loaded while the current slot's gather runs
+  int k = k_lo + t.sub;
+  bool mn = k < k_hi && k >= own && k < cnt && can_break;
+  int32_t jn = (int32_t)t.i;
+  double4 gn = make_double4(0.0, 0.0, 0.0, 0.0);
+  if (mn) {
+    jn = cl[(int64_t)k << 5];
+    gn = ta[(int64_t)k << 5];
+  }
+  for (; k < k_hi; k += SPLIT) {
+    const uint32_t wd = bw[k];  // this warp's owned bits change only here
+    const bool mine = mn && ((wd >> t.lane) & 1u);
+    const int32_t j = jn;
+    const double4 g = gn;
+    const int kn = k + SPLIT;
+    mn = kn < k_hi && kn >= own && kn < cnt && can_break;
+    if (mn) {
+      jn = cl[(int64_t)kn << 5];
+      gn = ta[(int64_t)kn << 5];
+    }
+    bool brk = false;
+    if (mine) {
+      const double4 uj = disp[j];
+      const double hx = uj.x - ui.x, hy = uj.y - ui.y, hz = DIM == 3 ? uj.z - ui.z : 0.0;
+      const double yx = g.x + hx, yy = g.y + hy, yz = g.z + hz;
+      double p = hx * (g.x + yx) + hy * (g.y + yy);
+      if (DIM == 3) p = fma(hz, g.z + yz, p);
+      const double xl = g.w;
+      brk = p >= s0nl * (xl * xl);
+    }
+    const unsigned m = __ballot_sync(kFull, brk);
+    if (m) {
+      if (t.lane == 0) atomicAnd(&bw[k], ~m);
+      if (brk) {
+        const int32_t te = a.twin[t.base + t.lane + ((int64_t)k << 5)];
+        atomicAnd(a.bits + (te >> 5), ~(1u << (te & 31)));
+      }
+    }
+  }
+}
+
 // The failure check alone in the pair form, applied to the current state before its bond status is
 // read between steps: ξ·(u_j − u_i) once per intact bond at its owned entry, as in pass 1a, but
 // with no bd store (the next step's pass 1a stores it) and the twin entry's index loaded only
@@ -2815,7 +2877,9 @@ cudaEvent_t take_event(pd_ctx* c) {
 
 template <int DIM, int SPLIT>
 void launch_pass1(pd_ctx* c, const StepArgs& a, int write_theta, unsigned grid, int block, size_t sm) {
-  if (c->kin == PD_NONLINEAR && a.bA && a.own0) {
+  if (c->kin == PD_NONLINEAR && a.bA && a.own0 && !write_theta) {
+    if (a.check) k_check_nlp<DIM, SPLIT><<<grid, block, 0, c->stream>>>(a, c->disp[c->cur]);
+  } else if (c->kin == PD_NONLINEAR && a.bA && a.own0) {
     if (c->vol_uniform)
       k_pass1a_nlp<DIM, SPLIT, true><<<grid, block, 0, c->stream>>>(a, c->disp[c->cur]);
     else
