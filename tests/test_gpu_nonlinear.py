@@ -162,6 +162,29 @@ def test_batch_nonlinear_equals_separate_runs_bitwise():
         assert np.array_equal(u, ub[:, bw.offsets[k]:bw.offsets[k + 1]]), k
 
 
+def test_nonlinear_reads_between_steps_keep_the_trajectory():
+    """The check before a read (nonlinear pair form: the criterion alone, with pass 1a's arithmetic)
+    takes the decisions the next step's pass 1a would take: reading the state after every step or
+    every 7 steps gives bitwise the u, v and bond status of the run that is read only at its end,
+    while bonds break throughout."""
+    w = W.notched_block(nx=24, ny=12, nz=10, dx=1e-3, notch_cells=9.5, nsteps=300, seed=3, amp=1e-7)
+    res = []
+    for every in (1, 7, w.nsteps):
+        sim = Simulation(w, s0=s0_of(w), kinematics=PD_NONLINEAR)
+        done = 0
+        while done < w.nsteps:
+            k = min(every, w.nsteps - done)
+            sim.step(k)
+            done += k
+            sim.state()
+        res.append(sim.state()[:2] + (sim.neighbors()[2],))
+        sim.close()
+    assert not res[-1][2].all()  # bonds broke
+    for got in res[:-1]:
+        for a, b in zip(got, res[-1]):
+            assert np.array_equal(a, b)
+
+
 @pytest.mark.parametrize("block,split", [(128, 2), (512, 4)])
 def test_nonlinear_mapping_variants_agree(block, split):
     w = W.notched_block(nx=30, ny=14, nz=12, dx=1e-3, notch_cells=11.5, nsteps=60, seed=1, amp=2e-6)
